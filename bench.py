@@ -1,0 +1,424 @@
+#!/usr/bin/env python3
+"""Benchmark of the regularized Stokes layer sums (libstokesreg, GB300).
+
+One step = one single-layer evaluation (SK_FP32C) of the high-resolution
+ellipsoid workload: axes (1, 0.8, 0.5), m = 257 (256 x 256 nodes per patch,
+N = 393,216, of which N_s = 239,880 carry nonzero weight), targets = the N
+nodes followed by 100,000 exterior probes at 0.1h-5h, delta = 2h, mu = 1.
+Interactions per step = targets x N_s. Inputs are resident in HBM when the
+timed region starts; L2 is flushed (256 MB write) between timed steps.
+
+Extra measurements on rank 0 (single GPU): the FP64 path on the same
+workload, the double layer on the rotated Evans-Fung cell (m = 65), a delta
+sweep {1.5, 2, 3}h, the end-to-end call with pinned host buffers, and the FP64
+CPU oracle on a bounded sample (the CPU baseline, which also supplies the
+relative errors).
+
+--impl reference times that oracle alone (the reference arm of this metric).
+Under torchrun every rank runs its own seeded copy of the workload (weak
+scaling, no collective on the data path); timing is max over ranks.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("Ginteractions/s, FP32 vs FP64 at stated rel. error vs oracle; "
+          "serving p50/p99 latency")
+UNIT = "Ginteractions/s"
+FLOPS_SL = 29  # flops credited per single-layer interaction (FMA = 2, MUFU = 1)
+FLOPS_DL = 33  # per double-layer interaction
+SM_COUNT = 152
+SM_MAX_MHZ = 2070.0
+FP32_PEAK_TFLOPS = 2 * 128 * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12  # 80.55
+FP64_PEAK_TFLOPS = 1.25  # nominal dense FP64 of GB300
+CPU_SAMPLE_TARGETS = 4096
+REF_STEP_TARGETS = 512
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--m", type=int, default=257, help="grid order (default 257)")
+    ap.add_argument("--probes", type=int, default=100_000)
+    ap.add_argument("--no-extras", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def workload(m, n_probes, rank=0):
+    import capsule_inputs as ci
+    return ci.ellipsoid_hires_workload(m=m, n_probes=n_probes, seed=3000 + 17 * rank)
+
+
+def workload_name(w):
+    s = w.surface
+    return (f"ellipsoid(1,0.8,0.5) m={s.m}: N={s.N} nodes (N_s={s.n_active} active) + "
+            f"{w.targets.shape[0] - s.N} exterior probes (0.1h-5h), single layer, "
+            f"delta=2h, mu=1")
+
+
+def sample_targets(w, n, seed=1234):
+    rng = np.random.default_rng(seed)
+    M = w.targets.shape[0]
+    n_on = w.n_on_surface
+    k_probe = min(n // 4, M - n_on)
+    return np.concatenate([rng.choice(n_on, n - k_probe, replace=False),
+                           n_on + rng.choice(M - n_on, k_probe, replace=False)])
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.remove(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    w = workload(args.m, args.probes)
+    s = w.surface
+    rng = np.random.default_rng(99)
+    times = []
+    n_src_active = s.n_active
+    for it in range(args.warmup + args.steps):
+        idx = rng.choice(w.targets.shape[0], REF_STEP_TARGETS, replace=False)
+        t0 = time.perf_counter()
+        oracle.sl(s.X, s.w, w.f, w.targets[idx], w.delta, w.mu)
+        dt = time.perf_counter() - t0
+        if it >= args.warmup:
+            times.append(dt)
+    per_step = float(np.mean(times))
+    value = REF_STEP_TARGETS * n_src_active / per_step / 1e9
+    cores = oracle.max_threads()
+    sample = (f"{REF_STEP_TARGETS} random targets of the workload per step x all "
+              f"{n_src_active} active sources")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": per_step * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(w), "targets_per_step": REF_STEP_TARGETS},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- our arm
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def traffic_from_profile(kernel_file):
+    """DRAM bytes per pair-kernel launch from the committed ncu summary, if it
+    was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "pair32_traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        rec = json.load(open(path))
+        src = open(kernel_file, "rb").read()
+        if rec.get("source_sha256") != hashlib.sha256(src).hexdigest():
+            return None
+        return rec.get("dram_bytes_per_launch_full_size")
+    except Exception:
+        return None
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    rank, world, local = dist_env()
+    import torch
+    import paper_2310_13908_gb300 as sk
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+
+    w = workload(args.m, args.probes, rank)
+    s = w.surface
+    M = w.targets.shape[0]
+    Ns = s.n_active
+    inter = M * Ns
+
+    def tdev(a):
+        return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)
+
+    X, W, F, Y, D = (tdev(a) for a in (s.X, s.w, w.f, w.targets, w.delta))
+    out = torch.empty((M, 3), dtype=torch.float64, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    ctx = sk.Context(local)
+    h = ctx.handle
+    sk.sk_set_profiling(h, True)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(prec=sk.SK_FP32C, delta=D):
+        sk.stokes_sl_eval(h, prec, sk.SK_DEVICE, X, W, F, Y, delta, 1.0, u_out=out,
+                          stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    if pg:
+        pg.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    pair_ms, launches = [], 0
+    torch.cuda.synchronize(dev)
+    t_wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+        st = sk.sk_last_eval_stats(h)  # waits for this step
+        pair_ms.append(st["pair_ms"])
+        launches += st["kernel_launches"]
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_step = float(np.mean(step_ms))
+    if pg:
+        tt = torch.tensor([t_step], device=dev)
+        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+        t_step = float(tt.item())
+    value = world * inter / (t_step * 1e-3) / 1e9
+    u_fp32 = out.cpu().numpy()
+    stats = sk.sk_last_eval_stats(h)
+
+    pair_avg = float(np.mean(pair_ms))
+    achieved = FLOPS_SL * inter / (pair_avg * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                "traffic": traffic_from_profile(
+                    os.path.join(ROOT, "paper_2310_13908_gb300", "csrc", "sk_pair32.cu")),
+                "kernel": "k_pair32<SLayer>", "pair_ms": pair_avg,
+                "flops_per_interaction": FLOPS_SL,
+                "peak_basis": "2 x 128 FP32 lanes x 152 SMs x 2070 MHz (max SM clock)"}
+
+    # ---- end to end through the C ABI with pinned host buffers (SK_HOST, synchronous)
+    def pinned(a):
+        t = torch.empty(a.shape, dtype=torch.float64, pin_memory=True)
+        t.numpy()[...] = a
+        return t.numpy()
+
+    hX, hW, hF, hY, hD = (pinned(np.ascontiguousarray(a, dtype=np.float64))
+                          for a in (s.X, s.w, w.f, w.targets, w.delta))
+    hU = pinned(np.zeros((M, 3)))
+    e2e_steps = max(3, min(args.steps, 10))
+    for _ in range(2):
+        sk.stokes_sl_eval(h, sk.SK_FP32C, sk.SK_HOST, hX, hW, hF, hY, hD, 1.0, u_out=hU)
+    e2e_t = []
+    for _ in range(e2e_steps):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        sk.stokes_sl_eval(h, sk.SK_FP32C, sk.SK_HOST, hX, hW, hF, hY, hD, 1.0, u_out=hU)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_step = float(np.mean(e2e_t))
+    h2d = (hX.nbytes + hW.nbytes + hF.nbytes + hY.nbytes + hD.nbytes)
+    e2e = {"value": world * inter / e2e_step / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+           "d2h_bytes_per_step": int(hU.nbytes), "ms_per_step": e2e_step * 1e3,
+           "path": "stokes_sl_eval(SK_FP32C, SK_HOST), pinned host buffers, synchronous"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 pairs + f64 near/final", "data": "synthetic",
+            "config": {"workload": workload_name(w), "targets": M, "sources_active": Ns,
+                       "interactions_per_step": inter, "precision": "SK_FP32C",
+                       "rho_T": 0.5, "rho_c": 5.0,
+                       "l2": "flushed between timed steps (256 MB write); inputs 58 MB",
+                       "parallelism": f"replicas x{world} (independent workloads)"},
+            "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches),
+            "clocks": clk, "wall_s_timed": wall,
+            "near_pairs_per_step": stats["near_pairs"],
+            "overflow_targets": stats["overflow_targets"]}
+
+    if rank == 0 and world == 1 and not args.no_extras:
+        line.update(extras(sk, h, w, X, W, F, Y, D, out, u_fp32, stream, dev, torch))
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+def extras(sk, h, w, X, W, F, Y, D, out, u_fp32, stream, dev, torch):
+    import capsule_inputs as ci
+    import oracle
+    res = {}
+    s = w.surface
+    M = w.targets.shape[0]
+    inter = M * s.n_active
+
+    # FP64 path, same workload, one timed step
+    sk.stokes_sl_eval(h, sk.SK_FP64, sk.SK_DEVICE, X, W, F, Y, D, 1.0, u_out=out, stream=stream)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sk.stokes_sl_eval(h, sk.SK_FP64, sk.SK_DEVICE, X, W, F, Y, D, 1.0, u_out=out, stream=stream)
+    e1.record(stream)
+    st64 = sk.sk_last_eval_stats(h)
+    torch.cuda.synchronize(dev)
+    ms64 = e0.elapsed_time(e1)
+    u_fp64 = out.cpu().numpy()
+    ach64 = FLOPS_SL * inter / (st64["pair_ms"] * 1e-3) / 1e12
+
+    # CPU oracle on a bounded sample: the CPU baseline and the error reference
+    idx = sample_targets(w, CPU_SAMPLE_TARGETS)
+    t0 = time.perf_counter()
+    ref = oracle.sl(s.X, s.w, w.f, w.targets[idx], w.delta, w.mu)
+    t_cpu = time.perf_counter() - t0
+    cpu_inter = len(idx) * s.n_active
+    res["cpu_baseline"] = {"value": cpu_inter / t_cpu / 1e9, "unit": UNIT,
+                           "cores": oracle.max_threads(), "kind": "oracle",
+                           "sample": f"{len(idx)} seeded targets ({len(idx) - len(idx) // 4} "
+                                     f"nodes + {len(idx) // 4} probes) x all {s.n_active} "
+                                     "active sources, FP64, OpenMP",
+                           "seconds": t_cpu}
+    res["rel_l2_vs_oracle"] = {"fp32c": rel_l2(u_fp32[idx], ref),
+                               "fp64": rel_l2(u_fp64[idx], ref),
+                               "sample_targets": int(len(idx))}
+    res["fp64"] = {"value": inter / (ms64 * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms64,
+                   "rel_l2_vs_oracle": res["rel_l2_vs_oracle"]["fp64"],
+                   "roofline": {"bound": "alu", "achieved": ach64, "peak": FP64_PEAK_TFLOPS,
+                                "unit": "TFLOP/s", "frac": ach64 / FP64_PEAK_TFLOPS,
+                                "kernel": "k_pair64<SL>", "pair_ms": st64["pair_ms"],
+                                "peak_basis": "nominal dense FP64 of GB300"}}
+
+    # delta sweep (FP32C), one step each
+    sweep = {}
+    for fac in (1.5, 2.0, 3.0):
+        Dd = torch.tensor([fac * s.h], dtype=torch.float64, device=dev)
+        sk.stokes_sl_eval(h, sk.SK_FP32C, sk.SK_DEVICE, X, W, F, Y, Dd, 1.0, u_out=out,
+                          stream=stream)
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sk.stokes_sl_eval(h, sk.SK_FP32C, sk.SK_DEVICE, X, W, F, Y, Dd, 1.0, u_out=out,
+                          stream=stream)
+        b.record(stream)
+        st = sk.sk_last_eval_stats(h)
+        torch.cuda.synchronize(dev)
+        sweep[f"{fac}h"] = {"value": inter / (a.elapsed_time(b) * 1e-3) / 1e9,
+                            "pair_ms": st["pair_ms"], "near_pairs": st["near_pairs"]}
+    res["delta_sweep_fp32c"] = sweep
+
+    # double layer on the rotated Evans-Fung cell (m = 65, N = 24,576)
+    rw = ci.rbc_workload()
+    rs = rw.surface
+
+    def td(a):
+        return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)
+
+    RX, RW, RN, RQ, RY, RD = (td(a) for a in (rs.X, rs.w, rs.n, rw.q, rw.targets, rw.delta))
+    rout = torch.empty((rw.targets.shape[0], 3), dtype=torch.float64, device=dev)
+    ridx = np.random.default_rng(5).choice(rs.N, 2048, replace=False)
+    dref = oracle.dl(rs.X, rs.w, rs.n, rw.q, rw.targets[ridx], rw.delta)
+    rinter = rw.targets.shape[0] * rs.n_active
+    dl = {}
+    for prec, name in ((sk.SK_FP32C, "fp32c"), (sk.SK_FP64, "fp64")):
+        for _ in range(2):
+            sk.stokes_dl_eval(h, prec, sk.SK_DEVICE, RX, RW, RN, RQ, RY, RD, u_out=rout,
+                              stream=stream)
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        reps = 5
+        for _ in range(reps):
+            sk.stokes_dl_eval(h, prec, sk.SK_DEVICE, RX, RW, RN, RQ, RY, RD, u_out=rout,
+                              stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = a.elapsed_time(b) / reps
+        dl[name] = {"value": rinter / (ms * 1e-3) / 1e9, "ms": ms,
+                    "rel_l2_vs_oracle": rel_l2(rout.cpu().numpy()[ridx], dref)}
+    res["dl_rbc_m65"] = {"workload": f"rotated Evans-Fung cell m=65 N={rs.N} "
+                                     f"(N_s={rs.n_active}), double layer, delta=2h",
+                         "interactions": rinter, "flops_per_interaction": FLOPS_DL, **dl}
+    return res
+
+
+if __name__ == "__main__":
+    sys.exit(main())

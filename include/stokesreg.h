@@ -1,0 +1,144 @@
+/*
+ * stokesreg.h -- C ABI of libstokesreg: regularized Stokes single- and
+ * double-layer sums on an overlapping-patch capsule surface, GB300 (sm_103a).
+ *
+ * Method: arXiv 2310.13908 (Agarwal & Biros), Sec. 3.3-3.4. For every target
+ * x with regularization parameter delta_x, the library evaluates the
+ * trapezoid-rule discretization (Eq. smoothint) of the regularized layer
+ * potentials over the N quadrature nodes y of the surface:
+ *
+ *   single layer (Eq. regstokes):
+ *     u(x) = 1/(8 pi mu) sum_y w_y [ f_y s1(r/delta)/r + (f_y . d) d s2(r/delta)/r^3 ]
+ *   double layer (the regularized stresslet the paper cites in Sec. 1,
+ *   Limitations (ii); the paper prints no formula):
+ *     D(x) = 1/(8 pi) sum_y w_y (-6) (d . q_y)(d . n_y) d s3(r/delta)/r^5
+ *
+ *   d = x - y, r = |d|; s1, s2 as printed in Sec. 3.4;
+ *   s3(p) = erf p - (2/9) p (8p^6 - 36p^4 + 6p^2 + 9) e^{-p^2}/sqrt(pi).
+ *   At r = 0 the single layer takes the limit of Sec. 3.4,
+ *   s1/r -> 16/(3 delta sqrt(pi)); the double layer's self term is zero.
+ *
+ * Conventions for every function below:
+ *   - Arrays are row-major FP64: points and vector densities are [n][3].
+ *   - All caller buffers stay owned by the caller and are not retained after
+ *     the call returns -- except for asynchronous calls (non-NULL stream),
+ *     whose buffers must stay valid until that stream has completed.
+ *   - Functions return a status (SK_OK = 0 on success) and never throw; the
+ *     message of the last failure is sk_last_error(ctx).
+ *   - A context is not thread-safe: one host thread at a time.
+ */
+#ifndef STOKESREG_H
+#define STOKESREG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes -------------------------------------------------------- */
+#define SK_OK        0
+#define SK_EINVAL    1  /* invalid argument (NULL pointer, negative size, delta <= 0, ...) */
+#define SK_ENOMEM    2  /* device or pinned memory exhausted, or a fixed workspace too small */
+#define SK_ECUDA     3  /* a CUDA runtime call failed */
+#define SK_EBUSY     4  /* serving queue full; retry later */
+#define SK_EAGAIN    5  /* result not ready yet */
+#define SK_ETIMEOUT  6  /* a bounded device-side wait or a host poll ran out of time */
+#define SK_ENOTIMPL  7  /* feature not available in this build */
+
+/* ---- precision and memory-space selectors -------------------------------- */
+#define SK_FP64   0  /* every pair in FP64 */
+#define SK_FP32C  1  /* FP32 pairs, compensated (two-sum) accumulation per target,
+                        FP64 series for pairs with r/delta < rho_T, FP64 final sum */
+#define SK_HOST   0  /* all array arguments are host pointers */
+#define SK_DEVICE 1  /* all array arguments are device pointers on the context's device */
+
+typedef struct sk_ctx sk_ctx;
+
+/* Create a context on CUDA device `device`. workspace_bytes = 0 lets the
+ * context grow its device workspace on demand; > 0 preallocates exactly
+ * that much and never grows it (calls needing more return SK_ENOMEM).
+ * The context owns one CUDA stream and its workspace. *out is set to NULL
+ * on failure. */
+int sk_create(sk_ctx** out, int device, size_t workspace_bytes);
+
+/* Release the context, its stream and workspace. NULL is ignored. */
+void sk_destroy(sk_ctx* ctx);
+
+/* Message of the most recent failure on ctx ("" if none). Valid until the
+ * next call on ctx. ctx may be NULL (returns a creation-failure message). */
+const char* sk_last_error(const sk_ctx* ctx);
+
+/* Library version, e.g. 100 for 0.1.0. */
+int sk_version(void);
+
+/* Tuning knobs of the SK_FP32C path (defaults: rho_T = 0.5, rho_c = 5.0).
+ *   rho_T: pairs with r/delta below it are evaluated in FP64 by power series
+ *          (Sec. 3.4: s1/r and s2/r^3 are smooth at r = 0). 0 < rho_T <= 2.
+ *   rho_c: pairs with r/delta at or above it use s1 = s2 = s3 = 1, the plain
+ *          Stokeslet/stresslet; the omitted terms are below 6e-8 of the pair's
+ *          value at rho_c = 5. rho_T < rho_c <= 8.
+ * Returns SK_EINVAL outside those ranges. */
+int sk_set_fp32c_thresholds(sk_ctx* ctx, double rho_T, double rho_c);
+
+/* Counters of the most recent *_eval on ctx. Waits for that evaluation's
+ * stream to complete before reading them. */
+typedef struct {
+  int64_t n_src_active;      /* sources with w != 0 (the N_s of the interaction count) */
+  int64_t n_tgt;             /* targets */
+  int64_t near_pairs;        /* pairs evaluated in FP64 by series (SK_FP32C) */
+  int64_t overflow_targets;  /* targets whose near pairs exceeded the list and were rescanned */
+  int64_t kernel_launches;   /* CUDA kernels the evaluation launched */
+  int32_t n_chunks;          /* source chunks per target block (split of the source sum) */
+  int32_t precision;         /* SK_FP64 or SK_FP32C */
+  double pair_ms;            /* device time of the pair kernel (profiling on), else -1 */
+  double eval_ms;            /* device time of the whole evaluation (profiling on), else -1 */
+} sk_eval_stats;
+int sk_last_eval_stats(const sk_ctx* ctx, sk_eval_stats* out);
+
+/* Profiling: enable = 1 records CUDA events on the evaluation's stream around
+ * the pair kernel and around the whole evaluation (see sk_eval_stats). */
+int sk_set_profiling(sk_ctx* ctx, int enable);
+
+/* Regularized single layer (Sec. 3.4, Eq. regstokes; Sec. 3.3, Eq. smoothint).
+ *   n_src    number of quadrature nodes N (>= 0)
+ *   src_xyz  [n_src][3] node positions y
+ *   src_w    [n_src]    quadrature weights w = psi W h^2 (zero weights allowed)
+ *   f        [n_src][3] density (traction) f at the nodes
+ *   n_tgt    number of targets M (>= 0; 0 is a no-op)
+ *   tgt_xyz  [n_tgt][3] targets x (nodes themselves and/or off-surface points)
+ *   delta    [n_delta]  regularization parameter per target (n_delta = n_tgt)
+ *                       or one global value (n_delta = 1); every delta > 0
+ *   mu       viscosity > 0
+ *   u_out    [n_tgt][3] result, FP64 in both precisions
+ *   cuda_stream  NULL: the call is synchronous (returns after u_out is written);
+ *                otherwise a cudaStream_t on the context's device: the work is
+ *                enqueued on it and the call returns without waiting.
+ * Targets may coincide with nodes; r = 0 takes the limit above. With n_src = 0
+ * or all weights zero, u_out is zero. Errors: SK_EINVAL, SK_ENOMEM, SK_ECUDA,
+ * SK_ETIMEOUT (a bounded device wait expired; u_out is then unspecified). */
+int stokes_sl_eval(sk_ctx* ctx, int precision, int mem,
+                   int64_t n_src, const double* src_xyz, const double* src_w, const double* f,
+                   int64_t n_tgt, const double* tgt_xyz,
+                   const double* delta, int64_t n_delta,
+                   double mu, double* u_out, void* cuda_stream);
+
+/* Regularized double layer (stresslet), same conventions as stokes_sl_eval.
+ *   src_n  [n_src][3] unit normals n at the nodes (orientation sets the sign)
+ *   q      [n_src][3] double-layer density q
+ * No viscosity argument: the stresslet is viscosity-free. For a constant q on
+ * a closed surface with outward normals the result is q inside, 0 outside and
+ * q/2 on the surface. */
+int stokes_dl_eval(sk_ctx* ctx, int precision, int mem,
+                   int64_t n_src, const double* src_xyz, const double* src_w,
+                   const double* src_n, const double* q,
+                   int64_t n_tgt, const double* tgt_xyz,
+                   const double* delta, int64_t n_delta,
+                   double* u_out, void* cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STOKESREG_H */

@@ -1,0 +1,263 @@
+"""Python binding of libstokesreg (regularized Stokes layer sums on GB300).
+
+Thin ctypes marshalling over the C ABI declared in include/stokesreg.h; the
+functions keep the C names. Every step of an evaluation runs in the CUDA
+library: this module only converts arrays to pointers. Host arrays are numpy
+float64 (mem = SK_HOST); device arrays are CUDA float64 torch tensors
+(mem = SK_DEVICE), whose memory and streams come from PyTorch.
+
+Importing the package does not load the library; the first call does, and
+fails loudly (RuntimeError) if libstokesreg.so has not been built: there is
+no CPU fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libstokesreg.so")
+
+SK_OK, SK_EINVAL, SK_ENOMEM, SK_ECUDA, SK_EBUSY, SK_EAGAIN, SK_ETIMEOUT, SK_ENOTIMPL = range(8)
+SK_FP64, SK_FP32C = 0, 1
+SK_HOST, SK_DEVICE = 0, 1
+
+_NAMES = {SK_OK: "SK_OK", SK_EINVAL: "SK_EINVAL", SK_ENOMEM: "SK_ENOMEM", SK_ECUDA: "SK_ECUDA",
+          SK_EBUSY: "SK_EBUSY", SK_EAGAIN: "SK_EAGAIN", SK_ETIMEOUT: "SK_ETIMEOUT",
+          SK_ENOTIMPL: "SK_ENOTIMPL"}
+
+_lib = None
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_dbl = ctypes.c_double
+_int = ctypes.c_int
+
+
+class SkError(RuntimeError):
+    def __init__(self, code: int, message: str):
+        super().__init__(f"{_NAMES.get(code, code)}: {message}")
+        self.code = code
+
+
+class sk_eval_stats(ctypes.Structure):
+    _fields_ = [("n_src_active", ctypes.c_int64), ("n_tgt", ctypes.c_int64),
+                ("near_pairs", ctypes.c_int64), ("overflow_targets", ctypes.c_int64),
+                ("kernel_launches", ctypes.c_int64), ("n_chunks", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("pair_ms", ctypes.c_double),
+                ("eval_ms", ctypes.c_double)]
+
+
+def _declare(lib):
+    lib.sk_version.restype = _int
+    lib.sk_create.argtypes = [ctypes.POINTER(_vp), _int, ctypes.c_size_t]
+    lib.sk_create.restype = _int
+    lib.sk_destroy.argtypes = [_vp]
+    lib.sk_destroy.restype = None
+    lib.sk_last_error.argtypes = [_vp]
+    lib.sk_last_error.restype = ctypes.c_char_p
+    lib.sk_set_fp32c_thresholds.argtypes = [_vp, _dbl, _dbl]
+    lib.sk_set_fp32c_thresholds.restype = _int
+    lib.sk_last_eval_stats.argtypes = [_vp, ctypes.POINTER(sk_eval_stats)]
+    lib.sk_last_eval_stats.restype = _int
+    lib.sk_set_profiling.argtypes = [_vp, _int]
+    lib.sk_set_profiling.restype = _int
+    lib.stokes_sl_eval.argtypes = [_vp, _int, _int, _i64, _vp, _vp, _vp, _i64, _vp, _vp, _i64,
+                                   _dbl, _vp, _vp]
+    lib.stokes_sl_eval.restype = _int
+    lib.stokes_dl_eval.argtypes = [_vp, _int, _int, _i64, _vp, _vp, _vp, _vp, _i64, _vp, _vp,
+                                   _i64, _vp, _vp]
+    lib.stokes_dl_eval.restype = _int
+    for name, args in _EXTRA_DECLS.items():
+        if hasattr(lib, name):
+            getattr(lib, name).argtypes = args[0]
+            getattr(lib, name).restype = args[1]
+
+
+_EXTRA_DECLS: dict = {}
+
+
+def load():
+    """Load libstokesreg.so (RuntimeError if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build the CUDA library first "
+                           "(python -c 'import __graft_entry__ as g; g.build()')")
+    lib = ctypes.CDLL(LIB_PATH)
+    _declare(lib)
+    _lib = lib
+    return lib
+
+
+def _check(ctx, code):
+    if code != SK_OK:
+        raise SkError(code, load().sk_last_error(ctx).decode())
+
+
+def sk_version() -> int:
+    return load().sk_version()
+
+
+def sk_create(device: int = 0, workspace_bytes: int = 0):
+    h = _vp()
+    code = load().sk_create(ctypes.byref(h), int(device), int(workspace_bytes))
+    if code != SK_OK:
+        raise SkError(code, load().sk_last_error(None).decode())
+    return h
+
+
+def sk_destroy(ctx) -> None:
+    if ctx:
+        load().sk_destroy(ctx)
+
+
+def sk_last_error(ctx) -> str:
+    return load().sk_last_error(ctx).decode()
+
+
+def sk_set_fp32c_thresholds(ctx, rho_T: float, rho_c: float) -> None:
+    _check(ctx, load().sk_set_fp32c_thresholds(ctx, float(rho_T), float(rho_c)))
+
+
+def sk_set_profiling(ctx, enable: bool) -> None:
+    _check(ctx, load().sk_set_profiling(ctx, 1 if enable else 0))
+
+
+def sk_last_eval_stats(ctx) -> dict:
+    st = sk_eval_stats()
+    _check(ctx, load().sk_last_eval_stats(ctx, ctypes.byref(st)))
+    return {f[0]: getattr(st, f[0]) for f in st._fields_}
+
+
+# ---- array marshalling ------------------------------------------------------
+
+def _is_torch(a) -> bool:
+    return type(a).__module__.startswith("torch")
+
+
+def _ptr(a, mem: int, shape_tail, name: str):
+    """Pointer of a float64 C-contiguous array in the expected memory space."""
+    if a is None:
+        return None, 0
+    if mem == SK_DEVICE:
+        if not _is_torch(a) or not a.is_cuda:
+            raise TypeError(f"{name}: SK_DEVICE expects a CUDA torch tensor")
+        import torch
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            raise TypeError(f"{name}: expected a contiguous float64 tensor")
+        n = a.shape[0] if a.dim() > 0 else 1
+        if shape_tail and tuple(a.shape[1:]) != tuple(shape_tail):
+            raise ValueError(f"{name}: expected shape (n, {shape_tail})")
+        return a.data_ptr(), n
+    arr = np.ascontiguousarray(a, dtype=np.float64)
+    if shape_tail:
+        arr = arr.reshape((-1,) + tuple(shape_tail))
+    else:
+        arr = arr.reshape(-1)
+    return arr, arr.shape[0]
+
+
+def _host_ptr(arr):
+    return None if arr is None else arr.ctypes.data_as(_vp)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream  # torch.cuda.Stream
+
+
+def _alloc_out(like_tensor, mem, M):
+    if mem == SK_DEVICE:
+        import torch
+        return torch.empty((M, 3), dtype=torch.float64, device=like_tensor.device)
+    return np.empty((M, 3), dtype=np.float64)
+
+
+def stokes_sl_eval(ctx, precision: int, mem: int, src_xyz, src_w, f, tgt_xyz, delta,
+                   mu: float = 1.0, u_out=None, stream=None):
+    """Regularized single layer (Sec. 3.4, Eq. regstokes). Returns u_out (M, 3).
+
+    stream=None makes the call synchronous; a torch.cuda.Stream (or raw
+    handle) enqueues it asynchronously on that stream.
+    """
+    lib = load()
+    X, n = _ptr(src_xyz, mem, (3,), "src_xyz")
+    W, nw = _ptr(src_w, mem, (), "src_w")
+    F, nf = _ptr(f, mem, (3,), "f")
+    Y, M = _ptr(tgt_xyz, mem, (3,), "tgt_xyz")
+    D, nd = _ptr(delta if mem == SK_DEVICE or not np.isscalar(delta) else [delta], mem, (),
+                 "delta")
+    if not (n == nw == nf):
+        raise ValueError("src_xyz, src_w and f must have the same number of nodes")
+    if u_out is None:
+        u_out = _alloc_out(tgt_xyz, mem, M)
+    U, _ = _ptr(u_out, mem, (3,), "u_out")
+    if mem == SK_HOST:
+        args = [_host_ptr(X), _host_ptr(W), _host_ptr(F), M, _host_ptr(Y), _host_ptr(D), nd,
+                float(mu), _host_ptr(U)]
+    else:
+        args = [X, W, F, M, Y, D, nd, float(mu), U]
+    code = lib.stokes_sl_eval(ctx, int(precision), int(mem), n, *args, _stream_handle(stream))
+    _check(ctx, code)
+    if mem == SK_HOST and U is not u_out:
+        np.copyto(u_out, U.reshape(np.shape(u_out)))
+    return u_out
+
+
+def stokes_dl_eval(ctx, precision: int, mem: int, src_xyz, src_w, src_n, q, tgt_xyz, delta,
+                   u_out=None, stream=None):
+    """Regularized double layer (stresslet). Returns u_out (M, 3)."""
+    lib = load()
+    X, n = _ptr(src_xyz, mem, (3,), "src_xyz")
+    W, nw = _ptr(src_w, mem, (), "src_w")
+    Nn, nn = _ptr(src_n, mem, (3,), "src_n")
+    Q, nq = _ptr(q, mem, (3,), "q")
+    Y, M = _ptr(tgt_xyz, mem, (3,), "tgt_xyz")
+    D, nd = _ptr(delta if mem == SK_DEVICE or not np.isscalar(delta) else [delta], mem, (),
+                 "delta")
+    if not (n == nw == nn == nq):
+        raise ValueError("src_xyz, src_w, src_n and q must have the same number of nodes")
+    if u_out is None:
+        u_out = _alloc_out(tgt_xyz, mem, M)
+    U, _ = _ptr(u_out, mem, (3,), "u_out")
+    if mem == SK_HOST:
+        args = [_host_ptr(X), _host_ptr(W), _host_ptr(Nn), _host_ptr(Q), M, _host_ptr(Y),
+                _host_ptr(D), nd, _host_ptr(U)]
+    else:
+        args = [X, W, Nn, Q, M, Y, D, nd, U]
+    code = lib.stokes_dl_eval(ctx, int(precision), int(mem), n, *args, _stream_handle(stream))
+    _check(ctx, code)
+    if mem == SK_HOST and U is not u_out:
+        np.copyto(u_out, U.reshape(np.shape(u_out)))
+    return u_out
+
+
+class Context:
+    """RAII holder of an sk_ctx*."""
+
+    def __init__(self, device: int = 0, workspace_bytes: int = 0):
+        self.handle = sk_create(device, workspace_bytes)
+
+    def close(self):
+        if self.handle:
+            sk_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

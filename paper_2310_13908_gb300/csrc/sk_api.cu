@@ -1,0 +1,406 @@
+// sk_api.cu -- host side of the C ABI: contexts, validation, workspace and
+// the launch sequence of one evaluation.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "sk_internal.h"
+
+namespace {
+
+constexpr int64_t MAX_POINTS = int64_t(1) << 30;
+const char* g_create_error = "";
+thread_local std::string g_create_error_buf;
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+int fail(sk_ctx* ctx, int code, const char* fmt, const char* detail = "") {
+  char buf[512];
+  std::snprintf(buf, sizeof(buf), fmt, detail);
+  if (ctx) ctx->err = buf;
+  return code;
+}
+
+int cuda_fail(sk_ctx* ctx, cudaError_t e, const char* where) {
+  char buf[512];
+  std::snprintf(buf, sizeof(buf), "%s: %s", where, cudaGetErrorString(e));
+  ctx->err = buf;
+  return e == cudaErrorMemoryAllocation ? SK_ENOMEM : SK_ECUDA;
+}
+
+}  // namespace
+
+namespace sk {
+
+size_t eval_workspace_bytes(const EvalShape& s) {
+  EvalBufs b;
+  Bump bp;
+  carve_eval_buffers(bp, s, b);
+  return bp.off;
+}
+
+void carve_eval_buffers(Bump& bp, const EvalShape& s, EvalBufs& b) {
+  const bool dl = s.layer == LAYER_DL;
+  const bool fp32 = s.precision == SK_FP32C;
+  b.N = s.N;
+  b.M = s.M;
+  b.N_pad = (int64_t)align_up((size_t)s.N, TILE);
+  b.M_pad = (int64_t)align_up((size_t)s.M, fp32 ? TGT_CTA32 : TGT_CTA64);
+  b.n_chunks = s.n_chunks;
+  const int64_t nsort = s.N > s.M ? s.N : s.M;
+  b.sort_blocks = sort_grid_blocks(nsort > 0 ? nsort : 1);
+  if (s.copy_inputs) {
+    b.src_xyz = bp.take<double>(3 * s.N);
+    b.src_w = bp.take<double>(s.N);
+    b.dens = bp.take<double>(3 * s.N);
+    if (dl) b.nrm = bp.take<double>(3 * s.N);
+    b.tgt_xyz = bp.take<double>(3 * s.M);
+    b.delta = bp.take<double>(s.n_delta);
+    b.u = bp.take<double>(3 * s.M);
+  }
+  b.keys_a = bp.take<uint32_t>(nsort);
+  b.keys_b = bp.take<uint32_t>(nsort);
+  b.vals_a = bp.take<int>(nsort);
+  b.vals_b = bp.take<int>(nsort);
+  b.hist = bp.take<uint32_t>(256 * (size_t)b.sort_blocks);
+  b.bbox_part = bp.take<float>(128 * 6);
+  b.bbox = bp.take<float>(8);
+  b.meta = bp.take<int>(N_META);
+  b.src_orig = bp.take<int>(b.N_pad);
+  if (fp32) {
+    b.srcF = bp.take<float4>((size_t)b.N_pad * (dl ? V_DL : V_SL));
+  } else {
+    b.src64 = bp.take<double4_32a>((size_t)b.N_pad * 2);
+    if (dl) b.nrm64 = bp.take<double4_32a>(b.N_pad);
+  }
+  b.segbox = bp.take<float4>((size_t)(b.N_pad / SEG) * 2);
+  b.tgt_perm = bp.take<int>(b.M_pad);
+  if (fp32) b.tgtF = bp.take<float4>((size_t)b.M_pad * 2);
+  b.tgt64 = bp.take<double4_32a>(b.M_pad);
+  b.part = bp.take<double>((size_t)s.n_chunks * b.M_pad * 3);
+  if (fp32) {
+    b.near_cnt = bp.take<int>(b.M_pad);
+    b.near_idx = bp.take<int>((size_t)b.M_pad * NEAR_K);
+    b.near_ovf = bp.take<double>((size_t)b.M_pad * 3);
+  }
+  b.flags = bp.take<unsigned long long>(N_FLAGS);
+}
+
+int choose_chunks(int precision, int64_t N, int64_t M, int sm_count) {
+  const int64_t tgt_cta = precision == SK_FP32C ? TGT_CTA32 : TGT_CTA64;
+  const int64_t tile = precision == SK_FP32C ? TILE : TILE64;
+  const int64_t n_tb = (int64_t)align_up((size_t)(M > 0 ? M : 1), tgt_cta) / tgt_cta;
+  const int64_t tiles = (int64_t)align_up((size_t)(N > 0 ? N : 1), tile) / tile;
+  const int64_t want = (int64_t)sm_count * 2 * 8;  // about eight waves of two CTAs per SM
+  int64_t nc = (want + n_tb - 1) / n_tb;
+  int64_t cap = tiles / 2;
+  if (cap < 1) cap = 1;
+  if (nc > cap) nc = cap;
+  if (nc > 64) nc = 64;
+  if (nc < 1) nc = 1;
+  return (int)nc;
+}
+
+__global__ void k_check_delta(const double* __restrict__ d, int64_t n,
+                              unsigned long long* __restrict__ flags) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n && !(d[i] > 0.0 && d[i] < INFINITY)) atomicExch(flags + FLAG_BAD_DELTA, 1ull);
+}
+
+// Enqueue one evaluation on `st`; inputs and output are device pointers in b.
+int enqueue_eval(const EvalShape& s, const EvalBufs& b, double rho_T, double rho_c,
+                 cudaStream_t st, cudaEvent_t* ev) {
+  const bool fp32 = s.precision == SK_FP32C;
+  constexpr int SORT_LAUNCHES = 3 + 4 * 3;  // bbox (2) + keys + 4 radix passes x 3
+  int launches = 0;
+  if (ev) cudaEventRecord(ev[0], st);
+  const double scale = s.layer == LAYER_SL ? 1.0 / (8.0 * PI_CONST * s.mu) : -6.0 / (8.0 * PI_CONST);
+  cudaMemsetAsync(b.flags, 0, N_FLAGS * sizeof(unsigned long long), st);
+  cudaMemsetAsync(b.meta, 0, N_META * sizeof(int), st);
+  if (fp32) cudaMemsetAsync(b.near_cnt, 0, b.M_pad * sizeof(int), st);
+  k_check_delta<<<(unsigned)((s.n_delta + 255) / 256), 256, 0, st>>>(b.delta, s.n_delta, b.flags);
+  launches += 1;
+  if (s.N > 0) {
+    launch_sort_points(b.src_xyz, b.src_w, s.N, b.keys_a, b.keys_b, b.vals_a, b.vals_b, b.hist,
+                       b.bbox_part, b.bbox, b.meta + META_NS, b.sort_blocks, st);
+    if (fp32)
+      launch_pack_sources32(s.layer, b, scale, st);
+    else
+      launch_pack_sources64(s.layer, b, scale, st);
+    launches += SORT_LAUNCHES + 1;
+  }
+  launch_sort_points(b.tgt_xyz, nullptr, s.M, b.keys_a, b.keys_b, b.vals_a, b.vals_b, b.hist,
+                     b.bbox_part, b.bbox, b.meta + META_SCRATCH, b.sort_blocks, st);
+  launches += SORT_LAUNCHES;
+  if (fp32) {
+    launch_pack_targets32(b, s.n_delta, rho_T, rho_c, st);
+    if (ev) cudaEventRecord(ev[1], st);
+    launch_pair32(s.layer, b, rho_T, st);
+    if (ev) cudaEventRecord(ev[2], st);
+    launch_finish32(s.layer, b, s.n_delta, scale, rho_T, st);
+    launches += 1 + 1 + 2;
+  } else {
+    launch_pack_targets64(b, s.n_delta, st);
+    if (ev) cudaEventRecord(ev[1], st);
+    launch_pair64(s.layer, b, scale, st);
+    if (ev) cudaEventRecord(ev[2], st);
+    launch_finish64(b, st);
+    launches += 1 + 1 + 1;
+  }
+  if (ev) cudaEventRecord(ev[3], st);
+  return launches;
+}
+
+}  // namespace sk
+
+using namespace sk;
+
+extern "C" {
+
+int sk_version(void) { return 100; }
+
+int sk_create(sk_ctx** out, int device, size_t workspace_bytes) {
+  if (!out) return SK_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || ndev == 0) {
+    g_create_error_buf = std::string("no CUDA device: ") + cudaGetErrorString(e);
+    g_create_error = g_create_error_buf.c_str();
+    return SK_ECUDA;
+  }
+  if (device < 0 || device >= ndev) {
+    g_create_error = "device index out of range";
+    return SK_EINVAL;
+  }
+  sk_ctx* ctx = new (std::nothrow) sk_ctx();
+  if (!ctx) return SK_ENOMEM;
+  ctx->device = device;
+  DeviceGuard g(device);
+  int code = SK_OK;
+  if ((e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device)) !=
+          cudaSuccess ||
+      (e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaMallocHost(&ctx->h_flags, 256)) != cudaSuccess) {
+    code = e == cudaErrorMemoryAllocation ? SK_ENOMEM : SK_ECUDA;
+  } else if (workspace_bytes > 0) {
+    if ((e = cudaMalloc(&ctx->ws, workspace_bytes)) != cudaSuccess)
+      code = SK_ENOMEM;
+    else {
+      ctx->ws_bytes = workspace_bytes;
+      ctx->ws_fixed = true;
+    }
+  }
+  if (code != SK_OK) {
+    g_create_error_buf = std::string("sk_create: ") + cudaGetErrorString(e);
+    g_create_error = g_create_error_buf.c_str();
+    sk_destroy(ctx);
+    return code;
+  }
+  std::memset(ctx->h_flags, 0, 256);
+  ctx->last_stream = ctx->stream;
+  *out = ctx;
+  return SK_OK;
+}
+
+void sk_destroy(sk_ctx* ctx) {
+  if (!ctx) return;
+  DeviceGuard g(ctx->device);
+  cudaDeviceSynchronize();
+  if (ctx->ws) cudaFree(ctx->ws);
+  if (ctx->h_flags) cudaFreeHost(ctx->h_flags);
+  for (int i = 0; i < 4; ++i)
+    if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
+  if (ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+const char* sk_last_error(const sk_ctx* ctx) { return ctx ? ctx->err.c_str() : g_create_error; }
+
+int sk_set_fp32c_thresholds(sk_ctx* ctx, double rho_T, double rho_c) {
+  if (!ctx) return SK_EINVAL;
+  if (!(rho_T > 0.0 && rho_T <= 2.0 && rho_c > rho_T && rho_c <= 8.0))
+    return fail(ctx, SK_EINVAL, "sk_set_fp32c_thresholds: need 0 < rho_T <= 2, rho_T < rho_c <= 8%s");
+  ctx->rho_T = rho_T;
+  ctx->rho_c = rho_c;
+  return SK_OK;
+}
+
+int sk_set_profiling(sk_ctx* ctx, int enable) {
+  if (!ctx) return SK_EINVAL;
+  DeviceGuard g(ctx->device);
+  if (enable && !ctx->ev[0]) {
+    for (int i = 0; i < 4; ++i) {
+      cudaError_t e = cudaEventCreate(&ctx->ev[i]);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "sk_set_profiling");
+    }
+  }
+  ctx->profile = enable != 0;
+  return SK_OK;
+}
+
+int sk_last_eval_stats(const sk_ctx* ctx, sk_eval_stats* out) {
+  if (!ctx || !out) return SK_EINVAL;
+  DeviceGuard g(ctx->device);
+  cudaStreamSynchronize(ctx->last_stream);
+  *out = ctx->stats;
+  out->pair_ms = out->eval_ms = -1.0;
+  if (ctx->stats.pair_ms == 0.0 && ctx->profile && ctx->ev[0]) {
+    float a = 0.f, b = 0.f;
+    if (cudaEventElapsedTime(&a, ctx->ev[1], ctx->ev[2]) == cudaSuccess &&
+        cudaEventElapsedTime(&b, ctx->ev[0], ctx->ev[3]) == cudaSuccess) {
+      out->pair_ms = a;
+      out->eval_ms = b;
+    }
+  }
+  const unsigned long long* f = ctx->h_flags;
+  const int* meta = reinterpret_cast<const int*>(ctx->h_flags + N_FLAGS);
+  out->n_src_active = meta[META_NS];
+  out->near_pairs = (int64_t)f[FLAG_NEAR_PAIRS];
+  out->overflow_targets = (int64_t)f[FLAG_OVERFLOW];
+  return SK_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+int ensure_workspace(sk_ctx* ctx, size_t need) {
+  if (need <= ctx->ws_bytes) return SK_OK;
+  if (ctx->ws_fixed) {
+    char buf[160];
+    std::snprintf(buf, sizeof(buf), "workspace of %zu bytes too small: this call needs %zu",
+                  ctx->ws_bytes, need);
+    ctx->err = buf;
+    return SK_ENOMEM;
+  }
+  cudaError_t e = cudaDeviceSynchronize();  // older work may still use the workspace
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "workspace grow (synchronize)");
+  if (ctx->ws) cudaFree(ctx->ws);
+  ctx->ws = nullptr;
+  ctx->ws_bytes = 0;
+  const size_t want = need + need / 4;
+  if ((e = cudaMalloc(&ctx->ws, want)) != cudaSuccess) return cuda_fail(ctx, e, "workspace cudaMalloc");
+  ctx->ws_bytes = want;
+  return SK_OK;
+}
+
+int eval_entry(sk_ctx* ctx, int layer, int precision, int mem, int64_t N, const double* xyz,
+               const double* w, const double* dens, const double* nrm, int64_t M,
+               const double* txyz, const double* delta, int64_t n_delta, double mu, double* u_out,
+               void* stream_v) {
+  const char* fn = layer == LAYER_SL ? "stokes_sl_eval" : "stokes_dl_eval";
+  if (!ctx) return SK_EINVAL;
+  ctx->err.clear();
+  if (precision != SK_FP64 && precision != SK_FP32C)
+    return fail(ctx, SK_EINVAL, "%s: precision must be SK_FP64 or SK_FP32C", fn);
+  if (mem != SK_HOST && mem != SK_DEVICE)
+    return fail(ctx, SK_EINVAL, "%s: mem must be SK_HOST or SK_DEVICE", fn);
+  if (N < 0 || M < 0) return fail(ctx, SK_EINVAL, "%s: negative size", fn);
+  if (N > MAX_POINTS || M > MAX_POINTS)
+    return fail(ctx, SK_EINVAL, "%s: more than 2^30 sources or targets", fn);
+  if (M == 0) return SK_OK;
+  if (N > 0 && (!xyz || !w || !dens || (layer == LAYER_DL && !nrm)))
+    return fail(ctx, SK_EINVAL, "%s: NULL source array", fn);
+  if (!txyz || !delta || !u_out) return fail(ctx, SK_EINVAL, "%s: NULL target/delta/output array", fn);
+  if (!(n_delta == 1 || n_delta == M))
+    return fail(ctx, SK_EINVAL, "%s: n_delta must be 1 or n_tgt", fn);
+  if (layer == LAYER_SL && !(mu > 0.0 && std::isfinite(mu)))
+    return fail(ctx, SK_EINVAL, "%s: mu must be positive and finite", fn);
+  if (mem == SK_HOST)
+    for (int64_t i = 0; i < n_delta; ++i)
+      if (!(delta[i] > 0.0 && std::isfinite(delta[i])))
+        return fail(ctx, SK_EINVAL, "%s: delta must be positive and finite", fn);
+
+  DeviceGuard g(ctx->device);
+  cudaStream_t st = stream_v ? (cudaStream_t)stream_v : ctx->stream;
+  EvalShape s;
+  s.layer = layer;
+  s.precision = precision;
+  s.N = N;
+  s.M = M;
+  s.n_delta = n_delta;
+  s.mu = mu;
+  s.copy_inputs = mem == SK_HOST;
+  s.n_chunks = choose_chunks(precision, N, M, ctx->sm_count);
+  const size_t need = eval_workspace_bytes(s);
+  int rc = ensure_workspace(ctx, need);
+  if (rc != SK_OK) return rc;
+  EvalBufs b;
+  Bump bp;
+  bp.base = ctx->ws;
+  carve_eval_buffers(bp, s, b);
+  cudaError_t e;
+  if (mem == SK_HOST) {
+    if (N > 0) {
+      cudaMemcpyAsync((void*)b.src_xyz, xyz, 3 * N * sizeof(double), cudaMemcpyHostToDevice, st);
+      cudaMemcpyAsync((void*)b.src_w, w, N * sizeof(double), cudaMemcpyHostToDevice, st);
+      cudaMemcpyAsync((void*)b.dens, dens, 3 * N * sizeof(double), cudaMemcpyHostToDevice, st);
+      if (layer == LAYER_DL)
+        cudaMemcpyAsync((void*)b.nrm, nrm, 3 * N * sizeof(double), cudaMemcpyHostToDevice, st);
+    }
+    cudaMemcpyAsync((void*)b.tgt_xyz, txyz, 3 * M * sizeof(double), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync((void*)b.delta, delta, n_delta * sizeof(double), cudaMemcpyHostToDevice, st);
+  } else {
+    b.src_xyz = xyz;
+    b.src_w = w;
+    b.dens = dens;
+    b.nrm = nrm;
+    b.tgt_xyz = txyz;
+    b.delta = delta;
+    b.u = u_out;
+  }
+  const int launches = enqueue_eval(s, b, ctx->rho_T, ctx->rho_c, st, ctx->profile ? ctx->ev : nullptr);
+  if (mem == SK_HOST)
+    cudaMemcpyAsync(u_out, b.u, 3 * M * sizeof(double), cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(ctx->h_flags, b.flags, N_FLAGS * sizeof(unsigned long long),
+                  cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(ctx->h_flags + N_FLAGS, b.meta, N_META * sizeof(int), cudaMemcpyDeviceToHost,
+                  st);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, fn);
+  ctx->last_stream = st;
+  ctx->stats = sk_eval_stats{};
+  ctx->stats.n_tgt = M;
+  ctx->stats.n_chunks = s.n_chunks;
+  ctx->stats.kernel_launches = launches;
+  ctx->stats.precision = precision;
+  if (stream_v) return SK_OK;
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(ctx, e, fn);
+  if (ctx->h_flags[FLAG_TIMEOUT]) return fail(ctx, SK_ETIMEOUT, "%s: a bounded device wait expired", fn);
+  if (ctx->h_flags[FLAG_BAD_DELTA])
+    return fail(ctx, SK_EINVAL, "%s: delta must be positive and finite", fn);
+  return SK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int stokes_sl_eval(sk_ctx* ctx, int precision, int mem, int64_t n_src, const double* src_xyz,
+                   const double* src_w, const double* f, int64_t n_tgt, const double* tgt_xyz,
+                   const double* delta, int64_t n_delta, double mu, double* u_out,
+                   void* cuda_stream) {
+  return eval_entry(ctx, LAYER_SL, precision, mem, n_src, src_xyz, src_w, f, nullptr, n_tgt,
+                    tgt_xyz, delta, n_delta, mu, u_out, cuda_stream);
+}
+
+int stokes_dl_eval(sk_ctx* ctx, int precision, int mem, int64_t n_src, const double* src_xyz,
+                   const double* src_w, const double* src_n, const double* q, int64_t n_tgt,
+                   const double* tgt_xyz, const double* delta, int64_t n_delta, double* u_out,
+                   void* cuda_stream) {
+  return eval_entry(ctx, LAYER_DL, precision, mem, n_src, src_xyz, src_w, q, src_n, n_tgt,
+                    tgt_xyz, delta, n_delta, 1.0, u_out, cuda_stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,170 @@
+// sk_internal.h -- shared declarations of libstokesreg (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+
+#include "../../include/stokesreg.h"
+
+namespace sk {
+
+// ---- work decomposition of the pair kernels --------------------------------
+constexpr int SEG = 32;                 // sources per segment (near/far classification unit)
+constexpr int TILE_SEGS = 8;
+constexpr int TILE = SEG * TILE_SEGS;   // sources per shared-memory tile (FP32 kernels)
+constexpr int TPB32 = 256;              // threads per CTA, FP32 kernels
+constexpr int TPL32 = 4;                // targets per lane (two f32x2 pairs)
+constexpr int TGT_WARP32 = 32 * TPL32;  // 128 targets per warp
+constexpr int TGT_CTA32 = TPB32 * TPL32;
+constexpr int TILE64 = 128;             // sources per tile, FP64 kernels
+constexpr int TPB64 = 256;
+constexpr int TPL64 = 2;
+constexpr int TGT_WARP64 = 32 * TPL64;
+constexpr int TGT_CTA64 = TPB64 * TPL64;
+constexpr int NEAR_K = 96;              // FP64 near-pair slots per target
+constexpr int RHO_C64 = 7;              // FP64 path: s_i == 1 to double precision beyond 7
+
+// layer kinds
+constexpr int LAYER_SL = 0;
+constexpr int LAYER_DL = 1;
+
+// float4 records per source in the packed FP32 layout
+constexpr int V_SL = 3;
+constexpr int V_DL = 5;
+
+// device flag slots (unsigned long long)
+constexpr int FLAG_TIMEOUT = 0;
+constexpr int FLAG_OVERFLOW = 1;
+constexpr int FLAG_NEAR_PAIRS = 2;
+constexpr int FLAG_BAD_DELTA = 3;
+constexpr int N_FLAGS = 8;
+
+// meta ints written on the device by the preparation kernels
+constexpr int META_NS = 0;       // active sources
+constexpr int META_NS_PAD = 1;   // padded to a multiple of TILE (FP32) / TILE64 (FP64)
+constexpr int META_SCRATCH = 2;  // count slot of the target sort (all targets are active)
+constexpr int N_META = 8;
+
+constexpr double PI_CONST = 3.14159265358979323846;
+
+// bounded waits: about one second at 2 GHz
+constexpr long long WAIT_CYCLES = 2000000000LL;
+
+__host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Bump allocator over one device buffer; a null base only measures.
+struct Bump {
+  char* base = nullptr;
+  size_t off = 0;
+  template <class T>
+  T* take(size_t n) {
+    off = align_up(off, 256);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += n * sizeof(T);
+    return p;
+  }
+};
+
+// Buffers of one evaluation, carved from the context workspace.
+struct EvalBufs {
+  // FP64 inputs on the device (caller's pointers or copies in the workspace)
+  const double* src_xyz = nullptr;
+  const double* src_w = nullptr;
+  const double* dens = nullptr;   // f (single layer) or q (double layer)
+  const double* nrm = nullptr;    // double layer only
+  const double* tgt_xyz = nullptr;
+  const double* delta = nullptr;
+  double* u = nullptr;            // device result
+  // sort scratch
+  uint32_t* keys_a = nullptr;
+  uint32_t* keys_b = nullptr;
+  int* vals_a = nullptr;
+  int* vals_b = nullptr;
+  uint32_t* hist = nullptr;
+  float* bbox_part = nullptr;
+  float* bbox = nullptr;
+  // prepared sources / targets
+  int* meta = nullptr;
+  int* src_orig = nullptr;        // packed source -> original index (-1: padding)
+  float4* srcF = nullptr;         // FP32 packed sources
+  double4_32a* src64 = nullptr;       // FP64 packed sources (pos, density)
+  double4_32a* nrm64 = nullptr;       // FP64 packed normals (double layer)
+  float4* segbox = nullptr;       // per segment: lo, hi
+  int* tgt_perm = nullptr;        // sorted target -> original index
+  float4* tgtF = nullptr;         // FP32 sorted targets: (x, y, z, 1/delta), (rc2, rt2, 0, 0)
+  double4_32a* tgt64 = nullptr;       // FP64 sorted targets: (x, y, z, delta)
+  // accumulation
+  double* part = nullptr;         // [n_chunks][M_pad][3]
+  int* near_cnt = nullptr;        // [M_pad]
+  int* near_idx = nullptr;        // [M_pad][NEAR_K]
+  double* near_ovf = nullptr;     // [M_pad][3]
+  unsigned long long* flags = nullptr;
+  // sizes
+  int64_t N = 0, M = 0, N_pad = 0, M_pad = 0;
+  int n_chunks = 1;
+  int sort_blocks = 0;
+};
+
+}  // namespace sk
+
+struct sk_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  bool ws_fixed = false;
+  unsigned long long* h_flags = nullptr;  // pinned copy of the device flags
+  cudaStream_t last_stream = nullptr;
+  int sm_count = 0;
+  double rho_T = 0.5;
+  double rho_c = 5.0;
+  bool profile = false;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // eval begin, pair begin/end, eval end
+  sk_eval_stats stats{};
+  std::string err;
+};
+
+namespace sk {
+
+// Shape of one evaluation.
+struct EvalShape {
+  int layer = LAYER_SL;
+  int precision = SK_FP32C;
+  int64_t N = 0, M = 0, n_delta = 1;
+  double mu = 1.0;
+  bool copy_inputs = false;  // inputs/outputs live in the workspace (host-memory calls)
+  int n_chunks = 1;
+};
+
+// sk_api.cu
+size_t eval_workspace_bytes(const EvalShape& s);
+void carve_eval_buffers(Bump& bp, const EvalShape& s, EvalBufs& b);
+int choose_chunks(int precision, int64_t N, int64_t M, int sm_count);
+// Returns the number of kernels launched. ev (optional, 4 events) brackets
+// the whole evaluation (ev[0], ev[3]) and the pair kernel (ev[1], ev[2]).
+int enqueue_eval(const EvalShape& s, const EvalBufs& b, double rho_T, double rho_c,
+                 cudaStream_t st, cudaEvent_t* ev = nullptr);
+
+// launchers (sk_prep.cu)
+void launch_sort_points(const double* xyz, const double* w, int64_t n, uint32_t* keys_a,
+                        uint32_t* keys_b, int* vals_a, int* vals_b, uint32_t* hist,
+                        float* bbox_part, float* bbox, int* count_out, int sort_blocks,
+                        cudaStream_t st);
+void launch_pack_sources32(int layer, const EvalBufs& b, double scale, cudaStream_t st);
+void launch_pack_sources64(int layer, const EvalBufs& b, double scale, cudaStream_t st);
+void launch_pack_targets32(const EvalBufs& b, int64_t n_delta, double rho_T, double rho_c,
+                           cudaStream_t st);
+void launch_pack_targets64(const EvalBufs& b, int64_t n_delta, cudaStream_t st);
+int sort_grid_blocks(int64_t n);
+
+// launchers (sk_pair32.cu / sk_pair64.cu)
+void launch_pair32(int layer, const EvalBufs& b, double rho_T, cudaStream_t st);
+void launch_finish32(int layer, const EvalBufs& b, int64_t n_delta, double scale,
+                     double rho_T, cudaStream_t st);
+void launch_pair64(int layer, const EvalBufs& b, double scale, cudaStream_t st);
+void launch_finish64(const EvalBufs& b, cudaStream_t st);
+
+}  // namespace sk

@@ -1,0 +1,373 @@
+// sk_prep.cu -- preparation of one evaluation: spatial ordering and packing.
+//
+// Sources with nonzero weight and all targets are put in Morton (Z-curve)
+// order of their position so that a warp's 128 targets and a segment's 32
+// sources are compact in space; the near/far test of the pair kernels then
+// touches few segments. Zero-weight sources get the largest key and fall
+// behind the active ones, which compacts them away. The sort is a stable
+// least-significant-digit radix sort (4 passes of 8 bits), so the order --
+// and every result -- is deterministic.
+#include "sk_internal.h"
+
+#include <cfloat>
+
+namespace sk {
+
+namespace {
+
+constexpr int RS_THREADS = 256;
+constexpr int RS_ITEMS = 8;
+constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
+constexpr int BBOX_BLOCKS = 128;
+constexpr unsigned FULL = 0xffffffffu;
+
+// ---- bounding box of the (active) points -----------------------------------
+__global__ void k_bbox_partial(const double* __restrict__ xyz, const double* __restrict__ w,
+                               int64_t n, float* __restrict__ part) {
+  float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (w && w[i] == 0.0) continue;
+    for (int c = 0; c < 3; ++c) {
+      float v = (float)xyz[3 * i + c];
+      lo[c] = fminf(lo[c], v);
+      hi[c] = fmaxf(hi[c], v);
+    }
+  }
+  __shared__ float s[6][RS_THREADS];
+  for (int c = 0; c < 3; ++c) {
+    s[c][threadIdx.x] = lo[c];
+    s[3 + c][threadIdx.x] = hi[c];
+  }
+  __syncthreads();
+  for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+    if (threadIdx.x < k) {
+      for (int c = 0; c < 3; ++c) {
+        s[c][threadIdx.x] = fminf(s[c][threadIdx.x], s[c][threadIdx.x + k]);
+        s[3 + c][threadIdx.x] = fmaxf(s[3 + c][threadIdx.x], s[3 + c][threadIdx.x + k]);
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < 6) part[blockIdx.x * 6 + threadIdx.x] = s[threadIdx.x][0];
+}
+
+__global__ void k_bbox_final(const float* __restrict__ part, int nblk, float* __restrict__ bbox) {
+  int c = threadIdx.x;
+  if (c >= 6) return;
+  float v = c < 3 ? FLT_MAX : -FLT_MAX;
+  for (int b = 0; b < nblk; ++b) v = c < 3 ? fminf(v, part[b * 6 + c]) : fmaxf(v, part[b * 6 + c]);
+  bbox[c] = v;
+}
+
+// Spread the low 10 bits of v so that bit i lands at bit 3i.
+__device__ __forceinline__ uint32_t spread3(uint32_t v) {
+  v &= 0x3ffu;
+  v = (v | (v << 16)) & 0x030000ffu;
+  v = (v | (v << 8)) & 0x0300f00fu;
+  v = (v | (v << 4)) & 0x030c30c3u;
+  v = (v | (v << 2)) & 0x09249249u;
+  return v;
+}
+
+__global__ void k_morton_keys(const double* __restrict__ xyz, const double* __restrict__ w,
+                              int64_t n, const float* __restrict__ bbox,
+                              uint32_t* __restrict__ keys, int* __restrict__ vals,
+                              int* __restrict__ count) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  bool active = false;
+  if (i < n) {
+    active = !(w && w[i] == 0.0);
+    uint32_t key = 0xffffffffu;
+    if (active) {
+      float ext = fmaxf(fmaxf(bbox[3] - bbox[0], bbox[4] - bbox[1]), bbox[5] - bbox[2]);
+      float sc = ext > 0.f ? 1023.0f / ext : 0.f;
+      uint32_t q[3];
+      for (int c = 0; c < 3; ++c) {
+        float v = ((float)xyz[3 * i + c] - bbox[c]) * sc;
+        v = fminf(fmaxf(v, 0.f), 1023.f);
+        q[c] = (uint32_t)v;
+      }
+      key = spread3(q[0]) | (spread3(q[1]) << 1) | (spread3(q[2]) << 2);
+    }
+    keys[i] = key;
+    vals[i] = (int)i;
+  }
+  unsigned b = __ballot_sync(FULL, active);
+  if ((threadIdx.x & 31) == 0 && b) atomicAdd(count, __popc(b));
+}
+
+// ---- radix sort: histogram, scan, stable scatter ----------------------------
+__global__ void k_rs_hist(const uint32_t* __restrict__ keys, int n, int shift,
+                          uint32_t* __restrict__ hist) {
+  __shared__ uint32_t h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  int base = blockIdx.x * RS_TILE;
+  for (int r = 0; r < RS_ITEMS; ++r) {
+    int i = base + r * RS_THREADS + threadIdx.x;
+    if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
+  }
+  __syncthreads();
+  hist[threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];
+}
+
+// Exclusive scan of `total` counts, one block of 1024 threads.
+__global__ void k_rs_scan(uint32_t* __restrict__ a, int total) {
+  __shared__ uint32_t warp_sums[32];
+  __shared__ uint32_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int base = 0; base < total; base += 1024) {
+    int i = base + threadIdx.x;
+    uint32_t v = i < total ? a[i] : 0u;
+    uint32_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(FULL, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+      uint32_t s = warp_sums[lane];
+      for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(FULL, s, o);
+        if (lane >= o) s += y;
+      }
+      warp_sums[lane] = s;  // inclusive
+    }
+    __syncthreads();
+    uint32_t excl = carry + (wid > 0 ? warp_sums[wid - 1] : 0u) + x - v;
+    if (i < total) a[i] = excl;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry = excl + v;
+    __syncthreads();
+  }
+}
+
+__global__ void k_rs_scatter(const uint32_t* __restrict__ kin, const int* __restrict__ vin,
+                             uint32_t* __restrict__ kout, int* __restrict__ vout, int n, int shift,
+                             const uint32_t* __restrict__ offs) {
+  __shared__ uint32_t base_d[256];
+  __shared__ uint32_t wcnt[RS_THREADS / 32][256];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  base_d[tid] = offs[tid * gridDim.x + blockIdx.x];
+  const unsigned lt = (1u << lane) - 1u;
+  const int base = blockIdx.x * RS_TILE;
+  for (int r = 0; r < RS_ITEMS; ++r) {
+    for (int w = 0; w < RS_THREADS / 32; ++w) wcnt[w][tid] = 0;
+    __syncthreads();
+    int i = base + r * RS_THREADS + tid;
+    bool valid = i < n;
+    uint32_t key = valid ? kin[i] : 0u;
+    uint32_t dig = (key >> shift) & 255u;
+    unsigned peers = __match_any_sync(FULL, valid ? dig : (256u + lane));
+    unsigned rank = __popc(peers & lt);
+    if (valid && rank == 0) wcnt[wid][dig] = __popc(peers);
+    __syncthreads();
+    if (valid) {
+      uint32_t off = 0;
+      for (int w = 0; w < wid; ++w) off += wcnt[w][dig];
+      uint32_t pos = base_d[dig] + off + rank;
+      kout[pos] = key;
+      vout[pos] = vin[i];
+    }
+    __syncthreads();
+    uint32_t add = 0;
+    for (int w = 0; w < RS_THREADS / 32; ++w) add += wcnt[w][tid];
+    base_d[tid] += add;
+    __syncthreads();
+  }
+}
+
+// ---- packing ----------------------------------------------------------------
+__device__ __forceinline__ void warp_box(bool real, float x, float y, float z, float4* out) {
+  float lx = real ? x : FLT_MAX, ly = real ? y : FLT_MAX, lz = real ? z : FLT_MAX;
+  float hx = real ? x : -FLT_MAX, hy = real ? y : -FLT_MAX, hz = real ? z : -FLT_MAX;
+  for (int o = 16; o > 0; o >>= 1) {
+    lx = fminf(lx, __shfl_xor_sync(FULL, lx, o));
+    ly = fminf(ly, __shfl_xor_sync(FULL, ly, o));
+    lz = fminf(lz, __shfl_xor_sync(FULL, lz, o));
+    hx = fmaxf(hx, __shfl_xor_sync(FULL, hx, o));
+    hy = fmaxf(hy, __shfl_xor_sync(FULL, hy, o));
+    hz = fmaxf(hz, __shfl_xor_sync(FULL, hz, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    out[0] = make_float4(lx, ly, lz, 0.f);
+    out[1] = make_float4(hx, hy, hz, 0.f);
+  }
+}
+
+constexpr float PAD_POS = 1.0e15f;  // padding sources sit far away with zero density
+
+// FP32 packed layout (duplicated lanes for f32x2 arithmetic):
+//   single layer: {-x,-x,-y,-y} {-z,-z,gx,gx} {gy,gy,gz,gz},  g = w f scale
+//   double layer: {-x,-x,-y,-y} {-z,-z,qx,qx} {qy,qy,qz,qz} {nx,nx,ny,ny} {nz,nz,0,0},
+//                 q = w q_in scale
+template <int LAYER>
+__global__ void k_pack_src32(const double* __restrict__ xyz, const double* __restrict__ w,
+                             const double* __restrict__ dens, const double* __restrict__ nrm,
+                             const int* __restrict__ sorted, int* __restrict__ meta,
+                             int64_t N_pad, double scale, float4* __restrict__ srcF,
+                             int* __restrict__ src_orig, float4* __restrict__ segbox) {
+  constexpr int V = LAYER == LAYER_SL ? V_SL : V_DL;
+  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int Ns = meta[META_NS];
+  const int Ns_pad = (int)align_up((size_t)Ns, TILE);
+  if (s == 0) meta[META_NS_PAD] = Ns_pad;
+  if (s >= Ns_pad || s >= N_pad) return;  // whole warps leave together (multiples of 32)
+  const bool real = s < Ns;
+  float x = PAD_POS, y = PAD_POS, z = PAD_POS;
+  float d0 = 0.f, d1 = 0.f, d2 = 0.f, n0 = 0.f, n1 = 0.f, n2 = 0.f;
+  int j = -1;
+  if (real) {
+    j = sorted[s];
+    x = (float)xyz[3 * j];
+    y = (float)xyz[3 * j + 1];
+    z = (float)xyz[3 * j + 2];
+    const double ws = w[j] * scale;
+    d0 = (float)(ws * dens[3 * j]);
+    d1 = (float)(ws * dens[3 * j + 1]);
+    d2 = (float)(ws * dens[3 * j + 2]);
+    if (LAYER == LAYER_DL) {
+      n0 = (float)nrm[3 * j];
+      n1 = (float)nrm[3 * j + 1];
+      n2 = (float)nrm[3 * j + 2];
+    }
+  }
+  float4* o = srcF + s * V;
+  o[0] = make_float4(-x, -x, -y, -y);
+  o[1] = make_float4(-z, -z, d0, d0);
+  o[2] = make_float4(d1, d1, d2, d2);
+  if (LAYER == LAYER_DL) {
+    o[3] = make_float4(n0, n0, n1, n1);
+    o[4] = make_float4(n2, n2, 0.f, 0.f);
+  }
+  src_orig[s] = j;
+  warp_box(real, x, y, z, segbox + 2 * (s / SEG));
+}
+
+// FP64 packed layout: src64[2s] = (x, y, z, 0), src64[2s+1] = (g or q scaled, 0);
+// normals in nrm64[s]. Segment boxes are FP32 (the kernel adds a margin).
+template <int LAYER>
+__global__ void k_pack_src64(const double* __restrict__ xyz, const double* __restrict__ w,
+                             const double* __restrict__ dens, const double* __restrict__ nrm,
+                             const int* __restrict__ sorted, int* __restrict__ meta,
+                             int64_t N_pad, double scale, double4_32a* __restrict__ src64,
+                             double4_32a* __restrict__ nrm64, float4* __restrict__ segbox) {
+  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int Ns = meta[META_NS];
+  const int Ns_pad = (int)align_up((size_t)Ns, TILE64);
+  if (s == 0) meta[META_NS_PAD] = Ns_pad;
+  if (s >= Ns_pad || s >= N_pad) return;
+  const bool real = s < Ns;
+  double x = PAD_POS, y = PAD_POS, z = PAD_POS, d0 = 0, d1 = 0, d2 = 0;
+  double4_32a nn = make_double4_32a(0, 0, 0, 0);
+  if (real) {
+    const int j = sorted[s];
+    x = xyz[3 * j];
+    y = xyz[3 * j + 1];
+    z = xyz[3 * j + 2];
+    const double ws = w[j] * scale;
+    d0 = ws * dens[3 * j];
+    d1 = ws * dens[3 * j + 1];
+    d2 = ws * dens[3 * j + 2];
+    if (LAYER == LAYER_DL) nn = make_double4_32a(nrm[3 * j], nrm[3 * j + 1], nrm[3 * j + 2], 0.0);
+  }
+  src64[2 * s] = make_double4_32a(x, y, z, 0.0);
+  src64[2 * s + 1] = make_double4_32a(d0, d1, d2, 0.0);
+  if (LAYER == LAYER_DL) nrm64[s] = nn;
+  warp_box(real, (float)x, (float)y, (float)z, segbox + 2 * (s / SEG));
+}
+
+__global__ void k_pack_tgt32(const double* __restrict__ xyz, const double* __restrict__ delta,
+                             int64_t n_delta, const int* __restrict__ sorted, int64_t M,
+                             int64_t M_pad, double rho_T, double rho_c, float4* __restrict__ tgtF,
+                             double4_32a* __restrict__ tgt64, int* __restrict__ perm) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= M_pad) return;
+  const bool real = t < M;
+  const int j = sorted[real ? t : M - 1];
+  const double x = xyz[3 * j], y = xyz[3 * j + 1], z = xyz[3 * j + 2];
+  const double d = delta[n_delta == 1 ? 0 : j];
+  const double rc = rho_c * d, rt = rho_T * d;
+  tgtF[2 * t] = make_float4((float)x, (float)y, (float)z, (float)(1.0 / d));
+  tgtF[2 * t + 1] = real ? make_float4((float)(rc * rc), (float)(rt * rt), 0.f, 0.f)
+                         : make_float4(-1.f, -1.f, 0.f, 0.f);
+  tgt64[t] = make_double4_32a(x, y, z, d);
+  perm[t] = real ? j : -1;
+}
+
+__global__ void k_pack_tgt64(const double* __restrict__ xyz, const double* __restrict__ delta,
+                             int64_t n_delta, const int* __restrict__ sorted, int64_t M,
+                             int64_t M_pad, double4_32a* __restrict__ tgt64, int* __restrict__ perm) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= M_pad) return;
+  const bool real = t < M;
+  const int j = sorted[real ? t : M - 1];
+  const double d = delta[n_delta == 1 ? 0 : j];
+  // padding targets get a negative delta: the pair kernel skips them
+  tgt64[t] = make_double4_32a(xyz[3 * j], xyz[3 * j + 1], xyz[3 * j + 2], real ? d : -1.0);
+  perm[t] = real ? j : -1;
+}
+
+inline unsigned blocks_for(int64_t n, int tpb) { return (unsigned)((n + tpb - 1) / tpb); }
+
+}  // namespace
+
+int sort_grid_blocks(int64_t n) { return (int)((n + RS_TILE - 1) / RS_TILE); }
+
+void launch_sort_points(const double* xyz, const double* w, int64_t n, uint32_t* keys_a,
+                        uint32_t* keys_b, int* vals_a, int* vals_b, uint32_t* hist,
+                        float* bbox_part, float* bbox, int* count_out, int sort_blocks,
+                        cudaStream_t st) {
+  if (n <= 0) return;
+  k_bbox_partial<<<BBOX_BLOCKS, RS_THREADS, 0, st>>>(xyz, w, n, bbox_part);
+  k_bbox_final<<<1, 32, 0, st>>>(bbox_part, BBOX_BLOCKS, bbox);
+  k_morton_keys<<<blocks_for(n, 256), 256, 0, st>>>(xyz, w, n, bbox, keys_a, vals_a, count_out);
+  uint32_t *ka = keys_a, *kb = keys_b;
+  int *va = vals_a, *vb = vals_b;
+  for (int shift = 0; shift < 32; shift += 8) {
+    k_rs_hist<<<sort_blocks, RS_THREADS, 0, st>>>(ka, (int)n, shift, hist);
+    k_rs_scan<<<1, 1024, 0, st>>>(hist, 256 * sort_blocks);
+    k_rs_scatter<<<sort_blocks, RS_THREADS, 0, st>>>(ka, va, kb, vb, (int)n, shift, hist);
+    uint32_t* tk = ka; ka = kb; kb = tk;
+    int* tv = va; va = vb; vb = tv;
+  }
+  // four passes: the sorted data is back in keys_a / vals_a
+}
+
+void launch_pack_sources32(int layer, const EvalBufs& b, double scale, cudaStream_t st) {
+  unsigned g = blocks_for(b.N_pad, 256);
+  if (layer == LAYER_SL)
+    k_pack_src32<LAYER_SL><<<g, 256, 0, st>>>(b.src_xyz, b.src_w, b.dens, b.nrm, b.vals_a, b.meta,
+                                              b.N_pad, scale, b.srcF, b.src_orig, b.segbox);
+  else
+    k_pack_src32<LAYER_DL><<<g, 256, 0, st>>>(b.src_xyz, b.src_w, b.dens, b.nrm, b.vals_a, b.meta,
+                                              b.N_pad, scale, b.srcF, b.src_orig, b.segbox);
+}
+
+void launch_pack_sources64(int layer, const EvalBufs& b, double scale, cudaStream_t st) {
+  unsigned g = blocks_for(b.N_pad, 256);
+  if (layer == LAYER_SL)
+    k_pack_src64<LAYER_SL><<<g, 256, 0, st>>>(b.src_xyz, b.src_w, b.dens, b.nrm, b.vals_a, b.meta,
+                                              b.N_pad, scale, b.src64, b.nrm64, b.segbox);
+  else
+    k_pack_src64<LAYER_DL><<<g, 256, 0, st>>>(b.src_xyz, b.src_w, b.dens, b.nrm, b.vals_a, b.meta,
+                                              b.N_pad, scale, b.src64, b.nrm64, b.segbox);
+}
+
+void launch_pack_targets32(const EvalBufs& b, int64_t n_delta, double rho_T, double rho_c,
+                           cudaStream_t st) {
+  k_pack_tgt32<<<blocks_for(b.M_pad, 256), 256, 0, st>>>(b.tgt_xyz, b.delta, n_delta, b.vals_a,
+                                                         b.M, b.M_pad, rho_T, rho_c, b.tgtF,
+                                                         b.tgt64, b.tgt_perm);
+}
+
+void launch_pack_targets64(const EvalBufs& b, int64_t n_delta, cudaStream_t st) {
+  k_pack_tgt64<<<blocks_for(b.M_pad, 256), 256, 0, st>>>(b.tgt_xyz, b.delta, n_delta, b.vals_a,
+                                                         b.M, b.M_pad, b.tgt64, b.tgt_perm);
+}
+
+}  // namespace sk

@@ -1,0 +1,64 @@
+"""The C-ABI library builds, loads and exports every declared symbol (no GPU)."""
+
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+import paper_2310_13908_gb300 as sk
+from paper_2310_13908_gb300 import _build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b([a-z_][a-z0-9_]*)\s*\(",
+                             text, flags=re.M):
+            name = m.group(1)
+            if name not in ("if", "for", "while", "return", "sizeof", "defined"):
+                names.add(name)
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return sk.load()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("sk_create", "sk_destroy", "sk_last_error", "stokes_sl_eval",
+                     "stokes_dl_eval"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_version_and_null_context_rejections(lib):
+    assert sk.sk_version() == 100
+    # argument checks that return before any CUDA call
+    assert lib.stokes_sl_eval(None, 1, 0, 0, None, None, None, 1, None, None, 1, 1.0, None,
+                              None) == sk.SK_EINVAL
+    assert lib.sk_create(None, 0, 0) == sk.SK_EINVAL
+    assert lib.sk_set_fp32c_thresholds(None, 0.5, 5.0) == sk.SK_EINVAL
+
+
+def test_library_fails_loudly_when_missing(monkeypatch, tmp_path):
+    monkeypatch.setattr(sk, "_lib", None)
+    monkeypatch.setattr(sk, "LIB_PATH", str(tmp_path / "libstokesreg.so"))
+    with pytest.raises(RuntimeError, match="build the CUDA library"):
+        sk.load()
+
+
+def test_build_flags_target_sm103a():
+    assert "arch=compute_103a,code=sm_103a" in _build.ARCH

@@ -1,0 +1,276 @@
+"""CUDA path vs the FP64 oracle, through the C ABI (needs a GB300).
+
+Tolerances (relative L2 over all targets x 3 components, the error measure of
+the benchmark): SK_FP64 <= 1e-12, SK_FP32C <= 1e-6. Element-wise, every
+component must also be within ATOL_FP32 * max|u| (FP32C) resp. 1e-12 * max|u|
+(FP64).
+"""
+
+import numpy as np
+import pytest
+
+import capsule_inputs as ci
+import oracle
+
+sk = pytest.importorskip("paper_2310_13908_gb300")
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+TOL = {sk.SK_FP64: 1e-12, sk.SK_FP32C: 1e-6}
+ELEM = {sk.SK_FP64: 1e-12, sk.SK_FP32C: 1e-5}
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def assert_close(u, ref, prec):
+    assert np.all(np.isfinite(u))
+    e = rel_l2(u, ref)
+    assert e <= TOL[prec], f"rel-L2 {e:.3e} > {TOL[prec]:.0e}"
+    scale = max(np.abs(ref).max(), 1e-300)
+    emax = np.abs(u - ref).max() / scale
+    assert emax <= ELEM[prec], f"max element error {emax:.3e} (of max|u|)"
+    return e
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = sk.Context(0)
+    yield c.handle
+    c.close()
+
+
+def to_dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda")
+
+
+PRECS = [sk.SK_FP64, sk.SK_FP32C]
+PREC_ID = {sk.SK_FP64: "fp64", sk.SK_FP32C: "fp32c"}
+
+
+@pytest.fixture(scope="module")
+def sphere():
+    w = ci.sphere_noise_workload()
+    s = w.surface
+    ref = oracle.sl(s.X, s.w, w.f, w.targets, w.delta, w.mu)
+    return w, ref
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=PREC_ID.get)
+@pytest.mark.parametrize("mem", [sk.SK_HOST, sk.SK_DEVICE], ids=["host", "device"])
+def test_sl_sphere_noise(ctx, sphere, prec, mem):
+    w, ref = sphere
+    s = w.surface
+    if mem == sk.SK_HOST:
+        u = sk.stokes_sl_eval(ctx, prec, mem, s.X, s.w, w.f, w.targets, w.delta, w.mu)
+    else:
+        u = sk.stokes_sl_eval(ctx, prec, mem, to_dev(s.X), to_dev(s.w), to_dev(w.f),
+                              to_dev(w.targets), to_dev(w.delta), w.mu).cpu().numpy()
+    assert_close(u, ref, prec)
+    st = sk.sk_last_eval_stats(ctx)
+    assert st["n_src_active"] == s.n_active and st["n_tgt"] == s.N
+
+
+@pytest.fixture(scope="module")
+def rbc():
+    w = ci.rbc_workload()
+    s = w.surface
+    ref_sl = oracle.sl(s.X, s.w, w.f, w.targets, w.delta, w.mu)
+    ref_dl = oracle.dl(s.X, s.w, s.n, w.q, w.targets, w.delta)
+    return w, ref_sl, ref_dl
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=PREC_ID.get)
+def test_sl_rbc(ctx, rbc, prec):
+    w, ref, _ = rbc
+    s = w.surface
+    u = sk.stokes_sl_eval(ctx, prec, sk.SK_HOST, s.X, s.w, w.f, w.targets, w.delta, w.mu)
+    assert_close(u, ref, prec)
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=PREC_ID.get)
+def test_dl_rbc(ctx, rbc, prec):
+    w, _, ref = rbc
+    s = w.surface
+    u = sk.stokes_dl_eval(ctx, prec, sk.SK_HOST, s.X, s.w, s.n, w.q, w.targets, w.delta)
+    assert_close(u, ref, prec)
+
+
+@pytest.fixture(scope="module")
+def ellipsoid_full():
+    # full-size workload: 393,216 nodes + 100,000 exterior probes, delta = 2h
+    return ci.ellipsoid_hires_workload()
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=PREC_ID.get)
+def test_sl_ellipsoid_full_size_sampled(ctx, ellipsoid_full, prec):
+    w = ellipsoid_full
+    s = w.surface
+    u = sk.stokes_sl_eval(ctx, prec, sk.SK_DEVICE, to_dev(s.X), to_dev(s.w), to_dev(w.f),
+                          to_dev(w.targets), to_dev(w.delta), w.mu).cpu().numpy()
+    rng = np.random.default_rng(77)
+    M = w.targets.shape[0]
+    idx = np.concatenate([rng.choice(w.n_on_surface, 384, replace=False),
+                          w.n_on_surface + rng.choice(M - w.n_on_surface, 128, replace=False)])
+    ref = oracle.sl(s.X, s.w, w.f, w.targets[idx], w.delta, w.mu)
+    assert_close(u[idx], ref, prec)
+    assert np.all(np.isfinite(u))
+
+
+def test_dl_ellipsoid_sampled_with_probes(ctx):
+    w = ci.ellipsoid_hires_workload(m=129, n_probes=20000, seed=3100)
+    s = w.surface
+    q = ci.sh_density(s.x0, np.random.default_rng(5), lmax=8)
+    u = sk.stokes_dl_eval(ctx, sk.SK_FP32C, sk.SK_HOST, s.X, s.w, s.n, q, w.targets, w.delta)
+    idx = np.random.default_rng(6).choice(w.targets.shape[0], 512, replace=False)
+    ref = oracle.dl(s.X, s.w, s.n, q, w.targets[idx], w.delta)
+    assert_close(u[idx], ref, sk.SK_FP32C)
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=PREC_ID.get)
+def test_ragged_sizes_and_per_target_delta(ctx, prec):
+    rng = np.random.default_rng(9)
+    s = ci.make_surface(ci.Ellipsoid(1.0, 0.7, 0.6), 21)
+    f = rng.standard_normal((s.N, 3))
+    for n_src, n_tgt in ((1, 1), (7, 33), (257, 1), (300, 1025), (s.N, 1023), (s.N, 2049)):
+        src = rng.choice(s.N, n_src, replace=False)
+        Y = np.concatenate([s.X, s.X + 0.03 * s.n])[rng.choice(2 * s.N, n_tgt, replace=False)]
+        delta = rng.uniform(0.5, 3.0, n_tgt) * s.h
+        u = sk.stokes_sl_eval(ctx, prec, sk.SK_HOST, s.X[src], s.w[src], f[src], Y, delta, 1.3)
+        ref = oracle.sl(s.X[src], s.w[src], f[src], Y, delta, 1.3)
+        if np.abs(ref).max() == 0:
+            assert np.all(u == 0)
+        else:
+            assert_close(u, ref, prec)
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=PREC_ID.get)
+def test_empty_and_degenerate_inputs(ctx, prec):
+    Y = np.array([[0.1, 0.2, 0.3], [1.0, 0.0, 0.0]])
+    # no targets: a no-op
+    out = sk.stokes_sl_eval(ctx, prec, sk.SK_HOST, np.zeros((3, 3)), np.ones(3), np.ones((3, 3)),
+                            np.zeros((0, 3)), 0.1)
+    assert out.shape == (0, 3)
+    # no sources, and only zero-weight sources: exactly zero
+    u = sk.stokes_sl_eval(ctx, prec, sk.SK_HOST, np.zeros((0, 3)), np.zeros(0), np.zeros((0, 3)),
+                          Y, 0.1)
+    assert np.all(u == 0)
+    u = sk.stokes_sl_eval(ctx, prec, sk.SK_HOST, np.random.rand(50, 3), np.zeros(50),
+                          np.random.rand(50, 3), Y, 0.1)
+    assert np.all(u == 0)
+    # a target on a node: the r = 0 limit of Sec. 3.4
+    delta, mu = 0.2, 1.5
+    u = sk.stokes_sl_eval(ctx, prec, sk.SK_HOST, [[1.0, 2.0, 3.0]], [0.7], [[0.3, -1.2, 2.0]],
+                          [[1.0, 2.0, 3.0]], delta, mu)
+    lim = 16.0 / (3.0 * delta * np.sqrt(np.pi))
+    ref = 0.7 * np.array([0.3, -1.2, 2.0]) * lim / (8 * np.pi * mu)
+    assert np.allclose(u[0], ref, rtol=1e-13 if prec == sk.SK_FP64 else 1e-12)
+    # double layer self term is zero
+    u = sk.stokes_dl_eval(ctx, prec, sk.SK_HOST, [[1.0, 1.0, 1.0]], [1.0], [[0.0, 0.0, 1.0]],
+                          [[1.0, 2.0, 3.0]], [[1.0, 1.0, 1.0]], 0.2)
+    assert np.all(u == 0)
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=PREC_ID.get)
+def test_coincident_nodes_even_m(ctx, prec):
+    s = ci.make_surface(ci.Sphere(1.0), 16)  # nodes of different patches coincide
+    f = np.random.default_rng(2).standard_normal((s.N, 3))
+    u = sk.stokes_sl_eval(ctx, prec, sk.SK_HOST, s.X, s.w, f, s.X, 2 * s.h)
+    assert_close(u, oracle.sl(s.X, s.w, f, s.X, 2 * s.h), prec)
+
+
+def test_validation_errors(ctx):
+    X = np.zeros((2, 3))
+    with pytest.raises(sk.SkError) as e:
+        sk.stokes_sl_eval(ctx, sk.SK_FP32C, sk.SK_HOST, X, np.ones(2), X, X, 0.0)
+    assert e.value.code == sk.SK_EINVAL
+    with pytest.raises(sk.SkError) as e:
+        sk.stokes_sl_eval(ctx, sk.SK_FP32C, sk.SK_HOST, X, np.ones(2), X, X, 0.1, mu=-1.0)
+    assert e.value.code == sk.SK_EINVAL
+    with pytest.raises(sk.SkError) as e:
+        sk.stokes_sl_eval(ctx, 7, sk.SK_HOST, X, np.ones(2), X, X, 0.1)
+    assert e.value.code == sk.SK_EINVAL
+    with pytest.raises(sk.SkError) as e:
+        sk.stokes_sl_eval(ctx, sk.SK_FP32C, sk.SK_HOST, X, np.ones(2), X, np.zeros((3, 3)),
+                          [0.1, 0.2])
+    assert e.value.code == sk.SK_EINVAL
+    # a non-positive delta in device memory is detected on the device
+    with pytest.raises(sk.SkError) as e:
+        sk.stokes_sl_eval(ctx, sk.SK_FP32C, sk.SK_DEVICE, to_dev(X), to_dev(np.ones(2)),
+                          to_dev(X), to_dev(X + 1), to_dev([0.1, -0.2]))
+    assert e.value.code == sk.SK_EINVAL
+    # the context is still usable afterwards
+    u = sk.stokes_sl_eval(ctx, sk.SK_FP32C, sk.SK_HOST, X + [[0, 0, 1], [0, 0, 0]], np.ones(2),
+                          X + 1, X + 3, 0.1)
+    assert np.all(np.isfinite(u))
+
+
+def test_near_list_overflow_rescan(ctx):
+    """rho_T = 2 at delta = 3h puts ~300 pairs per target below rho_T: every
+    list overflows and the exact FP32-classified rescan takes over."""
+    s = ci.make_surface(ci.Sphere(1.0), 33)
+    f = np.random.default_rng(4).standard_normal((s.N, 3))
+    try:
+        sk.sk_set_fp32c_thresholds(ctx, 2.0, 5.0)
+        u = sk.stokes_sl_eval(ctx, sk.SK_FP32C, sk.SK_HOST, s.X, s.w, f, s.X, 3 * s.h)
+        st = sk.sk_last_eval_stats(ctx)
+    finally:
+        sk.sk_set_fp32c_thresholds(ctx, 0.5, 5.0)
+    assert st["overflow_targets"] > 0
+    assert_close(u, oracle.sl(s.X, s.w, f, s.X, 3 * s.h), sk.SK_FP32C)
+
+
+@pytest.mark.parametrize("rho_T,rho_c", [(0.25, 5.0), (1.0, 5.0), (0.5, 4.5), (0.5, 6.0)])
+def test_fp32c_threshold_variants(ctx, rbc, rho_T, rho_c):
+    w, ref, _ = rbc
+    s = w.surface
+    try:
+        sk.sk_set_fp32c_thresholds(ctx, rho_T, rho_c)
+        u = sk.stokes_sl_eval(ctx, sk.SK_FP32C, sk.SK_HOST, s.X, s.w, w.f, w.targets, w.delta)
+    finally:
+        sk.sk_set_fp32c_thresholds(ctx, 0.5, 5.0)
+    assert_close(u, ref, sk.SK_FP32C)
+
+
+def test_deterministic_and_independent_of_target_order(ctx, rbc):
+    w, _, _ = rbc
+    s = w.surface
+    args = (s.X, s.w, w.f)
+    u1 = sk.stokes_sl_eval(ctx, sk.SK_FP32C, sk.SK_HOST, *args, w.targets, w.delta)
+    u2 = sk.stokes_sl_eval(ctx, sk.SK_FP32C, sk.SK_HOST, *args, w.targets, w.delta)
+    assert np.array_equal(u1, u2)
+    perm = np.random.default_rng(1).permutation(w.targets.shape[0])
+    u3 = sk.stokes_sl_eval(ctx, sk.SK_FP32C, sk.SK_HOST, *args, w.targets[perm], w.delta)
+    assert np.array_equal(u3, u1[perm])
+    # a subset of the targets gives bit-identical values
+    sub = perm[:1000]
+    u4 = sk.stokes_sl_eval(ctx, sk.SK_FP32C, sk.SK_HOST, *args, w.targets[sub], w.delta)
+    assert np.array_equal(u4, u1[sub])
+
+
+def test_async_stream_device_memory(ctx, rbc):
+    w, ref, _ = rbc
+    s = w.surface
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        X, W, F, Y, D = (to_dev(a) for a in (s.X, s.w, w.f, w.targets, w.delta))
+        out = torch.empty((Y.shape[0], 3), dtype=torch.float64, device="cuda")
+    sk.stokes_sl_eval(ctx, sk.SK_FP32C, sk.SK_DEVICE, X, W, F, Y, D, 1.0, u_out=out, stream=st)
+    st.synchronize()
+    assert_close(out.cpu().numpy(), ref, sk.SK_FP32C)
+
+
+def test_stats_near_pairs_match_independent_count(ctx, rbc):
+    from scipy.spatial import cKDTree
+    w, _, _ = rbc
+    s = w.surface
+    sk.stokes_sl_eval(ctx, sk.SK_FP32C, sk.SK_HOST, s.X, s.w, w.f, w.targets, w.delta)
+    st = sk.sk_last_eval_stats(ctx)
+    act = s.w != 0
+    n = cKDTree(s.X[act]).query_ball_point(w.targets, r=0.5 * w.delta[0], return_length=True)
+    assert abs(st["near_pairs"] - n.sum()) <= 1e-3 * n.sum()
+    assert st["overflow_targets"] == 0
