@@ -137,6 +137,44 @@ int stokes_dl_eval(sk_ctx* ctx, int precision, int mem,
                    const double* delta, int64_t n_delta,
                    double* u_out, void* cuda_stream);
 
+/* Single layer without any memory allocation (the paper has no counterpart:
+ * this is a service for callers that cannot allocate).
+ *
+ * Who needs it: code that runs under a fixed device-memory budget owned by
+ * a framework allocator, where a library's own cudaMalloc could fail or
+ * fragment the pool; latency-critical loops, where cudaMalloc/cudaFree
+ * would stall the device; and callers that cannot keep an sk_ctx. This
+ * call creates no context or stream and calls no cudaMalloc, cudaFree or
+ * other allocating routine.
+ *
+ * It computes exactly what stokes_sl_eval(ctx, SK_FP32C, SK_DEVICE, ...)
+ * computes, with the default thresholds rho_T = 0.5, rho_c = 5, on the
+ * calling thread's current CUDA device. All arrays are device pointers on
+ * that device, with the layout of stokes_sl_eval; the caller owns them.
+ *
+ * Scratch: one static device array of 32 MiB inside the library, shared by
+ * every call on a device. A GPU that loads the library's code holds it until
+ * the process exits. Problems whose scratch does not fit -- roughly beyond
+ * 40,000 targets with 40,000 nodes -- are rejected with SK_EINVAL before any
+ * work is enqueued. The array keeps the last call's contents; each call
+ * clears what has to start at zero. Calls that overlap on the GPU (on
+ * different streams, or from different host threads) race on the array and
+ * corrupt each other's results: serialize them.
+ *
+ * Set-up: the first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and caches it; make that first call before any
+ * stream capture on that device.
+ *
+ * cuda_stream NULL: the call runs on the legacy default stream, waits for
+ * completion and reports a device-side failure (SK_ETIMEOUT, SK_EINVAL for a
+ * non-positive delta). Otherwise it is enqueued on that stream and returns
+ * at once; device-side failures are then not reported.
+ * Errors: SK_EINVAL (bad argument or too large), SK_ECUDA, SK_ETIMEOUT. */
+int stokes_sl_eval_noalloc(int64_t n_src, const double* src_xyz, const double* src_w,
+                           const double* f, int64_t n_tgt, const double* tgt_xyz,
+                           const double* delta, int64_t n_delta, double mu, double* u_out,
+                           void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -76,7 +76,9 @@ def _declare(lib):
             getattr(lib, name).restype = args[1]
 
 
-_EXTRA_DECLS: dict = {}
+_EXTRA_DECLS: dict = {
+    "stokes_sl_eval_noalloc": ([_i64, _vp, _vp, _vp, _i64, _vp, _vp, _i64, _dbl, _vp, _vp], _int),
+}
 
 
 def load():
@@ -236,6 +238,33 @@ def stokes_dl_eval(ctx, precision: int, mem: int, src_xyz, src_w, src_n, q, tgt_
     _check(ctx, code)
     if mem == SK_HOST and U is not u_out:
         np.copyto(u_out, U.reshape(np.shape(u_out)))
+    return u_out
+
+
+def stokes_sl_eval_noalloc(src_xyz, src_w, f, tgt_xyz, delta, mu: float = 1.0, u_out=None,
+                           stream=None):
+    """Single layer (SK_FP32C) that allocates nothing inside the library.
+
+    All arrays are CUDA float64 torch tensors on the current device; the
+    library works in its own static 32 MiB device scratch array, so larger
+    problems are rejected (SkError SK_EINVAL). Calls that overlap on the GPU
+    share that array and must be serialized. Returns u_out (M, 3).
+    """
+    lib = load()
+    X, n = _ptr(src_xyz, SK_DEVICE, (3,), "src_xyz")
+    W, nw = _ptr(src_w, SK_DEVICE, (), "src_w")
+    F, nf = _ptr(f, SK_DEVICE, (3,), "f")
+    Y, M = _ptr(tgt_xyz, SK_DEVICE, (3,), "tgt_xyz")
+    D, nd = _ptr(delta, SK_DEVICE, (), "delta")
+    if not (n == nw == nf):
+        raise ValueError("src_xyz, src_w and f must have the same number of nodes")
+    if u_out is None:
+        u_out = _alloc_out(tgt_xyz, SK_DEVICE, M)
+    U, _ = _ptr(u_out, SK_DEVICE, (3,), "u_out")
+    code = lib.stokes_sl_eval_noalloc(n, X, W, F, M, Y, D, nd, float(mu), U,
+                                      _stream_handle(stream))
+    if code != SK_OK:
+        raise SkError(code, "stokes_sl_eval_noalloc failed")
     return u_out
 
 
