@@ -58,6 +58,7 @@ void carve_eval_buffers(Bump& bp, const EvalShape& s, EvalBufs& b) {
   b.N_pad = (int64_t)align_up((size_t)s.N, TILE);
   b.M_pad = (int64_t)align_up((size_t)s.M, fp32 ? TGT_CTA32 : TGT_CTA64);
   b.n_chunks = s.n_chunks;
+  b.pair_np = pair32_np(s.M);
   const int64_t nsort = s.N > s.M ? s.N : s.M;
   b.sort_blocks = sort_grid_blocks(nsort > 0 ? nsort : 1);
   if (s.copy_inputs) {
@@ -98,18 +99,31 @@ void carve_eval_buffers(Bump& bp, const EvalShape& s, EvalBufs& b) {
 }
 
 int choose_chunks(int precision, int64_t N, int64_t M, int sm_count) {
-  const int64_t tgt_cta = precision == SK_FP32C ? TGT_CTA32 : TGT_CTA64;
-  const int64_t tile = precision == SK_FP32C ? TILE : TILE64;
+  // Split the source sum into chunks so that the grid (target blocks x
+  // chunks) fills whole waves of resident CTAs: a partial last wave idles SMs.
+  const bool fp32 = precision == SK_FP32C;
+  const int np = pair32_np(M);
+  const int64_t tgt_cta = fp32 ? (int64_t)TPB32 * 2 * np : TGT_CTA64;
+  const int64_t tile = fp32 ? TILE : TILE64;
+  const int64_t slots = (int64_t)sm_count * (fp32 ? pair32_ctas_per_sm(np) : 2);
   const int64_t n_tb = (int64_t)align_up((size_t)(M > 0 ? M : 1), tgt_cta) / tgt_cta;
   const int64_t tiles = (int64_t)align_up((size_t)(N > 0 ? N : 1), tile) / tile;
-  const int64_t want = (int64_t)sm_count * 2 * 8;  // about eight waves of two CTAs per SM
-  int64_t nc = (want + n_tb - 1) / n_tb;
   int64_t cap = tiles / 2;
   if (cap < 1) cap = 1;
-  if (nc > cap) nc = cap;
-  if (nc > 64) nc = 64;
-  if (nc < 1) nc = 1;
-  return (int)nc;
+  if (cap > 64) cap = 64;
+  int best = (int)cap;
+  double best_eff = -1.0;
+  for (int64_t nc = 1; nc <= cap; ++nc) {
+    const int64_t grid = n_tb * nc;
+    if (grid < 4 * slots && nc < cap) continue;  // at least four waves when possible
+    const double waves = (double)grid / (double)slots;
+    const double eff = waves / std::ceil(waves);
+    if (eff > best_eff + 1e-3) {
+      best_eff = eff;
+      best = (int)nc;
+    }
+  }
+  return best;
 }
 
 __global__ void k_check_delta(const double* __restrict__ d, int64_t n,

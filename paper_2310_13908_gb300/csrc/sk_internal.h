@@ -105,8 +105,16 @@ struct EvalBufs {
   // sizes
   int64_t N = 0, M = 0, N_pad = 0, M_pad = 0;
   int n_chunks = 1;
+  int pair_np = 2;  // FP32 pair kernel: f32x2 target pairs per lane (1 or 2)
   int sort_blocks = 0;
 };
+
+// FP32 pair kernel configuration: two f32x2 target pairs per lane at two
+// CTAs per SM for large target counts, one pair per lane at three CTAs per SM
+// (more warps, smaller target blocks) otherwise.
+constexpr int64_t PAIR32_NP1_MAX_TARGETS = 131072;
+inline int pair32_np(int64_t M) { return M > PAIR32_NP1_MAX_TARGETS ? 2 : 1; }
+inline int pair32_ctas_per_sm(int np) { return np == 2 ? 2 : 3; }
 
 }  // namespace sk
 

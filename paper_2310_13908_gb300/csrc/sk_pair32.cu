@@ -24,10 +24,16 @@
 #include "sk_internal.h"
 #include "sk_series.cuh"
 
+// unroll factor of the far loop over the 32 sources of a segment
+#ifndef SK_FAR_UNROLL
+#define SK_FAR_UNROLL 8
+#endif
+
 namespace sk {
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
+constexpr int kFarUnroll = SK_FAR_UNROLL;
 
 __device__ __forceinline__ float rsq(float x) {
   float y;
@@ -98,6 +104,7 @@ __device__ __forceinline__ void near_append(int64_t t, int jo, int* __restrict__
 // targets of a pair are computed by the caller.
 struct SLayer {
   static constexpr int V = V_SL;
+  static constexpr int STAGES = 4;
   struct Src {
     float2 nx, ny, nz, gx, gy, gz;
   };
@@ -138,6 +145,7 @@ struct SLayer {
 
 struct DLayer {
   static constexpr int V = V_DL;
+  static constexpr int STAGES = 3;
   struct Src {
     float2 nx, ny, nz, qx, qy, qz, mx, my, mz;  // m: surface normal
   };
@@ -241,17 +249,25 @@ __device__ __forceinline__ void two_sum_merge(float2* U, float2* HI, float2* LO)
   }
 }
 
-template <class L>
-__global__ void __launch_bounds__(TPB32, 2)
+template <class L, int NP, int MINB>
+__global__ void __launch_bounds__(TPB32, MINB)
     k_pair32(const float4* __restrict__ srcF, const float4* __restrict__ segbox,
              const int* __restrict__ src_orig, const int* __restrict__ meta,
              const float4* __restrict__ tgtF, int64_t M_pad, int n_chunks,
              double* __restrict__ part, int* __restrict__ near_cnt, int* __restrict__ near_idx,
              unsigned long long* __restrict__ flags, float rho_lo, float rho_hi) {
   constexpr int V = L::V;
+  constexpr int STAGES = L::STAGES;
+  constexpr int WARPS = TPB32 / 32;
   constexpr uint32_t TILE_BYTES = TILE * V * sizeof(float4);
   extern __shared__ __align__(128) float4 sm[];
-  __shared__ __align__(8) uint64_t mbar[2];
+  // full[b]: the bulk copy of stage b landed (transaction count);
+  // rel[b]: warps that released stage b so far (monotonic);
+  // issued[b]: copies issued into stage b (for the drain after a timeout).
+  __shared__ __align__(8) uint64_t full[STAGES];
+  __shared__ int rel[STAGES];
+  __shared__ int issued[STAGES];
+  __shared__ int timed_out;
 
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int tb = blockIdx.x / n_chunks, ch = blockIdx.x % n_chunks;
@@ -260,18 +276,16 @@ __global__ void __launch_bounds__(TPB32, 2)
   const int k1 = (int)((long long)(ch + 1) * n_tiles / n_chunks);
 
   // ---- targets of this lane: pair p holds targets (base + 64p + lane, base + 64p + 32 + lane)
-  const int64_t wbase = (int64_t)tb * TGT_CTA32 + wid * TGT_WARP32;
-  Tgt2 T[2];
-  int64_t tix[2][2];
+  const int64_t wbase = (int64_t)tb * (TPB32 * 2 * NP) + wid * (64 * NP) + lane;
+  Tgt2 T[NP];
   float blo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, bhi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
   float rc2max = -1.f;
 #pragma unroll
-  for (int p = 0; p < 2; ++p) {
+  for (int p = 0; p < NP; ++p) {
     float4 a[2], b[2];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      const int64_t t = wbase + 64 * p + 32 * h + lane;
-      tix[p][h] = t;
+      const int64_t t = wbase + 64 * p + 32 * h;
       a[h] = tgtF[2 * t];
       b[h] = tgtF[2 * t + 1];
       if (b[h].x >= 0.f) {
@@ -300,35 +314,37 @@ __global__ void __launch_bounds__(TPB32, 2)
   const bool warp_live = rc2max >= 0.f;
   const float rc2test = rc2max * 1.0001f;
 
-  float2 U[2][3], HI[2][3], LO[2][3];
+  float2 U[NP][3], HI[NP][3], LO[NP][3];
 #pragma unroll
-  for (int p = 0; p < 2; ++p)
+  for (int p = 0; p < NP; ++p)
 #pragma unroll
     for (int c = 0; c < 3; ++c) U[p][c] = HI[p][c] = LO[p][c] = make_float2(0.f, 0.f);
 
-  // ---- tile pipeline
+  // ---- source pipeline: no CTA-wide barrier inside the loop; the last warp
+  // to release a stage issues the next bulk copy into it.
   if (tid == 0) {
-    mbar_init(&mbar[0]);
-    mbar_init(&mbar[1]);
+    for (int b = 0; b < STAGES; ++b) {
+      mbar_init(&full[b]);
+      rel[b] = 0;
+      issued[b] = 0;
+    }
+    timed_out = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  int issued[2] = {0, 0};
   if (tid == 0) {
-    for (int b = 0; b < 2; ++b)
+    for (int b = 0; b < STAGES; ++b)
       if (k0 + b < k1) {
-        bulk_load(sm + b * TILE * V, srcF + (size_t)(k0 + b) * TILE * V, TILE_BYTES, &mbar[b]);
-        issued[b]++;
+        bulk_load(sm + b * TILE * V, srcF + (size_t)(k0 + b) * TILE * V, TILE_BYTES, &full[b]);
+        issued[b] = 1;
       }
   }
-  int consumed[2] = {0, 0};
-  bool timed_out = false;
   for (int k = k0, it = 0; k < k1; ++k, ++it) {
-    const int buf = it & 1;
-    const bool ok = mbar_wait_bounded(&mbar[buf], (uint32_t)(consumed[buf] & 1));
-    consumed[buf]++;
-    if (__syncthreads_or(!ok)) {
-      timed_out = true;
+    const int buf = it % STAGES;
+    const int use = it / STAGES;
+    const bool ok = __all_sync(FULL, mbar_wait_bounded(&full[buf], (uint32_t)(use & 1)));
+    if (!ok) {
+      if (lane == 0) atomicExch(&timed_out, 1);
       break;
     }
     if (warp_live) {
@@ -347,11 +363,11 @@ __global__ void __launch_bounds__(TPB32, 2)
       for (int s = 0; s < TILE_SEGS; ++s) {
         const float4* SS = S + s * SEG * V;
         if (!((nm >> s) & 1u)) {
-#pragma unroll 4
+#pragma unroll kFarUnroll
           for (int j = 0; j < SEG; ++j) {
             const typename L::Src src = L::load(SS + j * V);
 #pragma unroll
-            for (int p = 0; p < 2; ++p) {
+            for (int p = 0; p < NP; ++p) {
               float2 dx, dy, dz, r2;
               pair_d(T[p], src.nx, src.ny, src.nz, dx, dy, dz, r2);
               L::far(src, dx, dy, dz, r2, U[p]);
@@ -362,54 +378,60 @@ __global__ void __launch_bounds__(TPB32, 2)
 #pragma unroll 1
           for (int j = 0; j < SEG; ++j) {
             const typename L::Src src = L::load(SS + j * V);
-            float2 dx[2], dy[2], dz[2], r2[2];
+            float2 dx[NP], dy[NP], dz[NP], r2[NP];
             bool any = false;
 #pragma unroll
-            for (int p = 0; p < 2; ++p) {
+            for (int p = 0; p < NP; ++p) {
               pair_d(T[p], src.nx, src.ny, src.nz, dx[p], dy[p], dz[p], r2[p]);
               any |= (r2[p].x < T[p].rc2.x) | (r2[p].y < T[p].rc2.y);
             }
             if (__any_sync(FULL, any)) {
 #pragma unroll
-              for (int p = 0; p < 2; ++p)
-                pair_general<L>(src, T[p], dx[p], dy[p], dz[p], r2[p], U[p], tix[p][0], tix[p][1],
-                                orig + j, near_cnt, near_idx, flags, rho_lo, rho_hi);
+              for (int p = 0; p < NP; ++p)
+                pair_general<L>(src, T[p], dx[p], dy[p], dz[p], r2[p], U[p], wbase + 64 * p,
+                                wbase + 64 * p + 32, orig + j, near_cnt, near_idx, flags, rho_lo,
+                                rho_hi);
             } else {
 #pragma unroll
-              for (int p = 0; p < 2; ++p) L::far(src, dx[p], dy[p], dz[p], r2[p], U[p]);
+              for (int p = 0; p < NP; ++p) L::far(src, dx[p], dy[p], dz[p], r2[p], U[p]);
             }
           }
         }
         if ((s & 3) == 3) {
-          two_sum_merge(U[0], HI[0], LO[0]);
-          two_sum_merge(U[1], HI[1], LO[1]);
+#pragma unroll
+          for (int p = 0; p < NP; ++p) two_sum_merge(U[p], HI[p], LO[p]);
         }
       }
     }
-    __syncthreads();  // every warp is done with this buffer
-    if (tid == 0 && k + 2 < k1) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      bulk_load(sm + buf * TILE * V, srcF + (size_t)(k + 2) * TILE * V, TILE_BYTES, &mbar[buf]);
-      issued[buf]++;
+    // release the stage; the last of the WARPS releases refills it
+    __syncwarp();
+    if (lane == 0) {
+      __threadfence_block();
+      const int prev = atomicAdd(&rel[buf], 1);
+      if (prev == (use + 1) * WARPS - 1 && k + STAGES < k1) {
+        __threadfence_block();
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        bulk_load(sm + buf * TILE * V, srcF + (size_t)(k + STAGES) * TILE * V, TILE_BYTES,
+                  &full[buf]);
+        atomicAdd(&issued[buf], 1);
+      }
     }
   }
+  __syncthreads();
   if (timed_out) {
     if (tid == 0) {
       atomicExch(flags + FLAG_TIMEOUT, 1ull);
-      // drain copies still in flight into this CTA's shared memory (bounded)
-      for (int b = 0; b < 2; ++b)
-        while (consumed[b] < issued[b]) {
-          if (!mbar_wait_bounded(&mbar[b], (uint32_t)(consumed[b] & 1))) break;
-          consumed[b]++;
-        }
+      // wait (bounded) for the last copy issued into each stage before leaving
+      for (int b = 0; b < STAGES; ++b)
+        if (issued[b] > 0) mbar_wait_bounded(&full[b], (uint32_t)((issued[b] - 1) & 1));
     }
     return;
   }
 #pragma unroll
-  for (int p = 0; p < 2; ++p)
+  for (int p = 0; p < NP; ++p)
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      const int64_t t = tix[p][h];
+      const int64_t t = wbase + 64 * p + 32 * h;
       double* o = part + ((size_t)ch * M_pad + t) * 3;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
@@ -543,19 +565,30 @@ __global__ void __launch_bounds__(128)
 
 }  // namespace
 
+template <class L, int NP>
+void launch_pair32_t(const EvalBufs& b, float rho_lo, float rho_hi, cudaStream_t st) {
+  constexpr int MINB = NP == 2 ? 2 : 3;
+  const unsigned grid = (unsigned)((b.M_pad / (TPB32 * 2 * NP)) * b.n_chunks);
+  const size_t smem = L::STAGES * TILE * L::V * sizeof(float4);
+  cudaFuncSetAttribute(k_pair32<L, NP, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)smem);
+  k_pair32<L, NP, MINB><<<grid, TPB32, smem, st>>>(b.srcF, b.segbox, b.src_orig, b.meta, b.tgtF,
+                                                  b.M_pad, b.n_chunks, b.part, b.near_cnt,
+                                                  b.near_idx, b.flags, rho_lo, rho_hi);
+}
+
 void launch_pair32(int layer, const EvalBufs& b, double rho_T, cudaStream_t st) {
-  const unsigned grid = (unsigned)((b.M_pad / TGT_CTA32) * b.n_chunks);
   const float rho_lo = (float)rho_T, rho_hi = 8.0f;
   if (layer == LAYER_SL) {
-    const size_t smem = 2 * TILE * V_SL * sizeof(float4);
-    k_pair32<SLayer><<<grid, TPB32, smem, st>>>(b.srcF, b.segbox, b.src_orig, b.meta, b.tgtF,
-                                                 b.M_pad, b.n_chunks, b.part, b.near_cnt,
-                                                 b.near_idx, b.flags, rho_lo, rho_hi);
+    if (b.pair_np == 2)
+      launch_pair32_t<SLayer, 2>(b, rho_lo, rho_hi, st);
+    else
+      launch_pair32_t<SLayer, 1>(b, rho_lo, rho_hi, st);
   } else {
-    const size_t smem = 2 * TILE * V_DL * sizeof(float4);
-    k_pair32<DLayer><<<grid, TPB32, smem, st>>>(b.srcF, b.segbox, b.src_orig, b.meta, b.tgtF,
-                                                 b.M_pad, b.n_chunks, b.part, b.near_cnt,
-                                                 b.near_idx, b.flags, rho_lo, rho_hi);
+    if (b.pair_np == 2)
+      launch_pair32_t<DLayer, 2>(b, rho_lo, rho_hi, st);
+    else
+      launch_pair32_t<DLayer, 1>(b, rho_lo, rho_hi, st);
   }
 }
 
