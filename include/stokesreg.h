@@ -137,6 +137,82 @@ int stokes_dl_eval(sk_ctx* ctx, int precision, int mem,
                    const double* delta, int64_t n_delta,
                    double* u_out, void* cuda_stream);
 
+/* ---- serving: continuous batching of single-layer requests -------------
+ *
+ * A server keeps up to max_slots requests resident on the device and runs
+ * one persistent kernel that takes work items (request, block of targets,
+ * chunk of sources) from all resident requests. A request that arrives while
+ * others run is admitted as soon as a slot and enough of the server's HBM
+ * arena are free; its items then interleave with the running ones. Each
+ * request is the SK_FP32C single layer of stokes_sl_eval (Sec. 3.4, Eq.
+ * regstokes) with the context's thresholds, and for up to 131,072 targets
+ * its result is bit-identical to stokes_sl_eval(ctx, SK_FP32C, ...) on the
+ * same inputs, whatever else is in flight. Work item order inside a request
+ * is fixed, so the mix cannot change a result.
+ *
+ * The server owns a host scheduler thread, four CUDA streams, an HBM arena,
+ * a slot table and a mapped host page; it uses the context's device and
+ * thresholds. One server per context at a time. serve_submit and serve_poll
+ * may be called from any host thread. */
+typedef struct sk_server sk_server;
+
+typedef struct {
+  int32_t max_slots;         /* resident requests (1..256; default 32) */
+  int32_t queue_capacity;    /* submitted, not yet admitted requests (default 4096) */
+  size_t hbm_budget_bytes;   /* arena for resident requests (0: a quarter of free memory,
+                                at most 16 GiB) */
+  int64_t idle_exit_us;      /* the persistent kernel exits after this long without work
+                                and is relaunched on demand (default 20000) */
+  size_t host_staging_bytes; /* pinned host pool holding submitted inputs and results
+                                (0: 512 MiB); a full pool makes serve_submit return
+                                SK_EBUSY until results are polled */
+} sk_serve_cfg;
+
+typedef struct {
+  int64_t n_src;             /* as in stokes_sl_eval; host pointers, copied by serve_submit */
+  const double* src_xyz;
+  const double* src_w;
+  const double* f;
+  int64_t n_tgt;
+  const double* tgt_xyz;
+  const double* delta;
+  int64_t n_delta;
+  double mu;
+} sk_request;
+
+typedef struct {
+  double submit_us;          /* host clock, microseconds since serve_create */
+  double admit_us;           /* slot and memory granted, preparation enqueued */
+  double publish_us;         /* work items visible to the persistent kernel */
+  double done_us;            /* last item finished (seen by the host) */
+  double ready_us;           /* result copied back, serve_poll can return it */
+  int64_t interactions;      /* n_tgt x sources with w != 0 */
+  int32_t n_chunks;
+  int32_t status;            /* SK_OK, SK_ETIMEOUT, ... */
+} sk_req_stats;
+
+/* Create a server on ctx. cfg may be NULL (defaults). Errors: SK_EINVAL,
+ * SK_ENOMEM (arena), SK_ECUDA, SK_EBUSY (ctx already serves). */
+int serve_create(sk_ctx* ctx, const sk_serve_cfg* cfg, sk_server** out);
+
+/* Queue one request; its arrays are copied before the call returns, so the
+ * caller may free them at once. *ticket identifies it for serve_poll.
+ * Errors: SK_EINVAL (bad request), SK_EBUSY (queue full: retry later),
+ * SK_ENOMEM (the request can never fit in the arena). */
+int serve_submit(sk_server* srv, const sk_request* req, uint64_t* ticket);
+
+/* Wait up to timeout_us (0: do not wait, < 0: wait forever) for a ticket.
+ * SK_OK: u_out [n_tgt][3] (host) and *st (may be NULL) are filled and the
+ * ticket is released. SK_EAGAIN: not ready yet. SK_EINVAL: unknown ticket.
+ * A request that failed on the device returns its error code (e.g.
+ * SK_ETIMEOUT) and releases the ticket. */
+int serve_poll(sk_server* srv, uint64_t ticket, double* u_out, sk_req_stats* st,
+               int64_t timeout_us);
+
+/* Finish every queued and resident request, stop the persistent kernel and
+ * free the server. Results that were never polled are discarded. */
+void serve_destroy(sk_server* srv);
+
 /* Single layer without any memory allocation (the paper has no counterpart:
  * this is a service for callers that cannot allocate).
  *

@@ -78,6 +78,10 @@ def _declare(lib):
 
 _EXTRA_DECLS: dict = {
     "stokes_sl_eval_noalloc": ([_i64, _vp, _vp, _vp, _i64, _vp, _vp, _i64, _dbl, _vp, _vp], _int),
+    "serve_create": ([_vp, _vp, ctypes.POINTER(_vp)], _int),
+    "serve_submit": ([_vp, _vp, ctypes.POINTER(ctypes.c_uint64)], _int),
+    "serve_poll": ([_vp, ctypes.c_uint64, _vp, _vp, ctypes.c_int64], _int),
+    "serve_destroy": ([_vp], None),
 }
 
 
@@ -239,6 +243,67 @@ def stokes_dl_eval(ctx, precision: int, mem: int, src_xyz, src_w, src_n, q, tgt_
     if mem == SK_HOST and U is not u_out:
         np.copyto(u_out, U.reshape(np.shape(u_out)))
     return u_out
+
+
+class sk_serve_cfg(ctypes.Structure):
+    _fields_ = [("max_slots", ctypes.c_int32), ("queue_capacity", ctypes.c_int32),
+                ("hbm_budget_bytes", ctypes.c_size_t), ("idle_exit_us", ctypes.c_int64),
+                ("host_staging_bytes", ctypes.c_size_t)]
+
+
+class sk_request(ctypes.Structure):
+    _fields_ = [("n_src", ctypes.c_int64), ("src_xyz", _vp), ("src_w", _vp), ("f", _vp),
+                ("n_tgt", ctypes.c_int64), ("tgt_xyz", _vp), ("delta", _vp),
+                ("n_delta", ctypes.c_int64), ("mu", ctypes.c_double)]
+
+
+class sk_req_stats(ctypes.Structure):
+    _fields_ = [("submit_us", ctypes.c_double), ("admit_us", ctypes.c_double),
+                ("publish_us", ctypes.c_double), ("done_us", ctypes.c_double),
+                ("ready_us", ctypes.c_double), ("interactions", ctypes.c_int64),
+                ("n_chunks", ctypes.c_int32), ("status", ctypes.c_int32)]
+
+
+def serve_create(ctx, max_slots: int = 0, queue_capacity: int = 0, hbm_budget_bytes: int = 0,
+                 idle_exit_us: int = 0, host_staging_bytes: int = 0):
+    """Start a continuous-batching server on ctx (0 = default for every knob)."""
+    cfg = sk_serve_cfg(max_slots, queue_capacity, hbm_budget_bytes, idle_exit_us,
+                       host_staging_bytes)
+    h = _vp()
+    _check(ctx, load().serve_create(ctx, ctypes.byref(cfg), ctypes.byref(h)))
+    return h
+
+
+def serve_submit(srv, src_xyz, src_w, f, tgt_xyz, delta, mu: float = 1.0) -> int:
+    """Queue one single-layer request (host arrays, copied at once). Returns
+    its ticket; raises SkError (SK_EBUSY: retry later, SK_ENOMEM: too large)."""
+    X, n = _ptr(src_xyz, SK_HOST, (3,), "src_xyz")
+    W, _ = _ptr(src_w, SK_HOST, (), "src_w")
+    F, _ = _ptr(f, SK_HOST, (3,), "f")
+    Y, M = _ptr(tgt_xyz, SK_HOST, (3,), "tgt_xyz")
+    D, nd = _ptr(delta if not np.isscalar(delta) else [delta], SK_HOST, (), "delta")
+    req = sk_request(n, _host_ptr(X), _host_ptr(W), _host_ptr(F), M, _host_ptr(Y), _host_ptr(D),
+                     nd, float(mu))
+    t = ctypes.c_uint64()
+    code = load().serve_submit(srv, ctypes.byref(req), ctypes.byref(t))
+    if code != SK_OK:
+        raise SkError(code, "serve_submit")
+    return t.value
+
+
+def serve_poll(srv, ticket: int, n_tgt: int, timeout_us: int = -1):
+    """(status, u (n_tgt, 3) or None, stats dict). SK_EAGAIN: not ready."""
+    u = np.empty((n_tgt, 3), dtype=np.float64)
+    st = sk_req_stats()
+    code = load().serve_poll(srv, ctypes.c_uint64(ticket), u.ctypes.data_as(_vp),
+                             ctypes.byref(st), int(timeout_us))
+    stats = {f[0]: getattr(st, f[0]) for f in st._fields_}
+    return code, (u if code == SK_OK else None), stats
+
+
+def serve_destroy(srv) -> None:
+    if srv:
+        load().serve_destroy(srv)
 
 
 def stokes_sl_eval_noalloc(src_xyz, src_w, f, tgt_xyz, delta, mu: float = 1.0, u_out=None,

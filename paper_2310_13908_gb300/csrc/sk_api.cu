@@ -126,20 +126,24 @@ int choose_chunks(int precision, int64_t N, int64_t M, int sm_count) {
   return best;
 }
 
+double layer_scale(const EvalShape& s) {
+  return s.layer == LAYER_SL ? 1.0 / (8.0 * PI_CONST * s.mu) : -6.0 / (8.0 * PI_CONST);
+}
+
 __global__ void k_check_delta(const double* __restrict__ d, int64_t n,
                               unsigned long long* __restrict__ flags) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n && !(d[i] > 0.0 && d[i] < INFINITY)) atomicExch(flags + FLAG_BAD_DELTA, 1ull);
 }
 
-// Enqueue one evaluation on `st`; inputs and output are device pointers in b.
-int enqueue_eval(const EvalShape& s, const EvalBufs& b, double rho_T, double rho_c,
-                 cudaStream_t st, cudaEvent_t* ev) {
+// Preparation of one evaluation on `st`: clear the counters, check delta,
+// sort and pack sources and targets. Returns the number of kernels launched.
+int enqueue_prep(const EvalShape& s, const EvalBufs& b, double rho_T, double rho_c,
+                 cudaStream_t st) {
   const bool fp32 = s.precision == SK_FP32C;
+  const double scale = layer_scale(s);
   constexpr int SORT_LAUNCHES = 3 + 4 * 3;  // bbox (2) + keys + 4 radix passes x 3
   int launches = 0;
-  if (ev) cudaEventRecord(ev[0], st);
-  const double scale = s.layer == LAYER_SL ? 1.0 / (8.0 * PI_CONST * s.mu) : -6.0 / (8.0 * PI_CONST);
   cudaMemsetAsync(b.flags, 0, N_FLAGS * sizeof(unsigned long long), st);
   cudaMemsetAsync(b.meta, 0, N_META * sizeof(int), st);
   if (fp32) cudaMemsetAsync(b.near_cnt, 0, b.M_pad * sizeof(int), st);
@@ -157,20 +161,32 @@ int enqueue_eval(const EvalShape& s, const EvalBufs& b, double rho_T, double rho
   launch_sort_points(b.tgt_xyz, nullptr, s.M, b.keys_a, b.keys_b, b.vals_a, b.vals_b, b.hist,
                      b.bbox_part, b.bbox, b.meta + META_SCRATCH, b.sort_blocks, st);
   launches += SORT_LAUNCHES;
-  if (fp32) {
+  if (fp32)
     launch_pack_targets32(b, s.n_delta, rho_T, rho_c, st);
-    if (ev) cudaEventRecord(ev[1], st);
-    launch_pair32(s.layer, b, rho_T, st);
-    if (ev) cudaEventRecord(ev[2], st);
-    launch_finish32(s.layer, b, s.n_delta, scale, rho_T, st);
-    launches += 1 + 1 + 2;
-  } else {
+  else
     launch_pack_targets64(b, s.n_delta, st);
-    if (ev) cudaEventRecord(ev[1], st);
+  return launches + 1;
+}
+
+// Enqueue one evaluation on `st`; inputs and output are device pointers in b.
+int enqueue_eval(const EvalShape& s, const EvalBufs& b, double rho_T, double rho_c,
+                 cudaStream_t st, cudaEvent_t* ev) {
+  const bool fp32 = s.precision == SK_FP32C;
+  const double scale = layer_scale(s);
+  if (ev) cudaEventRecord(ev[0], st);
+  int launches = enqueue_prep(s, b, rho_T, rho_c, st);
+  if (ev) cudaEventRecord(ev[1], st);
+  if (fp32)
+    launch_pair32(s.layer, b, rho_T, st);
+  else
     launch_pair64(s.layer, b, scale, st);
-    if (ev) cudaEventRecord(ev[2], st);
+  if (ev) cudaEventRecord(ev[2], st);
+  if (fp32) {
+    launch_finish32(s.layer, b, s.n_delta, scale, rho_T, st);
+    launches += 1 + 2;
+  } else {
     launch_finish64(b, st);
-    launches += 1 + 1 + 1;
+    launches += 1 + 1;
   }
   if (ev) cudaEventRecord(ev[3], st);
   return launches;
@@ -230,6 +246,7 @@ int sk_create(sk_ctx** out, int device, size_t workspace_bytes) {
 
 void sk_destroy(sk_ctx* ctx) {
   if (!ctx) return;
+  if (ctx->server) serve_destroy(ctx->server);
   DeviceGuard g(ctx->device);
   cudaDeviceSynchronize();
   if (ctx->ws) cudaFree(ctx->ws);

@@ -118,8 +118,11 @@ inline int pair32_ctas_per_sm(int np) { return np == 2 ? 2 : 3; }
 
 }  // namespace sk
 
+struct sk_server;
+
 struct sk_ctx {
   int device = 0;
+  sk_server* server = nullptr;  // at most one server per context
   cudaStream_t stream = nullptr;
   char* ws = nullptr;
   size_t ws_bytes = 0;
@@ -151,6 +154,9 @@ struct EvalShape {
 size_t eval_workspace_bytes(const EvalShape& s);
 void carve_eval_buffers(Bump& bp, const EvalShape& s, EvalBufs& b);
 int choose_chunks(int precision, int64_t N, int64_t M, int sm_count);
+double layer_scale(const EvalShape& s);  // 1/(8 pi mu) or -6/(8 pi)
+int enqueue_prep(const EvalShape& s, const EvalBufs& b, double rho_T, double rho_c,
+                 cudaStream_t st);
 // Returns the number of kernels launched. ev (optional, 4 events) brackets
 // the whole evaluation (ev[0], ev[3]) and the pair kernel (ev[1], ev[2]).
 int enqueue_eval(const EvalShape& s, const EvalBufs& b, double rho_T, double rho_c,

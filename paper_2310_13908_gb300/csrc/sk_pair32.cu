@@ -1,566 +1,38 @@
-// sk_pair32.cu -- FP32-compensated pair sums (single and double layer).
-//
-// Regimes per pair, rho = r/delta_x (delta of the target, Eq. regparam):
-//   rho >= rho_c          plain Stokeslet / stresslet (s_i = 1), FP32 f32x2
-//   rho_T <= rho < rho_c  closed-form s_i with erf/exp, FP32 (Sec. 3.4)
-//   rho < rho_T           recorded in a per-target list and summed in FP64
-//                         by power series (finish kernel), incl. r = 0
-//
-// Work item = (block of 1024 sorted targets, chunk of source tiles). A CTA
-// streams its chunk through shared memory in tiles of 256 sources with
-// double-buffered bulk async copies (cp.async.bulk + mbarrier). Per warp and
-// per 32-source segment a bounding-box test decides whether any pair can be
-// closer than rho_c delta; if not, the segment runs the branch-free far loop.
-// Each lane owns four targets held as two f32x2 pairs, so every arithmetic
-// instruction of the far loop is a packed FFMA2/FADD2/FMUL2.
-//
-// Accumulation (a4): plain FP32 inside 128-source groups, two-sum merge into
-// a (hi, lo) FP32 pair per target component, hi + lo written in FP64 per
-// chunk; the finish kernel adds the chunks in fixed order and the FP64 near
-// sum. The result of a target does not depend on which warp, CTA or chunk
-// order it landed in: the far formula is bit-identical in both loops.
-#include <cfloat>
-
-#include "sk_internal.h"
-#include "sk_series.cuh"
-
-// unroll factor of the far loop over the 32 sources of a segment
-#ifndef SK_FAR_UNROLL
-#define SK_FAR_UNROLL 8
-#endif
+// sk_pair32.cu -- kernels and launchers of the FP32-compensated pair sums
+// (device code in sk_pair32.cuh).
+#include "sk_pair32.cuh"
 
 namespace sk {
 namespace {
 
-constexpr unsigned FULL = 0xffffffffu;
-constexpr int kFarUnroll = SK_FAR_UNROLL;
-
-__device__ __forceinline__ float rsq(float x) {
-  float y;
-  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
-  return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
-}
-__device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
-__device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
-
-// ---- bulk async copy + mbarrier helpers (bounded waits) --------------------
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes,
-                                          uint64_t* bar) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-          "r"(smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-  const long long t0 = clock64();
-  while (!mbar_try(bar, parity)) {
-    if (clock64() - t0 > WAIT_CYCLES) return false;
-  }
-  return true;
-}
-
-// ---- per-lane target state --------------------------------------------------
-struct Tgt2 {
-  float2 x, y, z, idl, rc2, rt2;
-};
-
-__device__ __forceinline__ void near_append(int64_t t, int jo, int* __restrict__ cnt,
-                                            int* __restrict__ idx,
-                                            unsigned long long* __restrict__ flags) {
-  const int slot = atomicAdd(cnt + t, 1);
-  if (slot < NEAR_K)
-    idx[t * NEAR_K + slot] = jo;
-  else if (slot == NEAR_K)
-    atomicAdd(flags + FLAG_OVERFLOW, 1ull);
-}
-
-// ---- layer policies ---------------------------------------------------------
-// Source record s (V float4) is read from shared memory; d and r2 of both
-// targets of a pair are computed by the caller.
-struct SLayer {
-  static constexpr int V = V_SL;
-  static constexpr int STAGES = 4;
-  struct Src {
-    float2 nx, ny, nz, gx, gy, gz;
-  };
-  __device__ __forceinline__ static Src load(const float4* s) {
-    const float4 a = s[0], b = s[1], c = s[2];
-    return {lo2(a), hi2(a), lo2(b), hi2(b), lo2(c), hi2(c)};
-  }
-  // far: s1 = s2 = 1
-  __device__ __forceinline__ static void far(const Src& S, float2 dx, float2 dy, float2 dz,
-                                             float2 r2, float2* U) {
-    const float2 ri = make_float2(rsq(r2.x), rsq(r2.y));
-    const float2 ri2 = mul2(ri, ri);
-    const float2 gd = fma2(S.gz, dz, fma2(S.gy, dy, mul2(S.gx, dx)));
-    const float2 a = mul2(gd, ri2);
-    U[0] = fma2(fma2(dx, a, S.gx), ri, U[0]);
-    U[1] = fma2(fma2(dy, a, S.gy), ri, U[1]);
-    U[2] = fma2(fma2(dz, a, S.gz), ri, U[2]);
-  }
-  // general: ri may be 0 (pair excluded), s1/s2 == 1 reproduces far() bit for bit
-  __device__ __forceinline__ static void general(const Src& S, float2 dx, float2 dy, float2 dz,
-                                                 float2 ri, float2 s1, float2 s2, float2* U) {
-    const float2 ri2 = mul2(ri, ri);
-    const float2 gd = fma2(S.gz, dz, fma2(S.gy, dy, mul2(S.gx, dx)));
-    const float2 a = mul2(mul2(gd, ri2), s2);
-    U[0] = fma2(fma2(dx, a, mul2(S.gx, s1)), ri, U[0]);
-    U[1] = fma2(fma2(dy, a, mul2(S.gy, s1)), ri, U[1]);
-    U[2] = fma2(fma2(dz, a, mul2(S.gz, s1)), ri, U[2]);
-  }
-  // FP32 closed forms at rho (Sec. 3.4); the caller clamps rho into range.
-  __device__ __forceinline__ static void smooth(float rho, float& s1, float& s2) {
-    const float p2 = rho * rho;
-    const float e = __expf(-p2) * (float)INV_SQRT_PI;
-    const float er = erff(rho);
-    s1 = er - (2.f / 3.f) * rho * (2.f * p2 - 5.f) * e;
-    s2 = er - (2.f / 3.f) * rho * ((4.f * p2 - 14.f) * p2 + 3.f) * e;
-  }
-};
-
-struct DLayer {
-  static constexpr int V = V_DL;
-  static constexpr int STAGES = 3;
-  struct Src {
-    float2 nx, ny, nz, qx, qy, qz, mx, my, mz;  // m: surface normal
-  };
-  __device__ __forceinline__ static Src load(const float4* s) {
-    const float4 a = s[0], b = s[1], c = s[2], d = s[3], e = s[4];
-    return {lo2(a), hi2(a), lo2(b), hi2(b), lo2(c), hi2(c), lo2(d), hi2(d), lo2(e)};
-  }
-  __device__ __forceinline__ static void far(const Src& S, float2 dx, float2 dy, float2 dz,
-                                             float2 r2, float2* U) {
-    const float2 ri = make_float2(rsq(r2.x), rsq(r2.y));
-    const float2 ri2 = mul2(ri, ri);
-    const float2 ri5 = mul2(mul2(ri2, ri2), ri);
-    const float2 dq = fma2(S.qz, dz, fma2(S.qy, dy, mul2(S.qx, dx)));
-    const float2 dn = fma2(S.mz, dz, fma2(S.my, dy, mul2(S.mx, dx)));
-    const float2 c = mul2(mul2(dq, dn), ri5);
-    U[0] = fma2(c, dx, U[0]);
-    U[1] = fma2(c, dy, U[1]);
-    U[2] = fma2(c, dz, U[2]);
-  }
-  __device__ __forceinline__ static void general(const Src& S, float2 dx, float2 dy, float2 dz,
-                                                 float2 ri, float2 s3, float2 /*unused*/,
-                                                 float2* U) {
-    const float2 ri2 = mul2(ri, ri);
-    const float2 ri5 = mul2(mul2(ri2, ri2), ri);
-    const float2 dq = fma2(S.qz, dz, fma2(S.qy, dy, mul2(S.qx, dx)));
-    const float2 dn = fma2(S.mz, dz, fma2(S.my, dy, mul2(S.mx, dx)));
-    const float2 c = mul2(mul2(mul2(dq, dn), ri5), s3);
-    U[0] = fma2(c, dx, U[0]);
-    U[1] = fma2(c, dy, U[1]);
-    U[2] = fma2(c, dz, U[2]);
-  }
-  __device__ __forceinline__ static void smooth(float rho, float& s3, float& unused) {
-    const float p2 = rho * rho;
-    const float e = __expf(-p2) * (float)INV_SQRT_PI;
-    s3 = erff(rho) - (2.f / 9.f) * rho * (((8.f * p2 - 36.f) * p2 + 6.f) * p2 + 9.f) * e;
-    unused = 1.f;
-  }
-};
-
-__device__ __forceinline__ void pair_d(const Tgt2& T, float2 nx, float2 ny, float2 nz, float2& dx,
-                                       float2& dy, float2& dz, float2& r2) {
-  dx = add2(T.x, nx);
-  dy = add2(T.y, ny);
-  dz = add2(T.z, nz);
-  r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
-}
-
-// Slow path of one target pair for one source: regime per lane component.
-template <class L>
-__device__ __forceinline__ void pair_general(const typename L::Src& S, const Tgt2& T, float2 dx,
-                                             float2 dy, float2 dz, float2 r2, float2* U,
-                                             int64_t t0, int64_t t1, const int* src_orig_j,
-                                             int* near_cnt, int* near_idx,
-                                             unsigned long long* flags, float rho_lo,
-                                             float rho_hi) {
-  float2 ri = make_float2(rsq(r2.x), rsq(r2.y));
-  float2 sa = make_float2(1.f, 1.f), sb = make_float2(1.f, 1.f);
-  // component x
-  {
-    const bool vn = r2.x < T.rt2.x;
-    const bool in = !vn && r2.x < T.rc2.x;
-    if (vn) {
-      near_append(t0, *src_orig_j, near_cnt, near_idx, flags);
-      ri.x = 0.f;
-    }
-    float rho = fminf(fmaxf(r2.x * ri.x * T.idl.x, rho_lo), rho_hi);
-    float a, b;
-    L::smooth(rho, a, b);
-    if (in) {
-      sa.x = a;
-      sb.x = b;
-    }
-  }
-  {
-    const bool vn = r2.y < T.rt2.y;
-    const bool in = !vn && r2.y < T.rc2.y;
-    if (vn) {
-      near_append(t1, *src_orig_j, near_cnt, near_idx, flags);
-      ri.y = 0.f;
-    }
-    float rho = fminf(fmaxf(r2.y * ri.y * T.idl.y, rho_lo), rho_hi);
-    float a, b;
-    L::smooth(rho, a, b);
-    if (in) {
-      sa.y = a;
-      sb.y = b;
-    }
-  }
-  L::general(S, dx, dy, dz, ri, sa, sb, U);
-}
-
-__device__ __forceinline__ void two_sum_merge(float2* U, float2* HI, float2* LO) {
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const float2 s = add2(HI[c], U[c]);
-    const float2 bp = sub2(s, HI[c]);
-    const float2 e = add2(sub2(HI[c], sub2(s, bp)), sub2(U[c], bp));
-    LO[c] = add2(LO[c], e);
-    HI[c] = s;
-    U[c] = make_float2(0.f, 0.f);
-  }
-}
+using namespace p32;
 
 template <class L, int NP, int MINB>
 __global__ void __launch_bounds__(TPB32, MINB)
-    k_pair32(const float4* __restrict__ srcF, const float4* __restrict__ segbox,
-             const int* __restrict__ src_orig, const int* __restrict__ meta,
-             const float4* __restrict__ tgtF, int64_t M_pad, int n_chunks,
-             double* __restrict__ part, int* __restrict__ near_cnt, int* __restrict__ near_idx,
-             unsigned long long* __restrict__ flags, float rho_lo, float rho_hi) {
-  constexpr int V = L::V;
-  constexpr int STAGES = L::STAGES;
-  constexpr int WARPS = TPB32 / 32;
-  constexpr uint32_t TILE_BYTES = TILE * V * sizeof(float4);
+    k_pair32(PairArgs a) {
   extern __shared__ __align__(128) float4 sm[];
-  // full[b]: the bulk copy of stage b landed (transaction count);
-  // rel[b]: warps that released stage b so far (monotonic);
-  // issued[b]: copies issued into stage b (for the drain after a timeout).
-  __shared__ __align__(8) uint64_t full[STAGES];
-  __shared__ int rel[STAGES];
-  __shared__ int issued[STAGES];
-  __shared__ int timed_out;
-
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int tb = blockIdx.x / n_chunks, ch = blockIdx.x % n_chunks;
-  const int n_tiles = meta[META_NS_PAD] / TILE;
-  const int k0 = (int)((long long)ch * n_tiles / n_chunks);
-  const int k1 = (int)((long long)(ch + 1) * n_tiles / n_chunks);
-
-  // ---- targets of this lane: pair p holds targets (base + 64p + lane, base + 64p + 32 + lane)
-  const int64_t wbase = (int64_t)tb * (TPB32 * 2 * NP) + wid * (64 * NP) + lane;
-  Tgt2 T[NP];
-  float blo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, bhi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
-  float rc2max = -1.f;
-#pragma unroll
-  for (int p = 0; p < NP; ++p) {
-    float4 a[2], b[2];
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int64_t t = wbase + 64 * p + 32 * h;
-      a[h] = tgtF[2 * t];
-      b[h] = tgtF[2 * t + 1];
-      if (b[h].x >= 0.f) {
-        blo[0] = fminf(blo[0], a[h].x); bhi[0] = fmaxf(bhi[0], a[h].x);
-        blo[1] = fminf(blo[1], a[h].y); bhi[1] = fmaxf(bhi[1], a[h].y);
-        blo[2] = fminf(blo[2], a[h].z); bhi[2] = fmaxf(bhi[2], a[h].z);
-        rc2max = fmaxf(rc2max, b[h].x);
-      }
-    }
-    T[p].x = make_float2(a[0].x, a[1].x);
-    T[p].y = make_float2(a[0].y, a[1].y);
-    T[p].z = make_float2(a[0].z, a[1].z);
-    T[p].idl = make_float2(a[0].w, a[1].w);
-    T[p].rc2 = make_float2(b[0].x, b[1].x);
-    T[p].rt2 = make_float2(b[0].y, b[1].y);
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      blo[c] = fminf(blo[c], __shfl_xor_sync(FULL, blo[c], o));
-      bhi[c] = fmaxf(bhi[c], __shfl_xor_sync(FULL, bhi[c], o));
-    }
-    rc2max = fmaxf(rc2max, __shfl_xor_sync(FULL, rc2max, o));
-  }
-  const bool warp_live = rc2max >= 0.f;
-  const float rc2test = rc2max * 1.0001f;
-
-  float2 U[NP][3], HI[NP][3], LO[NP][3];
-#pragma unroll
-  for (int p = 0; p < NP; ++p)
-#pragma unroll
-    for (int c = 0; c < 3; ++c) U[p][c] = HI[p][c] = LO[p][c] = make_float2(0.f, 0.f);
-
-  // ---- source pipeline: no CTA-wide barrier inside the loop; the last warp
-  // to release a stage issues the next bulk copy into it.
-  if (tid == 0) {
-    for (int b = 0; b < STAGES; ++b) {
-      mbar_init(&full[b]);
-      rel[b] = 0;
-      issued[b] = 0;
-    }
-    timed_out = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();
-  if (tid == 0) {
-    for (int b = 0; b < STAGES; ++b)
-      if (k0 + b < k1) {
-        bulk_load(sm + b * TILE * V, srcF + (size_t)(k0 + b) * TILE * V, TILE_BYTES, &full[b]);
-        issued[b] = 1;
-      }
-  }
-  for (int k = k0, it = 0; k < k1; ++k, ++it) {
-    const int buf = it % STAGES;
-    const int use = it / STAGES;
-    const bool ok = __all_sync(FULL, mbar_wait_bounded(&full[buf], (uint32_t)(use & 1)));
-    if (!ok) {
-      if (lane == 0) atomicExch(&timed_out, 1);
-      break;
-    }
-    if (warp_live) {
-      const float4* S = sm + buf * TILE * V;
-      bool nb = false;
-      if (lane < TILE_SEGS) {
-        const float4 lo = segbox[2 * ((size_t)k * TILE_SEGS + lane)];
-        const float4 hi = segbox[2 * ((size_t)k * TILE_SEGS + lane) + 1];
-        const float dx = fmaxf(0.f, fmaxf(lo.x - bhi[0], blo[0] - hi.x));
-        const float dy = fmaxf(0.f, fmaxf(lo.y - bhi[1], blo[1] - hi.y));
-        const float dz = fmaxf(0.f, fmaxf(lo.z - bhi[2], blo[2] - hi.z));
-        nb = dx * dx + dy * dy + dz * dz < rc2test;
-      }
-      const unsigned nm = __ballot_sync(FULL, nb);
-#pragma unroll 1
-      for (int s = 0; s < TILE_SEGS; ++s) {
-        const float4* SS = S + s * SEG * V;
-        if (!((nm >> s) & 1u)) {
-#pragma unroll kFarUnroll
-          for (int j = 0; j < SEG; ++j) {
-            const typename L::Src src = L::load(SS + j * V);
-#pragma unroll
-            for (int p = 0; p < NP; ++p) {
-              float2 dx, dy, dz, r2;
-              pair_d(T[p], src.nx, src.ny, src.nz, dx, dy, dz, r2);
-              L::far(src, dx, dy, dz, r2, U[p]);
-            }
-          }
-        } else {
-          const int* orig = src_orig + (size_t)k * TILE + s * SEG;
-#pragma unroll 1
-          for (int j = 0; j < SEG; ++j) {
-            const typename L::Src src = L::load(SS + j * V);
-            float2 dx[NP], dy[NP], dz[NP], r2[NP];
-            bool any = false;
-#pragma unroll
-            for (int p = 0; p < NP; ++p) {
-              pair_d(T[p], src.nx, src.ny, src.nz, dx[p], dy[p], dz[p], r2[p]);
-              any |= (r2[p].x < T[p].rc2.x) | (r2[p].y < T[p].rc2.y);
-            }
-            if (__any_sync(FULL, any)) {
-#pragma unroll
-              for (int p = 0; p < NP; ++p)
-                pair_general<L>(src, T[p], dx[p], dy[p], dz[p], r2[p], U[p], wbase + 64 * p,
-                                wbase + 64 * p + 32, orig + j, near_cnt, near_idx, flags, rho_lo,
-                                rho_hi);
-            } else {
-#pragma unroll
-              for (int p = 0; p < NP; ++p) L::far(src, dx[p], dy[p], dz[p], r2[p], U[p]);
-            }
-          }
-        }
-        if ((s & 3) == 3) {
-#pragma unroll
-          for (int p = 0; p < NP; ++p) two_sum_merge(U[p], HI[p], LO[p]);
-        }
-      }
-    }
-    // release the stage; the last of the WARPS releases refills it
-    __syncwarp();
-    if (lane == 0) {
-      __threadfence_block();
-      const int prev = atomicAdd(&rel[buf], 1);
-      if (prev == (use + 1) * WARPS - 1 && k + STAGES < k1) {
-        __threadfence_block();
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        bulk_load(sm + buf * TILE * V, srcF + (size_t)(k + STAGES) * TILE * V, TILE_BYTES,
-                  &full[buf]);
-        atomicAdd(&issued[buf], 1);
-      }
-    }
-  }
-  __syncthreads();
-  if (timed_out) {
-    if (tid == 0) {
-      atomicExch(flags + FLAG_TIMEOUT, 1ull);
-      // wait (bounded) for the last copy issued into each stage before leaving
-      for (int b = 0; b < STAGES; ++b)
-        if (issued[b] > 0) mbar_wait_bounded(&full[b], (uint32_t)((issued[b] - 1) & 1));
-    }
-    return;
-  }
-#pragma unroll
-  for (int p = 0; p < NP; ++p)
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int64_t t = wbase + 64 * p + 32 * h;
-      double* o = part + ((size_t)ch * M_pad + t) * 3;
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const float hv = h ? HI[p][c].y : HI[p][c].x;
-        const float lv = h ? LO[p][c].y : LO[p][c].x;
-        o[c] = (double)hv + (double)lv;
-      }
-    }
+  __shared__ PipeSmem<L::STAGES> ps;
+  if (threadIdx.x == 0) ps.initialized = 0;
+  const int tb = blockIdx.x / a.n_chunks, ch = blockIdx.x % a.n_chunks;
+  pair_item<L, NP>(a, tb, ch, sm, ps);
 }
 
-// FP64 near pair of the finish/overflow kernels, by layer.
 template <class L>
-struct Near64;
-
-template <>
-struct Near64<SLayer> {
-  __device__ __forceinline__ static void eval(double4_32a x, const double* xyz, const double* w,
-                                              const double* f, const double* /*nrm*/, int j,
-                                              double scale, double invd, double& u0, double& u1,
-                                              double& u2) {
-    sl_pair64(x.x - xyz[3 * j], x.y - xyz[3 * j + 1], x.z - xyz[3 * j + 2], f[3 * j], f[3 * j + 1],
-              f[3 * j + 2], w[j] * scale, invd, u0, u1, u2);
-  }
-};
-
-template <>
-struct Near64<DLayer> {
-  __device__ __forceinline__ static void eval(double4_32a x, const double* xyz, const double* w,
-                                              const double* q, const double* nrm, int j,
-                                              double scale, double invd, double& u0, double& u1,
-                                              double& u2) {
-    dl_pair64(x.x - xyz[3 * j], x.y - xyz[3 * j + 1], x.z - xyz[3 * j + 2], q[3 * j], q[3 * j + 1],
-              q[3 * j + 2], nrm[3 * j], nrm[3 * j + 1], nrm[3 * j + 2], w[j] * scale, invd, u0, u1,
-              u2);
-  }
-};
-
-// Targets whose near list overflowed: one warp rescans all packed sources with
-// exactly the FP32 test of the pair kernel and sums the near pairs in FP64.
-template <class L>
-__global__ void k_overflow32(const float4* __restrict__ srcF, const int* __restrict__ src_orig,
-                             const int* __restrict__ meta, const float4* __restrict__ tgtF,
-                             const double4_32a* __restrict__ tgt64, int64_t M,
-                             const int* __restrict__ near_cnt, const double* __restrict__ xyz,
-                             const double* __restrict__ w, const double* __restrict__ dens,
-                             const double* __restrict__ nrm, double scale,
-                             const unsigned long long* __restrict__ flags,
-                             double* __restrict__ near_ovf) {
-  if (flags[FLAG_OVERFLOW] == 0ull) return;
+__global__ void k_overflow32(OverflowArgs a, int64_t M) {
+  if (a.flags[FLAG_OVERFLOW] == 0ull) return;
   const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
   if (t >= M) return;
-  if (near_cnt[t] <= NEAR_K) return;
-  constexpr int V = L::V;
-  const float4 a = tgtF[2 * t];
-  const float rt2 = tgtF[2 * t + 1].y;
-  const double4_32a x = tgt64[t];
-  const double invd = 1.0 / x.w;
-  const int Ns = meta[META_NS];
-  double u0 = 0, u1 = 0, u2 = 0;
-  for (int s = lane; s < Ns; s += 32) {
-    const float4 p0 = srcF[(size_t)s * V], p1 = srcF[(size_t)s * V + 1];
-    const float dx = __fadd_rn(a.x, p0.x), dy = __fadd_rn(a.y, p0.z), dz = __fadd_rn(a.z, p1.x);
-    const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-    if (r2 < rt2) Near64<L>::eval(x, xyz, w, dens, nrm, src_orig[s], scale, invd, u0, u1, u2);
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    u0 += __shfl_xor_sync(FULL, u0, o);
-    u1 += __shfl_xor_sync(FULL, u1, o);
-    u2 += __shfl_xor_sync(FULL, u2, o);
-  }
-  if (lane == 0) {
-    near_ovf[3 * t] = u0;
-    near_ovf[3 * t + 1] = u1;
-    near_ovf[3 * t + 2] = u2;
-  }
+  overflow_target<L>(a, t);
 }
 
 template <class L>
-__global__ void __launch_bounds__(128)
-    k_finish32(const double4_32a* __restrict__ tgt64, const int* __restrict__ perm, int64_t M,
-               int64_t M_pad, int n_chunks, const double* __restrict__ part,
-               const int* __restrict__ near_cnt, const int* __restrict__ near_idx,
-               const double* __restrict__ near_ovf, const double* __restrict__ xyz,
-               const double* __restrict__ w, const double* __restrict__ dens,
-               const double* __restrict__ nrm, double scale, double* __restrict__ u_out,
-               unsigned long long* __restrict__ flags) {
+__global__ void __launch_bounds__(128) k_finish32(FinishArgs a, int64_t M) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int cnt = 0;
-  if (t < M) {
-    double u0 = 0, u1 = 0, u2 = 0;
-    for (int c = 0; c < n_chunks; ++c) {
-      const double* p = part + ((size_t)c * M_pad + t) * 3;
-      u0 += p[0];
-      u1 += p[1];
-      u2 += p[2];
-    }
-    cnt = near_cnt[t];
-    double n0 = 0, n1 = 0, n2 = 0;
-    if (cnt <= NEAR_K) {
-      // sort the list so the FP64 sum has a fixed order
-      int li[NEAR_K];
-      for (int i = 0; i < cnt; ++i) {
-        const int v = near_idx[t * NEAR_K + i];
-        int k = i;
-        while (k > 0 && li[k - 1] > v) {
-          li[k] = li[k - 1];
-          --k;
-        }
-        li[k] = v;
-      }
-      const double4_32a x = tgt64[t];
-      const double invd = 1.0 / x.w;
-      for (int i = 0; i < cnt; ++i)
-        Near64<L>::eval(x, xyz, w, dens, nrm, li[i], scale, invd, n0, n1, n2);
-    } else {
-      n0 = near_ovf[3 * t];
-      n1 = near_ovf[3 * t + 1];
-      n2 = near_ovf[3 * t + 2];
-    }
-    const int j = perm[t];
-    u_out[3 * j] = u0 + n0;
-    u_out[3 * j + 1] = u1 + n1;
-    u_out[3 * j + 2] = u2 + n2;
-  }
+  if (t < M) cnt = finish_target<L>(a, t);
   // count near pairs: one atomic per warp
-  int c = cnt;
-  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(FULL, c, o);
-  if ((threadIdx.x & 31) == 0 && c) atomicAdd(flags + FLAG_NEAR_PAIRS, (unsigned long long)c);
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(FULL, cnt, o);
+  if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(a.flags + FLAG_NEAR_PAIRS, (unsigned long long)cnt);
 }
 
 }  // namespace
@@ -572,9 +44,9 @@ void launch_pair32_t(const EvalBufs& b, float rho_lo, float rho_hi, cudaStream_t
   const size_t smem = L::STAGES * TILE * L::V * sizeof(float4);
   cudaFuncSetAttribute(k_pair32<L, NP, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)smem);
-  k_pair32<L, NP, MINB><<<grid, TPB32, smem, st>>>(b.srcF, b.segbox, b.src_orig, b.meta, b.tgtF,
-                                                  b.M_pad, b.n_chunks, b.part, b.near_cnt,
-                                                  b.near_idx, b.flags, rho_lo, rho_hi);
+  PairArgs a{b.srcF,     b.segbox,   b.src_orig, b.meta,  b.tgtF, b.M_pad, b.n_chunks,
+             b.part,     b.near_cnt, b.near_idx, b.flags, rho_lo, rho_hi};
+  k_pair32<L, NP, MINB><<<grid, TPB32, smem, st>>>(a);
 }
 
 void launch_pair32(int layer, const EvalBufs& b, double rho_T, cudaStream_t st) {
@@ -596,20 +68,16 @@ void launch_finish32(int layer, const EvalBufs& b, int64_t /*n_delta*/, double s
                      double /*rho_T*/, cudaStream_t st) {
   const unsigned go = (unsigned)((b.M * 32 + 255) / 256);
   const unsigned gf = (unsigned)((b.M + 127) / 128);
+  OverflowArgs oa{b.srcF, b.src_orig, b.meta, b.tgtF, b.tgt64, b.near_cnt, b.src_xyz, b.src_w,
+                  b.dens, b.nrm, scale, b.flags, b.near_ovf};
+  FinishArgs fa{b.tgt64, b.tgt_perm, b.M_pad, b.n_chunks, b.part, b.near_cnt, b.near_idx,
+                b.near_ovf, b.src_xyz, b.src_w, b.dens, b.nrm, scale, b.u, b.flags};
   if (layer == LAYER_SL) {
-    k_overflow32<SLayer><<<go, 256, 0, st>>>(b.srcF, b.src_orig, b.meta, b.tgtF, b.tgt64, b.M,
-                                              b.near_cnt, b.src_xyz, b.src_w, b.dens, b.nrm, scale,
-                                              b.flags, b.near_ovf);
-    k_finish32<SLayer><<<gf, 128, 0, st>>>(b.tgt64, b.tgt_perm, b.M, b.M_pad, b.n_chunks, b.part,
-                                            b.near_cnt, b.near_idx, b.near_ovf, b.src_xyz, b.src_w,
-                                            b.dens, b.nrm, scale, b.u, b.flags);
+    k_overflow32<SLayer><<<go, 256, 0, st>>>(oa, b.M);
+    k_finish32<SLayer><<<gf, 128, 0, st>>>(fa, b.M);
   } else {
-    k_overflow32<DLayer><<<go, 256, 0, st>>>(b.srcF, b.src_orig, b.meta, b.tgtF, b.tgt64, b.M,
-                                              b.near_cnt, b.src_xyz, b.src_w, b.dens, b.nrm, scale,
-                                              b.flags, b.near_ovf);
-    k_finish32<DLayer><<<gf, 128, 0, st>>>(b.tgt64, b.tgt_perm, b.M, b.M_pad, b.n_chunks, b.part,
-                                            b.near_cnt, b.near_idx, b.near_ovf, b.src_xyz, b.src_w,
-                                            b.dens, b.nrm, scale, b.u, b.flags);
+    k_overflow32<DLayer><<<go, 256, 0, st>>>(oa, b.M);
+    k_finish32<DLayer><<<gf, 128, 0, st>>>(fa, b.M);
   }
 }
 

@@ -62,3 +62,13 @@ def test_library_fails_loudly_when_missing(monkeypatch, tmp_path):
 
 def test_build_flags_target_sm103a():
     assert "arch=compute_103a,code=sm_103a" in _build.ARCH
+
+
+def test_serving_entry_points_reject_null_arguments(lib):
+    import ctypes
+    h = ctypes.c_void_p()
+    assert lib.serve_create(None, None, ctypes.byref(h)) == sk.SK_EINVAL
+    t = ctypes.c_uint64()
+    assert lib.serve_submit(None, None, ctypes.byref(t)) == sk.SK_EINVAL
+    assert lib.serve_poll(None, ctypes.c_uint64(1), None, None, 0) == sk.SK_EINVAL
+    lib.serve_destroy(None)  # no-op

@@ -1,0 +1,156 @@
+"""Continuous-batching serving through the C ABI (needs a GB300).
+
+Each served request must equal stokes_sl_eval(SK_FP32C) on the same inputs
+bit for bit (same decomposition and order of every sum), alone and in any
+mix, and match the oracle within the FP32C tolerance.
+"""
+
+import time
+
+import numpy as np
+import pytest
+
+import capsule_inputs as ci
+from capsule_inputs.workloads import build_request
+import oracle
+
+sk = pytest.importorskip("paper_2310_13908_gb300")
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = sk.Context(0)
+    yield c.handle
+    c.close()
+
+
+def mixed_requests(n, m_choices=(9, 13, 17, 25, 33, 49, 65), seed=41):
+    rng = np.random.default_rng(seed)
+    specs = ci.serving_mix(n, seed=seed)
+    out = []
+    for s in specs:
+        s["m"] = int(rng.choice(m_choices))
+        surf, f, delta = build_request(s)
+        out.append((surf.X, surf.w, f, surf.X.copy(), np.array([delta])))
+    return out
+
+
+def submit_retry(srv, *args, tries=2000):
+    for _ in range(tries):
+        try:
+            return sk.serve_submit(srv, *args)
+        except sk.SkError as e:
+            if e.code != sk.SK_EBUSY:
+                raise
+            time.sleep(0.001)
+    raise TimeoutError("server stayed busy")
+
+
+def test_served_results_match_standalone_bitwise(ctx):
+    reqs = mixed_requests(16)
+    refs = [sk.stokes_sl_eval(ctx, sk.SK_FP32C, sk.SK_HOST, *r) for r in reqs]
+    srv = sk.serve_create(ctx, max_slots=6)
+    try:
+        tickets = [submit_retry(srv, *r) for r in reqs]
+        for t, r, ref in zip(tickets, reqs, refs):
+            code, u, st = sk.serve_poll(srv, t, r[3].shape[0], timeout_us=30_000_000)
+            assert code == sk.SK_OK
+            assert np.array_equal(u, ref)
+            assert st["interactions"] == r[3].shape[0] * np.count_nonzero(r[1])
+            assert st["submit_us"] <= st["admit_us"] <= st["publish_us"] <= st["done_us"] \
+                <= st["ready_us"]
+    finally:
+        sk.serve_destroy(srv)
+    # and the standalone path itself matches the oracle
+    for r, ref in list(zip(reqs, refs))[:3]:
+        o = oracle.sl(*r)
+        assert np.linalg.norm(ref - o) / np.linalg.norm(o) <= 1e-6
+
+
+def test_same_result_alone_and_in_the_mix(ctx):
+    reqs = mixed_requests(24, seed=43)
+    probe = reqs[5]
+    srv = sk.serve_create(ctx, max_slots=8)
+    try:
+        t = submit_retry(srv, *probe)
+        code, alone, _ = sk.serve_poll(srv, t, probe[3].shape[0], timeout_us=30_000_000)
+        assert code == sk.SK_OK
+        tickets = []
+        for i, r in enumerate(reqs):
+            tickets.append((submit_retry(srv, *r), r))
+            if i == 11:
+                tickets.append((submit_retry(srv, *probe), probe))
+        mixed = None
+        for tk, r in tickets:
+            code, u, _ = sk.serve_poll(srv, tk, r[3].shape[0], timeout_us=30_000_000)
+            assert code == sk.SK_OK
+            if r is probe:
+                mixed = u
+        assert mixed is not None and np.array_equal(mixed, alone)
+    finally:
+        sk.serve_destroy(srv)
+
+
+def test_busy_queue_and_too_large_request(ctx):
+    w = ci.rbc_workload()
+    s = w.surface
+    args = (s.X, s.w, w.f, w.targets, w.delta)
+    srv = sk.serve_create(ctx, max_slots=1, queue_capacity=1)
+    busy = 0
+    tickets = []
+    try:
+        for _ in range(6):
+            try:
+                tickets.append(sk.serve_submit(srv, *args))
+            except sk.SkError as e:
+                assert e.code == sk.SK_EBUSY
+                busy += 1
+        assert busy > 0
+        for t in tickets:
+            assert sk.serve_poll(srv, t, w.targets.shape[0], timeout_us=30_000_000)[0] == sk.SK_OK
+    finally:
+        sk.serve_destroy(srv)
+    small = sk.serve_create(ctx, hbm_budget_bytes=1 << 20)
+    try:
+        with pytest.raises(sk.SkError) as e:
+            sk.serve_submit(small, *args)
+        assert e.value.code == sk.SK_ENOMEM
+    finally:
+        sk.serve_destroy(small)
+
+
+def test_poll_modes_invalid_requests_and_relaunch(ctx):
+    r = mixed_requests(1, m_choices=(17,), seed=47)[0]
+    srv = sk.serve_create(ctx, idle_exit_us=2000)
+    try:
+        assert sk.serve_poll(srv, 123456, 3, timeout_us=0)[0] == sk.SK_EINVAL
+        with pytest.raises(sk.SkError) as e:
+            sk.serve_submit(srv, r[0], r[1], r[2], r[3], np.array([-1.0]))
+        assert e.value.code == sk.SK_EINVAL
+        t = sk.serve_submit(srv, *r)
+        code = sk.serve_poll(srv, t, r[3].shape[0], timeout_us=0)[0]
+        assert code in (sk.SK_EAGAIN, sk.SK_OK)
+        if code == sk.SK_EAGAIN:
+            assert sk.serve_poll(srv, t, r[3].shape[0], timeout_us=30_000_000)[0] == sk.SK_OK
+        time.sleep(0.05)  # the persistent kernel exits when idle ...
+        t = sk.serve_submit(srv, *r)  # ... and is relaunched for new work
+        code, u, _ = sk.serve_poll(srv, t, r[3].shape[0], timeout_us=30_000_000)
+        assert code == sk.SK_OK
+        assert np.array_equal(u, sk.stokes_sl_eval(ctx, sk.SK_FP32C, sk.SK_HOST, *r))
+    finally:
+        sk.serve_destroy(srv)
+
+
+def test_destroy_drains_pending_requests(ctx):
+    reqs = mixed_requests(8, seed=53)
+    srv = sk.serve_create(ctx, max_slots=2)
+    for r in reqs:
+        submit_retry(srv, *r)
+    sk.serve_destroy(srv)  # must finish the work and return
+    srv = sk.serve_create(ctx)  # the context can serve again
+    sk.serve_destroy(srv)
