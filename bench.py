@@ -210,6 +210,10 @@ def main():
         dist.init_process_group("nccl", device_id=dev)
         pg = dist
 
+    serve_future = None
+    if rank == 0 and world == 1 and not args.no_extras:
+        import concurrent.futures
+        serve_future = concurrent.futures.ThreadPoolExecutor(1).submit(build_serving_mix)
     w = workload(args.m, args.probes, rank)
     s = w.surface
     M = w.targets.shape[0]
@@ -315,7 +319,8 @@ def main():
             "overflow_targets": stats["overflow_targets"]}
 
     if rank == 0 and world == 1 and not args.no_extras:
-        line.update(extras(sk, h, w, X, W, F, Y, D, out, u_fp32, stream, dev, torch))
+        line.update(extras(sk, h, w, X, W, F, Y, D, out, u_fp32, stream, dev, torch,
+                           serve_future))
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -324,7 +329,86 @@ def main():
     return 0
 
 
-def extras(sk, h, w, X, W, F, Y, D, out, u_fp32, stream, dev, torch):
+SERVE_REQUESTS = 1000
+SERVE_LOADS = (0.3, 0.5, 0.7, 0.9)
+
+
+def build_serving_mix(n=SERVE_REQUESTS):
+    """The serving mix: n requests, ellipsoid or rotated cell, N = 6 n^2
+    log-uniform in [1536, 98304], seeded; arrays ready to submit."""
+    import capsule_inputs as ci
+    from capsule_inputs.workloads import build_request
+    out = []
+    for spec in ci.serving_mix(n):
+        surf, f, delta = build_request(spec)
+        out.append((surf.X, surf.w, f, surf.X, np.array([delta]), surf.n_active))
+    return out
+
+
+def run_serving(sk, h, reqs, arrivals=None):
+    """Serve reqs (all at once if arrivals is None, else at those times in s).
+    Returns (wall seconds, latencies in ms, interactions)."""
+    import collections
+    srv = sk.serve_create(h, max_slots=32)
+    n = len(reqs)
+    lat = [None] * n
+    inter = 0
+    outstanding = collections.OrderedDict()
+    nxt = 0
+    t0 = time.perf_counter()
+    while nxt < n or outstanding:
+        now = time.perf_counter() - t0
+        while nxt < n and (arrivals is None or arrivals[nxt] <= now):
+            X, W, F, Y, D, _ = reqs[nxt]
+            try:
+                tk = sk.serve_submit(srv, X, W, F, Y, D, 1.0)
+            except sk.SkError as e:
+                if e.code != sk.SK_EBUSY:
+                    raise
+                break
+            late_ms = 0.0 if arrivals is None else (time.perf_counter() - t0 - arrivals[nxt]) * 1e3
+            outstanding[tk] = (nxt, late_ms)
+            nxt += 1
+        progressed = False
+        for tk in list(outstanding):
+            i, late_ms = outstanding[tk]
+            code, _, st = sk.serve_poll(srv, tk, reqs[i][3].shape[0], timeout_us=0)
+            if code == sk.SK_EAGAIN:
+                continue
+            if code != sk.SK_OK:
+                raise RuntimeError(f"served request failed: {code}")
+            lat[i] = late_ms + (st["ready_us"] - st["submit_us"]) * 1e-3
+            inter += st["interactions"]
+            del outstanding[tk]
+            progressed = True
+        if not progressed:
+            time.sleep(50e-6)
+    wall = time.perf_counter() - t0
+    sk.serve_destroy(srv)
+    return wall, lat, inter
+
+
+def serving_bench(sk, h, reqs):
+    n = len(reqs)
+    run_serving(sk, h, reqs[:64])  # warm-up
+    wall, lat, inter = run_serving(sk, h, reqs)
+    cap = n / wall
+    res = {"requests": n, "mix": "ellipsoid (axes U[0.5,1]) or rotated Evans-Fung cell, "
+                                 "N = 6n^2 log-uniform in [1536, 98304], SH density, delta=2h",
+           "saturated": {"req_per_s": cap, "ginter_per_s": inter / wall / 1e9,
+                         "wall_s": wall, "p50_ms": float(np.percentile(lat, 50)),
+                         "p99_ms": float(np.percentile(lat, 99))}}
+    for frac in SERVE_LOADS:
+        rng = np.random.default_rng(int(frac * 1000))
+        arr = np.cumsum(rng.exponential(1.0 / (frac * cap), size=n))
+        wall, lat, inter = run_serving(sk, h, reqs, arr)
+        res[f"load_{frac}"] = {"lambda_req_per_s": frac * cap, "p50_ms": float(np.percentile(lat, 50)),
+                               "p99_ms": float(np.percentile(lat, 99)),
+                               "ginter_per_s": inter / wall / 1e9, "wall_s": wall}
+    return res
+
+
+def extras(sk, h, w, X, W, F, Y, D, out, u_fp32, stream, dev, torch, serve_future=None):
     import capsule_inputs as ci
     import oracle
     res = {}
@@ -417,6 +501,11 @@ def extras(sk, h, w, X, W, F, Y, D, out, u_fp32, stream, dev, torch):
     res["dl_rbc_m65"] = {"workload": f"rotated Evans-Fung cell m=65 N={rs.N} "
                                      f"(N_s={rs.n_active}), double layer, delta=2h",
                          "interactions": rinter, "flops_per_interaction": FLOPS_DL, **dl}
+    if serve_future is not None:
+        try:
+            res["serving"] = serving_bench(sk, h, serve_future.result())
+        except Exception as e:  # report, but keep the headline line
+            res["serving"] = {"error": repr(e)}
     return res
 
 

@@ -25,24 +25,27 @@ def real_sph_harm(lmax: int, x0: np.ndarray) -> np.ndarray:
     ph = np.arctan2(x0[:, 1], x0[:, 0])
     sint = np.sqrt(np.maximum(0.0, 1.0 - z * z))
     N = x0.shape[0]
-    out = np.zeros((N, (lmax + 1) ** 2))
+    out = np.empty(((lmax + 1) ** 2, N))  # rows are contiguous; returned transposed
     for mm in range(lmax + 1):
         # P_mm = (-1)^m (2m-1)!! sin^m
-        pmm = np.full(N, (-1.0) ** mm * _double_factorial(2 * mm - 1)) * sint ** mm
+        pmm = ((-1.0) ** mm * _double_factorial(2 * mm - 1)) * sint ** mm
         P = {mm: pmm}
         if mm + 1 <= lmax:
             P[mm + 1] = z * (2 * mm + 1) * pmm
         for ll in range(mm + 2, lmax + 1):
             P[ll] = ((2 * ll - 1) * z * P[ll - 1] - (ll + mm - 1) * P[ll - 2]) / (ll - mm)
+        if mm > 0:
+            cm, sm = np.cos(mm * ph), np.sin(mm * ph)
         for ll in range(mm, lmax + 1):
             norm = math.sqrt((2 * ll + 1) / (4 * math.pi)
                              * math.factorial(ll - mm) / math.factorial(ll + mm))
             if mm == 0:
-                out[:, ll * ll + ll] = norm * P[ll]
+                np.multiply(P[ll], norm, out=out[ll * ll + ll])
             else:
-                out[:, ll * ll + ll + mm] = math.sqrt(2.0) * norm * P[ll] * np.cos(mm * ph)
-                out[:, ll * ll + ll - mm] = math.sqrt(2.0) * norm * P[ll] * np.sin(mm * ph)
-    return out
+                a = (math.sqrt(2.0) * norm) * P[ll]
+                np.multiply(a, cm, out=out[ll * ll + ll + mm])
+                np.multiply(a, sm, out=out[ll * ll + ll - mm])
+    return out.T
 
 
 def _double_factorial(n: int) -> float:

@@ -16,6 +16,7 @@ The paper computes tangents by finite differences; here they are closed-form
 
 from __future__ import annotations
 
+import functools
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -254,27 +255,36 @@ class Surface:
         return int(np.count_nonzero(self.w))
 
 
+@functools.lru_cache(maxsize=48)
+def _sphere_grid(m: int):
+    """Shape-independent part of a surface of order m: grid, preimages on the
+    unit sphere, chart tangents and the POU value of the owning patch."""
+    patch, j, k, u, v, x0 = patch_grid(m)
+    du0 = np.empty_like(x0)
+    dv0 = np.empty_like(x0)
+    for i in range(1, 7):
+        sel = patch == i
+        du0[sel], dv0[sel] = chart_tangents(i, u[sel], v[sel])
+    psi = pou_all(x0)[np.arange(len(patch)), patch - 1]
+    for a in (patch, j, k, u, v, x0, du0, dv0, psi):
+        a.setflags(write=False)
+    return patch, j, k, u, v, x0, du0, dv0, psi
+
+
 def make_surface(shape, m: int) -> Surface:
     """Build grid, POU and weights for surface map `shape` at order m."""
-    patch, j, k, u, v, x0 = patch_grid(m)
+    patch, j, k, u, v, x0, du0, dv0, psi = _sphere_grid(m)
     h = np.pi / m
     J = shape.jacobian(x0)
     X = shape.phi(x0)
-    xu = np.empty_like(x0)
-    xv = np.empty_like(x0)
-    for i in range(1, 7):
-        sel = patch == i
-        du, dv = chart_tangents(i, u[sel], v[sel])
-        xu[sel] = np.einsum("nab,nb->na", J[sel], du)
-        xv[sel] = np.einsum("nab,nb->na", J[sel], dv)
+    xu = np.einsum("nab,nb->na", J, du0)
+    xv = np.einsum("nab,nb->na", J, dv0)
     cr = np.cross(xu, xv)
     W = np.linalg.norm(cr, axis=-1)
     nrm = cr / W[:, None]
-    psi_all = pou_all(x0)
-    psi = psi_all[np.arange(len(patch)), patch - 1]
     w = psi * W * h * h
     return Surface(m=m, h=h, patch=patch, j=j, k=k, x0=x0, X=X, W=W, n=nrm,
-                   psi=psi, w=w, shape=shape.describe())
+                   psi=psi.copy(), w=w, shape=shape.describe())
 
 
 def delta_star(surf: Surface, C: float = 1.0) -> np.ndarray:
