@@ -137,6 +137,54 @@ int stokes_dl_eval(sk_ctx* ctx, int precision, int mem,
                    const double* delta, int64_t n_delta,
                    double* u_out, void* cuda_stream);
 
+/* ---- capsule time stepping ----------------------------------------------
+ *
+ * A capsule keeps the N = 6 (m-1)^2 surface nodes of an m-th order grid
+ * resident on the device and advances them with explicit Euler steps of
+ * dx/dt = u_inf(x) + S[f](x) (Sec. 3.6, Eq. bi_combined): every step
+ * evaluates the regularized single layer at all nodes (targets = sources)
+ * and adds the background flow. Nodes are ordered patch-major, then by the
+ * u index j, then by the v index k (Sec. 3.2, Eq. grid). The quadrature
+ * weights w = psi W h^2 stay those given at creation (the finite-difference
+ * surface derivatives that would update W are not part of this library).
+ * One step is captured once into a CUDA graph and replayed. */
+typedef struct sk_capsule sk_capsule;
+
+#define SK_FLOW_NONE       0  /* u_inf = 0 */
+#define SK_FLOW_SHEAR      1  /* u_inf = (rate y, 0, 0)                  (Eq. shear_flow) */
+#define SK_FLOW_POISEUILLE 2  /* u_inf = (alpha (R0^2 - y^2 - z^2), 0, 0) (Eq. poiseuille_flow) */
+
+typedef struct {
+  int32_t kind;
+  double rate;   /* shear rate */
+  double alpha;  /* Poiseuille curvature */
+  double R0;     /* Poiseuille radius */
+} sk_flow;
+
+/* Create a capsule on ctx from host arrays (copied).
+ *   m      grid order (>= 3); X is [6 (m-1)^2][3], w is [6 (m-1)^2]
+ *   delta  NULL: delta = delta* recomputed on the device before every step
+ *          (largest distance from a node to its grid neighbours on its patch,
+ *          per patch, Eq. regparam with C = 1); otherwise [n_delta] fixed
+ *          values, n_delta in {1, N}
+ *   mu     viscosity > 0; precision SK_FP64 or SK_FP32C.
+ * Errors: SK_EINVAL, SK_ENOMEM, SK_ECUDA. */
+int capsule_create(sk_ctx* ctx, sk_capsule** out, int m, const double* X, const double* w,
+                   const double* delta, int64_t n_delta, double mu, int precision);
+
+/* Advance n_steps >= 0 Euler steps of size dt > 0 in the background flow
+ * (flow NULL: none) with the interfacial force density f [N][3] (host, held
+ * fixed over these steps). f = NULL would mean the Skalak membrane force of
+ * the current shape, which this build does not compute: SK_ENOTIMPL.
+ * Synchronous. Errors: SK_EINVAL, SK_ENOTIMPL, SK_ENOMEM, SK_ECUDA, SK_ETIMEOUT. */
+int capsule_step(sk_capsule* c, int n_steps, double dt, const sk_flow* flow, const double* f);
+
+/* Copy the current node positions [N][3] to host memory. */
+int capsule_get(sk_capsule* c, double* X_out);
+
+/* Release the capsule. NULL is ignored. */
+void capsule_destroy(sk_capsule* c);
+
 /* ---- serving: continuous batching of single-layer requests -------------
  *
  * A server keeps up to max_slots requests resident on the device and runs

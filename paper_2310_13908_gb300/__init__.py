@@ -82,6 +82,10 @@ _EXTRA_DECLS: dict = {
     "serve_submit": ([_vp, _vp, ctypes.POINTER(ctypes.c_uint64)], _int),
     "serve_poll": ([_vp, ctypes.c_uint64, _vp, _vp, ctypes.c_int64], _int),
     "serve_destroy": ([_vp], None),
+    "capsule_create": ([_vp, ctypes.POINTER(_vp), _int, _vp, _vp, _vp, _i64, _dbl, _int], _int),
+    "capsule_step": ([_vp, _int, _dbl, _vp, _vp], _int),
+    "capsule_get": ([_vp, _vp], _int),
+    "capsule_destroy": ([_vp], None),
 }
 
 
@@ -243,6 +247,48 @@ def stokes_dl_eval(ctx, precision: int, mem: int, src_xyz, src_w, src_n, q, tgt_
     if mem == SK_HOST and U is not u_out:
         np.copyto(u_out, U.reshape(np.shape(u_out)))
     return u_out
+
+
+SK_FLOW_NONE, SK_FLOW_SHEAR, SK_FLOW_POISEUILLE = 0, 1, 2
+
+
+class sk_flow(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("rate", ctypes.c_double), ("alpha", ctypes.c_double),
+                ("R0", ctypes.c_double)]
+
+
+class Capsule:
+    """Surface nodes advanced by explicit Euler steps (capsule_* of the C ABI)."""
+
+    def __init__(self, ctx, m: int, X, w, delta=None, mu: float = 1.0,
+                 precision: int = SK_FP32C):
+        Xa, N = _ptr(X, SK_HOST, (3,), "X")
+        Wa, _ = _ptr(w, SK_HOST, (), "w")
+        if N != 6 * (m - 1) ** 2:
+            raise ValueError("X must hold 6 (m-1)^2 nodes")
+        D, nd = (None, 0) if delta is None else _ptr(np.atleast_1d(delta), SK_HOST, (), "delta")
+        h = _vp()
+        _check(ctx, load().capsule_create(ctx, ctypes.byref(h), int(m), _host_ptr(Xa),
+                                          _host_ptr(Wa), _host_ptr(D), nd, float(mu),
+                                          int(precision)))
+        self.ctx, self.handle, self.N = ctx, h, N
+
+    def step(self, n_steps: int, dt: float, f, flow=None):
+        """flow: None or (kind, rate, alpha, R0)."""
+        F, _ = _ptr(f, SK_HOST, (3,), "f") if f is not None else (None, 0)
+        fl = ctypes.byref(sk_flow(*flow)) if flow is not None else None
+        _check(self.ctx, load().capsule_step(self.handle, int(n_steps), float(dt), fl,
+                                             _host_ptr(F)))
+
+    def positions(self):
+        X = np.empty((self.N, 3))
+        _check(self.ctx, load().capsule_get(self.handle, X.ctypes.data_as(_vp)))
+        return X
+
+    def close(self):
+        if self.handle:
+            load().capsule_destroy(self.handle)
+            self.handle = None
 
 
 class sk_serve_cfg(ctypes.Structure):

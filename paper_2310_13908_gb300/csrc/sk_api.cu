@@ -305,7 +305,7 @@ int sk_last_eval_stats(const sk_ctx* ctx, sk_eval_stats* out) {
 
 }  // extern "C"
 
-namespace {
+namespace sk {
 
 int ensure_workspace(sk_ctx* ctx, size_t need) {
   if (need <= ctx->ws_bytes) return SK_OK;
@@ -326,6 +326,10 @@ int ensure_workspace(sk_ctx* ctx, size_t need) {
   ctx->ws_bytes = want;
   return SK_OK;
 }
+
+}  // namespace sk
+
+namespace {
 
 int eval_entry(sk_ctx* ctx, int layer, int precision, int mem, int64_t N, const double* xyz,
                const double* w, const double* dens, const double* nrm, int64_t M,

@@ -1,0 +1,282 @@
+// sk_capsule.cu -- explicit Euler time stepping of a capsule's surface nodes
+// (Sec. 3.6, Eq. bi_combined) with the regularized single layer.
+//
+// The nodes stay resident in device memory. One step is: (optionally) the
+// patch-dependent regularization parameter delta* of Eq. regparam, the full
+// single-layer evaluation at all nodes, and the update
+// X += dt (S[f](X) + u_inf(X)). The step is captured once into a CUDA graph
+// and replayed n_steps times, so a step costs one graph launch on the host.
+#include <cstring>
+#include <new>
+
+#include "sk_internal.h"
+
+struct sk_capsule {
+  sk_ctx* ctx = nullptr;
+  int m = 0;
+  int64_t N = 0;
+  double* X = nullptr;
+  double* w = nullptr;
+  double* f = nullptr;
+  double* u = nullptr;
+  double* delta = nullptr;
+  int64_t n_delta = 0;
+  bool auto_delta = false;
+  unsigned long long* patch_max = nullptr;  // [6] delta* per patch (double bits)
+  unsigned long long* sticky = nullptr;     // [N_FLAGS] flags of all steps since the last call
+  double mu = 1.0;
+  int precision = SK_FP32C;
+  // captured step graph and the state it was captured for
+  cudaGraphExec_t exec = nullptr;
+  double g_dt = 0.0;
+  sk_flow g_flow{};
+  char* g_ws = nullptr;
+  size_t g_ws_bytes = 0;
+  double g_rho_T = 0.0, g_rho_c = 0.0;
+};
+
+namespace sk {
+namespace {
+
+// delta*_p = max over the nodes of patch p of the largest distance to an
+// existing grid neighbour (offsets a, b in {-1, 0, 1}) (Eq. regparam).
+__global__ void k_delta_star_patch(const double* __restrict__ X, int m,
+                                   unsigned long long* __restrict__ pmax) {
+  const int n = m - 1;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double best = 0.0;
+  int p = -1;
+  if (i < 6 * (int64_t)n * n) {
+    p = (int)(i / ((int64_t)n * n));
+    const int r = (int)(i % ((int64_t)n * n));
+    const int j = r / n, k = r % n;
+    const double x = X[3 * i], y = X[3 * i + 1], z = X[3 * i + 2];
+    for (int a = -1; a <= 1; ++a)
+      for (int b = -1; b <= 1; ++b) {
+        const int jj = j - a, kk = k - b;
+        if ((a == 0 && b == 0) || jj < 0 || jj >= n || kk < 0 || kk >= n) continue;
+        const int64_t q = (int64_t)p * n * n + (int64_t)jj * n + kk;
+        const double dx = x - X[3 * q], dy = y - X[3 * q + 1], dz = z - X[3 * q + 2];
+        best = fmax(best, sqrt(dx * dx + dy * dy + dz * dz));
+      }
+  }
+  // nonnegative doubles order like their bit patterns
+  if (p >= 0) atomicMax(pmax + p, (unsigned long long)__double_as_longlong(best));
+}
+
+__global__ void k_delta_fill(const unsigned long long* __restrict__ pmax, int m, double C,
+                             double* __restrict__ delta) {
+  const int n = m - 1;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < 6 * (int64_t)n * n) delta[i] = C * __longlong_as_double((long long)pmax[i / ((int64_t)n * n)]);
+}
+
+// X += dt (u + u_inf(X)); background flows of Eqs. shear_flow, poiseuille_flow.
+__global__ void k_euler(double* __restrict__ X, const double* __restrict__ u, int64_t N, double dt,
+                        sk_flow fl) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const double x = X[3 * i], y = X[3 * i + 1], z = X[3 * i + 2];
+  double ux = u[3 * i], uy = u[3 * i + 1], uz = u[3 * i + 2];
+  if (fl.kind == SK_FLOW_SHEAR) ux += fl.rate * y;
+  if (fl.kind == SK_FLOW_POISEUILLE) ux += fl.alpha * (fl.R0 * fl.R0 - y * y - z * z);
+  X[3 * i] = x + dt * ux;
+  X[3 * i + 1] = y + dt * uy;
+  X[3 * i + 2] = z + dt * uz;
+}
+
+__global__ void k_sticky(const unsigned long long* __restrict__ flags,
+                         unsigned long long* __restrict__ sticky) {
+  const int i = threadIdx.x;
+  if (i < N_FLAGS && flags[i]) atomicOr(sticky + i, flags[i]);
+}
+
+void free_capsule(sk_capsule* c) {
+  if (c->exec) cudaGraphExecDestroy(c->exec);
+  for (double* p : {c->X, c->w, c->f, c->u, c->delta})
+    if (p) cudaFree(p);
+  if (c->patch_max) cudaFree(c->patch_max);
+  if (c->sticky) cudaFree(c->sticky);
+  delete c;
+}
+
+inline unsigned blocks(int64_t n) { return (unsigned)((n + 255) / 256); }
+
+}  // namespace
+}  // namespace sk
+
+using namespace sk;
+
+extern "C" {
+
+int capsule_create(sk_ctx* ctx, sk_capsule** out, int m, const double* X, const double* w,
+                   const double* delta, int64_t n_delta, double mu, int precision) {
+  if (!ctx || !out) return SK_EINVAL;
+  *out = nullptr;
+  if (m < 3 || m > 16385 || !X || !w || !(mu > 0.0 && mu < INFINITY) ||
+      (precision != SK_FP64 && precision != SK_FP32C)) {
+    ctx->err = "capsule_create: need m >= 3, X and w, mu > 0, precision SK_FP64 or SK_FP32C";
+    return SK_EINVAL;
+  }
+  const int64_t N = 6 * (int64_t)(m - 1) * (m - 1);
+  if (delta) {
+    if (!(n_delta == 1 || n_delta == N)) {
+      ctx->err = "capsule_create: n_delta must be 1 or 6 (m-1)^2";
+      return SK_EINVAL;
+    }
+    for (int64_t i = 0; i < n_delta; ++i)
+      if (!(delta[i] > 0.0 && delta[i] < INFINITY)) {
+        ctx->err = "capsule_create: delta must be positive and finite";
+        return SK_EINVAL;
+      }
+  }
+  cudaSetDevice(ctx->device);
+  sk_capsule* c = new (std::nothrow) sk_capsule();
+  if (!c) return SK_ENOMEM;
+  c->ctx = ctx;
+  c->m = m;
+  c->N = N;
+  c->auto_delta = delta == nullptr;
+  c->n_delta = delta ? n_delta : N;
+  c->mu = mu;
+  c->precision = precision;
+  cudaError_t e = cudaSuccess;
+  auto ok = [&](cudaError_t x) {
+    if (x != cudaSuccess && e == cudaSuccess) e = x;
+  };
+  ok(cudaMalloc(&c->X, 3 * N * sizeof(double)));
+  ok(cudaMalloc(&c->w, N * sizeof(double)));
+  ok(cudaMalloc(&c->f, 3 * N * sizeof(double)));
+  ok(cudaMalloc(&c->u, 3 * N * sizeof(double)));
+  ok(cudaMalloc(&c->delta, c->n_delta * sizeof(double)));
+  ok(cudaMalloc(&c->patch_max, 8 * sizeof(unsigned long long)));
+  ok(cudaMalloc(&c->sticky, N_FLAGS * sizeof(unsigned long long)));
+  if (e == cudaSuccess) {
+    ok(cudaMemcpy(c->X, X, 3 * N * sizeof(double), cudaMemcpyHostToDevice));
+    ok(cudaMemcpy(c->w, w, N * sizeof(double), cudaMemcpyHostToDevice));
+    if (delta) ok(cudaMemcpy(c->delta, delta, n_delta * sizeof(double), cudaMemcpyHostToDevice));
+    ok(cudaMemset(c->f, 0, 3 * N * sizeof(double)));
+  }
+  if (e != cudaSuccess) {
+    ctx->err = std::string("capsule_create: ") + cudaGetErrorString(e);
+    free_capsule(c);
+    return e == cudaErrorMemoryAllocation ? SK_ENOMEM : SK_ECUDA;
+  }
+  *out = c;
+  return SK_OK;
+}
+
+int capsule_step(sk_capsule* c, int n_steps, double dt, const sk_flow* flow, const double* f) {
+  if (!c) return SK_EINVAL;
+  sk_ctx* ctx = c->ctx;
+  if (n_steps < 0 || !(dt > 0.0 && dt < INFINITY) ||
+      (flow && (flow->kind < SK_FLOW_NONE || flow->kind > SK_FLOW_POISEUILLE))) {
+    ctx->err = "capsule_step: need n_steps >= 0, dt > 0 and a known flow kind";
+    return SK_EINVAL;
+  }
+  if (!f) {
+    ctx->err = "capsule_step: the Skalak membrane force (f = NULL) is not built in this library";
+    return SK_ENOTIMPL;
+  }
+  if (n_steps == 0) return SK_OK;
+  cudaSetDevice(ctx->device);
+  cudaStream_t st = ctx->stream;
+  const sk_flow fl = flow ? *flow : sk_flow{SK_FLOW_NONE, 0.0, 0.0, 0.0};
+  cudaError_t e = cudaMemcpyAsync(c->f, f, 3 * c->N * sizeof(double), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return SK_ECUDA;
+  EvalShape s;
+  s.layer = LAYER_SL;
+  s.precision = c->precision;
+  s.N = c->N;
+  s.M = c->N;
+  s.n_delta = c->n_delta;
+  s.mu = c->mu;
+  s.copy_inputs = false;
+  s.n_chunks = choose_chunks(c->precision, c->N, c->N, ctx->sm_count);
+  int rc = ensure_workspace(ctx, eval_workspace_bytes(s));
+  if (rc != SK_OK) return rc;
+  const bool stale = !c->exec || c->g_dt != dt || std::memcmp(&c->g_flow, &fl, sizeof(fl)) != 0 ||
+                     c->g_ws != ctx->ws || c->g_ws_bytes != ctx->ws_bytes ||
+                     c->g_rho_T != ctx->rho_T || c->g_rho_c != ctx->rho_c;
+  if (stale) {
+    if (c->exec) cudaGraphExecDestroy(c->exec);
+    c->exec = nullptr;
+    EvalBufs b;
+    Bump bp;
+    bp.base = ctx->ws;
+    carve_eval_buffers(bp, s, b);
+    b.src_xyz = c->X;
+    b.src_w = c->w;
+    b.dens = c->f;
+    b.tgt_xyz = c->X;
+    b.delta = c->delta;
+    b.u = c->u;
+    cudaGraph_t g = nullptr;
+    if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
+      ctx->err = std::string("capsule_step: capture: ") + cudaGetErrorString(e);
+      return SK_ECUDA;
+    }
+    if (c->auto_delta) {
+      cudaMemsetAsync(c->patch_max, 0, 8 * sizeof(unsigned long long), st);
+      k_delta_star_patch<<<blocks(c->N), 256, 0, st>>>(c->X, c->m, c->patch_max);
+      k_delta_fill<<<blocks(c->N), 256, 0, st>>>(c->patch_max, c->m, 1.0, c->delta);
+    }
+    enqueue_eval(s, b, ctx->rho_T, ctx->rho_c, st);
+    k_sticky<<<1, 32, 0, st>>>(b.flags, c->sticky);
+    k_euler<<<blocks(c->N), 256, 0, st>>>(c->X, c->u, c->N, dt, fl);
+    e = cudaStreamEndCapture(st, &g);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&c->exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      c->exec = nullptr;
+      ctx->err = std::string("capsule_step: graph: ") + cudaGetErrorString(e);
+      return SK_ECUDA;
+    }
+    c->g_dt = dt;
+    c->g_flow = fl;
+    c->g_ws = ctx->ws;
+    c->g_ws_bytes = ctx->ws_bytes;
+    c->g_rho_T = ctx->rho_T;
+    c->g_rho_c = ctx->rho_c;
+  }
+  cudaMemsetAsync(c->sticky, 0, N_FLAGS * sizeof(unsigned long long), st);
+  for (int i = 0; i < n_steps; ++i)
+    if ((e = cudaGraphLaunch(c->exec, st)) != cudaSuccess) break;
+  unsigned long long flags[N_FLAGS] = {};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(flags, c->sticky, sizeof(flags), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    ctx->err = std::string("capsule_step: ") + cudaGetErrorString(e);
+    return SK_ECUDA;
+  }
+  ctx->last_stream = st;
+  if (flags[FLAG_TIMEOUT]) {
+    ctx->err = "capsule_step: a bounded device wait expired";
+    return SK_ETIMEOUT;
+  }
+  if (flags[FLAG_BAD_DELTA]) {
+    ctx->err = "capsule_step: delta must be positive and finite";
+    return SK_EINVAL;
+  }
+  return SK_OK;
+}
+
+int capsule_get(sk_capsule* c, double* X_out) {
+  if (!c || !X_out) return SK_EINVAL;
+  cudaSetDevice(c->ctx->device);
+  cudaError_t e = cudaMemcpy(X_out, c->X, 3 * c->N * sizeof(double), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) {
+    c->ctx->err = std::string("capsule_get: ") + cudaGetErrorString(e);
+    return SK_ECUDA;
+  }
+  return SK_OK;
+}
+
+void capsule_destroy(sk_capsule* c) {
+  if (!c) return;
+  cudaSetDevice(c->ctx->device);
+  cudaStreamSynchronize(c->ctx->stream);
+  free_capsule(c);
+}
+
+}  // extern "C"

@@ -151,6 +151,9 @@ struct EvalShape {
 };
 
 // sk_api.cu
+// Grow the context workspace to `need` bytes (synchronizes the device when it
+// reallocates); SK_ENOMEM for a fixed workspace that is too small.
+int ensure_workspace(sk_ctx* ctx, size_t need);
 size_t eval_workspace_bytes(const EvalShape& s);
 void carve_eval_buffers(Bump& bp, const EvalShape& s, EvalBufs& b);
 int choose_chunks(int precision, int64_t N, int64_t M, int sm_count);

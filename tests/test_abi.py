@@ -72,3 +72,12 @@ def test_serving_entry_points_reject_null_arguments(lib):
     assert lib.serve_submit(None, None, ctypes.byref(t)) == sk.SK_EINVAL
     assert lib.serve_poll(None, ctypes.c_uint64(1), None, None, 0) == sk.SK_EINVAL
     lib.serve_destroy(None)  # no-op
+
+
+def test_capsule_entry_points_reject_null_arguments(lib):
+    import ctypes
+    h = ctypes.c_void_p()
+    assert lib.capsule_create(None, ctypes.byref(h), 9, None, None, None, 0, 1.0, 1) == sk.SK_EINVAL
+    assert lib.capsule_step(None, 1, 0.1, None, None) == sk.SK_EINVAL
+    assert lib.capsule_get(None, None) == sk.SK_EINVAL
+    lib.capsule_destroy(None)  # no-op
