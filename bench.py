@@ -172,25 +172,56 @@ def run_reference(args):
     return 0
 
 
+# ----------------------------------------------------------------------------- ranks
+
+def max_over_ranks(x, pg=None, device=None):
+    """Largest x over all ranks (x itself without a process group)."""
+    if pg is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, units_per_rank, seconds):
+    """Whole-job rate in G units/s: every rank processes its own copy of the
+    workload (weak scaling), the job takes as long as its slowest rank."""
+    return world * units_per_rank / seconds / 1e9
+
+
 # ----------------------------------------------------------------------------- our arm
 
 def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-def traffic_from_profile(kernel_file):
-    """DRAM bytes per pair-kernel launch from the committed ncu summary, if it
-    was taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "pair32_traffic.json")
+PAIR32_SOURCES = ("sk_pair32.cuh", "sk_pair32.cu", "sk_series.cuh", "sk_internal.h")
+
+
+def pair32_source_hash():
+    h = hashlib.sha256()
+    for name in PAIR32_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2310_13908_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()
+
+
+def traffic_from_profile():
+    """DRAM bytes per pair-kernel launch (full-size workload) from the committed
+    ncu summary, if it was taken on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "pair32_dram_traffic.txt")
     if not os.path.exists(path):
         return None
+    rec = {}
+    for line in open(path):
+        if ":" in line and not line.startswith("#"):
+            k, v = line.split(":", 1)
+            rec[k.strip()] = v.strip()
     try:
-        rec = json.load(open(path))
-        src = open(kernel_file, "rb").read()
-        if rec.get("source_sha256") != hashlib.sha256(src).hexdigest():
+        if rec.get("source_sha256") != pair32_source_hash():
             return None
-        return rec.get("dram_bytes_per_launch_full_size")
-    except Exception:
+        return float(rec["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
         return None
 
 
@@ -257,15 +288,13 @@ def main():
         pair_ms.append(st["pair_ms"])
         launches += st["kernel_launches"]
     torch.cuda.synchronize(dev)
+    if pg:
+        pg.barrier()
     wall = time.perf_counter() - t_wall0
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    t_step = float(np.mean(step_ms))
-    if pg:
-        tt = torch.tensor([t_step], device=dev)
-        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-        t_step = float(tt.item())
-    value = world * inter / (t_step * 1e-3) / 1e9
+    t_step = max_over_ranks(np.mean(step_ms), pg, dev)
+    value = job_throughput(world, inter, t_step * 1e-3)
     u_fp32 = out.cpu().numpy()
     stats = sk.sk_last_eval_stats(h)
 
@@ -273,8 +302,7 @@ def main():
     achieved = FLOPS_SL * inter / (pair_avg * 1e-3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
-                "traffic": traffic_from_profile(
-                    os.path.join(ROOT, "paper_2310_13908_gb300", "csrc", "sk_pair32.cu")),
+                "traffic": traffic_from_profile(),
                 "kernel": "k_pair32<SLayer>", "pair_ms": pair_avg,
                 "flops_per_interaction": FLOPS_SL,
                 "peak_basis": "2 x 128 FP32 lanes x 152 SMs x 2070 MHz (max SM clock)"}
@@ -298,9 +326,9 @@ def main():
         t0 = time.perf_counter()
         sk.stokes_sl_eval(h, sk.SK_FP32C, sk.SK_HOST, hX, hW, hF, hY, hD, 1.0, u_out=hU)
         e2e_t.append(time.perf_counter() - t0)
-    e2e_step = float(np.mean(e2e_t))
+    e2e_step = max_over_ranks(np.mean(e2e_t), pg, dev)
     h2d = (hX.nbytes + hW.nbytes + hF.nbytes + hY.nbytes + hD.nbytes)
-    e2e = {"value": world * inter / e2e_step / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+    e2e = {"value": job_throughput(world, inter, e2e_step), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
            "d2h_bytes_per_step": int(hU.nbytes), "ms_per_step": e2e_step * 1e3,
            "path": "stokes_sl_eval(SK_FP32C, SK_HOST), pinned host buffers, synchronous"}
 

@@ -1,0 +1,70 @@
+"""The multi-GPU path of the benchmark on CPU: two gloo ranks.
+
+The path shards by replication: every rank evaluates its own seeded copy of
+the workload with no collective on the data path; the only communication is
+the barrier and the max-over-ranks reduction of the step time.
+"""
+
+import os
+import socket
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+import bench  # noqa: E402
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        local_ms = 10.0 + 5.0 * rank  # rank 1 is the slow one
+        t = bench.max_over_ranks(local_ms, dist, "cpu")
+        dist.barrier()
+        out[rank] = t
+        out[world + rank] = bench.job_throughput(world, 1e9, t * 1e-3)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_max_over_ranks_and_weak_scaling_value_two_gloo_ranks():
+    world = 2
+    out = mp.get_context("spawn").Array("d", 2 * world)
+    mp.start_processes(_rank_main, args=(world, _free_port(), out), nprocs=world,
+                       start_method="spawn", join=True)
+    assert list(out[:world]) == [15.0, 15.0]
+    # 2 ranks x 1e9 units each in 15 ms: 2 / 0.015 G units/s, same on both ranks
+    assert np.allclose(out[world:], 2.0 / 0.015)
+
+
+def test_single_process_helpers():
+    assert bench.max_over_ranks(3.5) == 3.5
+    assert bench.job_throughput(1, 2e9, 2.0) == 1.0
+
+
+def test_replicas_get_distinct_seeded_workloads():
+    w0 = bench.workload(17, 10, rank=0)
+    w1 = bench.workload(17, 10, rank=1)
+    assert not np.array_equal(w0.f, w1.f)
+    assert np.array_equal(w0.f, bench.workload(17, 10, rank=0).f)
+
+
+def test_reference_arm_other_ranks_exit_without_work(monkeypatch):
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+
+    class A:
+        m, probes, warmup, steps = 17, 10, 1, 1
+
+    assert bench.run_reference(A) == 0
