@@ -196,7 +196,7 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-PAIR32_SOURCES = ("sk_pair32.cuh", "sk_pair32.cu", "sk_series.cuh", "sk_internal.h")
+PAIR32_SOURCES = ("sk_pair32.cuh", "sk_pair32.cu", "sk_series.cuh", "sk_internal.h", "sk_api.cu")
 
 
 def pair32_source_hash():
@@ -247,6 +247,8 @@ def main():
         serve_future = concurrent.futures.ThreadPoolExecutor(1).submit(build_serving_mix)
     w = workload(args.m, args.probes, rank)
     s = w.surface
+    if serve_future is not None:
+        serve_future.result()  # keep the host idle (no GIL contention) while timing
     M = w.targets.shape[0]
     Ns = s.n_active
     inter = M * Ns

@@ -15,7 +15,10 @@ namespace sk {
 constexpr int SEG = 32;                 // sources per segment (near/far classification unit)
 constexpr int TILE_SEGS = 8;
 constexpr int TILE = SEG * TILE_SEGS;   // sources per shared-memory tile (FP32 kernels)
-constexpr int TPB32 = 256;              // threads per CTA, FP32 kernels
+#ifndef SK_TPB32
+#define SK_TPB32 256
+#endif
+constexpr int TPB32 = SK_TPB32;         // threads per CTA, FP32 kernels
 constexpr int TPL32 = 4;                // targets per lane (two f32x2 pairs)
 constexpr int TGT_WARP32 = 32 * TPL32;  // 128 targets per warp
 constexpr int TGT_CTA32 = TPB32 * TPL32;
@@ -114,7 +117,14 @@ struct EvalBufs {
 // (more warps, smaller target blocks) otherwise.
 constexpr int64_t PAIR32_NP1_MAX_TARGETS = 131072;
 inline int pair32_np(int64_t M) { return M > PAIR32_NP1_MAX_TARGETS ? 2 : 1; }
-inline int pair32_ctas_per_sm(int np) { return np == 2 ? 2 : 3; }
+#ifndef SK_MINB_NP2
+#define SK_MINB_NP2 (512 / SK_TPB32)
+#endif
+#ifndef SK_MINB_NP1
+#define SK_MINB_NP1 (768 / SK_TPB32)
+#endif
+constexpr int PAIR32_MINB_NP2 = SK_MINB_NP2, PAIR32_MINB_NP1 = SK_MINB_NP1;
+inline int pair32_ctas_per_sm(int np) { return np == 2 ? PAIR32_MINB_NP2 : PAIR32_MINB_NP1; }
 
 }  // namespace sk
 

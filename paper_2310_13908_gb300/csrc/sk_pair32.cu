@@ -39,9 +39,9 @@ __global__ void __launch_bounds__(128) k_finish32(FinishArgs a, int64_t M) {
 
 template <class L, int NP>
 void launch_pair32_t(const EvalBufs& b, float rho_lo, float rho_hi, cudaStream_t st) {
-  constexpr int MINB = NP == 2 ? 2 : 3;
+  constexpr int MINB = NP == 2 ? PAIR32_MINB_NP2 : PAIR32_MINB_NP1;
   const unsigned grid = (unsigned)((b.M_pad / (TPB32 * 2 * NP)) * b.n_chunks);
-  const size_t smem = L::STAGES * TILE * L::V * sizeof(float4);
+  const size_t smem = pair_smem_bytes<L, NP>();
   cudaFuncSetAttribute(k_pair32<L, NP, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)smem);
   PairArgs a{b.srcF,     b.segbox,   b.src_orig, b.meta,  b.tgtF, b.M_pad, b.n_chunks,

@@ -35,6 +35,7 @@
 #define SK_FAR_UNROLL 8
 #endif
 
+
 namespace sk {
 namespace p32 {
 
@@ -258,6 +259,15 @@ __device__ __forceinline__ void two_sum_merge(float2* U, float2* HI, float2* LO)
   }
 }
 
+// Where the compensated accumulators of a configuration live, and the dynamic
+// shared memory a pair item needs (source stages, plus the accumulators).
+__host__ __device__ constexpr bool hilo_in_smem(int np) { return np == 1; }
+template <class L, int NP>
+constexpr size_t pair_smem_bytes() {
+  return L::STAGES * TILE * L::V * sizeof(float4) +
+         (hilo_in_smem(NP) ? (size_t)NP * 6 * TPB32 * sizeof(float2) : 0);
+}
+
 // Shared-memory state of the source pipeline of one CTA.
 template <int STAGES>
 struct PipeSmem {
@@ -351,11 +361,21 @@ __device__ __forceinline__ bool pair_item(const PairArgs& a, int tb, int ch, flo
   const bool warp_live = rc2max >= 0.f;
   const float rc2test = rc2max * 1.0001f;
 
+  // Compensated accumulators: registers for two pairs per lane; shared
+  // memory (touched once per 128 sources) for one pair per lane, where the
+  // freed registers buy the third resident CTA without spills.
+  constexpr bool kHiLoSmem = hilo_in_smem(NP);
   float2 U[NP][3], HI[NP][3], LO[NP][3];
+  // [(p * 3 + c) * 2 + {0: hi, 1: lo}][thread]: one float2 column per thread
+  float2* acc = reinterpret_cast<float2*>(sm + STAGES * TILE * V);
 #pragma unroll
   for (int p = 0; p < NP; ++p)
 #pragma unroll
     for (int c = 0; c < 3; ++c) U[p][c] = HI[p][c] = LO[p][c] = make_float2(0.f, 0.f);
+  if constexpr (kHiLoSmem) {
+#pragma unroll
+    for (int i = 0; i < NP * 6; ++i) acc[i * TPB32 + tid] = make_float2(0.f, 0.f);
+  }
 
   // ---- source pipeline: no CTA-wide barrier inside the loop; the last warp
   // to release a stage issues the next bulk copy into it.
@@ -439,7 +459,23 @@ __device__ __forceinline__ bool pair_item(const PairArgs& a, int tb, int ch, flo
         }
         if ((s & 3) == 3) {
 #pragma unroll
-          for (int p = 0; p < NP; ++p) two_sum_merge(U[p], HI[p], LO[p]);
+          for (int p = 0; p < NP; ++p) {
+            if constexpr (kHiLoSmem) {
+#pragma unroll
+              for (int c = 0; c < 3; ++c) {
+                HI[p][c] = acc[((p * 3 + c) * 2) * TPB32 + tid];
+                LO[p][c] = acc[((p * 3 + c) * 2 + 1) * TPB32 + tid];
+              }
+            }
+            two_sum_merge(U[p], HI[p], LO[p]);
+            if constexpr (kHiLoSmem) {
+#pragma unroll
+              for (int c = 0; c < 3; ++c) {
+                acc[((p * 3 + c) * 2) * TPB32 + tid] = HI[p][c];
+                acc[((p * 3 + c) * 2 + 1) * TPB32 + tid] = LO[p][c];
+              }
+            }
+          }
         }
       }
     }
@@ -475,8 +511,10 @@ __device__ __forceinline__ bool pair_item(const PairArgs& a, int tb, int ch, flo
       double* o = a.part + ((size_t)ch * a.M_pad + t) * 3;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const float hv = h ? HI[p][c].y : HI[p][c].x;
-        const float lv = h ? LO[p][c].y : LO[p][c].x;
+        const float2 H2 = kHiLoSmem ? acc[((p * 3 + c) * 2) * TPB32 + tid] : HI[p][c];
+        const float2 L2 = kHiLoSmem ? acc[((p * 3 + c) * 2 + 1) * TPB32 + tid] : LO[p][c];
+        const float hv = h ? H2.y : H2.x;
+        const float lv = h ? L2.y : L2.x;
         o[c] = (double)hv + (double)lv;
       }
     }
