@@ -382,6 +382,7 @@ def run_serving(sk, h, reqs, arrivals=None):
     srv = sk.serve_create(h, max_slots=32)
     n = len(reqs)
     lat = [None] * n
+    phases = []
     inter = 0
     outstanding = collections.OrderedDict()
     nxt = 0
@@ -408,6 +409,8 @@ def run_serving(sk, h, reqs, arrivals=None):
             if code != sk.SK_OK:
                 raise RuntimeError(f"served request failed: {code}")
             lat[i] = late_ms + (st["ready_us"] - st["submit_us"]) * 1e-3
+            phases.append((st["admit_us"] - st["submit_us"], st["publish_us"] - st["admit_us"],
+                           st["done_us"] - st["publish_us"], st["ready_us"] - st["done_us"]))
             inter += st["interactions"]
             del outstanding[tk]
             progressed = True
@@ -415,6 +418,9 @@ def run_serving(sk, h, reqs, arrivals=None):
             time.sleep(50e-6)
     wall = time.perf_counter() - t0
     sk.serve_destroy(srv)
+    ph = np.mean(np.array(phases), axis=0) * 1e-3
+    run_serving.last_phases_ms = {"queue": ph[0], "prepare": ph[1], "device": ph[2],
+                                  "copy_back": ph[3]}
     return wall, lat, inter
 
 
@@ -427,14 +433,16 @@ def serving_bench(sk, h, reqs):
                                  "N = 6n^2 log-uniform in [1536, 98304], SH density, delta=2h",
            "saturated": {"req_per_s": cap, "ginter_per_s": inter / wall / 1e9,
                          "wall_s": wall, "p50_ms": float(np.percentile(lat, 50)),
-                         "p99_ms": float(np.percentile(lat, 99))}}
+                         "p99_ms": float(np.percentile(lat, 99)),
+                         "mean_phase_ms": run_serving.last_phases_ms}}
     for frac in SERVE_LOADS:
         rng = np.random.default_rng(int(frac * 1000))
         arr = np.cumsum(rng.exponential(1.0 / (frac * cap), size=n))
         wall, lat, inter = run_serving(sk, h, reqs, arr)
         res[f"load_{frac}"] = {"lambda_req_per_s": frac * cap, "p50_ms": float(np.percentile(lat, 50)),
                                "p99_ms": float(np.percentile(lat, 99)),
-                               "ginter_per_s": inter / wall / 1e9, "wall_s": wall}
+                               "ginter_per_s": inter / wall / 1e9, "wall_s": wall,
+                               "mean_phase_ms": run_serving.last_phases_ms}
     return res
 
 
@@ -531,6 +539,36 @@ def extras(sk, h, w, X, W, F, Y, D, out, u_fp32, stream, dev, torch, serve_futur
     res["dl_rbc_m65"] = {"workload": f"rotated Evans-Fung cell m=65 N={rs.N} "
                                      f"(N_s={rs.n_active}), double layer, delta=2h",
                          "interactions": rinter, "flops_per_interaction": FLOPS_DL, **dl}
+    # double layer at a size that fills the GPU: ellipsoid m=193 (221,184 nodes)
+    try:
+        ew = ci.ellipsoid_hires_workload(m=193, n_probes=0, seed=3300)
+        es = ew.surface
+        eq = ci.sh_density(es.x0, np.random.default_rng(33), lmax=8)
+        EX, EW, EN, EQ, EY, ED = (td(a) for a in (es.X, es.w, es.n, eq, ew.targets, ew.delta))
+        eout = torch.empty((ew.targets.shape[0], 3), dtype=torch.float64, device=dev)
+        for _ in range(2):
+            sk.stokes_dl_eval(h, sk.SK_FP32C, sk.SK_DEVICE, EX, EW, EN, EQ, EY, ED, u_out=eout,
+                              stream=stream)
+        pms = []
+        for _ in range(3):
+            sk.stokes_dl_eval(h, sk.SK_FP32C, sk.SK_DEVICE, EX, EW, EN, EQ, EY, ED, u_out=eout,
+                              stream=stream)
+            pms.append(sk.sk_last_eval_stats(h)["pair_ms"])
+        einter = ew.targets.shape[0] * es.n_active
+        eidx = np.random.default_rng(6).choice(ew.targets.shape[0], 512, replace=False)
+        eref = oracle.dl(es.X, es.w, es.n, eq, ew.targets[eidx], ew.delta)
+        ach = FLOPS_DL * einter / (np.mean(pms) * 1e-3) / 1e12
+        res["dl_ellipsoid_m193"] = {
+            "workload": f"ellipsoid(1,0.8,0.5) m=193 N={es.N} (N_s={es.n_active}), double layer, "
+                        "delta=2h, targets = nodes",
+            "value": einter / (np.mean(pms) * 1e-3) / 1e9, "unit": UNIT,
+            "rel_l2_vs_oracle_512": rel_l2(eout.cpu().numpy()[eidx], eref),
+            "roofline": {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS,
+                         "kernel": "k_pair32<DLayer>", "pair_ms": float(np.mean(pms)),
+                         "flops_per_interaction": FLOPS_DL}}
+    except Exception as e:
+        res["dl_ellipsoid_m193"] = {"error": repr(e)}
     if serve_future is not None:
         try:
             res["serving"] = serving_bench(sk, h, serve_future.result())
