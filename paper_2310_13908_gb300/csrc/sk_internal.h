@@ -58,6 +58,20 @@ constexpr long long WAIT_CYCLES = 2000000000LL;
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+#ifdef __CUDACC__
+// Local frame of a group of points (the 32 sources of a segment, the targets
+// of a warp): the FP32 midpoint of the group's FP32 bounding box, 0 for an
+// empty box (lo > hi). The FP32 pair kernels store coordinates relative to
+// these frames, taken from the FP64 input, so a source-target difference is
+// accurate to FP32 rounding of |x - y| plus the frames' extents rather than of
+// |x| and |y|. That matters for the stresslet, whose (x - y) . n cancels to
+// O(r^2) for close pairs on the surface. Pack, pair and rescan kernels all
+// call this one definition, so they agree bit for bit.
+__device__ __forceinline__ float frame_mid(float lo, float hi) {
+  return lo <= hi ? __fmul_rn(__fadd_rn(lo, hi), 0.5f) : 0.f;
+}
+#endif
+
 // Bump allocator over one device buffer; a null base only measures.
 struct Bump {
   char* base = nullptr;

@@ -11,7 +11,7 @@ template <class L, int NP, int MINB>
 __global__ void __launch_bounds__(TPB32, MINB)
     k_pair32(PairArgs a) {
   extern __shared__ __align__(128) float4 sm[];
-  __shared__ PipeSmem<L::STAGES> ps;
+  __shared__ PipeSmem<pair_stages<L, NP>()> ps;
   if (threadIdx.x == 0) ps.initialized = 0;
   const int tb = blockIdx.x / a.n_chunks, ch = blockIdx.x % a.n_chunks;
   pair_item<L, NP>(a, tb, ch, sm, ps);
@@ -44,8 +44,8 @@ void launch_pair32_t(const EvalBufs& b, float rho_lo, float rho_hi, cudaStream_t
   const size_t smem = pair_smem_bytes<L, NP>();
   cudaFuncSetAttribute(k_pair32<L, NP, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)smem);
-  PairArgs a{b.srcF,     b.segbox,   b.src_orig, b.meta,  b.tgtF, b.M_pad, b.n_chunks,
-             b.part,     b.near_cnt, b.near_idx, b.flags, rho_lo, rho_hi};
+  PairArgs a{b.srcF,  b.segbox,   b.src_orig, b.meta,     b.tgtF,  b.tgt64, b.M_pad,
+             b.n_chunks, b.part, b.near_cnt, b.near_idx, b.flags, rho_lo, rho_hi};
   k_pair32<L, NP, MINB><<<grid, TPB32, smem, st>>>(a);
 }
 
@@ -68,8 +68,8 @@ void launch_finish32(int layer, const EvalBufs& b, int64_t /*n_delta*/, double s
                      double /*rho_T*/, cudaStream_t st) {
   const unsigned go = (unsigned)((b.M * 32 + 255) / 256);
   const unsigned gf = (unsigned)((b.M + 127) / 128);
-  OverflowArgs oa{b.srcF, b.src_orig, b.meta, b.tgtF, b.tgt64, b.near_cnt, b.src_xyz, b.src_w,
-                  b.dens, b.nrm, scale, b.flags, b.near_ovf};
+  OverflowArgs oa{b.srcF, b.segbox, b.src_orig, b.meta,  b.tgtF,  b.tgt64,     b.near_cnt,
+                  b.src_xyz, b.src_w, b.dens,   b.nrm, scale, b.flags, b.near_ovf};
   FinishArgs fa{b.tgt64, b.tgt_perm, b.M_pad, b.n_chunks, b.part, b.near_cnt, b.near_idx,
                 b.near_ovf, b.src_xyz, b.src_w, b.dens, b.nrm, scale, b.u, b.flags};
   if (layer == LAYER_SL) {

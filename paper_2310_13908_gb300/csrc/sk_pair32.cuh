@@ -18,6 +18,14 @@
 // owns NP f32x2 target pairs, so every arithmetic instruction of the far loop
 // is a packed FFMA2/FADD2/FMUL2.
 //
+// Coordinates: a source is stored relative to its segment's frame (the FP32
+// midpoint of the segment's box, differenced in FP64 when packed); a target
+// keeps an FP32 (hi, lo) split and is moved into each segment's frame once per
+// segment. A pair difference x - y then carries FP32 rounding of |x - c| and
+// |y - c| instead of |x| and |y|: for the stresslet's (x - y) . n, which
+// cancels to O(r^2) on the surface, this removes an error that grew like
+// 1/delta with absolute FP32 coordinates.
+//
 // Accumulation (a4): plain FP32 inside 128-source groups, two-sum merge into
 // a (hi, lo) FP32 pair per target component, hi + lo written in FP64 per
 // chunk; the finish step adds the chunks in fixed order and the FP64 near
@@ -95,9 +103,31 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 }
 
 // ---- per-lane target state --------------------------------------------------
+// x, y, z: the pair's targets relative to the current segment's frame,
+// recomputed per segment from the targets' FP32 (hi, lo) splits.
 struct Tgt2 {
   float2 x, y, z, idl, rc2, rt2;
 };
+
+// A target coordinate x = hi + lo (hi = fl32(x), lo = fl32(x - hi)) relative
+// to a segment frame c: (hi - c) is exact for close pairs (Sterbenz), so the
+// result carries one rounding of |x - c|. It depends on the target and the
+// segment only, not on which warp or CTA holds the target. The pair kernel
+// (f32x2) and the overflow rescan (scalar) perform the same two roundings.
+__device__ __forceinline__ float shift_to_segment(float hi, float lo, float c) {
+  return __fadd_rn(__fsub_rn(hi, c), lo);
+}
+__device__ __forceinline__ float2 shift_to_segment2(float2 hi, float2 lo, float c) {
+  return __fadd2_rn(__ffma2_rn(make_float2(c, c), make_float2(-1.f, -1.f), hi), lo);
+}
+
+// Margin added to rho_c delta in the segment-versus-warp box test: the boxes
+// hold absolute FP32 coordinates, while pair distances come from frame-
+// relative coordinates; the two differ by a few FP32 roundings of the
+// coordinates' magnitude.
+__device__ __forceinline__ float box_margin(float coord_max, float rc) {
+  return 1.0e-6f * (coord_max + rc);
+}
 
 __device__ __forceinline__ void near_append(int64_t t, int jo, int* __restrict__ cnt,
                                             int* __restrict__ idx,
@@ -259,12 +289,21 @@ __device__ __forceinline__ void two_sum_merge(float2* U, float2* HI, float2* LO)
   }
 }
 
-// Where the compensated accumulators of a configuration live, and the dynamic
-// shared memory a pair item needs (source stages, plus the accumulators).
+// Shared memory of a pair item: the source stages; the per-thread target
+// state (TGT_SLOTS float4 per f32x2 pair: (hi, lo) of x, y, z, then
+// (1/delta, rho_c^2 delta^2), (rho_T^2 delta^2, -)), read once per segment;
+// and, for one pair per lane, the compensated accumulators. With one pair per
+// lane three CTAs share an SM, so that configuration runs one stage fewer.
 __host__ __device__ constexpr bool hilo_in_smem(int np) { return np == 1; }
 template <class L, int NP>
+__host__ __device__ constexpr int pair_stages() {
+  return NP == 1 ? L::STAGES - 1 : L::STAGES;
+}
+constexpr int TGT_SLOTS = 5;
+template <class L, int NP>
 constexpr size_t pair_smem_bytes() {
-  return L::STAGES * TILE * L::V * sizeof(float4) +
+  return (size_t)pair_stages<L, NP>() * TILE * L::V * sizeof(float4) +
+         (size_t)NP * TGT_SLOTS * TPB32 * sizeof(float4) +
          (hilo_in_smem(NP) ? (size_t)NP * 6 * TPB32 * sizeof(float2) : 0);
 }
 
@@ -285,6 +324,7 @@ struct PairArgs {
   const int* src_orig;
   const int* meta;
   const float4* tgtF;
+  const double4_32a* tgt64;
   int64_t M_pad;
   int n_chunks;
   double* part;
@@ -299,15 +339,16 @@ struct PairArgs {
 // false if a bounded wait expired (the flag is set, nothing is written).
 template <class L, int NP>
 __device__ __forceinline__ bool pair_item(const PairArgs& a, int tb, int ch, float4* sm,
-                                          PipeSmem<L::STAGES>& ps) {
+                                          PipeSmem<pair_stages<L, NP>()>& ps) {
   constexpr int V = L::V;
-  constexpr int STAGES = L::STAGES;
+  constexpr int STAGES = pair_stages<L, NP>();
   constexpr int WARPS = TPB32 / 32;
   constexpr uint32_t TILE_BYTES = TILE * V * sizeof(float4);
   const float4* __restrict__ srcF = a.srcF;
   const float4* __restrict__ segbox = a.segbox;
   const int* __restrict__ src_orig = a.src_orig;
   const float4* __restrict__ tgtF = a.tgtF;
+  const double4_32a* __restrict__ tgt64 = a.tgt64;
   const int n_chunks = a.n_chunks;
   int* __restrict__ near_cnt = a.near_cnt;
   int* __restrict__ near_idx = a.near_idx;
@@ -324,6 +365,8 @@ __device__ __forceinline__ bool pair_item(const PairArgs& a, int tb, int ch, flo
 
   // ---- targets of this lane: pair p holds targets (base + 64p + lane, base + 64p + 32 + lane)
   const int64_t wbase = (int64_t)tb * (TPB32 * 2 * NP) + wid * (64 * NP) + lane;
+  // per-thread target state: [(p * TGT_SLOTS + slot) * TPB32 + tid]
+  float4* const ts = sm + STAGES * TILE * V + tid;
   Tgt2 T[NP];
   float blo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, bhi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
   float rc2max = -1.f;
@@ -342,12 +385,8 @@ __device__ __forceinline__ bool pair_item(const PairArgs& a, int tb, int ch, flo
         rc2max = fmaxf(rc2max, b[h].x);
       }
     }
-    T[p].x = make_float2(a[0].x, a[1].x);
-    T[p].y = make_float2(a[0].y, a[1].y);
-    T[p].z = make_float2(a[0].z, a[1].z);
-    T[p].idl = make_float2(a[0].w, a[1].w);
-    T[p].rc2 = make_float2(b[0].x, b[1].x);
-    T[p].rt2 = make_float2(b[0].y, b[1].y);
+    ts[(p * TGT_SLOTS + 3) * TPB32] = make_float4(a[0].w, a[1].w, b[0].x, b[1].x);
+    ts[(p * TGT_SLOTS + 4) * TPB32] = make_float4(b[0].y, b[1].y, 0.f, 0.f);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -359,7 +398,27 @@ __device__ __forceinline__ bool pair_item(const PairArgs& a, int tb, int ch, flo
     rc2max = fmaxf(rc2max, __shfl_xor_sync(FULL, rc2max, o));
   }
   const bool warp_live = rc2max >= 0.f;
-  const float rc2test = rc2max * 1.0001f;
+  // FP32 (hi, lo) split of the targets' FP64 coordinates
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    const double4_32a x0 = tgt64[wbase + 64 * p], x1 = tgt64[wbase + 64 * p + 32];
+    const double a0[3] = {x0.x, x0.y, x0.z}, a1[3] = {x1.x, x1.y, x1.z};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float h0 = (float)a0[c], h1 = (float)a1[c];
+      ts[(p * TGT_SLOTS + c) * TPB32] =
+          make_float4(h0, h1, (float)(a0[c] - (double)h0), (float)(a1[c] - (double)h1));
+    }
+  }
+  float rc2test;
+  {
+    const float rc = sqrtf(fmaxf(rc2max, 0.f));
+    const float cmax = fmaxf(fmaxf(fmaxf(fabsf(blo[0]), fabsf(bhi[0])),
+                                   fmaxf(fabsf(blo[1]), fabsf(bhi[1]))),
+                             fmaxf(fabsf(blo[2]), fabsf(bhi[2])));
+    const float rm = rc * 1.00005f + box_margin(cmax, rc);
+    rc2test = rm * rm;
+  }
 
   // Compensated accumulators: registers for two pairs per lane; shared
   // memory (touched once per 128 sources) for one pair per lane, where the
@@ -367,7 +426,7 @@ __device__ __forceinline__ bool pair_item(const PairArgs& a, int tb, int ch, flo
   constexpr bool kHiLoSmem = hilo_in_smem(NP);
   float2 U[NP][3], HI[NP][3], LO[NP][3];
   // [(p * 3 + c) * 2 + {0: hi, 1: lo}][thread]: one float2 column per thread
-  float2* acc = reinterpret_cast<float2*>(sm + STAGES * TILE * V);
+  float2* acc = reinterpret_cast<float2*>(sm + STAGES * TILE * V + NP * TGT_SLOTS * TPB32);
 #pragma unroll
   for (int p = 0; p < NP; ++p)
 #pragma unroll
@@ -410,6 +469,7 @@ __device__ __forceinline__ bool pair_item(const PairArgs& a, int tb, int ch, flo
     if (warp_live) {
       const float4* S = sm + buf * TILE * V;
       bool nb = false;
+      float csx = 0.f, csy = 0.f, csz = 0.f;  // lane s < TILE_SEGS: segment s's frame
       if (lane < TILE_SEGS) {
         const float4 lo = segbox[2 * ((size_t)k * TILE_SEGS + lane)];
         const float4 hi = segbox[2 * ((size_t)k * TILE_SEGS + lane) + 1];
@@ -417,11 +477,26 @@ __device__ __forceinline__ bool pair_item(const PairArgs& a, int tb, int ch, flo
         const float dy = fmaxf(0.f, fmaxf(lo.y - bhi[1], blo[1] - hi.y));
         const float dz = fmaxf(0.f, fmaxf(lo.z - bhi[2], blo[2] - hi.z));
         nb = dx * dx + dy * dy + dz * dz < rc2test;
+        csx = frame_mid(lo.x, hi.x);
+        csy = frame_mid(lo.y, hi.y);
+        csz = frame_mid(lo.z, hi.z);
       }
       const unsigned nm = __ballot_sync(FULL, nb);
 #pragma unroll 1
       for (int s = 0; s < TILE_SEGS; ++s) {
         const float4* SS = S + s * SEG * V;
+        {
+          const float sx = __shfl_sync(FULL, csx, s), sy = __shfl_sync(FULL, csy, s),
+                      sz = __shfl_sync(FULL, csz, s);
+#pragma unroll
+          for (int p = 0; p < NP; ++p) {
+            const float4 hx = ts[(p * TGT_SLOTS) * TPB32], hy = ts[(p * TGT_SLOTS + 1) * TPB32],
+                         hz = ts[(p * TGT_SLOTS + 2) * TPB32];
+            T[p].x = shift_to_segment2(lo2(hx), hi2(hx), sx);
+            T[p].y = shift_to_segment2(lo2(hy), hi2(hy), sy);
+            T[p].z = shift_to_segment2(lo2(hz), hi2(hz), sz);
+          }
+        }
         if (!((nm >> s) & 1u)) {
 #pragma unroll kFarUnroll
           for (int j = 0; j < SEG; ++j) {
@@ -435,6 +510,13 @@ __device__ __forceinline__ bool pair_item(const PairArgs& a, int tb, int ch, flo
           }
         } else {
           const int* orig = src_orig + (size_t)k * TILE + s * SEG;
+#pragma unroll
+          for (int p = 0; p < NP; ++p) {
+            const float4 q = ts[(p * TGT_SLOTS + 3) * TPB32], r = ts[(p * TGT_SLOTS + 4) * TPB32];
+            T[p].idl = lo2(q);
+            T[p].rc2 = hi2(q);
+            T[p].rt2 = lo2(r);
+          }
 #pragma unroll 1
           for (int j = 0; j < SEG; ++j) {
             const typename L::Src src = L::load(SS + j * V);
@@ -551,6 +633,7 @@ struct Near64<DLayer> {
 // Arguments of the near-list overflow rescan and of the finish step.
 struct OverflowArgs {
   const float4* srcF;
+  const float4* segbox;
   const int* src_orig;
   const int* meta;
   const float4* tgtF;
@@ -591,15 +674,21 @@ __device__ __forceinline__ void overflow_target(const OverflowArgs& a, int64_t t
   const int lane = threadIdx.x & 31;
   if (a.near_cnt[t] <= NEAR_K) return;
   constexpr int V = L::V;
-  const float4 tx = a.tgtF[2 * t];
   const float rt2 = a.tgtF[2 * t + 1].y;
   const double4_32a x = a.tgt64[t];
   const double invd = 1.0 / x.w;
+  const float hx = (float)x.x, hy = (float)x.y, hz = (float)x.z;
+  const float lx = (float)(x.x - (double)hx), ly = (float)(x.y - (double)hy),
+              lz = (float)(x.z - (double)hz);
   const int Ns = a.meta[META_NS];
   double u0 = 0, u1 = 0, u2 = 0;
   for (int s = lane; s < Ns; s += 32) {
+    const float4 blo = a.segbox[2 * (s / SEG)], bhi = a.segbox[2 * (s / SEG) + 1];
+    const float tx = shift_to_segment(hx, lx, frame_mid(blo.x, bhi.x));
+    const float ty = shift_to_segment(hy, ly, frame_mid(blo.y, bhi.y));
+    const float tz = shift_to_segment(hz, lz, frame_mid(blo.z, bhi.z));
     const float4 p0 = a.srcF[(size_t)s * V], p1 = a.srcF[(size_t)s * V + 1];
-    const float dx = __fadd_rn(tx.x, p0.x), dy = __fadd_rn(tx.y, p0.z), dz = __fadd_rn(tx.z, p1.x);
+    const float dx = __fadd_rn(tx, p0.x), dy = __fadd_rn(ty, p0.z), dz = __fadd_rn(tz, p1.x);
     const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
     if (r2 < rt2) Near64<L>::eval(x, a.xyz, a.w, a.dens, a.nrm, a.src_orig[s], a.scale, invd, u0, u1, u2);
   }

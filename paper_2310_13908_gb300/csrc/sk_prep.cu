@@ -182,7 +182,9 @@ __global__ void k_rs_scatter(const uint32_t* __restrict__ kin, const int* __rest
 }
 
 // ---- packing ----------------------------------------------------------------
-__device__ __forceinline__ void warp_box(bool real, float x, float y, float z, float4* out) {
+// Writes the FP32 box of the warp's real points (lane 0) and returns its
+// midpoint frame to every lane.
+__device__ __forceinline__ float3 warp_box(bool real, float x, float y, float z, float4* out) {
   float lx = real ? x : FLT_MAX, ly = real ? y : FLT_MAX, lz = real ? z : FLT_MAX;
   float hx = real ? x : -FLT_MAX, hy = real ? y : -FLT_MAX, hz = real ? z : -FLT_MAX;
   for (int o = 16; o > 0; o >>= 1) {
@@ -197,11 +199,13 @@ __device__ __forceinline__ void warp_box(bool real, float x, float y, float z, f
     out[0] = make_float4(lx, ly, lz, 0.f);
     out[1] = make_float4(hx, hy, hz, 0.f);
   }
+  return make_float3(frame_mid(lx, hx), frame_mid(ly, hy), frame_mid(lz, hz));
 }
 
 constexpr float PAD_POS = 1.0e15f;  // padding sources sit far away with zero density
 
-// FP32 packed layout (duplicated lanes for f32x2 arithmetic):
+// FP32 packed layout (duplicated lanes for f32x2 arithmetic), x, y, z relative
+// to the segment's frame (frame_mid of its box; padding keeps PAD_POS):
 //   single layer: {-x,-x,-y,-y} {-z,-z,gx,gx} {gy,gy,gz,gz},  g = w f scale
 //   double layer: {-x,-x,-y,-y} {-z,-z,qx,qx} {qy,qy,qz,qz} {nx,nx,ny,ny} {nz,nz,0,0},
 //                 q = w q_in scale
@@ -218,14 +222,21 @@ __global__ void k_pack_src32(const double* __restrict__ xyz, const double* __res
   if (s == 0) meta[META_NS_PAD] = Ns_pad;
   if (s >= Ns_pad || s >= N_pad) return;  // whole warps leave together (multiples of 32)
   const bool real = s < Ns;
+  const int j = real ? sorted[s] : -1;
   float x = PAD_POS, y = PAD_POS, z = PAD_POS;
-  float d0 = 0.f, d1 = 0.f, d2 = 0.f, n0 = 0.f, n1 = 0.f, n2 = 0.f;
-  int j = -1;
   if (real) {
-    j = sorted[s];
     x = (float)xyz[3 * j];
     y = (float)xyz[3 * j + 1];
     z = (float)xyz[3 * j + 2];
+  }
+  // the box holds absolute FP32 positions; the record holds positions
+  // relative to the segment's frame, differenced in FP64
+  const float3 c = warp_box(real, x, y, z, segbox + 2 * (s / SEG));
+  float d0 = 0.f, d1 = 0.f, d2 = 0.f, n0 = 0.f, n1 = 0.f, n2 = 0.f;
+  if (real) {
+    x = (float)(xyz[3 * j] - (double)c.x);
+    y = (float)(xyz[3 * j + 1] - (double)c.y);
+    z = (float)(xyz[3 * j + 2] - (double)c.z);
     const double ws = w[j] * scale;
     d0 = (float)(ws * dens[3 * j]);
     d1 = (float)(ws * dens[3 * j + 1]);
@@ -245,7 +256,6 @@ __global__ void k_pack_src32(const double* __restrict__ xyz, const double* __res
     o[4] = make_float4(n2, n2, 0.f, 0.f);
   }
   src_orig[s] = j;
-  warp_box(real, x, y, z, segbox + 2 * (s / SEG));
 }
 
 // FP64 packed layout: src64[2s] = (x, y, z, 0), src64[2s+1] = (g or q scaled, 0);

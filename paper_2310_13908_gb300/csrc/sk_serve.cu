@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(TPB32, SERVE_MINB)
             const int* __restrict__ stop, unsigned* __restrict__ done_host,
             unsigned long long idle_ns) {
   extern __shared__ __align__(128) float4 sm[];
-  __shared__ PipeSmem<SLayer::STAGES> ps;
+  __shared__ PipeSmem<pair_stages<SLayer, SERVE_NP>()> ps;
   __shared__ SlotDesc d;
   __shared__ int s_slot, s_item, s_exit, s_finish;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -363,10 +363,10 @@ void publish(sk_server* srv, int slot) {
   const double scale = layer_scale(s);
   const float rho_lo = (float)srv->ctx->rho_T, rho_hi = 8.0f;
   SlotDesc d{};
-  d.pa = PairArgs{b.srcF, b.segbox, b.src_orig, b.meta, b.tgtF, b.M_pad, b.n_chunks,
+  d.pa = PairArgs{b.srcF, b.segbox, b.src_orig, b.meta, b.tgtF, b.tgt64, b.M_pad, b.n_chunks,
                   b.part, b.near_cnt, b.near_idx, b.flags, rho_lo, rho_hi};
-  d.oa = OverflowArgs{b.srcF, b.src_orig, b.meta, b.tgtF, b.tgt64, b.near_cnt, b.src_xyz,
-                      b.src_w, b.dens, b.nrm, scale, b.flags, b.near_ovf};
+  d.oa = OverflowArgs{b.srcF, b.segbox, b.src_orig, b.meta, b.tgtF, b.tgt64, b.near_cnt,
+                      b.src_xyz, b.src_w, b.dens, b.nrm, scale, b.flags, b.near_ovf};
   d.fa = FinishArgs{b.tgt64, b.tgt_perm, b.M_pad, b.n_chunks, b.part, b.near_cnt, b.near_idx,
                     b.near_ovf, b.src_xyz, b.src_w, b.dens, b.nrm, scale, b.u, b.flags};
   d.n_tb = (int)(b.M_pad / SERVE_TGT_CTA);

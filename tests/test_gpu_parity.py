@@ -131,6 +131,42 @@ def test_dl_ellipsoid_sampled_with_probes(ctx):
     assert_close(u[idx], ref, sk.SK_FP32C)
 
 
+@pytest.mark.parametrize("shape,m", [(ci.Sphere(1.0), 257), (ci.Ellipsoid(1.0, 0.8, 0.5), 193)],
+                         ids=["sphere-m257", "ellipsoid-m193"])
+def test_dl_fp32c_large_grids(ctx, shape, m):
+    """On the surface (x - y) . n cancels to O(r^2); the FP32 path differences
+    coordinates in local frames, so the error stays at the single-layer level
+    instead of growing like 1/delta with the grid."""
+    s = ci.make_surface(shape, m)
+    q = ci.sh_density(s.x0, np.random.default_rng(33), lmax=8)
+    delta = 2 * s.h
+    u = sk.stokes_dl_eval(ctx, sk.SK_FP32C, sk.SK_DEVICE, to_dev(s.X), to_dev(s.w), to_dev(s.n),
+                          to_dev(q), to_dev(s.X), to_dev(np.array([delta]))).cpu().numpy()
+    idx = np.random.default_rng(6).choice(s.N, 384, replace=False)
+    ref = oracle.dl(s.X, s.w, s.n, q, s.X[idx], delta)
+    e = assert_close(u[idx], ref, sk.SK_FP32C)
+    assert e <= 3e-7
+
+
+@pytest.mark.parametrize("layer", ["sl", "dl"])
+def test_fp32c_far_from_origin(ctx, layer):
+    """Translating the whole problem by O(100) leaves the FP32 path's accuracy
+    unchanged (coordinates enter the pair sums relative to local frames)."""
+    s = ci.make_surface(ci.Ellipsoid(1.0, 0.8, 0.5), 65)
+    q = ci.sh_density(s.x0, np.random.default_rng(8), lmax=8)
+    shift = np.array([100.0, -50.0, 25.0])
+    X = s.X + shift
+    delta = 2 * s.h
+    if layer == "sl":
+        u = sk.stokes_sl_eval(ctx, sk.SK_FP32C, sk.SK_HOST, X, s.w, q, X, delta)
+        ref = oracle.sl(X, s.w, q, X, delta)
+    else:
+        u = sk.stokes_dl_eval(ctx, sk.SK_FP32C, sk.SK_HOST, X, s.w, s.n, q, X, delta)
+        ref = oracle.dl(X, s.w, s.n, q, X, delta)
+    e = assert_close(u, ref, sk.SK_FP32C)
+    assert e <= 3e-7
+
+
 @pytest.mark.parametrize("prec", PRECS, ids=PREC_ID.get)
 def test_ragged_sizes_and_per_target_delta(ctx, prec):
     rng = np.random.default_rng(9)
