@@ -144,10 +144,12 @@ int stokes_dl_eval(sk_ctx* ctx, int precision, int mem,
  * dx/dt = u_inf(x) + S[f](x) (Sec. 3.6, Eq. bi_combined): every step
  * evaluates the regularized single layer at all nodes (targets = sources)
  * and adds the background flow. Nodes are ordered patch-major, then by the
- * u index j, then by the v index k (Sec. 3.2, Eq. grid). The quadrature
- * weights w = psi W h^2 stay those given at creation (the finite-difference
- * surface derivatives that would update W are not part of this library).
- * One step is captured once into a CUDA graph and replayed. */
+ * u index j, then by the v index k (Sec. 3.2, Eq. grid). Without a
+ * membrane the quadrature weights w = psi W h^2 stay those given at creation;
+ * after capsule_set_membrane every step recomputes them from the current
+ * tangents (overset finite differences, Sec. 3.5) and f = NULL selects the
+ * Skalak membrane force. One step is captured once into a CUDA graph and
+ * replayed. */
 typedef struct sk_capsule sk_capsule;
 
 #define SK_FLOW_NONE       0  /* u_inf = 0 */
@@ -174,16 +176,58 @@ int capsule_create(sk_ctx* ctx, sk_capsule** out, int m, const double* X, const 
 
 /* Advance n_steps >= 0 Euler steps of size dt > 0 in the background flow
  * (flow NULL: none) with the interfacial force density f [N][3] (host, held
- * fixed over these steps). f = NULL would mean the Skalak membrane force of
- * the current shape, which this build does not compute: SK_ENOTIMPL.
+ * fixed over these steps). f = NULL: the Skalak membrane force
+ * f = div_gamma Lambda of the current shape, recomputed every step (Sec. 2.1,
+ * Eqs. tensor and intf); needs capsule_set_membrane, else SK_ENOTIMPL.
  * Synchronous. Errors: SK_EINVAL, SK_ENOTIMPL, SK_ENOMEM, SK_ECUDA, SK_ETIMEOUT. */
 int capsule_step(sk_capsule* c, int n_steps, double dt, const sk_flow* flow, const double* f);
+
+/* Give the capsule a Skalak membrane (Sec. 2.1, Eq. tensor): stress-free
+ * reference nodes X_ref [N][3] (host, same grid order as X; copied), shear
+ * modulus Es >= 0 and dilatation modulus ED >= 0. Reference tangents come
+ * from the derivative scheme of Sec. 3.5. From now on every step updates the
+ * quadrature weights, and capsule_step(f = NULL) uses the membrane force.
+ * Needs m >= 6. Errors: SK_EINVAL, SK_ENOMEM, SK_ECUDA. */
+int capsule_set_membrane(sk_capsule* c, const double* X_ref, double Es, double ED);
+
+/* Area A = sum psi W h^2 and enclosed volume V = sum psi W h^2 x n_x (the
+ * divergence-theorem form of Sec. 4.1) of the current nodes, with W and n
+ * from the derivative scheme of Sec. 3.5. Needs m >= 6. Synchronous.
+ * Errors: SK_EINVAL, SK_ENOMEM, SK_ECUDA. */
+int capsule_area_volume(sk_capsule* c, double* area, double* volume);
 
 /* Copy the current node positions [N][3] to host memory. */
 int capsule_get(sk_capsule* c, double* X_out);
 
 /* Release the capsule. NULL is ignored. */
 void capsule_destroy(sk_capsule* c);
+
+/* ---- surface derivatives and the membrane force ------------------------
+ *
+ * The overset finite-difference scheme of Sec. 3.5 on the six-patch grid of
+ * order m (6 <= m <= 4097; N = 6 (m-1)^2 nodes in the capsule's order): patch
+ * extension to three ghost layers (Eq. ext) with tensor-product not-a-knot
+ * cubic splines, 7-point central differences (Eq. fdm) and blending with the
+ * transition-map Jacobians (Eqs. blendu / blendv). FP64 throughout. The
+ * operator depends only on m and is built on first use and kept in ctx.
+ * mem selects host or device pointers; stream as for stokes_sl_eval (device
+ * memory with a stream: asynchronous, buffers must stay valid until it
+ * completes). */
+
+/* u- and v-derivatives of n_fields functions g [N][n_fields] on the surface
+ * (values at the nodes; each node's derivatives are in its own patch's (u, v))
+ * into g_u, g_v [N][n_fields]. Errors: SK_EINVAL, SK_ENOMEM, SK_ECUDA. */
+int surface_derivatives(sk_ctx* ctx, int m, int mem, int64_t n_fields, const double* g,
+                        double* g_u, double* g_v, void* cuda_stream);
+
+/* Skalak membrane force f = div_gamma Lambda (Sec. 2.1, Eqs. tensor and
+ * intf; formulas of the Appendix) at nodes X [N][3] with stress-free
+ * reference X_ref [N][3], shear modulus Es >= 0, dilatation modulus ED >= 0,
+ * into f_out [N][3]; w_out [N] (may be NULL) receives the quadrature weights
+ * psi W h^2 of X (Sec. 3.3, Eq. smoothint). Errors: SK_EINVAL, SK_ENOMEM,
+ * SK_ECUDA. */
+int membrane_force(sk_ctx* ctx, int m, int mem, const double* X, const double* X_ref, double Es,
+                   double ED, double* f_out, double* w_out, void* cuda_stream);
 
 /* ---- serving: continuous batching of single-layer requests -------------
  *

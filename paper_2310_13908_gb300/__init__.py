@@ -85,6 +85,10 @@ _EXTRA_DECLS: dict = {
     "capsule_create": ([_vp, ctypes.POINTER(_vp), _int, _vp, _vp, _vp, _i64, _dbl, _int], _int),
     "capsule_step": ([_vp, _int, _dbl, _vp, _vp], _int),
     "capsule_get": ([_vp, _vp], _int),
+    "capsule_set_membrane": ([_vp, _vp, _dbl, _dbl], _int),
+    "capsule_area_volume": ([_vp, ctypes.POINTER(_dbl), ctypes.POINTER(_dbl)], _int),
+    "surface_derivatives": ([_vp, _int, _int, _i64, _vp, _vp, _vp, _vp], _int),
+    "membrane_force": ([_vp, _int, _int, _vp, _vp, _dbl, _dbl, _vp, _vp, _vp], _int),
     "capsule_destroy": ([_vp], None),
 }
 
@@ -249,6 +253,50 @@ def stokes_dl_eval(ctx, precision: int, mem: int, src_xyz, src_w, src_n, q, tgt_
     return u_out
 
 
+def surface_derivatives(ctx, m: int, mem: int, g, stream=None):
+    """u- and v-derivatives of node fields g (N, F) by the overset finite
+    differences of Sec. 3.5. Returns (g_u, g_v), each (N, F)."""
+    lib = load()
+    if mem == SK_DEVICE:
+        if not _is_torch(g) or not g.is_cuda:
+            raise TypeError("g: SK_DEVICE expects a CUDA torch tensor")
+        import torch
+        G = g.reshape(g.shape[0], -1).contiguous().to(torch.float64)
+        gu, gv = torch.empty_like(G), torch.empty_like(G)
+        F = G.shape[1]
+        _check(ctx, lib.surface_derivatives(ctx, int(m), SK_DEVICE, F, G.data_ptr(),
+                                            gu.data_ptr(), gv.data_ptr(), _stream_handle(stream)))
+        return gu.reshape(g.shape), gv.reshape(g.shape)
+    G = np.ascontiguousarray(g, dtype=np.float64)
+    flat = G.reshape(G.shape[0], -1)
+    gu, gv = np.empty_like(flat), np.empty_like(flat)
+    _check(ctx, lib.surface_derivatives(ctx, int(m), SK_HOST, flat.shape[1], _host_ptr(flat),
+                                        _host_ptr(gu), _host_ptr(gv), None))
+    return gu.reshape(G.shape), gv.reshape(G.shape)
+
+
+def membrane_force(ctx, m: int, mem: int, X, X_ref, Es: float, ED: float, weights: bool = False,
+                   stream=None):
+    """Skalak force f = div_gamma Lambda (Sec. 2.1) at nodes X with reference
+    X_ref; returns f (N, 3), or (f, w) with the quadrature weights."""
+    lib = load()
+    Xa, N = _ptr(X, mem, (3,), "X")
+    Xr, Nr = _ptr(X_ref, mem, (3,), "X_ref")
+    if N != Nr:
+        raise ValueError("X and X_ref must hold the same nodes")
+    if mem == SK_DEVICE:
+        import torch
+        f = torch.empty((N, 3), dtype=torch.float64, device=X.device)
+        w = torch.empty((N,), dtype=torch.float64, device=X.device) if weights else None
+        args = [Xa, Xr, float(Es), float(ED), f.data_ptr(), w.data_ptr() if weights else None]
+    else:
+        f = np.empty((N, 3))
+        w = np.empty(N) if weights else None
+        args = [_host_ptr(Xa), _host_ptr(Xr), float(Es), float(ED), _host_ptr(f), _host_ptr(w)]
+    _check(ctx, lib.membrane_force(ctx, int(m), int(mem), *args, _stream_handle(stream)))
+    return (f, w) if weights else f
+
+
 SK_FLOW_NONE, SK_FLOW_SHEAR, SK_FLOW_POISEUILLE = 0, 1, 2
 
 
@@ -274,11 +322,25 @@ class Capsule:
         self.ctx, self.handle, self.N = ctx, h, N
 
     def step(self, n_steps: int, dt: float, f, flow=None):
-        """flow: None or (kind, rate, alpha, R0)."""
+        """flow: None or (kind, rate, alpha, R0); f None: the membrane force."""
         F, _ = _ptr(f, SK_HOST, (3,), "f") if f is not None else (None, 0)
         fl = ctypes.byref(sk_flow(*flow)) if flow is not None else None
         _check(self.ctx, load().capsule_step(self.handle, int(n_steps), float(dt), fl,
                                              _host_ptr(F)))
+
+    def set_membrane(self, X_ref, Es: float, ED: float):
+        """Skalak membrane with stress-free reference X_ref (Sec. 2.1)."""
+        Xr, N = _ptr(X_ref, SK_HOST, (3,), "X_ref")
+        if N != self.N:
+            raise ValueError("X_ref must hold the capsule's nodes")
+        _check(self.ctx, load().capsule_set_membrane(self.handle, _host_ptr(Xr), float(Es),
+                                                     float(ED)))
+
+    def area_volume(self):
+        a, v = ctypes.c_double(), ctypes.c_double()
+        _check(self.ctx, load().capsule_area_volume(self.handle, ctypes.byref(a),
+                                                    ctypes.byref(v)))
+        return a.value, v.value
 
     def positions(self):
         X = np.empty((self.N, 3))

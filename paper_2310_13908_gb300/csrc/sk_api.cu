@@ -261,6 +261,7 @@ void sk_destroy(sk_ctx* ctx) {
   if (ctx->server) serve_destroy(ctx->server);
   DeviceGuard g(ctx->device);
   cudaDeviceSynchronize();
+  free_membrane_ops(ctx);
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->h_flags) cudaFreeHost(ctx->h_flags);
   for (int i = 0; i < 4; ++i)

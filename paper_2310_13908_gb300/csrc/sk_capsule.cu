@@ -1,11 +1,15 @@
 // sk_capsule.cu -- explicit Euler time stepping of a capsule's surface nodes
 // (Sec. 3.6, Eq. bi_combined) with the regularized single layer.
 //
-// The nodes stay resident in device memory. One step is: (optionally) the
-// patch-dependent regularization parameter delta* of Eq. regparam, the full
-// single-layer evaluation at all nodes, and the update
-// X += dt (S[f](X) + u_inf(X)). The step is captured once into a CUDA graph
-// and replayed n_steps times, so a step costs one graph launch on the host.
+// The nodes stay resident in device memory. One step is: with a membrane
+// (capsule_set_membrane), the quadrature weights psi W h^2 from the current
+// tangents and, when no force is supplied, the Skalak force f = div_gamma
+// Lambda (Sec. 2.1, Eqs. tensor and intf, by the overset finite differences
+// of Sec. 3.5); (optionally) the patch-dependent regularization parameter
+// delta* of Eq. regparam; the full single-layer evaluation at all nodes; and
+// the update X += dt (S[f](X) + u_inf(X)). The step is captured once into a
+// CUDA graph and replayed n_steps times, so a step costs one graph launch on
+// the host.
 #include <cstring>
 #include <new>
 
@@ -26,7 +30,13 @@ struct sk_capsule {
   unsigned long long* sticky = nullptr;     // [N_FLAGS] flags of all steps since the last call
   double mu = 1.0;
   int precision = SK_FP32C;
+  // membrane (capsule_set_membrane): reference tangents [6][N] and moduli
+  sk::MembraneOp* mop = nullptr;
+  double* ref6 = nullptr;
+  double Es = 0.0, ED = 0.0;
+  double* av = nullptr;  // [2] area, volume (device)
   // captured step graph and the state it was captured for
+  int g_mode = -1;  // 0: supplied f; 1: supplied f, membrane weights; 2: Skalak force
   cudaGraphExec_t exec = nullptr;
   double g_dt = 0.0;
   sk_flow g_flow{};
@@ -93,7 +103,7 @@ __global__ void k_sticky(const unsigned long long* __restrict__ flags,
 
 void free_capsule(sk_capsule* c) {
   if (c->exec) cudaGraphExecDestroy(c->exec);
-  for (double* p : {c->X, c->w, c->f, c->u, c->delta})
+  for (double* p : {c->X, c->w, c->f, c->u, c->delta, c->ref6, c->av})
     if (p) cudaFree(p);
   if (c->patch_max) cudaFree(c->patch_max);
   if (c->sticky) cudaFree(c->sticky);
@@ -174,15 +184,17 @@ int capsule_step(sk_capsule* c, int n_steps, double dt, const sk_flow* flow, con
     ctx->err = "capsule_step: need n_steps >= 0, dt > 0 and a known flow kind";
     return SK_EINVAL;
   }
-  if (!f) {
-    ctx->err = "capsule_step: the Skalak membrane force (f = NULL) is not built in this library";
+  if (!f && !c->mop) {
+    ctx->err = "capsule_step: f = NULL takes the Skalak force, which needs capsule_set_membrane";
     return SK_ENOTIMPL;
   }
+  const int mode = c->mop ? (f ? 1 : 2) : 0;
   if (n_steps == 0) return SK_OK;
   cudaSetDevice(ctx->device);
   cudaStream_t st = ctx->stream;
   const sk_flow fl = flow ? *flow : sk_flow{SK_FLOW_NONE, 0.0, 0.0, 0.0};
-  cudaError_t e = cudaMemcpyAsync(c->f, f, 3 * c->N * sizeof(double), cudaMemcpyHostToDevice, st);
+  cudaError_t e = cudaSuccess;
+  if (f) e = cudaMemcpyAsync(c->f, f, 3 * c->N * sizeof(double), cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return SK_ECUDA;
   EvalShape s;
   s.layer = LAYER_SL;
@@ -197,7 +209,7 @@ int capsule_step(sk_capsule* c, int n_steps, double dt, const sk_flow* flow, con
   if (rc != SK_OK) return rc;
   const bool stale = !c->exec || c->g_dt != dt || std::memcmp(&c->g_flow, &fl, sizeof(fl)) != 0 ||
                      c->g_ws != ctx->ws || c->g_ws_bytes != ctx->ws_bytes ||
-                     c->g_rho_T != ctx->rho_T || c->g_rho_c != ctx->rho_c;
+                     c->g_rho_T != ctx->rho_T || c->g_rho_c != ctx->rho_c || c->g_mode != mode;
   if (stale) {
     if (c->exec) cudaGraphExecDestroy(c->exec);
     c->exec = nullptr;
@@ -216,6 +228,8 @@ int capsule_step(sk_capsule* c, int n_steps, double dt, const sk_flow* flow, con
       ctx->err = std::string("capsule_step: capture: ") + cudaGetErrorString(e);
       return SK_ECUDA;
     }
+    if (mode == 1) enqueue_tangents(*c->mop, c->X, nullptr, c->w, st);
+    if (mode == 2) enqueue_skalak(*c->mop, c->X, c->ref6, c->Es, c->ED, c->f, c->w, st);
     if (c->auto_delta) {
       cudaMemsetAsync(c->patch_max, 0, 8 * sizeof(unsigned long long), st);
       k_delta_star_patch<<<blocks(c->N), 256, 0, st>>>(c->X, c->m, c->patch_max);
@@ -238,6 +252,7 @@ int capsule_step(sk_capsule* c, int n_steps, double dt, const sk_flow* flow, con
     c->g_ws_bytes = ctx->ws_bytes;
     c->g_rho_T = ctx->rho_T;
     c->g_rho_c = ctx->rho_c;
+    c->g_mode = mode;
   }
   cudaMemsetAsync(c->sticky, 0, N_FLAGS * sizeof(unsigned long long), st);
   for (int i = 0; i < n_steps; ++i)
@@ -258,6 +273,65 @@ int capsule_step(sk_capsule* c, int n_steps, double dt, const sk_flow* flow, con
     ctx->err = "capsule_step: delta must be positive and finite";
     return SK_EINVAL;
   }
+  return SK_OK;
+}
+
+int capsule_set_membrane(sk_capsule* c, const double* X_ref, double Es, double ED) {
+  if (!c) return SK_EINVAL;
+  sk_ctx* ctx = c->ctx;
+  if (!X_ref || !(Es >= 0.0 && Es < INFINITY) || !(ED >= 0.0 && ED < INFINITY)) {
+    ctx->err = "capsule_set_membrane: need X_ref and finite Es, ED >= 0";
+    return SK_EINVAL;
+  }
+  MembraneOp* op = nullptr;
+  int rc = membrane_op(ctx, c->m, &op);
+  if (rc != SK_OK) return rc;
+  cudaSetDevice(ctx->device);
+  cudaStream_t st = ctx->stream;
+  cudaError_t e = cudaSuccess;
+  if (!c->ref6) e = cudaMalloc(&c->ref6, 6 * c->N * sizeof(double));
+  if (e == cudaSuccess && !c->av) e = cudaMalloc(&c->av, 2 * sizeof(double));
+  // the reference nodes pass through u (free between steps)
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->u, X_ref, 3 * c->N * sizeof(double), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) {
+    enqueue_tangents(*op, c->u, c->ref6, nullptr, st);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    ctx->err = std::string("capsule_set_membrane: ") + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? SK_ENOMEM : SK_ECUDA;
+  }
+  c->mop = op;
+  c->Es = Es;
+  c->ED = ED;
+  c->g_mode = -1;  // recapture the step
+  return SK_OK;
+}
+
+int capsule_area_volume(sk_capsule* c, double* area, double* volume) {
+  if (!c || !area || !volume) return SK_EINVAL;
+  sk_ctx* ctx = c->ctx;
+  MembraneOp* op = nullptr;
+  int rc = membrane_op(ctx, c->m, &op);
+  if (rc != SK_OK) return rc;
+  cudaSetDevice(ctx->device);
+  cudaStream_t st = ctx->stream;
+  cudaError_t e = cudaSuccess;
+  if (!c->av) e = cudaMalloc(&c->av, 2 * sizeof(double));
+  double h[2] = {0.0, 0.0};
+  if (e == cudaSuccess) {
+    enqueue_area_volume(*op, c->X, c->av, st);
+    e = cudaMemcpyAsync(h, c->av, sizeof(h), cudaMemcpyDeviceToHost, st);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    ctx->err = std::string("capsule_area_volume: ") + cudaGetErrorString(e);
+    return SK_ECUDA;
+  }
+  *area = h[0];
+  *volume = h[1];
   return SK_OK;
 }
 

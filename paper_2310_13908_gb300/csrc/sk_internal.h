@@ -6,6 +6,8 @@
 #include <cstddef>
 #include <cstdint>
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "../../include/stokesreg.h"
 
@@ -144,6 +146,10 @@ inline int pair32_ctas_per_sm(int np) { return np == 2 ? PAIR32_MINB_NP2 : PAIR3
 
 struct sk_server;
 
+namespace sk {
+struct MembraneOp;
+}
+
 struct sk_ctx {
   int device = 0;
   sk_server* server = nullptr;  // at most one server per context
@@ -159,6 +165,7 @@ struct sk_ctx {
   bool profile = false;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // eval begin, pair begin/end, eval end
   sk_eval_stats stats{};
+  std::vector<std::pair<int, sk::MembraneOp*>> membrane_ops;  // derivative operators by m
   std::string err;
 };
 
@@ -207,5 +214,16 @@ void launch_finish32(int layer, const EvalBufs& b, int64_t n_delta, double scale
                      double rho_T, cudaStream_t st);
 void launch_pair64(int layer, const EvalBufs& b, double scale, cudaStream_t st);
 void launch_finish64(const EvalBufs& b, cudaStream_t st);
+
+// sk_membrane.cu: overset finite-difference derivatives and the Skalak force
+// on the six-patch grid of order m (built once per m and cached in ctx).
+int membrane_op(sk_ctx* ctx, int m, MembraneOp** out);
+void free_membrane_ops(sk_ctx* ctx);
+int64_t membrane_nodes(const MembraneOp& op);
+void enqueue_tangents(const MembraneOp& op, const double* X, double* t6, double* w,
+                      cudaStream_t st);
+void enqueue_skalak(const MembraneOp& op, const double* X, const double* ref6, double Es,
+                    double ED, double* f, double* w, cudaStream_t st);
+void enqueue_area_volume(const MembraneOp& op, const double* X, double* out2, cudaStream_t st);
 
 }  // namespace sk

@@ -1,0 +1,712 @@
+// sk_membrane.cu -- overset finite-difference surface derivatives and the
+// Skalak membrane force on the six-patch grid (Sec. 3.5; Sec. 2.1, Eqs.
+// tensor and intf; formulas of the Appendix).
+//
+// The derivative scheme is a fixed linear operator on node values that
+// depends only on m (the transition maps and partition of unity live on the
+// unit sphere), so it is built once per m on the host, in FP64, and cached in
+// the context:
+//   * ghost taps: for every ghost point of the extended grid that a 7-point
+//     stencil touches, the patches q with psi_q > 0 there, the point's (u, v)
+//     in patch q and psi_q (Eq. ext);
+//   * blend taps: for every node, psi of its own patch and, for the other
+//     patches q with psi_q > 0, (u, v) in q, psi_q and the Jacobian of the
+//     transition map (Eqs. blendu / blendv).
+// On the device, per batch of F fields (SoA [F][6][m-1][m-1], FP64):
+//   1. spline slopes: each patch grid function becomes the tensor-product
+//      not-a-knot cubic spline, stored as a bicubic Hermite interpolant
+//      (g, g_u, g_v, g_uv at the nodes; one tridiagonal solve per grid line);
+//   2. patch extension: ghost value = sum_q psi_q * spline_q(u_q, v_q);
+//   3. 7-point central differences on the extended grid (Eq. fdm);
+//   4. splines of the FD derivatives, then blending.
+// Skalak: tangents of the current and reference nodes by the scheme; Lambda
+// of Eq. tensor from the closed-form invariants of V^2 (tr V^2 and
+// det = (W / W_r)^2); f = div_gamma Lambda column by column.
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <vector>
+
+#include "sk_internal.h"
+
+namespace sk {
+
+constexpr int MEM_FMAX = 9;  // fields per pass (Lambda has 6, positions 3)
+
+struct MembraneOp {
+  int m = 0, n = 0, E = 0;  // E = m + 5: extended grid (indices -2..m+2)
+  int64_t N = 0;
+  double h = 0.0;
+  int G = 0;  // ghost points used by the stencils, per field
+  // operator tables (device)
+  int* ghost_dst = nullptr;    // [G] offset in a field's extended block (6 E^2)
+  int* gtap_ptr = nullptr;     // [G + 1]
+  int* gtap_patch = nullptr;   // [taps] 0..5
+  double* gtap_uvw = nullptr;  // [taps][3]: u, v, psi
+  double* psi_own = nullptr;   // [N]
+  int* btap_ptr = nullptr;     // [N + 1]
+  int* btap_patch = nullptr;
+  double* btap_d = nullptr;    // [taps][7]: u, v, psi, dtau1/du, dtau2/du, dtau1/dv, dtau2/dv
+  double* thomas = nullptr;    // [2 n]: c' and 1/den of the reduced slope system
+  // scratch for up to MEM_FMAX fields
+  double *g = nullptr, *sg = nullptr;    // values, spline data [3][F][N] (u, v, uv slopes)
+  double* ext = nullptr;                 // [F][6][E][E]
+  double *du = nullptr, *dv = nullptr;   // FD derivatives [F][N]
+  double *sdu = nullptr, *sdv = nullptr; // their spline data [3][F][N]
+  double *gu = nullptr, *gv = nullptr;   // blended derivatives [F][N]
+  double* cur_t = nullptr;               // current tangents [6][N]
+  double* red = nullptr;                 // reduction partials
+};
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Host geometry of the six charts (Sec. 3.1, Eq. param_maps) and the POU.
+struct D3 {
+  double x, y, z;
+};
+inline double dot3(D3 a, D3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+
+D3 h_chart(int p, double u, double v) {
+  const double su = std::sin(u), cu = std::cos(u), sv = std::sin(v), cv = std::cos(v);
+  switch (p) {
+    case 0: return {su * cv, su * sv, cu};
+    case 1: return {-su * cv, -su * sv, cu};
+    case 2: return {su * sv, -su * cv, cu};
+    case 3: return {-su * sv, su * cv, cu};
+    case 4: return {su * cv, -cu, su * sv};
+    default: return {su * cv, cu, -su * sv};
+  }
+}
+
+void h_chart_tangents(int p, double u, double v, D3& tu, D3& tv) {
+  const double su = std::sin(u), cu = std::cos(u), sv = std::sin(v), cv = std::cos(v);
+  switch (p) {
+    case 0: tu = {cu * cv, cu * sv, -su}; tv = {-su * sv, su * cv, 0.0}; break;
+    case 1: tu = {-cu * cv, -cu * sv, -su}; tv = {su * sv, -su * cv, 0.0}; break;
+    case 2: tu = {cu * sv, -cu * cv, -su}; tv = {su * cv, su * sv, 0.0}; break;
+    case 3: tu = {-cu * sv, cu * cv, -su}; tv = {-su * cv, -su * sv, 0.0}; break;
+    case 4: tu = {cu * cv, su, cu * sv}; tv = {-su * sv, 0.0, su * cv}; break;
+    default: tu = {cu * cv, -su, -cu * sv}; tv = {-su * sv, 0.0, -su * cv}; break;
+  }
+}
+
+// (u, v) of a unit vector in patch p: u from the chart's cos-u component,
+// v from its (sin u cos v, sin u sin v) components.
+void h_inverse_chart(int p, D3 x, double& u, double& v) {
+  double cu, a, b;
+  switch (p) {
+    case 0: cu = x.z; a = x.x; b = x.y; break;
+    case 1: cu = x.z; a = -x.x; b = -x.y; break;
+    case 2: cu = x.z; a = -x.y; b = x.x; break;
+    case 3: cu = x.z; a = x.y; b = -x.x; break;
+    case 4: cu = -x.y; a = x.x; b = x.z; break;
+    default: cu = x.y; a = x.x; b = -x.z; break;
+  }
+  u = std::acos(std::fmin(1.0, std::fmax(-1.0, cu)));
+  v = std::atan2(b, a);
+}
+
+// psi_q(x0) for all patches (Eq. pou0): bump of the great-circle distance to
+// the patch centre eta_q^0(pi/2, pi/2) over r0 = 5 pi / 12, normalized.
+void h_pou(D3 x0, double psi[6]) {
+  const double r0 = 5.0 * PI_CONST / 12.0;
+  double s = 0.0;
+  for (int q = 0; q < 6; ++q) {
+    const D3 c = h_chart(q, 0.5 * PI_CONST, 0.5 * PI_CONST);
+    const double d = std::acos(std::fmin(1.0, std::fmax(-1.0, dot3(x0, c)))) / r0;
+    double b = 0.0;
+    if (d < 1.0) b = std::exp(2.0 * (d > 0.0 ? std::exp(-1.0 / d) : 0.0) / (d - 1.0));
+    psi[q] = b;
+    s += b;
+  }
+  for (int q = 0; q < 6; ++q) psi[q] /= s;
+}
+
+// Jacobian of tau_pq at (u, v) in the layout of Eq. jacobian_diff:
+// J = (dtau1/du, dtau2/du, dtau1/dv, dtau2/dv), from the chain rule
+// eta_p,u = eta_q,u' dtau1/du + eta_q,v' dtau2/du (same for v).
+void h_transition_jacobian(int p, int q, double u, double v, double uq, double vq, double J[4]) {
+  D3 pu, pv, qu, qv;
+  h_chart_tangents(p, u, v, pu, pv);
+  h_chart_tangents(q, uq, vq, qu, qv);
+  const double a = dot3(qu, qu), b = dot3(qu, qv), c = dot3(qv, qv);
+  const double det = a * c - b * b;
+  auto solve = [&](D3 t, double& x, double& y) {
+    const double r1 = dot3(qu, t), r2 = dot3(qv, t);
+    x = (c * r1 - b * r2) / det;
+    y = (a * r2 - b * r1) / det;
+  };
+  solve(pu, J[0], J[1]);
+  solve(pv, J[2], J[3]);
+}
+
+// ---------------------------------------------------------------------------
+// Device kernels.
+inline unsigned blocks_of(int64_t n) { return (unsigned)((n + 255) / 256); }
+
+// Not-a-knot cubic-spline slopes along one grid line per thread. Lines: for
+// dir 0 the u-lines (fixed k, stride n), for dir 1 the v-lines (fixed j).
+// With uniform spacing the end conditions read s0 + 2 s1 = (-5 g0 + 4 g1 + g2)/2h
+// and 2 s_{n-2} + s_{n-1} = (5 g_{n-1} - 4 g_{n-2} - g_{n-3})/2h; eliminating s0
+// and s_{n-1} leaves a diagonally dominant tridiagonal system in s1..s_{n-2}
+// whose factorization (thomas) is shared by all lines.
+__global__ void k_slopes(const double* __restrict__ g, double* __restrict__ s, int64_t n_lines,
+                         int n, int dir, double h, const double* __restrict__ thomas) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n_lines) return;
+  const int64_t fp = t / n;
+  const int r = (int)(t % n);
+  const int64_t base = fp * n * n + (dir == 0 ? r : (int64_t)r * n);
+  const int64_t st = dir == 0 ? n : 1;
+  const double* c_ = thomas;
+  const double* iden = thomas + n;
+  const double r0 = (-5.0 * g[base] + 4.0 * g[base + st] + g[base + 2 * st]) / (2.0 * h);
+  const double rN = (5.0 * g[base + (n - 1) * st] - 4.0 * g[base + (n - 2) * st] -
+                     g[base + (n - 3) * st]) /
+                    (2.0 * h);
+  double prev = 0.0;
+  for (int q = 1; q <= n - 2; ++q) {
+    double rhs = 3.0 * (g[base + (q + 1) * st] - g[base + (q - 1) * st]) / h;
+    if (q == 1) rhs -= r0;
+    if (q == n - 2) rhs -= rN;
+    prev = (rhs - (q > 1 ? prev : 0.0)) * iden[q];
+    s[base + q * st] = prev;
+  }
+  double nxt = s[base + (n - 2) * st];
+  for (int q = n - 3; q >= 1; --q) {
+    nxt = s[base + q * st] - c_[q] * nxt;
+    s[base + q * st] = nxt;
+  }
+  s[base] = r0 - 2.0 * s[base + st];
+  s[base + (n - 1) * st] = rN - 2.0 * s[base + (n - 2) * st];
+}
+
+// Bicubic Hermite evaluation of the spline of field block `base` (one field,
+// one patch) at (u, v); cells continue the end pieces outside the nodes.
+__device__ __forceinline__ double spline_eval(const double* __restrict__ g,
+                                              const double* __restrict__ sd, int64_t plane,
+                                              int64_t base, int n, double h, double u, double v) {
+  const double tu = u / h - 1.0, tv = v / h - 1.0;  // node 0 sits at u = h
+  int a = (int)floor(tu), b = (int)floor(tv);
+  a = a < 0 ? 0 : (a > n - 2 ? n - 2 : a);
+  b = b < 0 ? 0 : (b > n - 2 ? n - 2 : b);
+  const double t = tu - a, s = tv - b;
+  // value and slope bases at the two ends of a cell (slopes in units of h)
+  const double A0 = (1.0 + 2.0 * t) * (1.0 - t) * (1.0 - t), A1 = t * t * (3.0 - 2.0 * t);
+  const double B0 = t * (1.0 - t) * (1.0 - t) * h, B1 = t * t * (t - 1.0) * h;
+  const double C0 = (1.0 + 2.0 * s) * (1.0 - s) * (1.0 - s), C1 = s * s * (3.0 - 2.0 * s);
+  const double D0 = s * (1.0 - s) * (1.0 - s) * h, D1 = s * s * (s - 1.0) * h;
+  const double* su = sd;
+  const double* sv = sd + plane;
+  const double* suv = sd + 2 * plane;
+  const int64_t i00 = base + (int64_t)a * n + b, i10 = i00 + n, i01 = i00 + 1, i11 = i00 + n + 1;
+  return A0 * (C0 * g[i00] + C1 * g[i01] + D0 * sv[i00] + D1 * sv[i01]) +
+         A1 * (C0 * g[i10] + C1 * g[i11] + D0 * sv[i10] + D1 * sv[i11]) +
+         B0 * (C0 * su[i00] + C1 * su[i01] + D0 * suv[i00] + D1 * suv[i01]) +
+         B1 * (C0 * su[i10] + C1 * su[i11] + D0 * suv[i10] + D1 * suv[i11]);
+}
+
+// Extended values: nodes copied, ghost points by patch extension (Eq. ext).
+__global__ void k_extend(const MembraneOp op, int F) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t N = op.N, blk = 6LL * op.E * op.E, plane = (int64_t)F * N;
+  if (i < F * N) {
+    const int f = (int)(i / N);
+    const int64_t node = i % N;
+    const int p = (int)(node / ((int64_t)op.n * op.n));
+    const int r = (int)(node % ((int64_t)op.n * op.n));
+    const int j = r / op.n, k = r % op.n;
+    op.ext[f * blk + ((int64_t)p * op.E + j + 3) * op.E + k + 3] = op.g[i];
+    return;
+  }
+  const int64_t gi = i - F * N;
+  if (gi >= (int64_t)F * op.G) return;
+  const int f = (int)(gi / op.G);
+  const int q = (int)(gi % op.G);
+  double val = 0.0;
+  for (int t = op.gtap_ptr[q]; t < op.gtap_ptr[q + 1]; ++t) {
+    const int p = op.gtap_patch[t];
+    const double* d = op.gtap_uvw + 3 * t;
+    val += d[2] * spline_eval(op.g, op.sg, plane, ((int64_t)f * 6 + p) * op.n * op.n, op.n, op.h,
+                              d[0], d[1]);
+  }
+  op.ext[f * blk + op.ghost_dst[q]] = val;
+}
+
+// Eq. fdm: 7-point central differences (-1, 9, -45, 0, 45, -9, 1) / 60h.
+__global__ void k_fd(const MembraneOp op, int F) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t N = op.N;
+  if (i >= F * N) return;
+  const int f = (int)(i / N);
+  const int64_t node = i % N;
+  const int p = (int)(node / ((int64_t)op.n * op.n));
+  const int r = (int)(node % ((int64_t)op.n * op.n));
+  const int j = r / op.n, k = r % op.n;
+  const int E = op.E;
+  const double* e = op.ext + (int64_t)f * 6 * E * E + ((int64_t)p * E + j + 3) * E + k + 3;
+  const double c1 = 45.0 / 60.0, c2 = -9.0 / 60.0, c3 = 1.0 / 60.0;
+  op.du[i] = (c1 * (e[E] - e[-E]) + c2 * (e[2 * E] - e[-2 * E]) + c3 * (e[3 * E] - e[-3 * E])) / op.h;
+  op.dv[i] = (c1 * (e[1] - e[-1]) + c2 * (e[2] - e[-2]) + c3 * (e[3] - e[-3])) / op.h;
+}
+
+// Eqs. blendu / blendv.
+__global__ void k_blend(const MembraneOp op, int F) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t N = op.N, plane = (int64_t)F * N;
+  if (i >= F * N) return;
+  const int f = (int)(i / N);
+  const int64_t node = i % N;
+  const double po = op.psi_own[node];
+  double ou = po * op.du[i], ov = po * op.dv[i];
+  for (int t = op.btap_ptr[node]; t < op.btap_ptr[node + 1]; ++t) {
+    const int64_t base = ((int64_t)f * 6 + op.btap_patch[t]) * op.n * op.n;
+    const double* d = op.btap_d + 7 * t;
+    const double eu = spline_eval(op.du, op.sdu, plane, base, op.n, op.h, d[0], d[1]);
+    const double ev = spline_eval(op.dv, op.sdv, plane, base, op.n, op.h, d[0], d[1]);
+    ou += d[2] * (eu * d[3] + ev * d[4]);
+    ov += d[2] * (eu * d[5] + ev * d[6]);
+  }
+  op.gu[i] = ou;
+  op.gv[i] = ov;
+}
+
+// [N][ld] column block c0..c0+F  <->  [F][N]
+__global__ void k_gather(const double* __restrict__ aos, int64_t N, int ld, int c0, int F,
+                         double* __restrict__ soa) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= F * N) return;
+  const int f = (int)(i / N);
+  const int64_t node = i % N;
+  soa[i] = aos[node * ld + c0 + f];
+}
+__global__ void k_scatter(const double* __restrict__ soa, int64_t N, int ld, int c0, int F,
+                          double* __restrict__ aos) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= F * N) return;
+  const int f = (int)(i / N);
+  const int64_t node = i % N;
+  aos[node * ld + c0 + f] = soa[i];
+}
+
+struct Frame {
+  double a1[3], a2[3], E, F, G, W, n[3];
+};
+__device__ __forceinline__ Frame frame_at(const double* __restrict__ t6, int64_t N, int64_t i) {
+  Frame fr;
+  for (int c = 0; c < 3; ++c) {
+    fr.a1[c] = t6[c * N + i];
+    fr.a2[c] = t6[(3 + c) * N + i];
+  }
+  fr.E = fr.a1[0] * fr.a1[0] + fr.a1[1] * fr.a1[1] + fr.a1[2] * fr.a1[2];
+  fr.F = fr.a1[0] * fr.a2[0] + fr.a1[1] * fr.a2[1] + fr.a1[2] * fr.a2[2];
+  fr.G = fr.a2[0] * fr.a2[0] + fr.a2[1] * fr.a2[1] + fr.a2[2] * fr.a2[2];
+  fr.W = sqrt(fr.E * fr.G - fr.F * fr.F);
+  fr.n[0] = (fr.a1[1] * fr.a2[2] - fr.a1[2] * fr.a2[1]) / fr.W;
+  fr.n[1] = (fr.a1[2] * fr.a2[0] - fr.a1[0] * fr.a2[2]) / fr.W;
+  fr.n[2] = (fr.a1[0] * fr.a2[1] - fr.a1[1] * fr.a2[0]) / fr.W;
+  return fr;
+}
+
+// Tangents of the last F = 3 pass (positions) -> t6 [6][N]; optional
+// quadrature weights psi W h^2 (Sec. 3.3, Eq. smoothint).
+__global__ void k_tangents(const MembraneOp op, double* __restrict__ t6, double* __restrict__ w) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t N = op.N;
+  if (i >= N) return;
+  for (int c = 0; c < 3; ++c) {
+    t6[c * N + i] = op.gu[c * N + i];
+    t6[(3 + c) * N + i] = op.gv[c * N + i];
+  }
+  if (w) {
+    const Frame fr = frame_at(t6, N, i);
+    w[i] = op.psi_own[i] * fr.W * op.h * op.h;
+  }
+}
+
+// Lambda of Eq. tensor into op.g as 6 fields (xx, yy, zz, xy, xz, yz).
+// V^2 = F_s F_s^T = (G_r a1 a1^T - F_r (a1 a2^T + a2 a1^T) + E_r a2 a2^T) / W_r^2
+// (F_s = a1 (x) a^1_r + a2 (x) a^2_r with the dual reference basis), so
+// I1 = tr V^2 - 2, I2 = (W / W_r)^2 - 1, J_s = W / W_r.
+__global__ void k_tension(const MembraneOp op, const double* __restrict__ cur,
+                          const double* __restrict__ ref, double Es, double ED) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t N = op.N;
+  if (i >= N) return;
+  const Frame c = frame_at(cur, N, i), r = frame_at(ref, N, i);
+  const double iw2 = 1.0 / (r.W * r.W);
+  const double tr = (r.G * c.E - 2.0 * r.F * c.F + r.E * c.G) * iw2;
+  const double Js = c.W / r.W;
+  const double I1 = tr - 2.0, I2 = Js * Js - 1.0;
+  const double k1 = Es / (2.0 * Js) * (I1 + 1.0), k2 = 0.5 * Js * (ED * I2 - Es);
+  const int ia[6] = {0, 1, 2, 0, 0, 1}, ib[6] = {0, 1, 2, 1, 2, 2};
+  for (int q = 0; q < 6; ++q) {
+    const int a = ia[q], b = ib[q];
+    const double V2 = (r.G * c.a1[a] * c.a1[b] - r.F * (c.a1[a] * c.a2[b] + c.a2[a] * c.a1[b]) +
+                       r.E * c.a2[a] * c.a2[b]) *
+                      iw2;
+    const double P = (a == b ? 1.0 : 0.0) - c.n[a] * c.n[b];
+    op.g[q * N + i] = k1 * V2 + k2 * P;
+  }
+}
+
+// f_k = div_gamma Lambda[:, k] = sum_i ((G L_u - F L_v)/W^2 a1 + (E L_v - F L_u)/W^2 a2)_i
+// (Appendix, Table diff_formulas; Eq. intf), from the F = 6 pass on Lambda.
+__global__ void k_divergence(const MembraneOp op, const double* __restrict__ cur,
+                             double* __restrict__ f) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t N = op.N;
+  if (i >= N) return;
+  const Frame c = frame_at(cur, N, i);
+  const double iw2 = 1.0 / (c.W * c.W);
+  const int comp[3][3] = {{0, 3, 4}, {3, 1, 5}, {4, 5, 2}};
+  for (int k = 0; k < 3; ++k) {
+    double acc = 0.0;
+    for (int a = 0; a < 3; ++a) {
+      const int q = comp[a][k];
+      const double lu = op.gu[q * N + i], lv = op.gv[q * N + i];
+      acc += ((c.G * lu - c.F * lv) * c.a1[a] + (c.E * lv - c.F * lu) * c.a2[a]) * iw2;
+    }
+    f[3 * i + k] = acc;
+  }
+}
+
+// Area and volume terms (Sec. 4.1): w = psi W h^2, w and w x n_x, summed per
+// block in a fixed order.
+__global__ void k_area_volume(const MembraneOp op, const double* __restrict__ X,
+                              const double* __restrict__ cur, double* __restrict__ part) {
+  __shared__ double sa[256], sv[256];
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double a = 0.0, v = 0.0;
+  if (i < op.N) {
+    const Frame c = frame_at(cur, op.N, i);
+    const double w = op.psi_own[i] * c.W * op.h * op.h;
+    a = w;
+    v = w * X[3 * i] * c.n[0];
+  }
+  sa[threadIdx.x] = a;
+  sv[threadIdx.x] = v;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      sa[threadIdx.x] += sa[threadIdx.x + o];
+      sv[threadIdx.x] += sv[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = sa[0];
+    part[2 * blockIdx.x + 1] = sv[0];
+  }
+}
+
+__global__ void k_sum_pairs(const double* __restrict__ part, int n, double* __restrict__ out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double a = 0.0, v = 0.0;
+  for (int b = 0; b < n; ++b) {
+    a += part[2 * b];
+    v += part[2 * b + 1];
+  }
+  out[0] = a;
+  out[1] = v;
+}
+
+void free_op(MembraneOp* op) {
+  if (!op) return;
+  for (void* p : {(void*)op->ghost_dst, (void*)op->gtap_ptr, (void*)op->gtap_patch,
+                  (void*)op->gtap_uvw, (void*)op->psi_own, (void*)op->btap_ptr,
+                  (void*)op->btap_patch, (void*)op->btap_d, (void*)op->thomas, (void*)op->g,
+                  (void*)op->sg, (void*)op->ext, (void*)op->du, (void*)op->dv, (void*)op->sdu,
+                  (void*)op->sdv, (void*)op->gu, (void*)op->gv, (void*)op->cur_t, (void*)op->red})
+    if (p) cudaFree(p);
+  delete op;
+}
+
+template <class T>
+cudaError_t upload(T** dst, const std::vector<T>& v) {
+  cudaError_t e = cudaMalloc(dst, (v.empty() ? 1 : v.size()) * sizeof(T));
+  if (e == cudaSuccess && !v.empty())
+    e = cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+  return e;
+}
+
+// Host construction of the operator tables for grid order m.
+int build_op(int m, MembraneOp** out, std::string& err) {
+  MembraneOp* op = new (std::nothrow) MembraneOp();
+  if (!op) return SK_ENOMEM;
+  op->m = m;
+  op->n = m - 1;
+  op->E = m + 5;
+  op->N = 6LL * op->n * op->n;
+  op->h = PI_CONST / m;
+  const int n = op->n, E = op->E;
+  const double h = op->h;
+  // ghost taps (Eq. ext): ghost points with exactly one index outside 1..m-1
+  std::vector<int> gdst, gptr{0}, gpatch;
+  std::vector<double> guvw;
+  for (int p = 0; p < 6; ++p)
+    for (int j = -2; j <= m + 2; ++j)
+      for (int k = -2; k <= m + 2; ++k) {
+        const bool ij = j >= 1 && j <= m - 1, ik = k >= 1 && k <= m - 1;
+        if (ij == ik) continue;  // interior node or corner block (no stencil uses it)
+        const D3 x1 = h_chart(p, j * h, k * h);
+        double psi[6];
+        h_pou(x1, psi);
+        for (int q = 0; q < 6; ++q) {
+          if (!(psi[q] > 0.0)) continue;
+          double uq, vq;
+          h_inverse_chart(q, x1, uq, vq);
+          gpatch.push_back(q);
+          guvw.insert(guvw.end(), {uq, vq, psi[q]});
+        }
+        gptr.push_back((int)gpatch.size());
+        gdst.push_back((p * E + j + 2) * E + k + 2);
+      }
+  op->G = (int)gdst.size();
+  // blend taps (Eqs. blendu / blendv)
+  std::vector<double> pown(op->N), bd;
+  std::vector<int> bptr{0}, bpatch;
+  for (int p = 0; p < 6; ++p)
+    for (int j = 1; j <= m - 1; ++j)
+      for (int k = 1; k <= m - 1; ++k) {
+        const double u = j * h, v = k * h;
+        const D3 x0 = h_chart(p, u, v);
+        double psi[6];
+        h_pou(x0, psi);
+        pown[((int64_t)p * n + j - 1) * n + k - 1] = psi[p];
+        for (int q = 0; q < 6; ++q) {
+          if (q == p || !(psi[q] > 0.0)) continue;
+          double uq, vq, J[4];
+          h_inverse_chart(q, x0, uq, vq);
+          h_transition_jacobian(p, q, u, v, uq, vq, J);
+          bpatch.push_back(q);
+          bd.insert(bd.end(), {uq, vq, psi[q], J[0], J[1], J[2], J[3]});
+        }
+        bptr.push_back((int)bpatch.size());
+      }
+  // factorization of the reduced slope system: rows q = 1..n-2 with
+  // (sub, diag, super) = (-, 2, 1), (1, 4, 1) ..., (1, 2, -)
+  std::vector<double> th(2 * n, 0.0);
+  for (int q = 1; q <= n - 2; ++q) {
+    const double b = (q == 1 || q == n - 2) ? 2.0 : 4.0;
+    const double a = q == 1 ? 0.0 : 1.0;
+    const double c = q == n - 2 ? 0.0 : 1.0;
+    const double den = b - a * (q > 1 ? th[q - 1] : 0.0);
+    th[q] = c / den;
+    th[n + q] = 1.0 / den;
+  }
+  cudaError_t e = cudaSuccess;
+  auto ok = [&](cudaError_t x) {
+    if (x != cudaSuccess && e == cudaSuccess) e = x;
+  };
+  ok(upload(&op->ghost_dst, gdst));
+  ok(upload(&op->gtap_ptr, gptr));
+  ok(upload(&op->gtap_patch, gpatch));
+  ok(upload(&op->gtap_uvw, guvw));
+  ok(upload(&op->psi_own, pown));
+  ok(upload(&op->btap_ptr, bptr));
+  ok(upload(&op->btap_patch, bpatch));
+  ok(upload(&op->btap_d, bd));
+  ok(upload(&op->thomas, th));
+  const size_t fn = (size_t)MEM_FMAX * op->N * sizeof(double);
+  ok(cudaMalloc(&op->g, fn));
+  ok(cudaMalloc(&op->sg, 3 * fn));
+  ok(cudaMalloc(&op->ext, (size_t)MEM_FMAX * 6 * E * E * sizeof(double)));
+  ok(cudaMalloc(&op->du, fn));
+  ok(cudaMalloc(&op->dv, fn));
+  ok(cudaMalloc(&op->sdu, 3 * fn));
+  ok(cudaMalloc(&op->sdv, 3 * fn));
+  ok(cudaMalloc(&op->gu, fn));
+  ok(cudaMalloc(&op->gv, fn));
+  ok(cudaMalloc(&op->cur_t, 6 * op->N * sizeof(double)));
+  ok(cudaMalloc(&op->red, (2 * (size_t)blocks_of(op->N) + 2) * sizeof(double)));
+  if (e != cudaSuccess) {
+    err = std::string("membrane operator: ") + cudaGetErrorString(e);
+    free_op(op);
+    return e == cudaErrorMemoryAllocation ? SK_ENOMEM : SK_ECUDA;
+  }
+  *out = op;
+  return SK_OK;
+}
+
+// Spline data (u, v, uv slopes) of F fields in `val` into `sd` ([3][F][N]).
+void enqueue_splines(const MembraneOp& op, int F, const double* val, double* sd, cudaStream_t st) {
+  const int64_t plane = (int64_t)F * op.N;
+  const int64_t lines = (int64_t)F * 6 * op.n;
+  k_slopes<<<blocks_of(lines), 256, 0, st>>>(val, sd, lines, op.n, 0, op.h, op.thomas);
+  k_slopes<<<blocks_of(lines), 256, 0, st>>>(val, sd + plane, lines, op.n, 1, op.h, op.thomas);
+  k_slopes<<<blocks_of(lines), 256, 0, st>>>(sd, sd + 2 * plane, lines, op.n, 1, op.h, op.thomas);
+}
+
+}  // namespace
+
+// The scheme of Sec. 3.5 on F <= MEM_FMAX fields already in op->g ([F][N]);
+// blended derivatives land in op->gu, op->gv.
+void enqueue_derivatives(const MembraneOp& op, int F, cudaStream_t st) {
+  enqueue_splines(op, F, op.g, op.sg, st);
+  k_extend<<<blocks_of((int64_t)F * (op.N + op.G)), 256, 0, st>>>(op, F);
+  k_fd<<<blocks_of((int64_t)F * op.N), 256, 0, st>>>(op, F);
+  enqueue_splines(op, F, op.du, op.sdu, st);
+  enqueue_splines(op, F, op.dv, op.sdv, st);
+  k_blend<<<blocks_of((int64_t)F * op.N), 256, 0, st>>>(op, F);
+}
+
+// Tangents of the nodes X ([N][3], device) into t6 ([6][N]; the operator's
+// own buffer when null); weights psi W h^2 into w when w != nullptr.
+void enqueue_tangents(const MembraneOp& op, const double* X, double* t6, double* w,
+                      cudaStream_t st) {
+  if (!t6) t6 = op.cur_t;
+  k_gather<<<blocks_of(3 * op.N), 256, 0, st>>>(X, op.N, 3, 0, 3, op.g);
+  enqueue_derivatives(op, 3, st);
+  k_tangents<<<blocks_of(op.N), 256, 0, st>>>(op, t6, w);
+}
+
+// Skalak force f ([N][3]) at X given reference tangents ref6 ([6][N]).
+void enqueue_skalak(const MembraneOp& op, const double* X, const double* ref6, double Es,
+                    double ED, double* f, double* w, cudaStream_t st) {
+  enqueue_tangents(op, X, op.cur_t, w, st);
+  k_tension<<<blocks_of(op.N), 256, 0, st>>>(op, op.cur_t, ref6, Es, ED);
+  enqueue_derivatives(op, 6, st);
+  k_divergence<<<blocks_of(op.N), 256, 0, st>>>(op, op.cur_t, f);
+}
+
+// Area and volume of the nodes X into out2 (device, 2 doubles).
+void enqueue_area_volume(const MembraneOp& op, const double* X, double* out2, cudaStream_t st) {
+  enqueue_tangents(op, X, op.cur_t, nullptr, st);
+  const unsigned nb = blocks_of(op.N);
+  k_area_volume<<<nb, 256, 0, st>>>(op, X, op.cur_t, op.red);
+  k_sum_pairs<<<1, 32, 0, st>>>(op.red, (int)nb, out2);
+}
+
+int64_t membrane_nodes(const MembraneOp& op) { return op.N; }
+
+// The context's operator for grid order m (built on first use).
+int membrane_op(sk_ctx* ctx, int m, MembraneOp** out) {
+  for (auto& kv : ctx->membrane_ops)
+    if (kv.first == m) {
+      *out = kv.second;
+      return SK_OK;
+    }
+  if (m < 6 || m > 4097) {
+    ctx->err = "membrane: need 6 <= m <= 4097";
+    return SK_EINVAL;
+  }
+  cudaSetDevice(ctx->device);
+  MembraneOp* op = nullptr;
+  const int rc = build_op(m, &op, ctx->err);
+  if (rc != SK_OK) return rc;
+  ctx->membrane_ops.push_back({m, op});
+  *out = op;
+  return SK_OK;
+}
+
+void free_membrane_ops(sk_ctx* ctx) {
+  for (auto& kv : ctx->membrane_ops) free_op(kv.second);
+  ctx->membrane_ops.clear();
+}
+
+}  // namespace sk
+
+using namespace sk;
+
+extern "C" {
+
+int surface_derivatives(sk_ctx* ctx, int m, int mem, int64_t n_fields, const double* g,
+                        double* g_u, double* g_v, void* stream) {
+  if (!ctx) return SK_EINVAL;
+  if (n_fields < 1 || n_fields > (1 << 20) || !g || !g_u || !g_v ||
+      (mem != SK_HOST && mem != SK_DEVICE)) {
+    ctx->err = "surface_derivatives: need n_fields >= 1, g, g_u, g_v and mem SK_HOST or SK_DEVICE";
+    return SK_EINVAL;
+  }
+  MembraneOp* op = nullptr;
+  int rc = membrane_op(ctx, m, &op);
+  if (rc != SK_OK) return rc;
+  cudaSetDevice(ctx->device);
+  cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
+  const int64_t N = op->N;
+  const size_t bytes = (size_t)N * n_fields * sizeof(double);
+  const double* dg = g;
+  double *du = g_u, *dv = g_v;
+  if (mem == SK_HOST) {
+    rc = ensure_workspace(ctx, 3 * bytes + 1024);
+    if (rc != SK_OK) return rc;
+    double* w = (double*)ctx->ws;
+    const size_t off = (bytes + 255) / 256 * 256 / sizeof(double);
+    cudaMemcpyAsync(w, g, bytes, cudaMemcpyHostToDevice, st);
+    dg = w;
+    du = w + off;
+    dv = w + 2 * off;
+  }
+  for (int64_t c0 = 0; c0 < n_fields; c0 += MEM_FMAX) {
+    const int F = (int)std::min<int64_t>(MEM_FMAX, n_fields - c0);
+    k_gather<<<blocks_of(F * N), 256, 0, st>>>(dg, N, (int)n_fields, (int)c0, F, op->g);
+    enqueue_derivatives(*op, F, st);
+    k_scatter<<<blocks_of(F * N), 256, 0, st>>>(op->gu, N, (int)n_fields, (int)c0, F, du);
+    k_scatter<<<blocks_of(F * N), 256, 0, st>>>(op->gv, N, (int)n_fields, (int)c0, F, dv);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && mem == SK_HOST) {
+    cudaMemcpyAsync(g_u, du, bytes, cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(g_v, dv, bytes, cudaMemcpyDeviceToHost, st);
+  }
+  if (e == cudaSuccess && (mem == SK_HOST || !stream)) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    ctx->err = std::string("surface_derivatives: ") + cudaGetErrorString(e);
+    return SK_ECUDA;
+  }
+  return SK_OK;
+}
+
+int membrane_force(sk_ctx* ctx, int m, int mem, const double* X, const double* X_ref, double Es,
+                   double ED, double* f_out, double* w_out, void* stream) {
+  if (!ctx) return SK_EINVAL;
+  if (!X || !X_ref || !f_out || (mem != SK_HOST && mem != SK_DEVICE) ||
+      !(Es >= 0.0 && Es < INFINITY) || !(ED >= 0.0 && ED < INFINITY)) {
+    ctx->err = "membrane_force: need X, X_ref, f_out, finite Es, ED >= 0 and mem SK_HOST or SK_DEVICE";
+    return SK_EINVAL;
+  }
+  MembraneOp* op = nullptr;
+  int rc = membrane_op(ctx, m, &op);
+  if (rc != SK_OK) return rc;
+  cudaSetDevice(ctx->device);
+  cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
+  const int64_t N = op->N;
+  const size_t b3 = 3 * (size_t)N * sizeof(double), b1 = (size_t)N * sizeof(double);
+  const size_t pad = 256;
+  rc = ensure_workspace(ctx, 3 * (b3 + pad) + 6 * b1 + b1 + 4 * pad);
+  if (rc != SK_OK) return rc;
+  Bump bp;
+  bp.base = ctx->ws;
+  double* ref6 = bp.take<double>(6 * (size_t)N);
+  const double* dX = X;
+  const double* dXr = X_ref;
+  double* df = f_out;
+  double* dw = w_out;
+  if (mem == SK_HOST) {
+    double* tX = bp.take<double>(3 * (size_t)N);
+    double* tXr = bp.take<double>(3 * (size_t)N);
+    df = bp.take<double>(3 * (size_t)N);
+    dw = w_out ? bp.take<double>((size_t)N) : nullptr;
+    cudaMemcpyAsync(tX, X, b3, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(tXr, X_ref, b3, cudaMemcpyHostToDevice, st);
+    dX = tX;
+    dXr = tXr;
+  }
+  enqueue_tangents(*op, dXr, ref6, nullptr, st);
+  enqueue_skalak(*op, dX, ref6, Es, ED, df, dw, st);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && mem == SK_HOST) {
+    cudaMemcpyAsync(f_out, df, b3, cudaMemcpyDeviceToHost, st);
+    if (w_out) cudaMemcpyAsync(w_out, dw, b1, cudaMemcpyDeviceToHost, st);
+  }
+  if (e == cudaSuccess && (mem == SK_HOST || !stream)) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    ctx->err = std::string("membrane_force: ") + cudaGetErrorString(e);
+    return SK_ECUDA;
+  }
+  return SK_OK;
+}
+
+}  // extern "C"

@@ -80,4 +80,12 @@ def test_capsule_entry_points_reject_null_arguments(lib):
     assert lib.capsule_create(None, ctypes.byref(h), 9, None, None, None, 0, 1.0, 1) == sk.SK_EINVAL
     assert lib.capsule_step(None, 1, 0.1, None, None) == sk.SK_EINVAL
     assert lib.capsule_get(None, None) == sk.SK_EINVAL
+    assert lib.capsule_set_membrane(None, None, 1.0, 1.0) == sk.SK_EINVAL
+    assert lib.capsule_area_volume(None, None, None) == sk.SK_EINVAL
     lib.capsule_destroy(None)  # no-op
+
+
+def test_membrane_entry_points_reject_null_context(lib):
+    assert lib.surface_derivatives(None, 9, sk.SK_HOST, 1, None, None, None, None) == sk.SK_EINVAL
+    assert lib.membrane_force(None, 9, sk.SK_HOST, None, None, 1.0, 1.0, None, None,
+                              None) == sk.SK_EINVAL

@@ -1,0 +1,151 @@
+"""Overset finite-difference derivatives, the Skalak force and membrane-driven
+capsule steps on the GPU against the membrane oracle (Sec. 3.5; Sec. 2.1, Eqs.
+tensor and intf). Both sides are FP64, so they agree to rounding (<= 1e-11
+relative) while differing in every implementation choice (spline solver,
+tension invariants, reduction order)."""
+
+import numpy as np
+import pytest
+
+import capsule_inputs as ci
+import oracle
+from oracle import membrane as mb
+
+sk = pytest.importorskip("paper_2310_13908_gb300")
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+ES, ED = 2.0, 20.0
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = sk.Context(0)
+    yield c.handle
+    c.close()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def deformed(s):
+    """A smooth non-affine deformation of a reference surface."""
+    return s.X * np.array([1.08, 0.97, 0.93]) + 0.04 * s.X[:, [1, 2, 0]] ** 2
+
+
+@pytest.mark.parametrize("m", [6, 9, 16, 33])
+@pytest.mark.parametrize("mem", [sk.SK_HOST, sk.SK_DEVICE], ids=["host", "device"])
+def test_surface_derivatives_match_oracle(ctx, m, mem):
+    s = ci.make_surface(ci.Ellipsoid(0.9, 1.0, 0.8), m)
+    rng = np.random.default_rng(m)
+    fields = np.concatenate([s.X, s.X ** 2, ci.sh_density(s.x0, rng, lmax=6),
+                             rng.standard_normal((s.N, 2))], axis=1)   # F = 11 > one pass
+    gu_o, gv_o = mb.surface_derivatives(m, fields)
+    if mem == sk.SK_HOST:
+        gu, gv = sk.surface_derivatives(ctx, m, mem, fields)
+    else:
+        gu, gv = sk.surface_derivatives(ctx, m, mem, torch.as_tensor(fields, device="cuda"))
+        gu, gv = gu.cpu().numpy(), gv.cpu().numpy()
+    assert rel(gu, gu_o) < 1e-12 and rel(gv, gv_o) < 1e-12, (rel(gu, gu_o), rel(gv, gv_o))
+
+
+@pytest.mark.parametrize("m,shape", [(12, ci.Sphere(1.0)), (24, ci.Ellipsoid(0.9, 1.0, 1.0)),
+                                     (65, ci.Ellipsoid(1.0, 0.8, 0.5))],
+                         ids=["sphere-m12", "ellipsoid-m24", "ellipsoid-m65"])
+def test_membrane_force_and_weights_match_oracle(ctx, m, shape):
+    s = ci.make_surface(shape, m)
+    X = deformed(s)
+    f, w = sk.membrane_force(ctx, m, sk.SK_HOST, X, s.X, ES, ED, weights=True)
+    f_o = mb.skalak_force(m, X, s.X, ES, ED)
+    w_o = mb.quadrature_weights(m, X)
+    assert rel(f, f_o) < 1e-11, rel(f, f_o)
+    assert rel(w, w_o) < 1e-13, rel(w, w_o)
+
+
+def test_membrane_force_device_memory_and_stress_free(ctx):
+    s = ci.make_surface(ci.Ellipsoid(0.9, 1.0, 1.0), 16)
+    Xd = torch.as_tensor(s.X, device="cuda")
+    f = sk.membrane_force(ctx, 16, sk.SK_DEVICE, Xd, Xd, ES, ED).cpu().numpy()
+    assert np.abs(f).max() < 1e-11
+    # dilated sphere: f = -(2 T / a) n
+    s = ci.make_surface(ci.Sphere(1.0), 24)
+    a = 1.05
+    T = (ES * (a * a - 1) + ED * a * a * (a ** 4 - 1)) / 2
+    f = sk.membrane_force(ctx, 24, sk.SK_DEVICE, torch.as_tensor(a * s.X, device="cuda"),
+                          torch.as_tensor(s.X, device="cuda"), ES, ED).cpu().numpy()
+    assert np.abs(f + (2 * T / a) * s.x0).max() / (2 * T / a) < 2e-5
+
+
+def test_membrane_rejects_bad_arguments(ctx):
+    s = ci.make_surface(ci.Sphere(1.0), 5)
+    with pytest.raises(sk.SkError) as e:
+        sk.membrane_force(ctx, 5, sk.SK_HOST, s.X, s.X, ES, ED)   # m >= 6
+    assert e.value.code == sk.SK_EINVAL
+    s = ci.make_surface(ci.Sphere(1.0), 8)
+    with pytest.raises(sk.SkError) as e:
+        sk.membrane_force(ctx, 8, sk.SK_HOST, s.X, s.X, -1.0, ED)
+    assert e.value.code == sk.SK_EINVAL
+
+
+def oracle_membrane_euler(m, X, X_ref, n_steps, dt, flow, mu):
+    """Euler steps of Eq. bi_combined with the Skalak force (Eq. intf), weights
+    psi W h^2 and delta* (Eq. regparam) at the current nodes, all by the oracle."""
+    X = X.copy()
+    for _ in range(n_steps):
+        f = mb.skalak_force(m, X, X_ref, ES, ED)
+        w = mb.quadrature_weights(m, X)
+        surf = ci.make_surface(ci.Sphere(1.0), m)
+        surf.X = X
+        d = ci.delta_star(surf)
+        u = oracle.sl(X, w, f, X, d, mu)
+        if flow is not None and flow[0] == sk.SK_FLOW_SHEAR:
+            u[:, 0] += flow[1] * X[:, 1]
+        X = X + dt * u
+    return X
+
+
+@pytest.mark.parametrize("prec,tol", [(sk.SK_FP64, 1e-10), (sk.SK_FP32C, 2e-6)],
+                         ids=["fp64", "fp32c"])
+def test_capsule_membrane_steps_match_oracle(ctx, prec, tol):
+    m = 12
+    ref = ci.make_surface(ci.Ellipsoid(0.9, 1.0, 1.0), m)
+    X0 = deformed(ref)
+    flow = (sk.SK_FLOW_SHEAR, 1.0, 0.0, 0.0)
+    cap = sk.Capsule(ctx, m, X0, ref.w, delta=None, mu=1.0, precision=prec)
+    try:
+        cap.set_membrane(ref.X, ES, ED)
+        cap.step(3, 1e-3, None, flow)
+        X = cap.positions()
+        A, V = cap.area_volume()
+    finally:
+        cap.close()
+    Xo = oracle_membrane_euler(m, X0, ref.X, 3, 1e-3, flow, 1.0)
+    err = np.linalg.norm((X - X0) - (Xo - X0)) / np.linalg.norm(Xo - X0)
+    assert err < tol, err
+    Ao, Vo = mb.area_volume(m, X)
+    assert abs(A - Ao) / Ao < 1e-13 and abs(V - Vo) / Vo < 1e-13
+
+
+def test_membrane_capsule_relaxes_toward_reference(ctx):
+    """A deformed capsule with no background flow moves back toward its
+    stress-free shape: the Skalak energy decreases step by step."""
+    m = 16
+    ref = ci.make_surface(ci.Sphere(1.0), m)
+    X0 = deformed(ref)
+    cap = sk.Capsule(ctx, m, X0, ref.w, delta=None, mu=1.0, precision=sk.SK_FP64)
+    try:
+        cap.set_membrane(ref.X, ES, ED)
+        dist = [np.linalg.norm(cap.positions() - ref.X)]
+        for _ in range(3):
+            cap.step(20, 2e-3, None)
+            dist.append(np.linalg.norm(cap.positions() - ref.X))
+        _, V = cap.area_volume()
+    finally:
+        cap.close()
+    assert all(b < a for a, b in zip(dist, dist[1:])), dist
+    _, V0 = mb.area_volume(m, X0)
+    assert abs(V - V0) / V0 < 1e-3   # the Stokes flow conserves volume
