@@ -446,6 +446,53 @@ def serving_bench(sk, h, reqs):
     return res
 
 
+def capsule_bench(sk, h, torch, dev, m=129, steps=100, dt=5e-4, Es=2.0, ED=20.0):
+    """Capsule with a Skalak membrane in shear flow: stress-free ellipsoid
+    (0.9, 1, 1), Es = 2, ED = 20, shear rate 1 (Sec. 4.3 setup), m = 129,
+    explicit Euler steps with f = div_gamma Lambda, weights and delta* updated
+    every step. dt = 5e-4: explicit Euler on this grid is unstable at 1e-3."""
+    import capsule_inputs as ci
+    ref = ci.make_surface(ci.Ellipsoid(0.9, 1.0, 1.0), m)
+    flow = (sk.SK_FLOW_SHEAR, 1.0, 0.0, 0.0)
+    res = {"workload": f"ellipsoid(0.9,1,1) stress-free, m={m} (N={ref.N}), Es={Es}, ED={ED}, "
+                       f"shear rate 1, explicit Euler dt={dt}, delta* per step",
+           "steps": steps, "dt": dt}
+    # the membrane force alone (device memory, CUDA events)
+    Xd = torch.as_tensor(ref.X * np.array([1.02, 0.99, 1.0]), device=dev)
+    Xr = torch.as_tensor(ref.X, device=dev)
+    for _ in range(2):
+        sk.membrane_force(h, m, sk.SK_DEVICE, Xd, Xr, Es, ED)
+    torch.cuda.synchronize(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(10):
+        sk.membrane_force(h, m, sk.SK_DEVICE, Xd, Xr, Es, ED)
+    b.record()
+    torch.cuda.synchronize(dev)
+    res["membrane_force_ms"] = a.elapsed_time(b) / 10
+
+    def run(prec, n):
+        cap = sk.Capsule(h, m, ref.X, ref.w, delta=None, mu=1.0, precision=prec)
+        try:
+            cap.set_membrane(ref.X, Es, ED)
+            A0, V0 = cap.area_volume()
+            cap.step(1, dt, None, flow)  # captures the step graph
+            t0 = time.perf_counter()
+            cap.step(n, dt, None, flow)
+            ms = (time.perf_counter() - t0) * 1e3 / n
+            A, V = cap.area_volume()
+            return cap.positions(), {"ms_per_step": ms, "area_change": A / A0 - 1.0,
+                                     "volume_drift": V / V0 - 1.0}
+        finally:
+            cap.close()
+
+    _, res["fp32c"] = run(sk.SK_FP32C, steps)
+    X64, res["fp64"] = run(sk.SK_FP64, 10)
+    X32, _ = run(sk.SK_FP32C, 10)
+    res["fp32c_vs_fp64_after_11_steps"] = rel_l2(X32 - ref.X, X64 - ref.X)
+    return res
+
+
 def extras(sk, h, w, X, W, F, Y, D, out, u_fp32, stream, dev, torch, serve_future=None):
     import capsule_inputs as ci
     import oracle
@@ -569,6 +616,10 @@ def extras(sk, h, w, X, W, F, Y, D, out, u_fp32, stream, dev, torch, serve_futur
                          "flops_per_interaction": FLOPS_DL}}
     except Exception as e:
         res["dl_ellipsoid_m193"] = {"error": repr(e)}
+    try:
+        res["capsule_skalak_m129"] = capsule_bench(sk, h, torch, dev)
+    except Exception as e:
+        res["capsule_skalak_m129"] = {"error": repr(e)}
     if serve_future is not None:
         try:
             res["serving"] = serving_bench(sk, h, serve_future.result())

@@ -8,6 +8,10 @@ The arithmetic lives in stokes_oracle.c (plain C, FP64, libm erf/exp); this
 module compiles it with gcc on first use and marshals numpy arrays through
 ctypes. See stokes_oracle.c for the formulas and their paper citations
 (Sec. 3.4, Eq. regstokes; Sec. 3.3, Eq. smoothint).
+
+Submodules (plain NumPy, same status): membrane.py -- overset finite-difference
+surface derivatives and the Skalak membrane force (Sec. 3.5; Sec. 2.1);
+timestep.py -- Runge-Kutta-Fehlberg 4(5) adaptive stepping (Sec. 3.6).
 """
 
 from __future__ import annotations
