@@ -182,6 +182,25 @@ int capsule_create(sk_ctx* ctx, sk_capsule** out, int m, const double* X, const 
  * Synchronous. Errors: SK_EINVAL, SK_ENOTIMPL, SK_ENOMEM, SK_ECUDA, SK_ETIMEOUT. */
 int capsule_step(sk_capsule* c, int n_steps, double dt, const sk_flow* flow, const double* f);
 
+/* Adaptive Runge-Kutta-Fehlberg 4(5) integration (Sec. 3.6) of
+ * dx/dt = u_inf(x) + S[f](x) from now over a time t_end > 0. Every stage
+ * recomputes what capsule_step does per step (membrane force and weights
+ * when a membrane is set and f is NULL, delta* when created with
+ * delta = NULL). The fourth-order solution is propagated; a step is accepted
+ * when max |x5 - x4| / max |x4| <= tol, and the next trial step is
+ * dt min(5, max(0.2, 0.9 (tol / err)^(1/5))); the last step lands on t_end.
+ *   dt_inout   first trial step in (> 0), the suggested next step out
+ *   f          as for capsule_step (host [N][3], or NULL for the membrane)
+ *   max_steps  bound on accepted + rejected steps (SK_EAGAIN if t_end is
+ *              not reached; the nodes hold the last accepted state)
+ *   stats_out  NULL or [2]: accepted, rejected steps
+ * Synchronous (one device-to-host read of two numbers per step).
+ * Errors: SK_EINVAL (also for a non-finite step), SK_ENOTIMPL, SK_EAGAIN,
+ * SK_ENOMEM, SK_ECUDA, SK_ETIMEOUT. */
+int capsule_integrate_rkf45(sk_capsule* c, double t_end, double* dt_inout, double tol,
+                            const sk_flow* flow, const double* f, int64_t max_steps,
+                            int64_t* stats_out);
+
 /* Give the capsule a Skalak membrane (Sec. 2.1, Eq. tensor): stress-free
  * reference nodes X_ref [N][3] (host, same grid order as X; copied), shear
  * modulus Es >= 0 and dilatation modulus ED >= 0. Reference tangents come

@@ -86,6 +86,8 @@ _EXTRA_DECLS: dict = {
     "capsule_step": ([_vp, _int, _dbl, _vp, _vp], _int),
     "capsule_get": ([_vp, _vp], _int),
     "capsule_set_membrane": ([_vp, _vp, _dbl, _dbl], _int),
+    "capsule_integrate_rkf45": ([_vp, _dbl, ctypes.POINTER(_dbl), _dbl, _vp, _vp, _i64,
+                                 ctypes.POINTER(ctypes.c_int64)], _int),
     "capsule_area_volume": ([_vp, ctypes.POINTER(_dbl), ctypes.POINTER(_dbl)], _int),
     "surface_derivatives": ([_vp, _int, _int, _i64, _vp, _vp, _vp, _vp], _int),
     "membrane_force": ([_vp, _int, _int, _vp, _vp, _dbl, _dbl, _vp, _vp, _vp], _int),
@@ -335,6 +337,18 @@ class Capsule:
             raise ValueError("X_ref must hold the capsule's nodes")
         _check(self.ctx, load().capsule_set_membrane(self.handle, _host_ptr(Xr), float(Es),
                                                      float(ED)))
+
+    def integrate_rkf45(self, t_end: float, dt: float, tol: float = 1e-6, f=None, flow=None,
+                        max_steps: int = 100000):
+        """Adaptive RKF45 over t_end (Sec. 3.6); returns (next dt, accepted, rejected)."""
+        F, _ = _ptr(f, SK_HOST, (3,), "f") if f is not None else (None, 0)
+        fl = ctypes.byref(sk_flow(*flow)) if flow is not None else None
+        d = ctypes.c_double(dt)
+        stats = (ctypes.c_int64 * 2)()
+        _check(self.ctx, load().capsule_integrate_rkf45(self.handle, float(t_end), ctypes.byref(d),
+                                                        float(tol), fl, _host_ptr(F),
+                                                        int(max_steps), stats))
+        return d.value, int(stats[0]), int(stats[1])
 
     def area_volume(self):
         a, v = ctypes.c_double(), ctypes.c_double()

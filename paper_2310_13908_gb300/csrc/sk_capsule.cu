@@ -10,6 +10,7 @@
 // the update X += dt (S[f](X) + u_inf(X)). The step is captured once into a
 // CUDA graph and replayed n_steps times, so a step costs one graph launch on
 // the host.
+#include <cmath>
 #include <cstring>
 #include <new>
 
@@ -35,6 +36,16 @@ struct sk_capsule {
   double* ref6 = nullptr;
   double Es = 0.0, ED = 0.0;
   double* av = nullptr;  // [2] area, volume (device)
+  // RKF45 (capsule_integrate_rkf45): stage positions, stage slopes, reductions
+  double* Y = nullptr;    // [N][3]
+  double* K = nullptr;    // [6][N][3]
+  double* red = nullptr;  // block maxima, then [2] (error, |x4|)
+  cudaGraphExec_t rhs_exec = nullptr;  // u = u_inf(Y) + S[f(Y)](Y)
+  sk_flow r_flow{};
+  char* r_ws = nullptr;
+  size_t r_ws_bytes = 0;
+  double r_rho_T = 0.0, r_rho_c = 0.0;
+  int r_mode = -1;
   // captured step graph and the state it was captured for
   int g_mode = -1;  // 0: supplied f; 1: supplied f, membrane weights; 2: Skalak force
   cudaGraphExec_t exec = nullptr;
@@ -101,9 +112,88 @@ __global__ void k_sticky(const unsigned long long* __restrict__ flags,
   if (i < N_FLAGS && flags[i]) atomicOr(sticky + i, flags[i]);
 }
 
+// Fehlberg's RK4(5) tableau (Sec. 3.6 names the scheme): stage coefficients,
+// fourth-order weights (propagated) and fifth-order weights (error estimate).
+__constant__ double RK_A[6][5] = {
+    {0, 0, 0, 0, 0},
+    {1.0 / 4, 0, 0, 0, 0},
+    {3.0 / 32, 9.0 / 32, 0, 0, 0},
+    {1932.0 / 2197, -7200.0 / 2197, 7296.0 / 2197, 0, 0},
+    {439.0 / 216, -8.0, 3680.0 / 513, -845.0 / 4104, 0},
+    {-8.0 / 27, 2.0, -3544.0 / 2565, 1859.0 / 4104, -11.0 / 40}};
+__constant__ double RK_B4[6] = {25.0 / 216, 0, 1408.0 / 2565, 2197.0 / 4104, -1.0 / 5, 0};
+__constant__ double RK_B5[6] = {16.0 / 135, 0, 6656.0 / 12825, 28561.0 / 56430, -9.0 / 50,
+                                2.0 / 55};
+
+// Y = X + dt sum_{j < s} a_sj K_j
+__global__ void k_rk_stage(const double* __restrict__ X, const double* __restrict__ K, int s,
+                           double dt, int64_t n3, double* __restrict__ Y) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n3) return;
+  double acc = 0.0;
+  for (int j = 0; j < s; ++j) acc += RK_A[s][j] * K[j * n3 + i];
+  Y[i] = X[i] + dt * acc;
+}
+
+// u += u_inf(Y) (Eqs. shear_flow, poiseuille_flow)
+__global__ void k_add_uinf(double* __restrict__ u, const double* __restrict__ Y, int64_t N,
+                           sk_flow fl) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const double y = Y[3 * i + 1], z = Y[3 * i + 2];
+  if (fl.kind == SK_FLOW_SHEAR) u[3 * i] += fl.rate * y;
+  if (fl.kind == SK_FLOW_POISEUILLE) u[3 * i] += fl.alpha * (fl.R0 * fl.R0 - y * y - z * z);
+}
+
+// Y = X + dt sum b4_j K_j; per block: max |dt sum (b5_j - b4_j) K_j| and max |Y|.
+__global__ void k_rk_finish(const double* __restrict__ X, const double* __restrict__ K, double dt,
+                            int64_t n3, double* __restrict__ Y, double* __restrict__ part) {
+  __shared__ double se[256], sy[256];
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double e = 0.0, a = 0.0;
+  if (i < n3) {
+    double y4 = 0.0, d = 0.0;
+    for (int j = 0; j < 6; ++j) {
+      const double k = K[j * n3 + i];
+      y4 += RK_B4[j] * k;
+      d += (RK_B5[j] - RK_B4[j]) * k;
+    }
+    const double y = X[i] + dt * y4;
+    Y[i] = y;
+    e = fabs(dt * d);
+    a = fabs(y);
+  }
+  se[threadIdx.x] = e;
+  sy[threadIdx.x] = a;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      se[threadIdx.x] = fmax(se[threadIdx.x], se[threadIdx.x + o]);
+      sy[threadIdx.x] = fmax(sy[threadIdx.x], sy[threadIdx.x + o]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = se[0];
+    part[2 * blockIdx.x + 1] = sy[0];
+  }
+}
+
+__global__ void k_max_pairs(const double* __restrict__ part, int n, double* __restrict__ out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double e = 0.0, a = 0.0;
+  for (int b = 0; b < n; ++b) {
+    e = fmax(e, part[2 * b]);
+    a = fmax(a, part[2 * b + 1]);
+  }
+  out[0] = e;
+  out[1] = a;
+}
+
 void free_capsule(sk_capsule* c) {
   if (c->exec) cudaGraphExecDestroy(c->exec);
-  for (double* p : {c->X, c->w, c->f, c->u, c->delta, c->ref6, c->av})
+  if (c->rhs_exec) cudaGraphExecDestroy(c->rhs_exec);
+  for (double* p : {c->X, c->w, c->f, c->u, c->delta, c->ref6, c->av, c->Y, c->K, c->red})
     if (p) cudaFree(p);
   if (c->patch_max) cudaFree(c->patch_max);
   if (c->sticky) cudaFree(c->sticky);
@@ -276,6 +366,156 @@ int capsule_step(sk_capsule* c, int n_steps, double dt, const sk_flow* flow, con
   return SK_OK;
 }
 
+int capsule_integrate_rkf45(sk_capsule* c, double t_end, double* dt_inout, double tol,
+                            const sk_flow* flow, const double* f, int64_t max_steps,
+                            int64_t* stats_out) {
+  if (!c) return SK_EINVAL;
+  sk_ctx* ctx = c->ctx;
+  if (!dt_inout || !(t_end > 0.0 && t_end < INFINITY) || !(*dt_inout > 0.0 && *dt_inout < INFINITY) ||
+      !(tol > 0.0 && tol < 1.0) || max_steps < 1 ||
+      (flow && (flow->kind < SK_FLOW_NONE || flow->kind > SK_FLOW_POISEUILLE))) {
+    ctx->err = "capsule_integrate_rkf45: need t_end > 0, *dt_inout > 0, 0 < tol < 1, "
+               "max_steps >= 1 and a known flow kind";
+    return SK_EINVAL;
+  }
+  if (!f && !c->mop) {
+    ctx->err = "capsule_integrate_rkf45: f = NULL takes the Skalak force, which needs "
+               "capsule_set_membrane";
+    return SK_ENOTIMPL;
+  }
+  const int mode = c->mop ? (f ? 1 : 2) : 0;
+  cudaSetDevice(ctx->device);
+  cudaStream_t st = ctx->stream;
+  const sk_flow fl = flow ? *flow : sk_flow{SK_FLOW_NONE, 0.0, 0.0, 0.0};
+  const int64_t n3 = 3 * c->N;
+  const unsigned nb = blocks(n3);
+  cudaError_t e = cudaSuccess;
+  if (!c->Y) e = cudaMalloc(&c->Y, n3 * sizeof(double));
+  if (e == cudaSuccess && !c->K) e = cudaMalloc(&c->K, 6 * n3 * sizeof(double));
+  if (e == cudaSuccess && !c->red) e = cudaMalloc(&c->red, (2 * (size_t)nb + 2) * sizeof(double));
+  if (e == cudaSuccess && f) e = cudaMemcpyAsync(c->f, f, n3 * sizeof(double), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) {
+    ctx->err = std::string("capsule_integrate_rkf45: ") + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? SK_ENOMEM : SK_ECUDA;
+  }
+  EvalShape s;
+  s.layer = LAYER_SL;
+  s.precision = c->precision;
+  s.N = c->N;
+  s.M = c->N;
+  s.n_delta = c->n_delta;
+  s.mu = c->mu;
+  s.copy_inputs = false;
+  s.n_chunks = choose_chunks(c->precision, c->N, c->N, ctx->sm_count);
+  int rc = ensure_workspace(ctx, eval_workspace_bytes(s));
+  if (rc != SK_OK) return rc;
+  // right-hand side graph on the stage positions Y: u = u_inf(Y) + S[f(Y)](Y)
+  const bool stale = !c->rhs_exec || std::memcmp(&c->r_flow, &fl, sizeof(fl)) != 0 ||
+                     c->r_ws != ctx->ws || c->r_ws_bytes != ctx->ws_bytes ||
+                     c->r_rho_T != ctx->rho_T || c->r_rho_c != ctx->rho_c || c->r_mode != mode;
+  if (stale) {
+    if (c->rhs_exec) cudaGraphExecDestroy(c->rhs_exec);
+    c->rhs_exec = nullptr;
+    EvalBufs b;
+    Bump bp;
+    bp.base = ctx->ws;
+    carve_eval_buffers(bp, s, b);
+    b.src_xyz = c->Y;
+    b.src_w = c->w;
+    b.dens = c->f;
+    b.tgt_xyz = c->Y;
+    b.delta = c->delta;
+    b.u = c->u;
+    cudaGraph_t g = nullptr;
+    if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
+      ctx->err = std::string("capsule_integrate_rkf45: capture: ") + cudaGetErrorString(e);
+      return SK_ECUDA;
+    }
+    if (mode == 1) enqueue_tangents(*c->mop, c->Y, nullptr, c->w, st);
+    if (mode == 2) enqueue_skalak(*c->mop, c->Y, c->ref6, c->Es, c->ED, c->f, c->w, st);
+    if (c->auto_delta) {
+      cudaMemsetAsync(c->patch_max, 0, 8 * sizeof(unsigned long long), st);
+      k_delta_star_patch<<<blocks(c->N), 256, 0, st>>>(c->Y, c->m, c->patch_max);
+      k_delta_fill<<<blocks(c->N), 256, 0, st>>>(c->patch_max, c->m, 1.0, c->delta);
+    }
+    enqueue_eval(s, b, ctx->rho_T, ctx->rho_c, st);
+    k_sticky<<<1, 32, 0, st>>>(b.flags, c->sticky);
+    k_add_uinf<<<blocks(c->N), 256, 0, st>>>(c->u, c->Y, c->N, fl);
+    e = cudaStreamEndCapture(st, &g);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&c->rhs_exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      c->rhs_exec = nullptr;
+      ctx->err = std::string("capsule_integrate_rkf45: graph: ") + cudaGetErrorString(e);
+      return SK_ECUDA;
+    }
+    c->r_flow = fl;
+    c->r_ws = ctx->ws;
+    c->r_ws_bytes = ctx->ws_bytes;
+    c->r_rho_T = ctx->rho_T;
+    c->r_rho_c = ctx->rho_c;
+    c->r_mode = mode;
+  }
+  // adaptive loop: accept when max|x5 - x4| / max|x4| <= tol, then
+  // dt <- dt min(5, max(0.2, 0.9 (tol / err)^(1/5))); the last step lands on t_end
+  cudaMemsetAsync(c->sticky, 0, N_FLAGS * sizeof(unsigned long long), st);
+  double t = 0.0, dt = *dt_inout;
+  int64_t acc = 0, rej = 0;
+  while (t < t_end && acc + rej < max_steps) {
+    const double hstep = std::fmin(dt, t_end - t);
+    for (int sidx = 0; sidx < 6 && e == cudaSuccess; ++sidx) {
+      k_rk_stage<<<nb, 256, 0, st>>>(c->X, c->K, sidx, hstep, n3, c->Y);
+      if ((e = cudaGraphLaunch(c->rhs_exec, st)) != cudaSuccess) break;
+      e = cudaMemcpyAsync(c->K + sidx * n3, c->u, n3 * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    }
+    if (e != cudaSuccess) break;
+    k_rk_finish<<<nb, 256, 0, st>>>(c->X, c->K, hstep, n3, c->Y, c->red);
+    k_max_pairs<<<1, 32, 0, st>>>(c->red, (int)nb, c->red + 2 * nb);
+    double h2[2];
+    e = cudaMemcpyAsync(h2, c->red + 2 * nb, sizeof(h2), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) break;
+    const double err = h2[0] / std::fmax(h2[1], 1e-300);
+    if (!(err == err)) {  // NaN: the step blew up
+      ctx->err = "capsule_integrate_rkf45: non-finite step";
+      return SK_EINVAL;
+    }
+    if (err <= tol) {
+      e = cudaMemcpyAsync(c->X, c->Y, n3 * sizeof(double), cudaMemcpyDeviceToDevice, st);
+      t += hstep;
+      ++acc;
+    } else {
+      ++rej;
+    }
+    dt = err == 0.0 ? hstep * 5.0 : hstep * std::fmin(5.0, std::fmax(0.2, 0.9 * std::pow(tol / err, 0.2)));
+  }
+  unsigned long long flags[N_FLAGS] = {};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(flags, c->sticky, sizeof(flags), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    ctx->err = std::string("capsule_integrate_rkf45: ") + cudaGetErrorString(e);
+    return SK_ECUDA;
+  }
+  *dt_inout = dt;
+  if (stats_out) {
+    stats_out[0] = acc;
+    stats_out[1] = rej;
+  }
+  if (flags[FLAG_TIMEOUT]) {
+    ctx->err = "capsule_integrate_rkf45: a bounded device wait expired";
+    return SK_ETIMEOUT;
+  }
+  if (flags[FLAG_BAD_DELTA]) {
+    ctx->err = "capsule_integrate_rkf45: delta must be positive and finite";
+    return SK_EINVAL;
+  }
+  if (t < t_end) {
+    ctx->err = "capsule_integrate_rkf45: max_steps reached before t_end";
+    return SK_EAGAIN;
+  }
+  return SK_OK;
+}
+
 int capsule_set_membrane(sk_capsule* c, const double* X_ref, double Es, double ED) {
   if (!c) return SK_EINVAL;
   sk_ctx* ctx = c->ctx;
@@ -306,7 +546,8 @@ int capsule_set_membrane(sk_capsule* c, const double* X_ref, double Es, double E
   c->mop = op;
   c->Es = Es;
   c->ED = ED;
-  c->g_mode = -1;  // recapture the step
+  c->g_mode = -1;  // recapture the step graphs
+  c->r_mode = -1;
   return SK_OK;
 }
 

@@ -36,17 +36,20 @@ constexpr int MEM_FMAX = 9;  // fields per pass (Lambda has 6, positions 3)
 struct MembraneOp {
   int m = 0, n = 0, E = 0;  // E = m + 5: extended grid (indices -2..m+2)
   int64_t N = 0;
-  double h = 0.0;
+  double h = 0.0, ih = 0.0;
   int G = 0;  // ghost points used by the stencils, per field
-  // operator tables (device)
+  // operator tables (device). A tap is a spline evaluation at a fixed point
+  // of one patch: its cell (node index p n^2 + a n + b of the cell's first
+  // corner) and the eight Hermite basis values there (u: value left/right,
+  // slope left/right; v likewise), followed by the tap's weights.
   int* ghost_dst = nullptr;    // [G] offset in a field's extended block (6 E^2)
   int* gtap_ptr = nullptr;     // [G + 1]
-  int* gtap_patch = nullptr;   // [taps] 0..5
-  double* gtap_uvw = nullptr;  // [taps][3]: u, v, psi
+  int* gtap_cell = nullptr;    // [taps]
+  double* gtap_w = nullptr;    // [taps][9]: basis[8], psi
   double* psi_own = nullptr;   // [N]
   int* btap_ptr = nullptr;     // [N + 1]
-  int* btap_patch = nullptr;
-  double* btap_d = nullptr;    // [taps][7]: u, v, psi, dtau1/du, dtau2/du, dtau1/dv, dtau2/dv
+  int* btap_cell = nullptr;
+  double* btap_w = nullptr;    // [taps][13]: basis[8], psi, dtau1/du, dtau2/du, dtau1/dv, dtau2/dv
   double* thomas = nullptr;    // [2 n]: c' and 1/den of the reduced slope system
   // scratch for up to MEM_FMAX fields
   double *g = nullptr, *sg = nullptr;    // values, spline data [3][F][N] (u, v, uv slopes)
@@ -141,66 +144,130 @@ void h_transition_jacobian(int p, int q, double u, double v, double uq, double v
   solve(pv, J[2], J[3]);
 }
 
+// Cell and cubic Hermite bases of the point (u, v) on a patch grid with n
+// nodes per line at u = h, 2h, ..: the cell is clamped to the first/last one,
+// so points beyond the nodes continue the end pieces.
+int h_cell_basis(int p, int n, double h, double u, double v, double basis[8]) {
+  const double tu = u / h - 1.0, tv = v / h - 1.0;
+  int a = (int)std::floor(tu), b = (int)std::floor(tv);
+  a = a < 0 ? 0 : (a > n - 2 ? n - 2 : a);
+  b = b < 0 ? 0 : (b > n - 2 ? n - 2 : b);
+  const double t = tu - a, s = tv - b;
+  basis[0] = (1.0 + 2.0 * t) * (1.0 - t) * (1.0 - t);  // value at the left node
+  basis[1] = t * t * (3.0 - 2.0 * t);                  // value at the right node
+  basis[2] = t * (1.0 - t) * (1.0 - t) * h;            // slope at the left node
+  basis[3] = t * t * (t - 1.0) * h;                    // slope at the right node
+  basis[4] = (1.0 + 2.0 * s) * (1.0 - s) * (1.0 - s);
+  basis[5] = s * s * (3.0 - 2.0 * s);
+  basis[6] = s * (1.0 - s) * (1.0 - s) * h;
+  basis[7] = s * s * (s - 1.0) * h;
+  return (p * n + a) * n + b;
+}
+
 // ---------------------------------------------------------------------------
 // Device kernels.
 inline unsigned blocks_of(int64_t n) { return (unsigned)((n + 255) / 256); }
 
-// Not-a-knot cubic-spline slopes along one grid line per thread. Lines: for
-// dir 0 the u-lines (fixed k, stride n), for dir 1 the v-lines (fixed j).
-// With uniform spacing the end conditions read s0 + 2 s1 = (-5 g0 + 4 g1 + g2)/2h
-// and 2 s_{n-2} + s_{n-1} = (5 g_{n-1} - 4 g_{n-2} - g_{n-3})/2h; eliminating s0
-// and s_{n-1} leaves a diagonally dominant tridiagonal system in s1..s_{n-2}
-// whose factorization (thomas) is shared by all lines.
+// Not-a-knot cubic-spline slopes, one warp per grid line. Lines: for dir 0
+// the u-lines (fixed k, stride n), for dir 1 the v-lines (fixed j). With
+// uniform spacing the end conditions read s0 + 2 s1 = (-5 g0 + 4 g1 + g2)/2h
+// and 2 s_{n-2} + s_{n-1} = (5 g_{n-1} - 4 g_{n-2} - g_{n-3})/2h; eliminating
+// s0 and s_{n-1} leaves a diagonally dominant tridiagonal system in
+// s1..s_{n-2} whose factorization (thomas: c'_q, 1/den_q) is shared by all
+// lines. Both sweeps of the solve are affine recurrences,
+//   forward   d_q = -(1/den_q) d_{q-1} + rhs_q / den_q,
+//   backward  s_q = -c'_q s_{q+1} + d_q,
+// each with |multiplier| <= 1/2. Each lane composes the maps of its own run
+// of consecutive terms, a warp scan of the lane aggregates (composition
+// (a2, b2) o (a1, b1) = (a2 a1, a2 b1 + b2)) gives every lane its incoming
+// value, and the lane then replays its run.
+__device__ __forceinline__ void affine_scan(double& a, double& b, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double pa = __shfl_up_sync(0xffffffffu, a, o);
+    const double pb = __shfl_up_sync(0xffffffffu, b, o);
+    if (lane >= o) {
+      b = a * pb + b;
+      a = a * pa;
+    }
+  }
+}
+
 __global__ void k_slopes(const double* __restrict__ g, double* __restrict__ s, int64_t n_lines,
-                         int n, int dir, double h, const double* __restrict__ thomas) {
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= n_lines) return;
+                         int n, int dir, double ih, const double* __restrict__ thomas) {
+  const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (t >= n_lines) return;  // whole warps leave together
   const int64_t fp = t / n;
   const int r = (int)(t % n);
   const int64_t base = fp * n * n + (dir == 0 ? r : (int64_t)r * n);
   const int64_t st = dir == 0 ? n : 1;
-  const double* c_ = thomas;
+  const double* cp = thomas;
   const double* iden = thomas + n;
-  const double r0 = (-5.0 * g[base] + 4.0 * g[base + st] + g[base + 2 * st]) / (2.0 * h);
-  const double rN = (5.0 * g[base + (n - 1) * st] - 4.0 * g[base + (n - 2) * st] -
-                     g[base + (n - 3) * st]) /
-                    (2.0 * h);
-  double prev = 0.0;
-  for (int q = 1; q <= n - 2; ++q) {
-    double rhs = 3.0 * (g[base + (q + 1) * st] - g[base + (q - 1) * st]) / h;
-    if (q == 1) rhs -= r0;
-    if (q == n - 2) rhs -= rN;
-    prev = (rhs - (q > 1 ? prev : 0.0)) * iden[q];
-    s[base + q * st] = prev;
+  const double i2h = 0.5 * ih, i3h = 3.0 * ih;
+  const double r0 = (-5.0 * g[base] + 4.0 * g[base + st] + g[base + 2 * st]) * i2h;
+  const double rN =
+      (5.0 * g[base + (n - 1) * st] - 4.0 * g[base + (n - 2) * st] - g[base + (n - 3) * st]) *
+      i2h;
+  const int K = (n - 2 + 31) / 32;          // terms per lane
+  const int qa = 1 + lane * K;              // this lane's run [qa, qb) of q = 1..n-2
+  const int qb = min(qa + K, n - 1);
+  // forward sweep
+  double A = 1.0, B = 0.0;
+  for (int q = qa; q < qb; ++q) {
+    const double rhs = i3h * (g[base + (q + 1) * st] - g[base + (q - 1) * st]) -
+                       (q == 1 ? r0 : 0.0) - (q == n - 2 ? rN : 0.0);
+    const double a = q == 1 ? 0.0 : -iden[q];
+    B = a * B + rhs * iden[q];
+    A = a * A;
   }
-  double nxt = s[base + (n - 2) * st];
-  for (int q = n - 3; q >= 1; --q) {
-    nxt = s[base + q * st] - c_[q] * nxt;
-    s[base + q * st] = nxt;
+  affine_scan(A, B, lane);
+  double x = __shfl_up_sync(0xffffffffu, B, 1);
+  if (lane == 0) x = 0.0;
+  for (int q = qa; q < qb; ++q) {
+    const double rhs = i3h * (g[base + (q + 1) * st] - g[base + (q - 1) * st]) -
+                       (q == 1 ? r0 : 0.0) - (q == n - 2 ? rN : 0.0);
+    x = (q == 1 ? 0.0 : -iden[q]) * x + rhs * iden[q];
+    s[base + q * st] = x;
   }
-  s[base] = r0 - 2.0 * s[base + st];
-  s[base + (n - 1) * st] = rN - 2.0 * s[base + (n - 2) * st];
+  __syncwarp();
+  // backward sweep over p = 1..n-2, q = n-1-p (s_{n-2} = d_{n-2})
+  A = 1.0;
+  B = 0.0;
+  for (int p = qa; p < qb; ++p) {
+    const int q = n - 1 - p;
+    const double a = q == n - 2 ? 0.0 : -cp[q];
+    B = a * B + s[base + q * st];
+    A = a * A;
+  }
+  affine_scan(A, B, lane);
+  x = __shfl_up_sync(0xffffffffu, B, 1);
+  if (lane == 0) x = 0.0;
+  for (int p = qa; p < qb; ++p) {
+    const int q = n - 1 - p;
+    x = (q == n - 2 ? 0.0 : -cp[q]) * x + s[base + q * st];
+    s[base + q * st] = x;
+  }
+  __syncwarp();
+  if (lane == 0) {
+    s[base] = r0 - 2.0 * s[base + st];
+    s[base + (n - 1) * st] = rN - 2.0 * s[base + (n - 2) * st];
+  }
 }
 
-// Bicubic Hermite evaluation of the spline of field block `base` (one field,
-// one patch) at (u, v); cells continue the end pieces outside the nodes.
-__device__ __forceinline__ double spline_eval(const double* __restrict__ g,
-                                              const double* __restrict__ sd, int64_t plane,
-                                              int64_t base, int n, double h, double u, double v) {
-  const double tu = u / h - 1.0, tv = v / h - 1.0;  // node 0 sits at u = h
-  int a = (int)floor(tu), b = (int)floor(tv);
-  a = a < 0 ? 0 : (a > n - 2 ? n - 2 : a);
-  b = b < 0 ? 0 : (b > n - 2 ? n - 2 : b);
-  const double t = tu - a, s = tv - b;
-  // value and slope bases at the two ends of a cell (slopes in units of h)
-  const double A0 = (1.0 + 2.0 * t) * (1.0 - t) * (1.0 - t), A1 = t * t * (3.0 - 2.0 * t);
-  const double B0 = t * (1.0 - t) * (1.0 - t) * h, B1 = t * t * (t - 1.0) * h;
-  const double C0 = (1.0 + 2.0 * s) * (1.0 - s) * (1.0 - s), C1 = s * s * (3.0 - 2.0 * s);
-  const double D0 = s * (1.0 - s) * (1.0 - s) * h, D1 = s * s * (s - 1.0) * h;
+// Bicubic Hermite evaluation of one field's spline at a tap: node values g,
+// spline data sd (u, v, uv slopes at plane strides), field offset fo, the
+// tap's cell (index of the cell's first corner) and bases w[0..7].
+__device__ __forceinline__ double spline_tap(const double* __restrict__ g,
+                                             const double* __restrict__ sd, int64_t plane,
+                                             int64_t fo, int cell, int n,
+                                             const double* __restrict__ w) {
   const double* su = sd;
   const double* sv = sd + plane;
   const double* suv = sd + 2 * plane;
-  const int64_t i00 = base + (int64_t)a * n + b, i10 = i00 + n, i01 = i00 + 1, i11 = i00 + n + 1;
+  const int64_t i00 = fo + cell, i10 = i00 + n, i01 = i00 + 1, i11 = i00 + n + 1;
+  const double A0 = w[0], A1 = w[1], B0 = w[2], B1 = w[3];
+  const double C0 = w[4], C1 = w[5], D0 = w[6], D1 = w[7];
   return A0 * (C0 * g[i00] + C1 * g[i01] + D0 * sv[i00] + D1 * sv[i01]) +
          A1 * (C0 * g[i10] + C1 * g[i11] + D0 * sv[i10] + D1 * sv[i11]) +
          B0 * (C0 * su[i00] + C1 * su[i01] + D0 * suv[i00] + D1 * suv[i01]) +
@@ -226,10 +293,8 @@ __global__ void k_extend(const MembraneOp op, int F) {
   const int q = (int)(gi % op.G);
   double val = 0.0;
   for (int t = op.gtap_ptr[q]; t < op.gtap_ptr[q + 1]; ++t) {
-    const int p = op.gtap_patch[t];
-    const double* d = op.gtap_uvw + 3 * t;
-    val += d[2] * spline_eval(op.g, op.sg, plane, ((int64_t)f * 6 + p) * op.n * op.n, op.n, op.h,
-                              d[0], d[1]);
+    const double* w = op.gtap_w + 9 * t;
+    val += w[8] * spline_tap(op.g, op.sg, plane, (int64_t)f * N, op.gtap_cell[t], op.n, w);
   }
   op.ext[f * blk + op.ghost_dst[q]] = val;
 }
@@ -247,8 +312,8 @@ __global__ void k_fd(const MembraneOp op, int F) {
   const int E = op.E;
   const double* e = op.ext + (int64_t)f * 6 * E * E + ((int64_t)p * E + j + 3) * E + k + 3;
   const double c1 = 45.0 / 60.0, c2 = -9.0 / 60.0, c3 = 1.0 / 60.0;
-  op.du[i] = (c1 * (e[E] - e[-E]) + c2 * (e[2 * E] - e[-2 * E]) + c3 * (e[3 * E] - e[-3 * E])) / op.h;
-  op.dv[i] = (c1 * (e[1] - e[-1]) + c2 * (e[2] - e[-2]) + c3 * (e[3] - e[-3])) / op.h;
+  op.du[i] = (c1 * (e[E] - e[-E]) + c2 * (e[2 * E] - e[-2 * E]) + c3 * (e[3 * E] - e[-3 * E])) * op.ih;
+  op.dv[i] = (c1 * (e[1] - e[-1]) + c2 * (e[2] - e[-2]) + c3 * (e[3] - e[-3])) * op.ih;
 }
 
 // Eqs. blendu / blendv.
@@ -261,12 +326,12 @@ __global__ void k_blend(const MembraneOp op, int F) {
   const double po = op.psi_own[node];
   double ou = po * op.du[i], ov = po * op.dv[i];
   for (int t = op.btap_ptr[node]; t < op.btap_ptr[node + 1]; ++t) {
-    const int64_t base = ((int64_t)f * 6 + op.btap_patch[t]) * op.n * op.n;
-    const double* d = op.btap_d + 7 * t;
-    const double eu = spline_eval(op.du, op.sdu, plane, base, op.n, op.h, d[0], d[1]);
-    const double ev = spline_eval(op.dv, op.sdv, plane, base, op.n, op.h, d[0], d[1]);
-    ou += d[2] * (eu * d[3] + ev * d[4]);
-    ov += d[2] * (eu * d[5] + ev * d[6]);
+    const double* w = op.btap_w + 13 * t;
+    const int cell = op.btap_cell[t];
+    const double eu = spline_tap(op.du, op.sdu, plane, (int64_t)f * N, cell, op.n, w);
+    const double ev = spline_tap(op.dv, op.sdv, plane, (int64_t)f * N, cell, op.n, w);
+    ou += w[8] * (eu * w[9] + ev * w[10]);
+    ov += w[8] * (eu * w[11] + ev * w[12]);
   }
   op.gu[i] = ou;
   op.gv[i] = ov;
@@ -414,9 +479,9 @@ __global__ void k_sum_pairs(const double* __restrict__ part, int n, double* __re
 
 void free_op(MembraneOp* op) {
   if (!op) return;
-  for (void* p : {(void*)op->ghost_dst, (void*)op->gtap_ptr, (void*)op->gtap_patch,
-                  (void*)op->gtap_uvw, (void*)op->psi_own, (void*)op->btap_ptr,
-                  (void*)op->btap_patch, (void*)op->btap_d, (void*)op->thomas, (void*)op->g,
+  for (void* p : {(void*)op->ghost_dst, (void*)op->gtap_ptr, (void*)op->gtap_cell,
+                  (void*)op->gtap_w, (void*)op->psi_own, (void*)op->btap_ptr,
+                  (void*)op->btap_cell, (void*)op->btap_w, (void*)op->thomas, (void*)op->g,
                   (void*)op->sg, (void*)op->ext, (void*)op->du, (void*)op->dv, (void*)op->sdu,
                   (void*)op->sdv, (void*)op->gu, (void*)op->gv, (void*)op->cur_t, (void*)op->red})
     if (p) cudaFree(p);
@@ -440,11 +505,12 @@ int build_op(int m, MembraneOp** out, std::string& err) {
   op->E = m + 5;
   op->N = 6LL * op->n * op->n;
   op->h = PI_CONST / m;
+  op->ih = m / PI_CONST;
   const int n = op->n, E = op->E;
   const double h = op->h;
   // ghost taps (Eq. ext): ghost points with exactly one index outside 1..m-1
-  std::vector<int> gdst, gptr{0}, gpatch;
-  std::vector<double> guvw;
+  std::vector<int> gdst, gptr{0}, gcell;
+  std::vector<double> gw;
   for (int p = 0; p < 6; ++p)
     for (int j = -2; j <= m + 2; ++j)
       for (int k = -2; k <= m + 2; ++k) {
@@ -455,18 +521,19 @@ int build_op(int m, MembraneOp** out, std::string& err) {
         h_pou(x1, psi);
         for (int q = 0; q < 6; ++q) {
           if (!(psi[q] > 0.0)) continue;
-          double uq, vq;
+          double uq, vq, bs[8];
           h_inverse_chart(q, x1, uq, vq);
-          gpatch.push_back(q);
-          guvw.insert(guvw.end(), {uq, vq, psi[q]});
+          gcell.push_back(h_cell_basis(q, n, h, uq, vq, bs));
+          gw.insert(gw.end(), bs, bs + 8);
+          gw.push_back(psi[q]);
         }
-        gptr.push_back((int)gpatch.size());
+        gptr.push_back((int)gcell.size());
         gdst.push_back((p * E + j + 2) * E + k + 2);
       }
   op->G = (int)gdst.size();
   // blend taps (Eqs. blendu / blendv)
-  std::vector<double> pown(op->N), bd;
-  std::vector<int> bptr{0}, bpatch;
+  std::vector<double> pown(op->N), bw;
+  std::vector<int> bptr{0}, bcell;
   for (int p = 0; p < 6; ++p)
     for (int j = 1; j <= m - 1; ++j)
       for (int k = 1; k <= m - 1; ++k) {
@@ -477,13 +544,14 @@ int build_op(int m, MembraneOp** out, std::string& err) {
         pown[((int64_t)p * n + j - 1) * n + k - 1] = psi[p];
         for (int q = 0; q < 6; ++q) {
           if (q == p || !(psi[q] > 0.0)) continue;
-          double uq, vq, J[4];
+          double uq, vq, J[4], bs[8];
           h_inverse_chart(q, x0, uq, vq);
           h_transition_jacobian(p, q, u, v, uq, vq, J);
-          bpatch.push_back(q);
-          bd.insert(bd.end(), {uq, vq, psi[q], J[0], J[1], J[2], J[3]});
+          bcell.push_back(h_cell_basis(q, n, h, uq, vq, bs));
+          bw.insert(bw.end(), bs, bs + 8);
+          bw.insert(bw.end(), {psi[q], J[0], J[1], J[2], J[3]});
         }
-        bptr.push_back((int)bpatch.size());
+        bptr.push_back((int)bcell.size());
       }
   // factorization of the reduced slope system: rows q = 1..n-2 with
   // (sub, diag, super) = (-, 2, 1), (1, 4, 1) ..., (1, 2, -)
@@ -502,12 +570,12 @@ int build_op(int m, MembraneOp** out, std::string& err) {
   };
   ok(upload(&op->ghost_dst, gdst));
   ok(upload(&op->gtap_ptr, gptr));
-  ok(upload(&op->gtap_patch, gpatch));
-  ok(upload(&op->gtap_uvw, guvw));
+  ok(upload(&op->gtap_cell, gcell));
+  ok(upload(&op->gtap_w, gw));
   ok(upload(&op->psi_own, pown));
   ok(upload(&op->btap_ptr, bptr));
-  ok(upload(&op->btap_patch, bpatch));
-  ok(upload(&op->btap_d, bd));
+  ok(upload(&op->btap_cell, bcell));
+  ok(upload(&op->btap_w, bw));
   ok(upload(&op->thomas, th));
   const size_t fn = (size_t)MEM_FMAX * op->N * sizeof(double);
   ok(cudaMalloc(&op->g, fn));
@@ -534,9 +602,10 @@ int build_op(int m, MembraneOp** out, std::string& err) {
 void enqueue_splines(const MembraneOp& op, int F, const double* val, double* sd, cudaStream_t st) {
   const int64_t plane = (int64_t)F * op.N;
   const int64_t lines = (int64_t)F * 6 * op.n;
-  k_slopes<<<blocks_of(lines), 256, 0, st>>>(val, sd, lines, op.n, 0, op.h, op.thomas);
-  k_slopes<<<blocks_of(lines), 256, 0, st>>>(val, sd + plane, lines, op.n, 1, op.h, op.thomas);
-  k_slopes<<<blocks_of(lines), 256, 0, st>>>(sd, sd + 2 * plane, lines, op.n, 1, op.h, op.thomas);
+  const unsigned nb = blocks_of(32 * lines);  // one warp per line
+  k_slopes<<<nb, 256, 0, st>>>(val, sd, lines, op.n, 0, op.ih, op.thomas);
+  k_slopes<<<nb, 256, 0, st>>>(val, sd + plane, lines, op.n, 1, op.ih, op.thomas);
+  k_slopes<<<nb, 256, 0, st>>>(sd, sd + 2 * plane, lines, op.n, 1, op.ih, op.thomas);
 }
 
 }  // namespace

@@ -82,6 +82,7 @@ def test_capsule_entry_points_reject_null_arguments(lib):
     assert lib.capsule_get(None, None) == sk.SK_EINVAL
     assert lib.capsule_set_membrane(None, None, 1.0, 1.0) == sk.SK_EINVAL
     assert lib.capsule_area_volume(None, None, None) == sk.SK_EINVAL
+    assert lib.capsule_integrate_rkf45(None, 1.0, None, 1e-6, None, None, 10, None) == sk.SK_EINVAL
     lib.capsule_destroy(None)  # no-op
 
 

@@ -10,6 +10,7 @@ import pytest
 import capsule_inputs as ci
 import oracle
 from oracle import membrane as mb
+from oracle import timestep as ts
 
 sk = pytest.importorskip("paper_2310_13908_gb300")
 torch = pytest.importorskip("torch")
@@ -149,3 +150,58 @@ def test_membrane_capsule_relaxes_toward_reference(ctx):
     assert all(b < a for a, b in zip(dist, dist[1:])), dist
     _, V0 = mb.area_volume(m, X0)
     assert abs(V - V0) / V0 < 1e-3   # the Stokes flow conserves volume
+
+
+def oracle_membrane_rhs(m, X_ref, flow, mu):
+    """u_inf(Y) + S[f(Y)](Y) at stage positions Y, all by the oracle: Skalak
+    force, weights psi W h^2 and delta* (Eq. regparam) at Y."""
+    def rhs(t, y):
+        Y = y.reshape(-1, 3)
+        surf = ci.make_surface(ci.Sphere(1.0), m)
+        surf.X = Y
+        u = oracle.sl(Y, mb.quadrature_weights(m, Y), mb.skalak_force(m, Y, X_ref, ES, ED), Y,
+                      ci.delta_star(surf), mu)
+        if flow is not None and flow[0] == sk.SK_FLOW_SHEAR:
+            u[:, 0] += flow[1] * Y[:, 1]
+        return u.ravel()
+    return rhs
+
+
+def test_rkf45_membrane_matches_oracle(ctx):
+    m = 8
+    ref = ci.make_surface(ci.Ellipsoid(0.9, 1.0, 1.0), m)
+    X0 = deformed(ref)
+    flow = (sk.SK_FLOW_SHEAR, 1.0, 0.0, 0.0)
+    cap = sk.Capsule(ctx, m, X0, ref.w, delta=None, mu=1.0, precision=sk.SK_FP64)
+    try:
+        cap.set_membrane(ref.X, ES, ED)
+        dt, acc, rej = cap.integrate_rkf45(4e-3, 2e-3, tol=1e-6, flow=flow)
+        X = cap.positions()
+    finally:
+        cap.close()
+    y, dto, acco, rejo = ts.integrate(oracle_membrane_rhs(m, ref.X, flow, 1.0), X0.ravel(),
+                                      4e-3, 2e-3, 1e-6)
+    assert (acc, rej) == (acco, rejo) and acc >= 2, (acc, rej, acco, rejo)
+    Xo = y.reshape(-1, 3)
+    assert np.linalg.norm((X - X0) - (Xo - X0)) / np.linalg.norm(Xo - X0) < 1e-9
+    assert abs(dt - dto) / dto < 1e-6
+
+
+def test_rkf45_errors_and_step_bound(ctx):
+    m = 8
+    ref = ci.make_surface(ci.Sphere(1.0), m)
+    cap = sk.Capsule(ctx, m, ref.X, ref.w, delta=None, mu=1.0, precision=sk.SK_FP64)
+    try:
+        with pytest.raises(sk.SkError) as e:
+            cap.integrate_rkf45(1e-3, 1e-4)          # no membrane, no force
+        assert e.value.code == sk.SK_ENOTIMPL
+        f = np.zeros((ref.N, 3))
+        f[:, 2] = 1.0
+        with pytest.raises(sk.SkError) as e:
+            cap.integrate_rkf45(1.0, 1e-3, f=f, max_steps=2)
+        assert e.value.code == sk.SK_EAGAIN
+        with pytest.raises(sk.SkError) as e:
+            cap.integrate_rkf45(-1.0, 1e-3, f=f)
+        assert e.value.code == sk.SK_EINVAL
+    finally:
+        cap.close()
