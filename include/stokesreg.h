@@ -248,6 +248,20 @@ int surface_derivatives(sk_ctx* ctx, int m, int mem, int64_t n_fields, const dou
 int membrane_force(sk_ctx* ctx, int m, int mem, const double* X, const double* X_ref, double Es,
                    double ED, double* f_out, double* w_out, void* cuda_stream);
 
+/* Single layer on the four-times upsampled grid (Sec. 3.4, "Upsampling"):
+ * node positions X [N][3], area elements W [N] (e.g. from the derivative
+ * scheme) and densities f [N][3] of the m-th order grid are interpolated by
+ * each patch's tensor-product not-a-knot cubic spline to the 4m-th order
+ * grid (6 (4m-1)^2 nodes); the fine weights are psi_u W_u h_u^2 (h_u =
+ * pi / (4m)) and delta is Eq. regparam (C = 1) on the fine grid, per patch.
+ * The regularized sum (Eq. regstokes, viscosity mu) over the fine nodes is
+ * evaluated at the m-th order nodes, which are fine nodes, so downsampling
+ * there is the identity. u_out [N][3]. 6 <= m <= 4097. Errors as for
+ * stokes_sl_eval. */
+int stokes_sl_eval_upsampled(sk_ctx* ctx, int precision, int mem, int m, const double* X,
+                             const double* W, const double* f, double mu, double* u_out,
+                             void* cuda_stream);
+
 /* ---- serving: continuous batching of single-layer requests -------------
  *
  * A server keeps up to max_slots requests resident on the device and runs

@@ -91,6 +91,7 @@ _EXTRA_DECLS: dict = {
     "capsule_area_volume": ([_vp, ctypes.POINTER(_dbl), ctypes.POINTER(_dbl)], _int),
     "surface_derivatives": ([_vp, _int, _int, _i64, _vp, _vp, _vp, _vp], _int),
     "membrane_force": ([_vp, _int, _int, _vp, _vp, _dbl, _dbl, _vp, _vp, _vp], _int),
+    "stokes_sl_eval_upsampled": ([_vp, _int, _int, _int, _vp, _vp, _vp, _dbl, _vp, _vp], _int),
     "capsule_destroy": ([_vp], None),
 }
 
@@ -297,6 +298,28 @@ def membrane_force(ctx, m: int, mem: int, X, X_ref, Es: float, ED: float, weight
         args = [_host_ptr(Xa), _host_ptr(Xr), float(Es), float(ED), _host_ptr(f), _host_ptr(w)]
     _check(ctx, lib.membrane_force(ctx, int(m), int(mem), *args, _stream_handle(stream)))
     return (f, w) if weights else f
+
+
+def stokes_sl_eval_upsampled(ctx, precision: int, mem: int, m: int, X, W, f, mu: float = 1.0,
+                             stream=None):
+    """Single layer at the m-th order nodes from the four-times upsampled grid
+    (Sec. 3.4). Returns u (N, 3)."""
+    lib = load()
+    Xa, N = _ptr(X, mem, (3,), "X")
+    Wa, nw = _ptr(W, mem, (), "W")
+    Fa, nf = _ptr(f, mem, (3,), "f")
+    if not (N == nw == nf):
+        raise ValueError("X, W and f must hold the same nodes")
+    if mem == SK_DEVICE:
+        import torch
+        u = torch.empty((N, 3), dtype=torch.float64, device=X.device)
+        args = [Xa, Wa, Fa, float(mu), u.data_ptr()]
+    else:
+        u = np.empty((N, 3))
+        args = [_host_ptr(Xa), _host_ptr(Wa), _host_ptr(Fa), float(mu), _host_ptr(u)]
+    _check(ctx, lib.stokes_sl_eval_upsampled(ctx, int(precision), int(mem), int(m), *args,
+                                             _stream_handle(stream)))
+    return u
 
 
 SK_FLOW_NONE, SK_FLOW_SHEAR, SK_FLOW_POISEUILLE = 0, 1, 2

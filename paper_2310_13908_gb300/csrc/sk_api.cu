@@ -433,6 +433,16 @@ int eval_entry(sk_ctx* ctx, int layer, int precision, int mem, int64_t N, const 
 
 }  // namespace
 
+namespace sk {
+int eval_call(sk_ctx* ctx, int layer, int precision, int mem, int64_t N, const double* xyz,
+              const double* w, const double* dens, const double* nrm, int64_t M,
+              const double* txyz, const double* delta, int64_t n_delta, double mu,
+              double* u_out, void* stream) {
+  return eval_entry(ctx, layer, precision, mem, N, xyz, w, dens, nrm, M, txyz, delta, n_delta, mu,
+                    u_out, stream);
+}
+}  // namespace sk
+
 extern "C" {
 
 int stokes_sl_eval(sk_ctx* ctx, int precision, int mem, int64_t n_src, const double* src_xyz,

@@ -215,6 +215,13 @@ void launch_finish32(int layer, const EvalBufs& b, int64_t n_delta, double scale
 void launch_pair64(int layer, const EvalBufs& b, double scale, cudaStream_t st);
 void launch_finish64(const EvalBufs& b, cudaStream_t st);
 
+// One evaluation with the argument checks, statistics and flags of the
+// public entry points (stokes_sl_eval / stokes_dl_eval).
+int eval_call(sk_ctx* ctx, int layer, int precision, int mem, int64_t N, const double* xyz,
+              const double* w, const double* dens, const double* nrm, int64_t M,
+              const double* txyz, const double* delta, int64_t n_delta, double mu,
+              double* u_out, void* stream);
+
 // sk_membrane.cu: overset finite-difference derivatives and the Skalak force
 // on the six-patch grid of order m (built once per m and cached in ctx).
 int membrane_op(sk_ctx* ctx, int m, MembraneOp** out);

@@ -25,6 +25,7 @@
 #include <algorithm>
 #include <cmath>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "sk_internal.h"
@@ -59,6 +60,16 @@ struct MembraneOp {
   double *gu = nullptr, *gv = nullptr;   // blended derivatives [F][N]
   double* cur_t = nullptr;               // current tangents [6][N]
   double* red = nullptr;                 // reduction partials
+  // four-times upsampled single layer (built on first use)
+  int nf = 0;                    // fine nodes per line, 4m - 1
+  int64_t Nup = 0;               // 6 nf^2
+  int* ucell1 = nullptr;         // [nf] cell of fine index J (both directions)
+  double* ubasis1 = nullptr;     // [nf][4] Hermite bases there
+  double* psi_up = nullptr;      // [Nup] POU of each fine node's patch
+  double *Xu = nullptr, *Fu = nullptr, *wu = nullptr;   // fine sources
+  double *Xc = nullptr, *Wc = nullptr, *fc = nullptr, *uc = nullptr;  // coarse staging
+  double* dtgt = nullptr;        // [N] delta per coarse target
+  unsigned long long* pmax = nullptr;  // [8] delta_u per patch (double bits)
 };
 
 namespace {
@@ -477,13 +488,70 @@ __global__ void k_sum_pairs(const double* __restrict__ part, int n, double* __re
   out[1] = v;
 }
 
+// Upsampling I_u (Sec. 3.4): the patch splines of the 7 fields in op.g
+// (x, y, z, f_x, f_y, f_z, W) at the fine nodes; writes fine positions and
+// densities [Nup][3] and weights psi_u W_u h_u^2.
+__global__ void k_upsample(const MembraneOp op, double hu2) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= op.Nup) return;
+  const int64_t nf2 = (int64_t)op.nf * op.nf;
+  const int p = (int)(i / nf2);
+  const int r = (int)(i % nf2);
+  const int J = r / op.nf, K = r % op.nf;
+  double w[8];
+  for (int c = 0; c < 4; ++c) {
+    w[c] = op.ubasis1[4 * J + c];
+    w[4 + c] = op.ubasis1[4 * K + c];
+  }
+  const int cell = (p * op.n + op.ucell1[J]) * op.n + op.ucell1[K];
+  const int64_t plane = 7 * op.N;
+  double v[7];
+  for (int f = 0; f < 7; ++f) v[f] = spline_tap(op.g, op.sg, plane, (int64_t)f * op.N, cell, op.n, w);
+  for (int c = 0; c < 3; ++c) {
+    op.Xu[3 * i + c] = v[c];
+    op.Fu[3 * i + c] = v[3 + c];
+  }
+  op.wu[i] = op.psi_up[i] * v[6] * hu2;
+}
+
+// delta_u per patch: Eq. regparam on the fine grid (largest distance from a
+// node to an existing grid neighbour, maximized over the patch).
+__global__ void k_fine_delta(const MembraneOp op) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= op.Nup) return;
+  const int nf = op.nf;
+  const int p = (int)(i / ((int64_t)nf * nf));
+  const int r = (int)(i % ((int64_t)nf * nf));
+  const int j = r / nf, k = r % nf;
+  const double x = op.Xu[3 * i], y = op.Xu[3 * i + 1], z = op.Xu[3 * i + 2];
+  double best = 0.0;
+  for (int a = -1; a <= 1; ++a)
+    for (int b = -1; b <= 1; ++b) {
+      const int jj = j + a, kk = k + b;
+      if ((a == 0 && b == 0) || jj < 0 || jj >= nf || kk < 0 || kk >= nf) continue;
+      const int64_t q = ((int64_t)p * nf + jj) * nf + kk;
+      const double dx = x - op.Xu[3 * q], dy = y - op.Xu[3 * q + 1], dz = z - op.Xu[3 * q + 2];
+      best = fmax(best, sqrt(dx * dx + dy * dy + dz * dz));
+    }
+  // nonnegative doubles order like their bit patterns
+  atomicMax(op.pmax + p, (unsigned long long)__double_as_longlong(best));
+}
+
+__global__ void k_delta_targets(const MembraneOp op) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < op.N) op.dtgt[i] = __longlong_as_double((long long)op.pmax[i / ((int64_t)op.n * op.n)]);
+}
+
 void free_op(MembraneOp* op) {
   if (!op) return;
   for (void* p : {(void*)op->ghost_dst, (void*)op->gtap_ptr, (void*)op->gtap_cell,
                   (void*)op->gtap_w, (void*)op->psi_own, (void*)op->btap_ptr,
                   (void*)op->btap_cell, (void*)op->btap_w, (void*)op->thomas, (void*)op->g,
                   (void*)op->sg, (void*)op->ext, (void*)op->du, (void*)op->dv, (void*)op->sdu,
-                  (void*)op->sdv, (void*)op->gu, (void*)op->gv, (void*)op->cur_t, (void*)op->red})
+                  (void*)op->sdv, (void*)op->gu, (void*)op->gv, (void*)op->cur_t, (void*)op->red,
+                  (void*)op->ucell1, (void*)op->ubasis1, (void*)op->psi_up, (void*)op->Xu,
+                  (void*)op->Fu, (void*)op->wu, (void*)op->Xc, (void*)op->Wc, (void*)op->fc,
+                  (void*)op->uc, (void*)op->dtgt, (void*)op->pmax})
     if (p) cudaFree(p);
   delete op;
 }
@@ -595,6 +663,63 @@ int build_op(int m, MembraneOp** out, std::string& err) {
     return e == cudaErrorMemoryAllocation ? SK_ENOMEM : SK_ECUDA;
   }
   *out = op;
+  return SK_OK;
+}
+
+// Tables and buffers of the upsampled single layer (host work: the POU at
+// every fine node, one thread per patch).
+int ensure_upsampling(MembraneOp* op, std::string& err) {
+  if (op->Xu) return SK_OK;
+  const int m = op->m, n = op->n, nf = 4 * m - 1;
+  const double h = op->h, hf = PI_CONST / (4.0 * m);
+  std::vector<int> cell(nf);
+  std::vector<double> basis(4 * (size_t)nf);
+  for (int J = 0; J < nf; ++J) {
+    double bs[8];
+    const double u = (J + 1) * hf;
+    cell[J] = h_cell_basis(0, n, h, u, u, bs) / n;  // a of the cell (patch 0, b = a)
+    for (int c = 0; c < 4; ++c) basis[4 * J + c] = bs[c];
+  }
+  const int64_t nf2 = (int64_t)nf * nf, Nup = 6 * nf2;
+  std::vector<double> psi(Nup);
+  std::vector<std::thread> th;
+  for (int p = 0; p < 6; ++p)
+    th.emplace_back([&, p] {
+      for (int J = 0; J < nf; ++J)
+        for (int K = 0; K < nf; ++K) {
+          double ps[6];
+          h_pou(h_chart(p, (J + 1) * hf, (K + 1) * hf), ps);
+          psi[p * nf2 + (int64_t)J * nf + K] = ps[p];
+        }
+    });
+  for (auto& t : th) t.join();
+  cudaError_t e = cudaSuccess;
+  auto ok = [&](cudaError_t x) {
+    if (x != cudaSuccess && e == cudaSuccess) e = x;
+  };
+  ok(upload(&op->ucell1, cell));
+  ok(upload(&op->ubasis1, basis));
+  ok(upload(&op->psi_up, psi));
+  ok(cudaMalloc(&op->Xu, 3 * Nup * sizeof(double)));
+  ok(cudaMalloc(&op->Fu, 3 * Nup * sizeof(double)));
+  ok(cudaMalloc(&op->wu, Nup * sizeof(double)));
+  ok(cudaMalloc(&op->Xc, 3 * op->N * sizeof(double)));
+  ok(cudaMalloc(&op->Wc, op->N * sizeof(double)));
+  ok(cudaMalloc(&op->fc, 3 * op->N * sizeof(double)));
+  ok(cudaMalloc(&op->uc, 3 * op->N * sizeof(double)));
+  ok(cudaMalloc(&op->dtgt, op->N * sizeof(double)));
+  ok(cudaMalloc(&op->pmax, 8 * sizeof(unsigned long long)));
+  if (e != cudaSuccess) {
+    err = std::string("upsampled single layer: ") + cudaGetErrorString(e);
+    for (double** q : {&op->Xu, &op->Fu, &op->wu, &op->Xc, &op->Wc, &op->fc, &op->uc, &op->dtgt})
+      if (*q) {
+        cudaFree(*q);
+        *q = nullptr;
+      }
+    return e == cudaErrorMemoryAllocation ? SK_ENOMEM : SK_ECUDA;
+  }
+  op->nf = nf;
+  op->Nup = Nup;
   return SK_OK;
 }
 
@@ -774,6 +899,63 @@ int membrane_force(sk_ctx* ctx, int m, int mem, const double* X, const double* X
   if (e != cudaSuccess) {
     ctx->err = std::string("membrane_force: ") + cudaGetErrorString(e);
     return SK_ECUDA;
+  }
+  return SK_OK;
+}
+
+int stokes_sl_eval_upsampled(sk_ctx* ctx, int precision, int mem, int m, const double* X,
+                             const double* W, const double* f, double mu, double* u_out,
+                             void* stream) {
+  if (!ctx) return SK_EINVAL;
+  if (!X || !W || !f || !u_out || (mem != SK_HOST && mem != SK_DEVICE) ||
+      (precision != SK_FP64 && precision != SK_FP32C) || !(mu > 0.0 && mu < INFINITY)) {
+    ctx->err = "stokes_sl_eval_upsampled: need X, W, f, u_out, mu > 0, precision SK_FP64 or "
+               "SK_FP32C and mem SK_HOST or SK_DEVICE";
+    return SK_EINVAL;
+  }
+  MembraneOp* op = nullptr;
+  int rc = membrane_op(ctx, m, &op);
+  if (rc == SK_OK) rc = ensure_upsampling(op, ctx->err);
+  if (rc != SK_OK) return rc;
+  cudaSetDevice(ctx->device);
+  cudaStream_t st = (mem == SK_DEVICE && stream) ? (cudaStream_t)stream : ctx->stream;
+  const int64_t N = op->N;
+  const double *dX = X, *dW = W, *df = f;
+  if (mem == SK_HOST) {
+    cudaMemcpyAsync(op->Xc, X, 3 * N * sizeof(double), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(op->Wc, W, N * sizeof(double), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(op->fc, f, 3 * N * sizeof(double), cudaMemcpyHostToDevice, st);
+    dX = op->Xc;
+    dW = op->Wc;
+    df = op->fc;
+  }
+  // I_u of positions, densities and area element (fields 0..6 of op->g)
+  k_gather<<<blocks_of(3 * N), 256, 0, st>>>(dX, N, 3, 0, 3, op->g);
+  k_gather<<<blocks_of(3 * N), 256, 0, st>>>(df, N, 3, 0, 3, op->g + 3 * N);
+  k_gather<<<blocks_of(N), 256, 0, st>>>(dW, N, 1, 0, 1, op->g + 6 * N);
+  enqueue_splines(*op, 7, op->g, op->sg, st);
+  const double hu = PI_CONST / (4.0 * m);
+  k_upsample<<<blocks_of(op->Nup), 256, 0, st>>>(*op, hu * hu);
+  cudaMemsetAsync(op->pmax, 0, 8 * sizeof(unsigned long long), st);
+  k_fine_delta<<<blocks_of(op->Nup), 256, 0, st>>>(*op);
+  k_delta_targets<<<blocks_of(N), 256, 0, st>>>(*op);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    ctx->err = std::string("stokes_sl_eval_upsampled: ") + cudaGetErrorString(e);
+    return SK_ECUDA;
+  }
+  // the sum at the coarse nodes over the fine sources; I_d is the identity
+  // there (every coarse node is a fine node)
+  double* du = mem == SK_HOST ? op->uc : u_out;
+  rc = eval_call(ctx, LAYER_SL, precision, SK_DEVICE, op->Nup, op->Xu, op->wu, op->Fu, nullptr, N,
+                 dX, op->dtgt, N, mu, du, mem == SK_DEVICE ? (void*)stream : nullptr);
+  if (rc != SK_OK) return rc;
+  if (mem == SK_HOST) {
+    e = cudaMemcpy(u_out, op->uc, 3 * N * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+      ctx->err = std::string("stokes_sl_eval_upsampled: ") + cudaGetErrorString(e);
+      return SK_ECUDA;
+    }
   }
   return SK_OK;
 }

@@ -90,3 +90,5 @@ def test_membrane_entry_points_reject_null_context(lib):
     assert lib.surface_derivatives(None, 9, sk.SK_HOST, 1, None, None, None, None) == sk.SK_EINVAL
     assert lib.membrane_force(None, 9, sk.SK_HOST, None, None, 1.0, 1.0, None, None,
                               None) == sk.SK_EINVAL
+    assert lib.stokes_sl_eval_upsampled(None, sk.SK_FP64, sk.SK_HOST, 9, None, None, None, 1.0,
+                                        None, None) == sk.SK_EINVAL

@@ -1,0 +1,68 @@
+"""Four-times upsampled single layer (Sec. 3.4) on the GPU against the oracle's
+upsampled sum (oracle/upsample.py): same interpolant definition, independent
+implementations (spline solver, Hermite evaluation, delta_u, the sum)."""
+
+import numpy as np
+import pytest
+
+import capsule_inputs as ci
+from oracle import membrane as mb
+from oracle import upsample as up
+
+sk = pytest.importorskip("paper_2310_13908_gb300")
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+TOL = {sk.SK_FP64: 1e-12, sk.SK_FP32C: 1e-6}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = sk.Context(0)
+    yield c.handle
+    c.close()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("prec", [sk.SK_FP64, sk.SK_FP32C], ids=["fp64", "fp32c"])
+@pytest.mark.parametrize("m", [8, 16, 33])
+def test_upsampled_single_layer_matches_oracle(ctx, prec, m):
+    s = ci.make_surface(ci.Ellipsoid(0.6, 1.0, 1.0), m)
+    W = mb.geometry(m, s.X)["W"]
+    f = s.X ** 2
+    u = sk.stokes_sl_eval_upsampled(ctx, prec, sk.SK_HOST, m, s.X, W, f, 1.3)
+    ref = up.sl_upsampled(m, s.X, W, f, 1.3)
+    assert rel(u, ref) < TOL[prec], rel(u, ref)
+
+
+def test_upsampled_device_memory_and_stream(ctx):
+    m = 12
+    s = ci.make_surface(ci.EvansFungRBC(ci.random_rotation(np.random.default_rng(2))), m)
+    W = mb.geometry(m, s.X)["W"]
+    f = ci.sh_density(s.x0, np.random.default_rng(3), lmax=6)
+    st = torch.cuda.Stream()
+    d = lambda a: torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+    with torch.cuda.stream(st):
+        u = sk.stokes_sl_eval_upsampled(ctx, sk.SK_FP64, sk.SK_DEVICE, m, d(s.X), d(W), d(f),
+                                        1.0, stream=st)
+    st.synchronize()
+    ref = up.sl_upsampled(m, s.X, W, f)
+    assert rel(u.cpu().numpy(), ref) < 1e-12
+
+
+def test_upsampling_reduces_the_sphere_translation_error(ctx):
+    m = 10
+    s = ci.make_surface(ci.Sphere(1.0), m)
+    f = np.zeros((s.N, 3))
+    f[:, 2] = 1.0
+    u_up = sk.stokes_sl_eval_upsampled(ctx, sk.SK_FP64, sk.SK_HOST, m, s.X, s.W, f, 1.0)
+    u = sk.stokes_sl_eval(ctx, sk.SK_FP64, sk.SK_HOST, s.X, s.w, f, s.X, ci.delta_star(s), 1.0)
+    e_up = np.abs(u_up[:, 2] - 2 / 3).max()
+    e = np.abs(u[:, 2] - 2 / 3).max()
+    assert e_up < e / 5
