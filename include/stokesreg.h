@@ -209,6 +209,13 @@ int capsule_integrate_rkf45(sk_capsule* c, double t_end, double* dt_inout, doubl
  * Needs m >= 6. Errors: SK_EINVAL, SK_ENOMEM, SK_ECUDA. */
 int capsule_set_membrane(sk_capsule* c, const double* X_ref, double Es, double ED);
 
+/* Evaluate the single layer of every step on the four-times upsampled grid
+ * (factor 4, as stokes_sl_eval_upsampled; W from the derivative scheme at
+ * the current nodes; delta_u per patch replaces delta) or on the nodes
+ * themselves (factor 1, the default). Needs m >= 6 for factor 4.
+ * Errors: SK_EINVAL, SK_ENOMEM, SK_ECUDA. */
+int capsule_set_upsampling(sk_capsule* c, int factor);
+
 /* Area A = sum psi W h^2 and enclosed volume V = sum psi W h^2 x n_x (the
  * divergence-theorem form of Sec. 4.1) of the current nodes, with W and n
  * from the derivative scheme of Sec. 3.5. Needs m >= 6. Synchronous.

@@ -86,6 +86,7 @@ _EXTRA_DECLS: dict = {
     "capsule_step": ([_vp, _int, _dbl, _vp, _vp], _int),
     "capsule_get": ([_vp, _vp], _int),
     "capsule_set_membrane": ([_vp, _vp, _dbl, _dbl], _int),
+    "capsule_set_upsampling": ([_vp, _int], _int),
     "capsule_integrate_rkf45": ([_vp, _dbl, ctypes.POINTER(_dbl), _dbl, _vp, _vp, _i64,
                                  ctypes.POINTER(ctypes.c_int64)], _int),
     "capsule_area_volume": ([_vp, ctypes.POINTER(_dbl), ctypes.POINTER(_dbl)], _int),
@@ -372,6 +373,10 @@ class Capsule:
                                                         float(tol), fl, _host_ptr(F),
                                                         int(max_steps), stats))
         return d.value, int(stats[0]), int(stats[1])
+
+    def set_upsampling(self, factor: int):
+        """Single layer of every step on the 4x upsampled grid (4) or not (1)."""
+        _check(self.ctx, load().capsule_set_upsampling(self.handle, int(factor)))
 
     def area_volume(self):
         a, v = ctypes.c_double(), ctypes.c_double()

@@ -36,6 +36,9 @@ struct sk_capsule {
   double* ref6 = nullptr;
   double Es = 0.0, ED = 0.0;
   double* av = nullptr;  // [2] area, volume (device)
+  // four-times upsampled single layer (capsule_set_upsampling)
+  int up = 1;
+  sk::MembraneOp* uop = nullptr;
   // RKF45 (capsule_integrate_rkf45): stage positions, stage slopes, reductions
   double* Y = nullptr;    // [N][3]
   double* K = nullptr;    // [6][N][3]
@@ -46,8 +49,10 @@ struct sk_capsule {
   size_t r_ws_bytes = 0;
   double r_rho_T = 0.0, r_rho_c = 0.0;
   int r_mode = -1;
+  int r_up = 0;
   // captured step graph and the state it was captured for
   int g_mode = -1;  // 0: supplied f; 1: supplied f, membrane weights; 2: Skalak force
+  int g_up = 0;
   cudaGraphExec_t exec = nullptr;
   double g_dt = 0.0;
   sk_flow g_flow{};
@@ -58,6 +63,8 @@ struct sk_capsule {
 
 namespace sk {
 namespace {
+
+inline unsigned blocks(int64_t n) { return (unsigned)((n + 255) / 256); }
 
 // delta*_p = max over the nodes of patch p of the largest distance to an
 // existing grid neighbour (offsets a, b in {-1, 0, 1}) (Eq. regparam).
@@ -190,6 +197,65 @@ __global__ void k_max_pairs(const double* __restrict__ part, int n, double* __re
   out[1] = a;
 }
 
+// Shape of the capsule's single-layer evaluation: targets are the nodes;
+// sources the nodes, or the fine nodes of the upsampled grid.
+EvalShape capsule_shape(const sk_capsule* c) {
+  EvalShape s;
+  s.layer = LAYER_SL;
+  s.precision = c->precision;
+  s.mu = c->mu;
+  s.copy_inputs = false;
+  s.M = c->N;
+  if (c->up == 4) {
+    s.N = upsampled_sources(*c->uop).Nup;
+    s.n_delta = c->N;
+  } else {
+    s.N = c->N;
+    s.n_delta = c->n_delta;
+  }
+  s.n_chunks = choose_chunks(c->precision, s.N, s.M, c->ctx->sm_count);
+  return s;
+}
+
+// Enqueue u = S[f](P) at nodes P (device [N][3]) into c->u: membrane force
+// and weights per mode (0: supplied f; 1: supplied f, membrane weights;
+// 2: Skalak force), then delta* and the sum, or the upsampled sum.
+void enqueue_velocity(sk_capsule* c, const double* P, int mode, const EvalShape& s,
+                      cudaStream_t st) {
+  sk_ctx* ctx = c->ctx;
+  EvalBufs b;
+  Bump bp;
+  bp.base = ctx->ws;
+  carve_eval_buffers(bp, s, b);
+  const bool upsampled = c->up == 4;
+  double* Wraw = upsampled ? upsampled_sources(*c->uop).W : nullptr;
+  if (mode == 1) enqueue_tangents(*c->mop, P, nullptr, c->w, st, Wraw);
+  if (mode == 2) enqueue_skalak(*c->mop, P, c->ref6, c->Es, c->ED, c->f, c->w, st, Wraw);
+  if (mode == 0 && upsampled) enqueue_tangents(*c->uop, P, nullptr, nullptr, st, Wraw);
+  if (upsampled) {
+    enqueue_upsample(*c->uop, P, Wraw, c->f, st);
+    const UpsampledSources us = upsampled_sources(*c->uop);
+    b.src_xyz = us.X;
+    b.src_w = us.w;
+    b.dens = us.f;
+    b.delta = us.delta;
+  } else {
+    if (c->auto_delta) {
+      cudaMemsetAsync(c->patch_max, 0, 8 * sizeof(unsigned long long), st);
+      k_delta_star_patch<<<blocks(c->N), 256, 0, st>>>(P, c->m, c->patch_max);
+      k_delta_fill<<<blocks(c->N), 256, 0, st>>>(c->patch_max, c->m, 1.0, c->delta);
+    }
+    b.src_xyz = P;
+    b.src_w = c->w;
+    b.dens = c->f;
+    b.delta = c->delta;
+  }
+  b.tgt_xyz = P;
+  b.u = c->u;
+  enqueue_eval(s, b, ctx->rho_T, ctx->rho_c, st);
+  k_sticky<<<1, 32, 0, st>>>(b.flags, c->sticky);
+}
+
 void free_capsule(sk_capsule* c) {
   if (c->exec) cudaGraphExecDestroy(c->exec);
   if (c->rhs_exec) cudaGraphExecDestroy(c->rhs_exec);
@@ -199,8 +265,6 @@ void free_capsule(sk_capsule* c) {
   if (c->sticky) cudaFree(c->sticky);
   delete c;
 }
-
-inline unsigned blocks(int64_t n) { return (unsigned)((n + 255) / 256); }
 
 }  // namespace
 }  // namespace sk
@@ -286,47 +350,22 @@ int capsule_step(sk_capsule* c, int n_steps, double dt, const sk_flow* flow, con
   cudaError_t e = cudaSuccess;
   if (f) e = cudaMemcpyAsync(c->f, f, 3 * c->N * sizeof(double), cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return SK_ECUDA;
-  EvalShape s;
-  s.layer = LAYER_SL;
-  s.precision = c->precision;
-  s.N = c->N;
-  s.M = c->N;
-  s.n_delta = c->n_delta;
-  s.mu = c->mu;
-  s.copy_inputs = false;
-  s.n_chunks = choose_chunks(c->precision, c->N, c->N, ctx->sm_count);
+  const EvalShape s = capsule_shape(c);
   int rc = ensure_workspace(ctx, eval_workspace_bytes(s));
   if (rc != SK_OK) return rc;
   const bool stale = !c->exec || c->g_dt != dt || std::memcmp(&c->g_flow, &fl, sizeof(fl)) != 0 ||
                      c->g_ws != ctx->ws || c->g_ws_bytes != ctx->ws_bytes ||
-                     c->g_rho_T != ctx->rho_T || c->g_rho_c != ctx->rho_c || c->g_mode != mode;
+                     c->g_rho_T != ctx->rho_T || c->g_rho_c != ctx->rho_c || c->g_mode != mode ||
+                     c->g_up != c->up;
   if (stale) {
     if (c->exec) cudaGraphExecDestroy(c->exec);
     c->exec = nullptr;
-    EvalBufs b;
-    Bump bp;
-    bp.base = ctx->ws;
-    carve_eval_buffers(bp, s, b);
-    b.src_xyz = c->X;
-    b.src_w = c->w;
-    b.dens = c->f;
-    b.tgt_xyz = c->X;
-    b.delta = c->delta;
-    b.u = c->u;
     cudaGraph_t g = nullptr;
     if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
       ctx->err = std::string("capsule_step: capture: ") + cudaGetErrorString(e);
       return SK_ECUDA;
     }
-    if (mode == 1) enqueue_tangents(*c->mop, c->X, nullptr, c->w, st);
-    if (mode == 2) enqueue_skalak(*c->mop, c->X, c->ref6, c->Es, c->ED, c->f, c->w, st);
-    if (c->auto_delta) {
-      cudaMemsetAsync(c->patch_max, 0, 8 * sizeof(unsigned long long), st);
-      k_delta_star_patch<<<blocks(c->N), 256, 0, st>>>(c->X, c->m, c->patch_max);
-      k_delta_fill<<<blocks(c->N), 256, 0, st>>>(c->patch_max, c->m, 1.0, c->delta);
-    }
-    enqueue_eval(s, b, ctx->rho_T, ctx->rho_c, st);
-    k_sticky<<<1, 32, 0, st>>>(b.flags, c->sticky);
+    enqueue_velocity(c, c->X, mode, s, st);
     k_euler<<<blocks(c->N), 256, 0, st>>>(c->X, c->u, c->N, dt, fl);
     e = cudaStreamEndCapture(st, &g);
     if (e == cudaSuccess) e = cudaGraphInstantiate(&c->exec, g, 0);
@@ -343,6 +382,7 @@ int capsule_step(sk_capsule* c, int n_steps, double dt, const sk_flow* flow, con
     c->g_rho_T = ctx->rho_T;
     c->g_rho_c = ctx->rho_c;
     c->g_mode = mode;
+    c->g_up = c->up;
   }
   cudaMemsetAsync(c->sticky, 0, N_FLAGS * sizeof(unsigned long long), st);
   for (int i = 0; i < n_steps; ++i)
@@ -398,48 +438,23 @@ int capsule_integrate_rkf45(sk_capsule* c, double t_end, double* dt_inout, doubl
     ctx->err = std::string("capsule_integrate_rkf45: ") + cudaGetErrorString(e);
     return e == cudaErrorMemoryAllocation ? SK_ENOMEM : SK_ECUDA;
   }
-  EvalShape s;
-  s.layer = LAYER_SL;
-  s.precision = c->precision;
-  s.N = c->N;
-  s.M = c->N;
-  s.n_delta = c->n_delta;
-  s.mu = c->mu;
-  s.copy_inputs = false;
-  s.n_chunks = choose_chunks(c->precision, c->N, c->N, ctx->sm_count);
+  const EvalShape s = capsule_shape(c);
   int rc = ensure_workspace(ctx, eval_workspace_bytes(s));
   if (rc != SK_OK) return rc;
   // right-hand side graph on the stage positions Y: u = u_inf(Y) + S[f(Y)](Y)
   const bool stale = !c->rhs_exec || std::memcmp(&c->r_flow, &fl, sizeof(fl)) != 0 ||
                      c->r_ws != ctx->ws || c->r_ws_bytes != ctx->ws_bytes ||
-                     c->r_rho_T != ctx->rho_T || c->r_rho_c != ctx->rho_c || c->r_mode != mode;
+                     c->r_rho_T != ctx->rho_T || c->r_rho_c != ctx->rho_c || c->r_mode != mode ||
+                     c->r_up != c->up;
   if (stale) {
     if (c->rhs_exec) cudaGraphExecDestroy(c->rhs_exec);
     c->rhs_exec = nullptr;
-    EvalBufs b;
-    Bump bp;
-    bp.base = ctx->ws;
-    carve_eval_buffers(bp, s, b);
-    b.src_xyz = c->Y;
-    b.src_w = c->w;
-    b.dens = c->f;
-    b.tgt_xyz = c->Y;
-    b.delta = c->delta;
-    b.u = c->u;
     cudaGraph_t g = nullptr;
     if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
       ctx->err = std::string("capsule_integrate_rkf45: capture: ") + cudaGetErrorString(e);
       return SK_ECUDA;
     }
-    if (mode == 1) enqueue_tangents(*c->mop, c->Y, nullptr, c->w, st);
-    if (mode == 2) enqueue_skalak(*c->mop, c->Y, c->ref6, c->Es, c->ED, c->f, c->w, st);
-    if (c->auto_delta) {
-      cudaMemsetAsync(c->patch_max, 0, 8 * sizeof(unsigned long long), st);
-      k_delta_star_patch<<<blocks(c->N), 256, 0, st>>>(c->Y, c->m, c->patch_max);
-      k_delta_fill<<<blocks(c->N), 256, 0, st>>>(c->patch_max, c->m, 1.0, c->delta);
-    }
-    enqueue_eval(s, b, ctx->rho_T, ctx->rho_c, st);
-    k_sticky<<<1, 32, 0, st>>>(b.flags, c->sticky);
+    enqueue_velocity(c, c->Y, mode, s, st);
     k_add_uinf<<<blocks(c->N), 256, 0, st>>>(c->u, c->Y, c->N, fl);
     e = cudaStreamEndCapture(st, &g);
     if (e == cudaSuccess) e = cudaGraphInstantiate(&c->rhs_exec, g, 0);
@@ -455,6 +470,7 @@ int capsule_integrate_rkf45(sk_capsule* c, double t_end, double* dt_inout, doubl
     c->r_rho_T = ctx->rho_T;
     c->r_rho_c = ctx->rho_c;
     c->r_mode = mode;
+    c->r_up = c->up;
   }
   // adaptive loop: accept when max|x5 - x4| / max|x4| <= tol, then
   // dt <- dt min(5, max(0.2, 0.9 (tol / err)^(1/5))); the last step lands on t_end
@@ -513,6 +529,24 @@ int capsule_integrate_rkf45(sk_capsule* c, double t_end, double* dt_inout, doubl
     ctx->err = "capsule_integrate_rkf45: max_steps reached before t_end";
     return SK_EAGAIN;
   }
+  return SK_OK;
+}
+
+int capsule_set_upsampling(sk_capsule* c, int factor) {
+  if (!c) return SK_EINVAL;
+  sk_ctx* ctx = c->ctx;
+  if (factor != 1 && factor != 4) {
+    ctx->err = "capsule_set_upsampling: factor must be 1 or 4";
+    return SK_EINVAL;
+  }
+  if (factor == 4) {
+    MembraneOp* op = nullptr;
+    int rc = membrane_op(ctx, c->m, &op);
+    if (rc == SK_OK) rc = membrane_upsampling(ctx, op);
+    if (rc != SK_OK) return rc;
+    c->uop = op;
+  }
+  c->up = factor;
   return SK_OK;
 }
 

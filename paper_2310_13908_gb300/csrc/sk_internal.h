@@ -227,10 +227,22 @@ int eval_call(sk_ctx* ctx, int layer, int precision, int mem, int64_t N, const d
 int membrane_op(sk_ctx* ctx, int m, MembraneOp** out);
 void free_membrane_ops(sk_ctx* ctx);
 int64_t membrane_nodes(const MembraneOp& op);
+// Wraw (optional): the area element W itself.
 void enqueue_tangents(const MembraneOp& op, const double* X, double* t6, double* w,
-                      cudaStream_t st);
+                      cudaStream_t st, double* Wraw = nullptr);
 void enqueue_skalak(const MembraneOp& op, const double* X, const double* ref6, double Es,
-                    double ED, double* f, double* w, cudaStream_t st);
+                    double ED, double* f, double* w, cudaStream_t st, double* Wraw = nullptr);
+// Four-times upsampled single layer (Sec. 3.4): buffers built on first use;
+// enqueue_upsample fills the fine sources and the coarse targets' delta.
+struct UpsampledSources {
+  int64_t Nup;
+  const double *X, *w, *f, *delta;
+  double* W;  // [N] staging for the coarse area element
+};
+int membrane_upsampling(sk_ctx* ctx, MembraneOp* op);
+void enqueue_upsample(const MembraneOp& op, const double* X, const double* W, const double* f,
+                      cudaStream_t st);
+UpsampledSources upsampled_sources(const MembraneOp& op);
 void enqueue_area_volume(const MembraneOp& op, const double* X, double* out2, cudaStream_t st);
 
 }  // namespace sk

@@ -387,7 +387,8 @@ __device__ __forceinline__ Frame frame_at(const double* __restrict__ t6, int64_t
 
 // Tangents of the last F = 3 pass (positions) -> t6 [6][N]; optional
 // quadrature weights psi W h^2 (Sec. 3.3, Eq. smoothint).
-__global__ void k_tangents(const MembraneOp op, double* __restrict__ t6, double* __restrict__ w) {
+__global__ void k_tangents(const MembraneOp op, double* __restrict__ t6, double* __restrict__ w,
+                           double* __restrict__ Wraw) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t N = op.N;
   if (i >= N) return;
@@ -395,9 +396,10 @@ __global__ void k_tangents(const MembraneOp op, double* __restrict__ t6, double*
     t6[c * N + i] = op.gu[c * N + i];
     t6[(3 + c) * N + i] = op.gv[c * N + i];
   }
-  if (w) {
+  if (w || Wraw) {
     const Frame fr = frame_at(t6, N, i);
-    w[i] = op.psi_own[i] * fr.W * op.h * op.h;
+    if (w) w[i] = op.psi_own[i] * fr.W * op.h * op.h;
+    if (Wraw) Wraw[i] = fr.W;
   }
 }
 
@@ -749,17 +751,17 @@ void enqueue_derivatives(const MembraneOp& op, int F, cudaStream_t st) {
 // Tangents of the nodes X ([N][3], device) into t6 ([6][N]; the operator's
 // own buffer when null); weights psi W h^2 into w when w != nullptr.
 void enqueue_tangents(const MembraneOp& op, const double* X, double* t6, double* w,
-                      cudaStream_t st) {
+                      cudaStream_t st, double* Wraw) {
   if (!t6) t6 = op.cur_t;
   k_gather<<<blocks_of(3 * op.N), 256, 0, st>>>(X, op.N, 3, 0, 3, op.g);
   enqueue_derivatives(op, 3, st);
-  k_tangents<<<blocks_of(op.N), 256, 0, st>>>(op, t6, w);
+  k_tangents<<<blocks_of(op.N), 256, 0, st>>>(op, t6, w, Wraw);
 }
 
 // Skalak force f ([N][3]) at X given reference tangents ref6 ([6][N]).
 void enqueue_skalak(const MembraneOp& op, const double* X, const double* ref6, double Es,
-                    double ED, double* f, double* w, cudaStream_t st) {
-  enqueue_tangents(op, X, op.cur_t, w, st);
+                    double ED, double* f, double* w, cudaStream_t st, double* Wraw) {
+  enqueue_tangents(op, X, op.cur_t, w, st, Wraw);
   k_tension<<<blocks_of(op.N), 256, 0, st>>>(op, op.cur_t, ref6, Es, ED);
   enqueue_derivatives(op, 6, st);
   k_divergence<<<blocks_of(op.N), 256, 0, st>>>(op, op.cur_t, f);
@@ -774,6 +776,28 @@ void enqueue_area_volume(const MembraneOp& op, const double* X, double* out2, cu
 }
 
 int64_t membrane_nodes(const MembraneOp& op) { return op.N; }
+
+int membrane_upsampling(sk_ctx* ctx, MembraneOp* op) { return ensure_upsampling(op, ctx->err); }
+
+// I_u of the nodes X, area elements W and densities f (device) into the
+// operator's fine sources, and delta_u per coarse target (Sec. 3.4).
+void enqueue_upsample(const MembraneOp& op, const double* X, const double* W, const double* f,
+                      cudaStream_t st) {
+  const int64_t N = op.N;
+  k_gather<<<blocks_of(3 * N), 256, 0, st>>>(X, N, 3, 0, 3, op.g);
+  k_gather<<<blocks_of(3 * N), 256, 0, st>>>(f, N, 3, 0, 3, op.g + 3 * N);
+  k_gather<<<blocks_of(N), 256, 0, st>>>(W, N, 1, 0, 1, op.g + 6 * N);
+  enqueue_splines(op, 7, op.g, op.sg, st);
+  const double hu = PI_CONST / (4.0 * op.m);
+  k_upsample<<<blocks_of(op.Nup), 256, 0, st>>>(op, hu * hu);
+  cudaMemsetAsync(op.pmax, 0, 8 * sizeof(unsigned long long), st);
+  k_fine_delta<<<blocks_of(op.Nup), 256, 0, st>>>(op);
+  k_delta_targets<<<blocks_of(N), 256, 0, st>>>(op);
+}
+
+UpsampledSources upsampled_sources(const MembraneOp& op) {
+  return {op.Nup, op.Xu, op.wu, op.Fu, op.dtgt, op.Wc};
+}
 
 // The context's operator for grid order m (built on first use).
 int membrane_op(sk_ctx* ctx, int m, MembraneOp** out) {
@@ -929,16 +953,8 @@ int stokes_sl_eval_upsampled(sk_ctx* ctx, int precision, int mem, int m, const d
     dW = op->Wc;
     df = op->fc;
   }
-  // I_u of positions, densities and area element (fields 0..6 of op->g)
-  k_gather<<<blocks_of(3 * N), 256, 0, st>>>(dX, N, 3, 0, 3, op->g);
-  k_gather<<<blocks_of(3 * N), 256, 0, st>>>(df, N, 3, 0, 3, op->g + 3 * N);
-  k_gather<<<blocks_of(N), 256, 0, st>>>(dW, N, 1, 0, 1, op->g + 6 * N);
-  enqueue_splines(*op, 7, op->g, op->sg, st);
-  const double hu = PI_CONST / (4.0 * m);
-  k_upsample<<<blocks_of(op->Nup), 256, 0, st>>>(*op, hu * hu);
-  cudaMemsetAsync(op->pmax, 0, 8 * sizeof(unsigned long long), st);
-  k_fine_delta<<<blocks_of(op->Nup), 256, 0, st>>>(*op);
-  k_delta_targets<<<blocks_of(N), 256, 0, st>>>(*op);
+  // I_u of positions, densities and area element
+  enqueue_upsample(*op, dX, dW, df, st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     ctx->err = std::string("stokes_sl_eval_upsampled: ") + cudaGetErrorString(e);

@@ -66,3 +66,45 @@ def test_upsampling_reduces_the_sphere_translation_error(ctx):
     e_up = np.abs(u_up[:, 2] - 2 / 3).max()
     e = np.abs(u[:, 2] - 2 / 3).max()
     assert e_up < e / 5
+
+
+def oracle_upsampled_velocity(m, X, X_ref, flow, mu, ES=2.0, ED=20.0):
+    """u_inf(X) + S[f](X) with f the Skalak force and the upsampled sum."""
+    W = mb.geometry(m, X)["W"]
+    f = mb.skalak_force(m, X, X_ref, ES, ED)
+    u = up.sl_upsampled(m, X, W, f, mu)
+    if flow is not None:
+        u[:, 0] += flow[1] * X[:, 1]
+    return u
+
+
+def test_capsule_upsampled_euler_and_rkf45_match_oracle(ctx):
+    from oracle import timestep as ts
+    m = 8
+    ref = ci.make_surface(ci.Ellipsoid(0.9, 1.0, 1.0), m)
+    X0 = ref.X * np.array([1.05, 0.98, 0.97])
+    flow = (sk.SK_FLOW_SHEAR, 1.0, 0.0, 0.0)
+    cap = sk.Capsule(ctx, m, X0, ref.w, delta=None, mu=1.0, precision=sk.SK_FP64)
+    try:
+        cap.set_membrane(ref.X, 2.0, 20.0)
+        cap.set_upsampling(4)
+        cap.step(2, 1e-3, None, flow)
+        Xe = cap.positions()
+    finally:
+        cap.close()
+    Xo = X0.copy()
+    for _ in range(2):
+        Xo = Xo + 1e-3 * oracle_upsampled_velocity(m, Xo, ref.X, flow, 1.0)
+    assert rel(Xe - X0, Xo - X0) < 1e-10
+    cap = sk.Capsule(ctx, m, X0, ref.w, delta=None, mu=1.0, precision=sk.SK_FP64)
+    try:
+        cap.set_membrane(ref.X, 2.0, 20.0)
+        cap.set_upsampling(4)
+        dt, acc, rej = cap.integrate_rkf45(3e-3, 1.5e-3, tol=1e-6, flow=flow)
+        Xr = cap.positions()
+    finally:
+        cap.close()
+    rhs = lambda t, y: oracle_upsampled_velocity(m, y.reshape(-1, 3), ref.X, flow, 1.0).ravel()
+    y, dto, acco, rejo = ts.integrate(rhs, X0.ravel(), 3e-3, 1.5e-3, 1e-6)
+    assert (acc, rej) == (acco, rejo)
+    assert rel(Xr - X0, y.reshape(-1, 3) - X0) < 1e-9
