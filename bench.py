@@ -493,6 +493,44 @@ def capsule_bench(sk, h, torch, dev, m=129, steps=100, dt=5e-4, Es=2.0, ED=20.0)
     return res
 
 
+# Wall clock per RKF45 time step with 4x upsampling, sphere in shear, printed
+# in Table wall_clock_sph (hardware and precision unstated): context only.
+PAPER_RKF45_STEP_S = {8: 0.61, 16: 1.26, 32: 10.10, 48: 46.46}
+
+
+def rkf45_upsampled_bench(sk, h, ms=(16, 32, 48), t_end=0.02, Es=2.0, ED=20.0):
+    """The paper's production loop (Sec. 3.6): unit sphere with a stress-free
+    Skalak membrane in shear flow (rate 1), RKF45 with relative tolerance
+    1e-6, single layer on the four-times upsampled grid, membrane force by
+    the overset finite differences. Wall clock per accepted step."""
+    import capsule_inputs as ci
+    flow = (sk.SK_FLOW_SHEAR, 1.0, 0.0, 0.0)
+    out = {"workload": f"unit sphere, Skalak Es={Es} ED={ED}, shear rate 1, RKF45 tol 1e-6, "
+                       f"4x upsampled single layer, t in [0, {t_end}]",
+           "paper_s_per_step": PAPER_RKF45_STEP_S}
+    for m in ms:
+        ref = ci.make_surface(ci.Sphere(1.0), m)
+        row = {"N": ref.N, "N_up": 6 * (4 * m - 1) ** 2}
+        for prec, name in ((sk.SK_FP32C, "fp32c"), (sk.SK_FP64, "fp64")):
+            if prec == sk.SK_FP64 and m > 32:
+                continue
+            cap = sk.Capsule(h, m, ref.X, ref.w, delta=None, mu=1.0, precision=prec)
+            try:
+                cap.set_membrane(ref.X, Es, ED)
+                cap.set_upsampling(4)
+                dt, _, _ = cap.integrate_rkf45(1e-4, 1e-4, tol=1e-6, flow=flow)  # captures
+                t0 = time.perf_counter()
+                dt, acc, rej = cap.integrate_rkf45(t_end, dt, tol=1e-6, flow=flow)
+                el = time.perf_counter() - t0
+                A, V = cap.area_volume()
+            finally:
+                cap.close()
+            row[name] = {"s_per_step": el / max(acc, 1), "accepted": acc, "rejected": rej,
+                         "final_dt": dt, "area": A, "volume": V}
+        out[f"m{m}"] = row
+    return out
+
+
 def extras(sk, h, w, X, W, F, Y, D, out, u_fp32, stream, dev, torch, serve_future=None):
     import capsule_inputs as ci
     import oracle
@@ -620,6 +658,10 @@ def extras(sk, h, w, X, W, F, Y, D, out, u_fp32, stream, dev, torch, serve_futur
         res["capsule_skalak_m129"] = capsule_bench(sk, h, torch, dev)
     except Exception as e:
         res["capsule_skalak_m129"] = {"error": repr(e)}
+    try:
+        res["capsule_rkf45_upsampled"] = rkf45_upsampled_bench(sk, h)
+    except Exception as e:
+        res["capsule_rkf45_upsampled"] = {"error": repr(e)}
     if serve_future is not None:
         try:
             res["serving"] = serving_bench(sk, h, serve_future.result())
