@@ -294,7 +294,14 @@ __device__ __forceinline__ void two_sum_merge(float2* U, float2* HI, float2* LO)
 // (1/delta, rho_c^2 delta^2), (rho_T^2 delta^2, -)), read once per segment;
 // and, for one pair per lane, the compensated accumulators. With one pair per
 // lane three CTAs share an SM, so that configuration runs one stage fewer.
-__host__ __device__ constexpr bool hilo_in_smem(int np) { return np == 1; }
+template <class L>
+__host__ __device__ constexpr bool hilo_in_smem(int np) {
+  // one pair per lane: the freed registers buy the third CTA per SM; two
+  // pairs, single layer: still two CTAs per SM in shared memory, and the
+  // freed registers measured 1% faster (the stresslet's larger records would
+  // drop it to one CTA per SM, so it keeps them in registers)
+  return np == 1 || (np == 2 && L::V == V_SL);
+}
 template <class L, int NP>
 __host__ __device__ constexpr int pair_stages() {
   return NP == 1 ? L::STAGES - 1 : L::STAGES;
@@ -304,7 +311,7 @@ template <class L, int NP>
 constexpr size_t pair_smem_bytes() {
   return (size_t)pair_stages<L, NP>() * TILE * L::V * sizeof(float4) +
          (size_t)NP * TGT_SLOTS * TPB32 * sizeof(float4) +
-         (hilo_in_smem(NP) ? (size_t)NP * 6 * TPB32 * sizeof(float2) : 0);
+         (hilo_in_smem<L>(NP) ? (size_t)NP * 6 * TPB32 * sizeof(float2) : 0);
 }
 
 // Shared-memory state of the source pipeline of one CTA.
@@ -420,10 +427,9 @@ __device__ __forceinline__ bool pair_item(const PairArgs& a, int tb, int ch, flo
     rc2test = rm * rm;
   }
 
-  // Compensated accumulators: registers for two pairs per lane; shared
-  // memory (touched once per 128 sources) for one pair per lane, where the
-  // freed registers buy the third resident CTA without spills.
-  constexpr bool kHiLoSmem = hilo_in_smem(NP);
+  // Compensated accumulators (hi, lo): in shared memory, touched once per 128
+  // sources, or in registers (hilo_in_smem gives the measured choice).
+  constexpr bool kHiLoSmem = hilo_in_smem<L>(NP);
   float2 U[NP][3], HI[NP][3], LO[NP][3];
   // [(p * 3 + c) * 2 + {0: hi, 1: lo}][thread]: one float2 column per thread
   float2* acc = reinterpret_cast<float2*>(sm + STAGES * TILE * V + NP * TGT_SLOTS * TPB32);
