@@ -12,7 +12,8 @@ ctypes. See stokes_oracle.c for the formulas and their paper citations
 Submodules (plain NumPy, same status): membrane.py -- overset finite-difference
 surface derivatives and the Skalak membrane force (Sec. 3.5; Sec. 2.1);
 timestep.py -- Runge-Kutta-Fehlberg 4(5) adaptive stepping (Sec. 3.6);
-upsample.py -- the four-times upsampled single layer (Sec. 3.4).
+upsample.py -- the four-times upsampled single layer (Sec. 3.4);
+fmm.py -- the single-level kernel-independent FMM of Sec. 5.
 """
 
 from __future__ import annotations

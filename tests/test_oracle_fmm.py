@@ -1,0 +1,76 @@
+"""Pins of the single-level FMM oracle (oracle/fmm.py, Sec. 5):
+
+* the cube surface grid has 6p^2 - 12p + 8 points, all on the surface;
+* k-means returns the nearest-centre assignment of its final centres, and
+  a cluster's centre is the mean of its points at a fixed point of Lloyd;
+* one cluster's equivalent sources reproduce its plain-Stokeslet potential
+  outside the check cube, with an error that falls quickly with p;
+* with every cluster near (huge delta), the FMM is the direct sum;
+* on an ellipsoid, the FMM approaches the direct regularized sum as p grows.
+"""
+
+import numpy as np
+
+import capsule_inputs as ci
+import oracle
+from oracle import fmm
+
+
+def test_cube_surface_grid():
+    for p in (3, 4, 5, 6):
+        pts = fmm.cube_surface(p)
+        assert len(pts) == 6 * p * p - 12 * p + 8
+        assert np.allclose(np.abs(pts).max(axis=1), 1.0)
+        assert len(np.unique(pts.round(12), axis=0)) == len(pts)
+
+
+def test_kmeans_invariants():
+    rng = np.random.default_rng(0)
+    pts = rng.standard_normal((500, 3))
+    c, lab = fmm.kmeans(pts, pts[:8], 50)
+    d2 = ((pts[:, None] - c[None]) ** 2).sum(-1)
+    assert np.array_equal(lab, np.argmin(d2, axis=1))
+    for j in range(8):
+        assert np.allclose(c[j], pts[lab == j].mean(axis=0), atol=1e-12)
+
+
+def test_equivalent_sources_reproduce_far_potential():
+    rng = np.random.default_rng(1)
+    pts = rng.uniform(-0.5, 0.5, (300, 3))
+    w = rng.uniform(0.5, 1.5, 300)
+    f = rng.standard_normal((300, 3))
+    lab = np.zeros(300, dtype=int)
+    cen, a = fmm.boxes(pts, lab, 1)
+    d = rng.standard_normal((200, 3))
+    far = cen[0] + 3.0 * a[0] * d / np.abs(d).max(axis=1, keepdims=True)   # on the 3a cube
+    exact = fmm.stokeslet_matrix(far, pts) @ (w[:, None] * f).ravel()
+    errs = []
+    for p in (4, 6, 8):
+        E, phi = fmm.equivalent_densities(pts, w, f, lab, cen, a, p)
+        approx = fmm.stokeslet_matrix(far, E[0]) @ phi[0].ravel()
+        errs.append(np.abs(approx - exact).max() / np.abs(exact).max())
+    assert errs[-1] < 1e-5 and errs[-1] < errs[0] / 100, errs
+
+
+def test_all_near_is_the_direct_sum():
+    s = ci.make_surface(ci.Sphere(1.0), 9)
+    f = ci.sh_density(s.x0, np.random.default_rng(2), lmax=4)
+    c0 = s.X[s.w != 0][::40]
+    u = fmm.sl_fmm(s.X, s.w, f, s.X, 10.0, 1.3, c0, 5, 4)
+    ref = oracle.sl(s.X, s.w, f, s.X, 10.0, 1.3)
+    assert np.allclose(u, ref, rtol=1e-13, atol=1e-13 * np.abs(ref).max())
+
+
+def test_fmm_converges_to_the_direct_sum():
+    s = ci.make_surface(ci.Ellipsoid(1.0, 0.8, 0.5), 24)
+    f = ci.sh_density(s.x0, np.random.default_rng(3), lmax=6)
+    act = np.flatnonzero(s.w)
+    c0 = s.X[act[:: len(act) // 30][:30]]
+    tgt = s.X[::7]
+    delta = 0.02   # small enough that most clusters are far (7 delta from their cube)
+    ref = oracle.sl(s.X, s.w, f, tgt, delta)
+    errs = []
+    for p in (4, 6, 8):
+        u = fmm.sl_fmm(s.X, s.w, f, tgt, delta, 1.0, c0, 8, p)
+        errs.append(np.linalg.norm(u - ref) / np.linalg.norm(ref))
+    assert errs[2] < 1e-5 and errs[2] < errs[1] < errs[0], errs
