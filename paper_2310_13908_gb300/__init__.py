@@ -93,6 +93,8 @@ _EXTRA_DECLS: dict = {
     "surface_derivatives": ([_vp, _int, _int, _i64, _vp, _vp, _vp, _vp], _int),
     "membrane_force": ([_vp, _int, _int, _vp, _vp, _dbl, _dbl, _vp, _vp, _vp], _int),
     "stokes_sl_eval_upsampled": ([_vp, _int, _int, _int, _vp, _vp, _vp, _dbl, _vp, _vp], _int),
+    "stokes_sl_eval_fmm": ([_vp, _int, _i64, _vp, _vp, _vp, _i64, _vp, _vp, _i64, _dbl, _int, _vp,
+                            _int, _int, _vp, _vp], _int),
     "capsule_destroy": ([_vp], None),
 }
 
@@ -320,6 +322,29 @@ def stokes_sl_eval_upsampled(ctx, precision: int, mem: int, m: int, X, W, f, mu:
         args = [_host_ptr(Xa), _host_ptr(Wa), _host_ptr(Fa), float(mu), _host_ptr(u)]
     _check(ctx, lib.stokes_sl_eval_upsampled(ctx, int(precision), int(mem), int(m), *args,
                                              _stream_handle(stream)))
+    return u
+
+
+def stokes_sl_eval_fmm(ctx, mem: int, src_xyz, src_w, f, tgt_xyz, delta, mu: float, centers0,
+                       lloyd_iters: int = 10, p: int = 6, stream=None):
+    """Single layer by the single-level FMM of Sec. 5 (FP64). Returns u (M, 3)."""
+    lib = load()
+    X, n = _ptr(src_xyz, mem, (3,), "src_xyz")
+    W, nw = _ptr(src_w, mem, (), "src_w")
+    F, nf = _ptr(f, mem, (3,), "f")
+    Y, M = _ptr(tgt_xyz, mem, (3,), "tgt_xyz")
+    D, nd = _ptr(delta if mem == SK_DEVICE or not np.isscalar(delta) else [delta], mem, (),
+                 "delta")
+    C, k = _ptr(centers0, mem, (3,), "centers0")
+    if not (n == nw == nf):
+        raise ValueError("src_xyz, src_w and f must have the same number of nodes")
+    u = _alloc_out(tgt_xyz, mem, M)
+    if mem == SK_HOST:
+        args = [_host_ptr(X), _host_ptr(W), _host_ptr(F), M, _host_ptr(Y), _host_ptr(D), nd,
+                float(mu), k, _host_ptr(C), int(lloyd_iters), int(p), _host_ptr(u)]
+    else:
+        args = [X, W, F, M, Y, D, nd, float(mu), k, C, int(lloyd_iters), int(p), u.data_ptr()]
+    _check(ctx, lib.stokes_sl_eval_fmm(ctx, int(mem), n, *args, _stream_handle(stream)))
     return u
 
 

@@ -262,6 +262,7 @@ void sk_destroy(sk_ctx* ctx) {
   DeviceGuard g(ctx->device);
   cudaDeviceSynchronize();
   free_membrane_ops(ctx);
+  free_fmm_ops(ctx);
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->h_flags) cudaFreeHost(ctx->h_flags);
   for (int i = 0; i < 4; ++i)

@@ -148,6 +148,7 @@ struct sk_server;
 
 namespace sk {
 struct MembraneOp;
+struct FmmOp;
 }
 
 struct sk_ctx {
@@ -166,6 +167,7 @@ struct sk_ctx {
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // eval begin, pair begin/end, eval end
   sk_eval_stats stats{};
   std::vector<std::pair<int, sk::MembraneOp*>> membrane_ops;  // derivative operators by m
+  std::vector<std::pair<int, sk::FmmOp*>> fmm_ops;            // FMM operators by p
   std::string err;
 };
 
@@ -221,6 +223,9 @@ int eval_call(sk_ctx* ctx, int layer, int precision, int mem, int64_t N, const d
               const double* w, const double* dens, const double* nrm, int64_t M,
               const double* txyz, const double* delta, int64_t n_delta, double mu,
               double* u_out, void* stream);
+
+// sk_fmm.cu: single-level FMM operators (cached per p in ctx)
+void free_fmm_ops(sk_ctx* ctx);
 
 // sk_membrane.cu: overset finite-difference derivatives and the Skalak force
 // on the six-patch grid of order m (built once per m and cached in ctx).
