@@ -277,10 +277,11 @@ int stokes_sl_eval_upsampled(sk_ctx* ctx, int precision, int mem, int m, const d
  *   p           equivalent/check points per cube edge (3..10; 6 p^2 - 12 p + 8
  *               points per cube)
  * Clusters get a cube (half width a), equivalent sources on the 1.05 a cube
- * and check points on the 2.95 a cube; a target takes a cluster's
- * equivalent sources when it lies outside the check cube and at least
- * 7 delta from the cluster cube, else the direct regularized sum over the
- * cluster's points. Deterministic. Errors: SK_EINVAL, SK_ENOMEM, SK_ECUDA. */
+ * and check points on the 2.95 a cube; targets go in groups of 32
+ * consecutive indices, and a group takes a cluster's equivalent sources when
+ * every target lies outside the check cube and at least 7 delta from the
+ * cluster cube, else the direct regularized sum over the cluster's points.
+ * Deterministic. Errors: SK_EINVAL, SK_ENOMEM, SK_ECUDA. */
 int stokes_sl_eval_fmm(sk_ctx* ctx, int mem, int64_t n_src, const double* src_xyz,
                        const double* src_w, const double* f, int64_t n_tgt, const double* tgt_xyz,
                        const double* delta, int64_t n_delta, double mu, int k,

@@ -26,7 +26,10 @@ Readings (the paper gives no more detail):
     cube size, phi(a) = a phi(1).)
   * Far: the target lies outside the check cube and at least 7 delta from
     the cluster cube, so the regularized kernel of every source in the
-    cluster equals the plain one to double precision.
+    cluster equals the plain one to double precision. As the paper decides
+    box against box, targets are taken in groups of GROUP consecutive
+    indices: a group uses a cluster's equivalent sources only when the
+    cluster is far for every target of the group.
 """
 
 from __future__ import annotations
@@ -39,6 +42,7 @@ R_EQUIV = 1.05
 R_CHECK = 2.95
 RHO_FAR = 7.0
 TIKHONOV = 1e-8
+GROUP = 32
 
 
 def kmeans(points: np.ndarray, centers0: np.ndarray, iters: int):
@@ -46,7 +50,8 @@ def kmeans(points: np.ndarray, centers0: np.ndarray, iters: int):
     c = np.array(centers0, dtype=np.float64, copy=True)
 
     def assign(c):
-        d2 = ((points[:, None, :] - c[None, :, :]) ** 2).sum(-1)
+        d = points[:, None, :] - c[None, :, :]
+        d2 = (d[..., 0] * d[..., 0] + d[..., 1] * d[..., 1]) + d[..., 2] * d[..., 2]
         return np.argmin(d2, axis=1)   # first minimum: lowest index on ties
 
     for _ in range(iters):
@@ -132,8 +137,12 @@ def sl_fmm(src, w, f, tgt, delta, mu, centers0, iters, p):
             continue
         rel = np.abs(tgt - cen[j])
         outside_check = rel.max(axis=1) >= R_CHECK * a[j]
-        gap = np.linalg.norm(np.maximum(rel - a[j], 0.0), axis=1)
-        far = outside_check & (gap >= RHO_FAR * delta)
+        g = np.maximum(rel - a[j], 0.0)
+        gap2 = (g[:, 0] * g[:, 0] + g[:, 1] * g[:, 1]) + g[:, 2] * g[:, 2]
+        far_t = outside_check & (gap2 >= (RHO_FAR * delta) * (RHO_FAR * delta))
+        far = np.empty_like(far_t)
+        for g0 in range(0, len(tgt), GROUP):
+            far[g0:g0 + GROUP] = np.all(far_t[g0:g0 + GROUP])
         if np.any(far):
             u[far] += scale * (stokeslet_matrix(tgt[far], eq_pts[j]) @ eq_den[j].ravel()).reshape(-1, 3)
         near = ~far

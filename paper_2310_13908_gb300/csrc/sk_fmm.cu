@@ -9,10 +9,11 @@
 //      the 2.95 a cube; equivalent densities phi solve, in the Tikhonov
 //      sense, K phi = u_check (plain Stokeslet), u_check being the cluster's
 //      potential at the check points;
-//   3. a target takes a cluster's equivalent sources when it lies outside the
-//      check cube and at least 7 delta from the cluster cube (the regularized
-//      kernel then equals the plain one to double precision), else the direct
-//      regularized sum over the cluster's points.
+//   3. a group of 32 consecutive targets takes a cluster's equivalent
+//      sources when every target lies outside the check cube and at least
+//      7 delta from the cluster cube (the regularized kernel then equals the
+//      plain one to double precision), else the direct regularized sum over
+//      the cluster's points.
 // The Tikhonov operator P1 = (K1^T K1 + alpha^2 I)^{-1} K1^T of the unit cube
 // (alpha = 1e-8 |K1|_F) is built once per p on the host by Householder QR of
 // [K1; alpha I]; K scales like 1/a, so phi = a P1 u_check for a cube of half
@@ -301,7 +302,7 @@ __global__ void k_fmm_upward(const double* __restrict__ X, const double* __restr
       const int i = list[q];
       const double dx = px - X[3 * i], dy = py - X[3 * i + 1], dz = pz - X[3 * i + 2];
       const double r2 = dx * dx + dy * dy + dz * dz;
-      const double ir = 1.0 / sqrt(r2), ir3 = ir / r2;
+      const double ir = rsqrt(r2), ir3 = ir * ir * ir;
       const double gx = w[i] * f[3 * i], gy = w[i] * f[3 * i + 1], gz = w[i] * f[3 * i + 2];
       const double gd = (gx * dx + gy * dy + gz * dz) * ir3;
       u0 += gx * ir + gd * dx;
@@ -320,8 +321,11 @@ __global__ void k_fmm_upward(const double* __restrict__ X, const double* __restr
   }
 }
 
-// one thread per target: equivalent sources of far clusters, direct
-// regularized sum over the points of the others
+// One thread per target, one warp per group of 32 consecutive targets: a
+// group takes a cluster's equivalent sources only when the cluster is far
+// for every target of the group (box-against-box, as the paper decides),
+// else the direct regularized sum over the cluster's points; beyond 7 delta
+// the regularized pair is the plain Stokeslet.
 __global__ void k_fmm_eval(const double* __restrict__ Y, const double* __restrict__ delta,
                            int64_t n_delta, int64_t M, int k, const double* __restrict__ box,
                            const int* __restrict__ off, const int* __restrict__ list,
@@ -329,9 +333,11 @@ __global__ void k_fmm_eval(const double* __restrict__ Y, const double* __restric
                            const double* __restrict__ X, const double* __restrict__ w,
                            const double* __restrict__ f, double scale, double* __restrict__ u) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= M) return;
-  const double x = Y[3 * t], y = Y[3 * t + 1], z = Y[3 * t + 2];
-  const double d = delta[n_delta == 1 ? 0 : t], invd = 1.0 / d;
+  const bool live = t < M;
+  const int64_t tt = live ? t : M - 1;
+  const double x = Y[3 * tt], y = Y[3 * tt + 1], z = Y[3 * tt + 2];
+  const double d = delta[n_delta == 1 ? 0 : tt], invd = 1.0 / d;
+  const double rf = RHO_FAR * d, rf2 = __dmul_rn(rf, rf);
   double fx0 = 0.0, fx1 = 0.0, fx2 = 0.0;  // far, without 1/(8 pi mu)
   double n0 = 0.0, n1 = 0.0, n2 = 0.0;     // near
   for (int c = 0; c < k; ++c) {
@@ -340,16 +346,15 @@ __global__ void k_fmm_eval(const double* __restrict__ Y, const double* __restric
     const double rx = fabs(x - cx), ry = fabs(y - cy), rz = fabs(z - cz);
     const double gx = fmax(rx - a, 0.0), gy = fmax(ry - a, 0.0), gz = fmax(rz - a, 0.0);
     const double gap2 = __dadd_rn(__dadd_rn(__dmul_rn(gx, gx), __dmul_rn(gy, gy)), __dmul_rn(gz, gz));
-    const double rf = RHO_FAR * d;
-    const bool far = fmax(rx, fmax(ry, rz)) >= R_CHECK * a && gap2 >= __dmul_rn(rf, rf);
-    if (far) {
+    const bool far = !live || (fmax(rx, fmax(ry, rz)) >= R_CHECK * a && gap2 >= rf2);
+    if (__all_sync(0xffffffffu, far)) {
       const double* ph = phi + (int64_t)c * 3 * Np;
       for (int j = 0; j < Np; ++j) {
         const double dx = x - (cx + R_EQUIV * a * unit[3 * j]);
         const double dy = y - (cy + R_EQUIV * a * unit[3 * j + 1]);
         const double dz = z - (cz + R_EQUIV * a * unit[3 * j + 2]);
         const double r2 = dx * dx + dy * dy + dz * dz;
-        const double ir = 1.0 / sqrt(r2), ir3 = ir / r2;
+        const double ir = rsqrt(r2), ir3 = ir * ir * ir;
         const double px = ph[3 * j], py = ph[3 * j + 1], pz = ph[3 * j + 2];
         const double pd = (px * dx + py * dy + pz * dz) * ir3;
         fx0 += px * ir + pd * dx;
@@ -359,14 +364,28 @@ __global__ void k_fmm_eval(const double* __restrict__ Y, const double* __restric
     } else {
       for (int q = off[c]; q < off[c + 1]; ++q) {
         const int i = list[q];
-        sl_pair64(x - X[3 * i], y - X[3 * i + 1], z - X[3 * i + 2], f[3 * i], f[3 * i + 1],
-                  f[3 * i + 2], w[i] * scale, invd, n0, n1, n2);
+        const double dx = x - X[3 * i], dy = y - X[3 * i + 1], dz = z - X[3 * i + 2];
+        const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+        if (r2 >= rf2) {  // s1 = s2 = 1 to double precision
+          const double ir = rsqrt(r2), ir3 = ir * ir * ir;
+          const double ws = w[i] * scale;
+          const double fx = f[3 * i], fy = f[3 * i + 1], fz = f[3 * i + 2];
+          const double fd = (fx * dx + fy * dy + fz * dz) * ir3;
+          n0 = fma(ws, fx * ir + fd * dx, n0);
+          n1 = fma(ws, fy * ir + fd * dy, n1);
+          n2 = fma(ws, fz * ir + fd * dz, n2);
+        } else {
+          sl_pair64(dx, dy, dz, f[3 * i], f[3 * i + 1], f[3 * i + 2], w[i] * scale, invd, n0, n1,
+                    n2);
+        }
       }
     }
   }
-  u[3 * t] = scale * fx0 + n0;
-  u[3 * t + 1] = scale * fx1 + n1;
-  u[3 * t + 2] = scale * fx2 + n2;
+  if (live) {
+    u[3 * t] = scale * fx0 + n0;
+    u[3 * t + 1] = scale * fx1 + n1;
+    u[3 * t + 2] = scale * fx2 + n2;
+  }
 }
 
 }  // namespace
