@@ -531,6 +531,41 @@ def rkf45_upsampled_bench(sk, h, ms=(16, 32, 48), t_end=0.02, Es=2.0, ED=20.0):
     return out
 
 
+def fmm_bench(sk, h, torch, dev, m=129, k=64, p=6):
+    """Single-level FMM (Sec. 5, FP64) against the direct FP64 and FP32C sums:
+    ellipsoid (1, 0.8, 0.5) nodes as sources and targets, delta = 2h."""
+    import capsule_inputs as ci
+    s = ci.make_surface(ci.Ellipsoid(1.0, 0.8, 0.5), m)
+    f = ci.sh_density(s.x0, np.random.default_rng(5), lmax=8)
+
+    def td(a):
+        return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)
+
+    X, W, F, D = td(s.X), td(s.w), td(f), td(np.array([2 * s.h]))
+    act = np.flatnonzero(s.w)
+    C0 = td(s.X[act[:: len(act) // k][:k]])
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            u = fn()
+        torch.cuda.synchronize(dev)
+        return (time.perf_counter() - t0) * 1e3 / reps, u.cpu().numpy()
+
+    t64, u64 = timed(lambda: sk.stokes_sl_eval(h, sk.SK_FP64, sk.SK_DEVICE, X, W, F, X, D, 1.0), 2)
+    t32, u32 = timed(lambda: sk.stokes_sl_eval(h, sk.SK_FP32C, sk.SK_DEVICE, X, W, F, X, D, 1.0), 5)
+    tf, uf = timed(lambda: sk.stokes_sl_eval_fmm(h, sk.SK_DEVICE, X, W, F, X, D, 1.0, C0, 10, p), 2)
+    return {"workload": f"ellipsoid(1,0.8,0.5) m={m}: N={s.N} targets x N_s={s.n_active} sources, "
+                        f"delta=2h; FMM k={k} clusters (10 Lloyd steps), p={p} "
+                        f"({6 * p * p - 12 * p + 8} equivalent points per cube)",
+            "direct_fp64_ms": t64, "direct_fp32c_ms": t32, "fmm_fp64_ms": tf,
+            "fmm_rel_l2_vs_direct_fp64": rel_l2(uf, u64),
+            "fp32c_rel_l2_vs_direct_fp64": rel_l2(u32, u64),
+            "paper_speedup_fmm_vs_direct": {"m32": 1.02, "m64": 1.57, "m96": 1.81}}
+
+
 def extras(sk, h, w, X, W, F, Y, D, out, u_fp32, stream, dev, torch, serve_future=None):
     import capsule_inputs as ci
     import oracle
@@ -662,6 +697,10 @@ def extras(sk, h, w, X, W, F, Y, D, out, u_fp32, stream, dev, torch, serve_futur
         res["capsule_rkf45_upsampled"] = rkf45_upsampled_bench(sk, h)
     except Exception as e:
         res["capsule_rkf45_upsampled"] = {"error": repr(e)}
+    try:
+        res["fmm_m129"] = fmm_bench(sk, h, torch, dev)
+    except Exception as e:
+        res["fmm_m129"] = {"error": repr(e)}
     if serve_future is not None:
         try:
             res["serving"] = serving_bench(sk, h, serve_future.result())
