@@ -41,6 +41,7 @@ constexpr int SERVE_MINB = 3;                         // CTAs per SM
 constexpr int SERVE_TGT_CTA = TPB32 * 2 * SERVE_NP;  // targets per block (512)
 constexpr int SERVE_RESERVE_CTAS = 24;  // CTA slots left free for the preparation kernels
 constexpr int MAX_SLOTS = 256;
+constexpr int SERVE_PREP_STREAMS = 4;
 
 // Device descriptor of one resident request.
 struct SlotDesc {
@@ -262,7 +263,11 @@ struct sk_server {
   sk_ctx* ctx = nullptr;
   sk_serve_cfg cfg{};
   int n_slots = 0;
-  cudaStream_t s_kernel = nullptr, s_prep = nullptr, s_ctl = nullptr, s_copy = nullptr;
+  cudaStream_t s_kernel = nullptr, s_ctl = nullptr, s_copy = nullptr;
+  // preparation streams: independent requests prepare concurrently (slot i
+  // uses stream i mod SERVE_PREP_STREAMS), so a burst of admissions does not
+  // queue behind one stream
+  cudaStream_t s_prep[sk::SERVE_PREP_STREAMS] = {};
   sk::SlotDesc* d_desc = nullptr;
   sk::SlotClaim* d_claim = nullptr;
   int* d_stop = nullptr;
@@ -324,7 +329,7 @@ void launch_kernel(sk_server* srv) {
 
 // Admit: bind a queued request to a free slot and its arena block, enqueue
 // the H2D copy and the preparation kernels.
-bool admit_one(sk_server* srv, Req* r, Slot& sl) {
+bool admit_one(sk_server* srv, Req* r, Slot& sl, int slot) {
   size_t off = 0;
   if (!srv->arena_alloc.alloc(r->footprint, &off)) return false;
   sl.state = SlotState::Prep;
@@ -340,7 +345,7 @@ bool admit_one(sk_server* srv, Req* r, Slot& sl) {
   const int n_tb = (int)(b.M_pad / SERVE_TGT_CTA);
   sl.tb_counters = bp.take<int>(n_tb + 1);
   const EvalShape& s = r->shape;
-  cudaStream_t st = srv->s_prep;
+  cudaStream_t st = srv->s_prep[slot % SERVE_PREP_STREAMS];
   if (s.N > 0) {
     cudaMemcpyAsync((void*)b.src_xyz, r->h_xyz, 3 * s.N * sizeof(double), cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync((void*)b.src_w, r->h_w, s.N * sizeof(double), cudaMemcpyHostToDevice, st);
@@ -400,7 +405,7 @@ void scheduler(sk_server* srv) {
         Slot& sl = srv->slots[i];
         if (sl.state != SlotState::Free) continue;
         Req* r = srv->queue.front();
-        if (!admit_one(srv, r, sl)) break;  // not enough arena yet
+        if (!admit_one(srv, r, sl, i)) break;  // not enough arena yet
         srv->queue.pop_front();
         progress = true;
       }
@@ -487,7 +492,9 @@ void free_server(sk_server* srv) {
     if (sl.copy_done) cudaEventDestroy(sl.copy_done);
   }
   if (srv->kernel_done) cudaEventDestroy(srv->kernel_done);
-  for (cudaStream_t s : {srv->s_kernel, srv->s_prep, srv->s_ctl, srv->s_copy})
+  for (cudaStream_t s : {srv->s_kernel, srv->s_ctl, srv->s_copy})
+    if (s) cudaStreamDestroy(s);
+  for (cudaStream_t s : srv->s_prep)
     if (s) cudaStreamDestroy(s);
   for (auto& kv : srv->reqs) delete kv.second;
   delete srv;
@@ -537,7 +544,7 @@ int serve_create(sk_ctx* ctx, const sk_serve_cfg* cfg_in, sk_server** out) {
     return x == cudaSuccess;
   };
   ok(cudaStreamCreateWithFlags(&srv->s_kernel, cudaStreamNonBlocking));
-  ok(cudaStreamCreateWithFlags(&srv->s_prep, cudaStreamNonBlocking));
+  for (cudaStream_t& s : srv->s_prep) ok(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
   ok(cudaStreamCreateWithFlags(&srv->s_ctl, cudaStreamNonBlocking));
   ok(cudaStreamCreateWithFlags(&srv->s_copy, cudaStreamNonBlocking));
   ok(cudaMalloc(&srv->d_desc, MAX_SLOTS * sizeof(SlotDesc)));
