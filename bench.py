@@ -196,13 +196,22 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-PAIR32_SOURCES = ("sk_pair32.cuh", "sk_pair32.cu", "sk_series.cuh", "sk_internal.h", "sk_api.cu")
+PAIR32_SOURCES = ("sk_pair32.cuh", "sk_pair32.cu", "sk_series.cuh")
 
 
 def pair32_source_hash():
+    """Hash of what shapes the FP32 pair kernel's launch: its own sources, the
+    chunk policy (choose_chunks in sk_api.cu) and the work-decomposition
+    constants of sk_internal.h (up to the Bump allocator)."""
+    csrc = os.path.join(ROOT, "paper_2310_13908_gb300", "csrc")
     h = hashlib.sha256()
     for name in PAIR32_SOURCES:
-        h.update(open(os.path.join(ROOT, "paper_2310_13908_gb300", "csrc", name), "rb").read())
+        h.update(open(os.path.join(csrc, name), "rb").read())
+    api = open(os.path.join(csrc, "sk_api.cu")).read()
+    i = api.index("int choose_chunks(")
+    h.update(api[i:api.index("\n}\n", i)].encode())
+    hdr = open(os.path.join(csrc, "sk_internal.h")).read()
+    h.update(hdr[hdr.index("namespace sk {"):hdr.index("// Bump allocator")].encode())
     return h.hexdigest()
 
 
@@ -566,6 +575,54 @@ def fmm_bench(sk, h, torch, dev, m=129, k=64, p=6):
             "paper_speedup_fmm_vs_direct": {"m32": 1.02, "m64": 1.57, "m96": 1.81}}
 
 
+# Relative errors at T = 0.5 against the m = 48 solution printed in Table
+# convg_full (shear: convg_shear, Poiseuille: convg_poiseuille): (A, V, J).
+PAPER_CONVERGENCE = {"shear": {8: (2e-2, 4e-2, 3e-2), 16: (2e-3, 1e-3, 2e-3), 32: (1e-4, 1e-4, 1e-4)},
+                     "poiseuille": {8: (2e-2, 4e-2, 2e-2), 16: (3e-3, 1e-3, 2e-3),
+                                    32: (2e-4, 1e-4, 1e-4)}}
+
+
+def capsule_run(sk, h, m, flow, T, precision, Es=2.0, ED=20.0, tol=1e-6):
+    """Stress-free ellipsoid (0.9, 1, 1) capsule, Skalak membrane, RKF45 with
+    the 4x upsampled single layer (Sec. 3.6) to time T; returns
+    (A, V, centroid, J, accepted, rejected, seconds)."""
+    import capsule_inputs as ci
+    ref = ci.make_surface(ci.Ellipsoid(0.9, 1.0, 1.0), m)
+    cap = sk.Capsule(h, m, ref.X, ref.w, delta=None, mu=1.0, precision=precision)
+    try:
+        cap.set_membrane(ref.X, Es, ED)
+        cap.set_upsampling(4)
+        t0 = time.perf_counter()
+        _, acc, rej = cap.integrate_rkf45(T, 1e-3, tol=tol, flow=flow)
+        el = time.perf_counter() - t0
+        A, V, c, J = cap.shape_moments()
+    finally:
+        cap.close()
+    return A, V, c, J, acc, rej, el
+
+
+def convergence_bench(sk, h, ms=(8, 16, 32), m_ref=48, T=0.5):
+    """Self-convergence of area, volume and inertia tensor at T = 0.5 (Sec. 4.2,
+    Table convg_full): Es = 2, ED = 20, shear rate 1 / Poiseuille (25 - y^2 -
+    z^2, 0, 0), RKF45 tol 1e-6, 4x upsampling; reference m = 48."""
+    flows = {"shear": (sk.SK_FLOW_SHEAR, 1.0, 0.0, 0.0),
+             "poiseuille": (sk.SK_FLOW_POISEUILLE, 0.0, 1.0, 5.0)}
+    out = {"setup": "ellipsoid (0.9, 1, 1) stress-free, Es=2, ED=20, RKF45 tol 1e-6, 4x "
+                    f"upsampled single layer (FP32C), T={T}, reference m={m_ref}; "
+                    "errors: |A - A_ref|/A_ref, |V - V_ref|/V_ref, |J - J_ref|_F/|J_ref|_F",
+           "paper": PAPER_CONVERGENCE}
+    for name, fl in flows.items():
+        Ar, Vr, _, Jr, acc, rej, el = capsule_run(sk, h, m_ref, fl, T, sk.SK_FP32C)
+        row = {f"m{m_ref}": {"accepted": acc, "rejected": rej, "seconds": el}}
+        for m in ms:
+            A, V, _, J, acc, rej, el = capsule_run(sk, h, m, fl, T, sk.SK_FP32C)
+            row[f"m{m}"] = {"eps_A": abs(A - Ar) / Ar, "eps_V": abs(V - Vr) / Vr,
+                            "eps_J": float(np.linalg.norm(J - Jr) / np.linalg.norm(Jr)),
+                            "accepted": acc, "rejected": rej, "seconds": el}
+        out[name] = row
+    return out
+
+
 def extras(sk, h, w, X, W, F, Y, D, out, u_fp32, stream, dev, torch, serve_future=None):
     import capsule_inputs as ci
     import oracle
@@ -701,6 +758,10 @@ def extras(sk, h, w, X, W, F, Y, D, out, u_fp32, stream, dev, torch, serve_futur
         res["fmm_m129"] = fmm_bench(sk, h, torch, dev)
     except Exception as e:
         res["fmm_m129"] = {"error": repr(e)}
+    try:
+        res["capsule_self_convergence"] = convergence_bench(sk, h)
+    except Exception as e:
+        res["capsule_self_convergence"] = {"error": repr(e)}
     if serve_future is not None:
         try:
             res["serving"] = serving_bench(sk, h, serve_future.result())

@@ -222,6 +222,15 @@ int capsule_set_upsampling(sk_capsule* c, int factor);
  * Errors: SK_EINVAL, SK_ENOMEM, SK_ECUDA. */
 int capsule_area_volume(sk_capsule* c, double* area, double* volume);
 
+/* Shape moments of the current nodes (Sec. 4.2, Table convg_full): out[14]
+ * = area A, volume V, centroid c (3), moment of inertia tensor about the
+ * centroid J = int_V (|x - c|^2 I - (x - c)(x - c)^T) (3 x 3, row-major).
+ * Volume integrals by the divergence theorem (int_V x_i = 1/4 int x_i x.n,
+ * int_V x_i x_j = 1/5 int x_i x_j x.n) with W and n from the derivative
+ * scheme and the POU quadrature. Needs m >= 6. Synchronous.
+ * Errors: SK_EINVAL, SK_ENOMEM, SK_ECUDA. */
+int capsule_shape_moments(sk_capsule* c, double* out);
+
 /* Copy the current node positions [N][3] to host memory. */
 int capsule_get(sk_capsule* c, double* X_out);
 

@@ -87,6 +87,7 @@ _EXTRA_DECLS: dict = {
     "capsule_get": ([_vp, _vp], _int),
     "capsule_set_membrane": ([_vp, _vp, _dbl, _dbl], _int),
     "capsule_set_upsampling": ([_vp, _int], _int),
+    "capsule_shape_moments": ([_vp, _vp], _int),
     "capsule_integrate_rkf45": ([_vp, _dbl, ctypes.POINTER(_dbl), _dbl, _vp, _vp, _i64,
                                  ctypes.POINTER(ctypes.c_int64)], _int),
     "capsule_area_volume": ([_vp, ctypes.POINTER(_dbl), ctypes.POINTER(_dbl)], _int),
@@ -402,6 +403,12 @@ class Capsule:
     def set_upsampling(self, factor: int):
         """Single layer of every step on the 4x upsampled grid (4) or not (1)."""
         _check(self.ctx, load().capsule_set_upsampling(self.handle, int(factor)))
+
+    def shape_moments(self):
+        """(A, V, centroid (3,), inertia tensor about the centroid (3, 3))."""
+        out = np.zeros(14)
+        _check(self.ctx, load().capsule_shape_moments(self.handle, out.ctypes.data_as(_vp)))
+        return out[0], out[1], out[2:5].copy(), out[5:].reshape(3, 3).copy()
 
     def area_volume(self):
         a, v = ctypes.c_double(), ctypes.c_double()

@@ -610,6 +610,48 @@ int capsule_area_volume(sk_capsule* c, double* area, double* volume) {
   return SK_OK;
 }
 
+int capsule_shape_moments(sk_capsule* c, double* out) {
+  if (!c || !out) return SK_EINVAL;
+  sk_ctx* ctx = c->ctx;
+  MembraneOp* op = nullptr;
+  int rc = membrane_op(ctx, c->m, &op);
+  if (rc != SK_OK) return rc;
+  cudaSetDevice(ctx->device);
+  cudaStream_t st = ctx->stream;
+  double* d = nullptr;
+  cudaError_t e = cudaMallocAsync(&d, 16 * sizeof(double), st);
+  double mo[16] = {};
+  if (e == cudaSuccess) {
+    enqueue_moments(*op, c->X, d, st);
+    e = cudaMemcpyAsync(mo, d, sizeof(mo), cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(d, st);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    ctx->err = std::string("capsule_shape_moments: ") + cudaGetErrorString(e);
+    return SK_ECUDA;
+  }
+  // out: A, V, centroid (3), inertia tensor about the centroid (3 x 3); the
+  // moments mo[3..] are about the node mean o = mo[0..2]
+  const double* o = mo;
+  const double* m = mo + 3;
+  const double A = m[0], V = m[1];
+  const double cx[3] = {m[2] / V, m[3] / V, m[4] / V};  // centroid - o
+  double S[3][3];
+  int q = 5;
+  for (int a = 0; a < 3; ++a)
+    for (int b = a; b < 3; ++b) S[a][b] = S[b][a] = m[q++];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) S[a][b] -= V * cx[a] * cx[b];  // central second moments
+  const double tr = S[0][0] + S[1][1] + S[2][2];
+  out[0] = A;
+  out[1] = V;
+  for (int a = 0; a < 3; ++a) out[2 + a] = o[a] + cx[a];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) out[5 + 3 * a + b] = (a == b ? tr : 0.0) - S[a][b];
+  return SK_OK;
+}
+
 int capsule_get(sk_capsule* c, double* X_out) {
   if (!c || !X_out) return SK_EINVAL;
   cudaSetDevice(c->ctx->device);

@@ -249,5 +249,6 @@ void enqueue_upsample(const MembraneOp& op, const double* X, const double* W, co
                       cudaStream_t st);
 UpsampledSources upsampled_sources(const MembraneOp& op);
 void enqueue_area_volume(const MembraneOp& op, const double* X, double* out2, cudaStream_t st);
+void enqueue_moments(const MembraneOp& op, const double* X, double* out16, cudaStream_t st);
 
 }  // namespace sk

@@ -479,6 +479,67 @@ __global__ void k_area_volume(const MembraneOp op, const double* __restrict__ X,
   }
 }
 
+// Shape moments by the divergence theorem, POU quadrature (Sec. 3.3), with
+// x taken relative to an origin o near the body (the node mean): A = int 1,
+// V = int x n_x (Sec. 4.1), int_V x_i = (1/4) int x_i (x.n),
+// int_V x_i x_j = (1/5) int x_i x_j (x.n); per block, fixed order, 13 sums.
+// (About the coordinate origin, the central second moments of a body far from
+// it would cancel catastrophically.)
+constexpr int N_MOM = 13;
+__global__ void k_node_mean(const double* __restrict__ X, int64_t N, double* __restrict__ o) {
+  __shared__ double sm[3][256];
+  const int t = threadIdx.x;
+  double v[3] = {0.0, 0.0, 0.0};
+  for (int64_t i = t; i < N; i += 256)
+    for (int a = 0; a < 3; ++a) v[a] += X[3 * i + a];
+  for (int a = 0; a < 3; ++a) sm[a][t] = v[a];
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (t < s)
+      for (int a = 0; a < 3; ++a) sm[a][t] += sm[a][t + s];
+    __syncthreads();
+  }
+  if (t == 0)
+    for (int a = 0; a < 3; ++a) o[a] = sm[a][0] / (double)N;
+}
+
+__global__ void k_moments(const MembraneOp op, const double* __restrict__ X,
+                          const double* __restrict__ cur, const double* __restrict__ o,
+                          double* __restrict__ part) {
+  __shared__ double sm[N_MOM][128];
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double v[N_MOM] = {};
+  if (i < op.N) {
+    const Frame c = frame_at(cur, op.N, i);
+    const double w = op.psi_own[i] * c.W * op.h * op.h;
+    const double x[3] = {X[3 * i] - o[0], X[3 * i + 1] - o[1], X[3 * i + 2] - o[2]};
+    const double xn = x[0] * c.n[0] + x[1] * c.n[1] + x[2] * c.n[2];
+    v[0] = w;
+    v[1] = w * x[0] * c.n[0];
+    for (int a = 0; a < 3; ++a) v[2 + a] = 0.25 * w * x[a] * xn;
+    int q = 5;
+    for (int a = 0; a < 3; ++a)
+      for (int b = a; b < 3; ++b) v[q++] = 0.2 * w * x[a] * x[b] * xn;
+  }
+  for (int q = 0; q < N_MOM; ++q) sm[q][threadIdx.x] = v[q];
+  __syncthreads();
+  for (int o = 64; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o)
+      for (int q = 0; q < N_MOM; ++q) sm[q][threadIdx.x] += sm[q][threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int q = 0; q < N_MOM; ++q) part[(int64_t)blockIdx.x * N_MOM + q] = sm[q][0];
+}
+
+__global__ void k_sum_moments(const double* __restrict__ part, int nb, double* __restrict__ out) {
+  const int q = threadIdx.x;
+  if (q >= N_MOM || blockIdx.x != 0) return;
+  double s = 0.0;
+  for (int b = 0; b < nb; ++b) s += part[(int64_t)b * N_MOM + q];
+  out[q] = s;
+}
+
 __global__ void k_sum_pairs(const double* __restrict__ part, int n, double* __restrict__ out) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double a = 0.0, v = 0.0;
@@ -658,7 +719,7 @@ int build_op(int m, MembraneOp** out, std::string& err) {
   ok(cudaMalloc(&op->gu, fn));
   ok(cudaMalloc(&op->gv, fn));
   ok(cudaMalloc(&op->cur_t, 6 * op->N * sizeof(double)));
-  ok(cudaMalloc(&op->red, (2 * (size_t)blocks_of(op->N) + 2) * sizeof(double)));
+  ok(cudaMalloc(&op->red, (13 * (((size_t)op->N + 127) / 128) + 16) * sizeof(double)));
   if (e != cudaSuccess) {
     err = std::string("membrane operator: ") + cudaGetErrorString(e);
     free_op(op);
@@ -776,6 +837,16 @@ void enqueue_area_volume(const MembraneOp& op, const double* X, double* out2, cu
 }
 
 int64_t membrane_nodes(const MembraneOp& op) { return op.N; }
+
+// Origin o (node mean, 3) followed by A, V, int_V x (3), int_V x_a x_b
+// (a <= b, 6), x relative to o, of the nodes X into out16.
+void enqueue_moments(const MembraneOp& op, const double* X, double* out16, cudaStream_t st) {
+  enqueue_tangents(op, X, op.cur_t, nullptr, st);
+  const unsigned nb = (unsigned)((op.N + 127) / 128);
+  k_node_mean<<<1, 256, 0, st>>>(X, op.N, out16);
+  k_moments<<<nb, 128, 0, st>>>(op, X, op.cur_t, out16, op.red);
+  k_sum_moments<<<1, 32, 0, st>>>(op.red, (int)nb, out16 + 3);
+}
 
 int membrane_upsampling(sk_ctx* ctx, MembraneOp* op) { return ensure_upsampling(op, ctx->err); }
 

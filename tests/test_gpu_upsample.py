@@ -108,3 +108,37 @@ def test_capsule_upsampled_euler_and_rkf45_match_oracle(ctx):
     y, dto, acco, rejo = ts.integrate(rhs, X0.ravel(), 3e-3, 1.5e-3, 1e-6)
     assert (acc, rej) == (acco, rejo)
     assert rel(Xr - X0, y.reshape(-1, 3) - X0) < 1e-9
+
+
+def test_shape_moments_of_an_ellipsoid(ctx):
+    """A, V and the inertia tensor of the ellipsoid (a, b, c) against closed
+    forms: V = 4 pi abc / 3, J = V/5 diag(b^2 + c^2, a^2 + c^2, a^2 + b^2)."""
+    a, b, c = 0.9, 1.0, 0.8
+    m = 33
+    s = ci.make_surface(ci.Ellipsoid(a, b, c), m)
+    shift = np.array([12.0, -0.2, 0.1])   # far from the origin, like a capsule carried downstream
+    cap = sk.Capsule(ctx, m, s.X + shift, s.w, delta=None, mu=1.0, precision=sk.SK_FP64)
+    try:
+        A, V, cen, J = cap.shape_moments()
+    finally:
+        cap.close()
+    V_ex = 4 * np.pi * a * b * c / 3
+    J_ex = V_ex / 5 * np.diag([b * b + c * c, a * a + c * c, a * a + b * b])
+    assert abs(V - V_ex) / V_ex < 1e-5
+    assert np.allclose(cen, shift, atol=1e-6)
+    assert np.linalg.norm(J - J_ex) / np.linalg.norm(J_ex) < 1e-5
+    Ao, Vo = mb.area_volume(m, s.X)
+    assert abs(A - Ao) / Ao < 1e-12
+
+
+def test_capsule_self_convergence_in_shear(ctx):
+    """Shortened Table convg_shear: errors against a finer run fall with m."""
+    import bench
+    flow = (sk.SK_FLOW_SHEAR, 1.0, 0.0, 0.0)
+    Ar, Vr, _, Jr, *_ = bench.capsule_run(sk, ctx, 24, flow, 0.05, sk.SK_FP64)
+    errs = {}
+    for m in (8, 12):
+        A, V, _, J, *_ = bench.capsule_run(sk, ctx, m, flow, 0.05, sk.SK_FP64)
+        errs[m] = (abs(A - Ar) / Ar, abs(V - Vr) / Vr, np.linalg.norm(J - Jr) / np.linalg.norm(Jr))
+    assert all(e12 < e8 for e8, e12 in zip(errs[8], errs[12])), errs
+    assert max(errs[12]) < 2e-3, errs
