@@ -42,6 +42,10 @@ constexpr int SERVE_TGT_CTA = TPB32 * 2 * SERVE_NP;  // targets per block (512)
 constexpr int SERVE_RESERVE_CTAS = 24;  // CTA slots left free for the preparation kernels
 constexpr int MAX_SLOTS = 256;
 constexpr int SERVE_PREP_STREAMS = 4;
+#ifndef SK_SERVE_AGE
+#define SK_SERVE_AGE 16
+#endif
+constexpr int SERVE_AGE_LIMIT = SK_SERVE_AGE;  // admissions that may overtake a request
 
 // Device descriptor of one resident request.
 struct SlotDesc {
@@ -100,24 +104,40 @@ __global__ void __launch_bounds__(TPB32, SERVE_MINB)
   unsigned long long idle_since = gtimer();
   while (true) {
     if (wid == 0) {
-      // pick the resident request with free items that was admitted first
-      unsigned best_seq = 0xffffffffu;
+      // pick the resident request with the fewest unclaimed items (shortest
+      // remaining work first; the admission order breaks ties), so small
+      // requests do not wait behind large ones admitted just before them;
+      // a request that SERVE_AGE_LIMIT later admissions have passed is
+      // overdue and goes first (oldest first), which bounds how long a large
+      // request can be overtaken
+      unsigned newest = 0;
+      for (int s = lane; s < n_slots; s += 32) {
+        const unsigned long long w = *(volatile const unsigned long long*)&claim[s].word;
+        if ((unsigned)w < (unsigned)(w >> 32))
+          newest = max(newest, *(volatile const unsigned*)&desc[s].seq);
+      }
+      for (int o = 16; o > 0; o >>= 1) newest = max(newest, __shfl_xor_sync(0xffffffffu, newest, o));
+      unsigned long long best_key = ~0ull;
       int best = -1;
       for (int s = lane; s < n_slots; s += 32) {
         const unsigned long long w = *(volatile const unsigned long long*)&claim[s].word;
-        if ((unsigned)w < (unsigned)(w >> 32)) {
+        const unsigned n_items = (unsigned)(w >> 32), next = (unsigned)w;
+        if (next < n_items) {
           const unsigned q = *(volatile const unsigned*)&desc[s].seq;
-          if (q < best_seq || best < 0) {
-            best_seq = q;
+          const bool overdue = newest - q >= (unsigned)SERVE_AGE_LIMIT;
+          const unsigned long long key =
+              ((unsigned long long)(overdue ? 0u : n_items - next) << 32) | q;
+          if (key < best_key || best < 0) {
+            best_key = key;
             best = s;
           }
         }
       }
       for (int o = 16; o > 0; o >>= 1) {
-        const unsigned q = __shfl_xor_sync(0xffffffffu, best_seq, o);
+        const unsigned long long q = __shfl_xor_sync(0xffffffffu, best_key, o);
         const int b = __shfl_xor_sync(0xffffffffu, best, o);
-        if (b >= 0 && (best < 0 || q < best_seq || (q == best_seq && b < best))) {
-          best_seq = q;
+        if (b >= 0 && (best < 0 || q < best_key || (q == best_key && b < best))) {
+          best_key = q;
           best = b;
         }
       }
