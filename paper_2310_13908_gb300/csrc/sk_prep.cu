@@ -112,37 +112,37 @@ __global__ void k_rs_hist(const uint32_t* __restrict__ keys, int n, int shift,
   hist[threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];
 }
 
-// Exclusive scan of `total` counts, one block of 1024 threads.
+// Exclusive scan of `total` counts, one block of 1024 threads: each thread
+// sums its own contiguous run, one block scan of the run totals gives every
+// run its offset, and the thread rewrites its run (exact integer sums).
 __global__ void k_rs_scan(uint32_t* __restrict__ a, int total) {
   __shared__ uint32_t warp_sums[32];
-  __shared__ uint32_t carry;
-  if (threadIdx.x == 0) carry = 0;
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  const int K = (total + 1023) / 1024;
+  const int b = min(t * K, total), e = min(b + K, total);
+  uint32_t v = 0;
+  for (int i = b; i < e; ++i) v += a[i];
+  uint32_t x = v;  // inclusive warp scan of the run totals
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(FULL, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_sums[wid] = x;
   __syncthreads();
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int base = 0; base < total; base += 1024) {
-    int i = base + threadIdx.x;
-    uint32_t v = i < total ? a[i] : 0u;
-    uint32_t x = v;
+  if (wid == 0) {
+    uint32_t s = warp_sums[lane];
     for (int o = 1; o < 32; o <<= 1) {
-      uint32_t y = __shfl_up_sync(FULL, x, o);
-      if (lane >= o) x += y;
+      const uint32_t y = __shfl_up_sync(FULL, s, o);
+      if (lane >= o) s += y;
     }
-    if (lane == 31) warp_sums[wid] = x;
-    __syncthreads();
-    if (wid == 0) {
-      uint32_t s = warp_sums[lane];
-      for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(FULL, s, o);
-        if (lane >= o) s += y;
-      }
-      warp_sums[lane] = s;  // inclusive
-    }
-    __syncthreads();
-    uint32_t excl = carry + (wid > 0 ? warp_sums[wid - 1] : 0u) + x - v;
-    if (i < total) a[i] = excl;
-    __syncthreads();
-    if (threadIdx.x == 1023) carry = excl + v;
-    __syncthreads();
+    warp_sums[lane] = s;  // inclusive over warps
+  }
+  __syncthreads();
+  uint32_t run = (wid > 0 ? warp_sums[wid - 1] : 0u) + x - v;  // exclusive offset of this run
+  for (int i = b; i < e; ++i) {
+    const uint32_t c = a[i];
+    a[i] = run;
+    run += c;
   }
 }
 
