@@ -163,7 +163,7 @@ int enqueue_prep(const EvalShape& s, const EvalBufs& b, double rho_T, double rho
   launches += 1;
   if (s.N > 0) {
     launch_sort_points(b.src_xyz, b.src_w, s.N, b.keys_a, b.keys_b, b.vals_a, b.vals_b, b.hist,
-                       b.bbox_part, b.bbox, b.meta + META_NS, b.sort_blocks, st);
+                       b.bbox_part, b.bbox, b.meta + META_NS, b.sort_blocks, s.narrow_prep, st);
     if (fp32)
       launch_pack_sources32(s.layer, b, scale, st);
     else
@@ -171,7 +171,7 @@ int enqueue_prep(const EvalShape& s, const EvalBufs& b, double rho_T, double rho
     launches += SORT_LAUNCHES + 1;
   }
   launch_sort_points(b.tgt_xyz, nullptr, s.M, b.keys_a, b.keys_b, b.vals_a, b.vals_b, b.hist,
-                     b.bbox_part, b.bbox, b.meta + META_SCRATCH, b.sort_blocks, st);
+                     b.bbox_part, b.bbox, b.meta + META_SCRATCH, b.sort_blocks, s.narrow_prep, st);
   launches += SORT_LAUNCHES;
   if (fp32)
     launch_pack_targets32(b, s.n_delta, rho_T, rho_c, st);

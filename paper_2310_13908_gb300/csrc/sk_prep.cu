@@ -115,10 +115,12 @@ __global__ void k_rs_hist(const uint32_t* __restrict__ keys, int n, int shift,
 // Exclusive scan of `total` counts, one block of 1024 threads: each thread
 // sums its own contiguous run, one block scan of the run totals gives every
 // run its offset, and the thread rewrites its run (exact integer sums).
-__global__ void k_rs_scan(uint32_t* __restrict__ a, int total) {
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS) k_rs_scan(uint32_t* __restrict__ a, int total) {
+  static_assert(THREADS % 32 == 0 && THREADS <= 1024, "one block of whole warps");
   __shared__ uint32_t warp_sums[32];
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-  const int K = (total + 1023) / 1024;
+  const int K = (total + THREADS - 1) / THREADS;
   const int b = min(t * K, total), e = min(b + K, total);
   uint32_t v = 0;
   for (int i = b; i < e; ++i) v += a[i];
@@ -130,7 +132,7 @@ __global__ void k_rs_scan(uint32_t* __restrict__ a, int total) {
   if (lane == 31) warp_sums[wid] = x;
   __syncthreads();
   if (wid == 0) {
-    uint32_t s = warp_sums[lane];
+    uint32_t s = lane < THREADS / 32 ? warp_sums[lane] : 0u;
     for (int o = 1; o < 32; o <<= 1) {
       const uint32_t y = __shfl_up_sync(FULL, s, o);
       if (lane >= o) s += y;
@@ -331,7 +333,7 @@ int sort_grid_blocks(int64_t n) { return (int)((n + RS_TILE - 1) / RS_TILE); }
 void launch_sort_points(const double* xyz, const double* w, int64_t n, uint32_t* keys_a,
                         uint32_t* keys_b, int* vals_a, int* vals_b, uint32_t* hist,
                         float* bbox_part, float* bbox, int* count_out, int sort_blocks,
-                        cudaStream_t st) {
+                        bool narrow, cudaStream_t st) {
   if (n <= 0) return;
   k_bbox_partial<<<BBOX_BLOCKS, RS_THREADS, 0, st>>>(xyz, w, n, bbox_part);
   k_bbox_final<<<1, 32, 0, st>>>(bbox_part, BBOX_BLOCKS, bbox);
@@ -340,7 +342,10 @@ void launch_sort_points(const double* xyz, const double* w, int64_t n, uint32_t*
   int *va = vals_a, *vb = vals_b;
   for (int shift = 0; shift < 32; shift += 8) {
     k_rs_hist<<<sort_blocks, RS_THREADS, 0, st>>>(ka, (int)n, shift, hist);
-    k_rs_scan<<<1, 1024, 0, st>>>(hist, 256 * sort_blocks);
+    if (narrow)
+      k_rs_scan<RS_THREADS><<<1, RS_THREADS, 0, st>>>(hist, 256 * sort_blocks);
+    else
+      k_rs_scan<1024><<<1, 1024, 0, st>>>(hist, 256 * sort_blocks);
     k_rs_scatter<<<sort_blocks, RS_THREADS, 0, st>>>(ka, va, kb, vb, (int)n, shift, hist);
     uint32_t* tk = ka; ka = kb; kb = tk;
     int* tv = va; va = vb; vb = tv;

@@ -11,6 +11,11 @@
 // a claim is valid iff item < n_items, so a request's descriptor is never
 // rewritten while a CTA holds one of its items. All waits are bounded: the
 // kernel exits after idle_exit_us without work and is relaunched on demand.
+// The exit is collective: a CTA leaves on idleness only while no CTA holds
+// an item, and it then raises a flag on which every other CTA leaves after
+// its current item. (CTAs that left one by one could leave a few of them
+// alive, busy with later arrivals, and the host relaunches only a kernel
+// that has ended.)
 //
 // Host side: a scheduler thread admits queued requests when a slot and
 // enough arena memory are free, prepares them (H2D copy from the pinned
@@ -42,6 +47,8 @@ constexpr int SERVE_TGT_CTA = TPB32 * 2 * SERVE_NP;  // targets per block (512)
 constexpr int SERVE_RESERVE_CTAS = 24;  // CTA slots left free for the preparation kernels
 constexpr int MAX_SLOTS = 256;
 constexpr int SERVE_PREP_STREAMS = 4;
+// device control words: host stop request, CTAs holding an item, exit raised
+constexpr int CTL_STOP = 0, CTL_BUSY = 1, CTL_EXIT = 2, CTL_WORDS = 4;
 #ifndef SK_SERVE_AGE
 #define SK_SERVE_AGE 16
 #endif
@@ -93,7 +100,7 @@ __device__ __noinline__ void finish_block(const SlotDesc& d, int tb) {
 
 __global__ void __launch_bounds__(TPB32, SERVE_MINB)
     k_serve(const SlotDesc* __restrict__ desc, SlotClaim* __restrict__ claim, int n_slots,
-            const int* __restrict__ stop, unsigned* __restrict__ done_host,
+            int* __restrict__ ctl, unsigned* __restrict__ done_host,
             unsigned long long idle_ns) {
   extern __shared__ __align__(128) float4 sm[];
   __shared__ PipeSmem<pair_stages<SLayer, SERVE_NP>()> ps;
@@ -144,13 +151,20 @@ __global__ void __launch_bounds__(TPB32, SERVE_MINB)
       if (lane == 0) {
         s_slot = -1;
         s_exit = 0;
-        if (best >= 0) {
+        volatile int* vctl = ctl;
+        if (vctl[CTL_EXIT]) {
+          s_exit = 1;  // another CTA has decided to leave: unclaimed items wait for the relaunch
+        } else if (best >= 0) {
           const unsigned long long old = atomicAdd(&claim[best].word, 1ull);
           if ((unsigned)old < (unsigned)(old >> 32)) {
+            atomicAdd(&ctl[CTL_BUSY], 1);
             s_slot = best;
             s_item = (int)(unsigned)old;
           }
-        } else if (*(volatile const int*)stop || gtimer() - idle_since > idle_ns) {
+        } else if (vctl[CTL_STOP]) {
+          s_exit = 1;
+        } else if (gtimer() - idle_since > idle_ns && vctl[CTL_BUSY] == 0) {
+          atomicExch(&ctl[CTL_EXIT], 1);
           s_exit = 1;
         }
       }
@@ -180,18 +194,20 @@ __global__ void __launch_bounds__(TPB32, SERVE_MINB)
       s_finish = atomicAdd(&d.tb_done[tb], 1) == d.n_chunks - 1;
     }
     __syncthreads();
-    if (!s_finish) continue;
-    // last chunk of this target block: finish the block's targets
-    __threadfence();
-    finish_block(d, tb);
-    __syncthreads();
-    if (tid == 0) {
+    if (s_finish) {
+      // last chunk of this target block: finish the block's targets
       __threadfence();
-      if (atomicAdd(d.tb_finished, 1) == d.n_tb - 1) {
-        __threadfence_system();
-        *(volatile unsigned*)&done_host[slot] = d.seq;
+      finish_block(d, tb);
+      __syncthreads();
+      if (tid == 0) {
+        __threadfence();
+        if (atomicAdd(d.tb_finished, 1) == d.n_tb - 1) {
+          __threadfence_system();
+          *(volatile unsigned*)&done_host[slot] = d.seq;
+        }
       }
     }
+    if (tid == 0) atomicSub(&ctl[CTL_BUSY], 1);
   }
 }
 
@@ -290,7 +306,7 @@ struct sk_server {
   cudaStream_t s_prep[sk::SERVE_PREP_STREAMS] = {};
   sk::SlotDesc* d_desc = nullptr;
   sk::SlotClaim* d_claim = nullptr;
-  int* d_stop = nullptr;
+  int* d_ctl = nullptr;  // CTL_WORDS device control words
   unsigned* h_done = nullptr;  // mapped pinned page
   unsigned* d_done = nullptr;
   unsigned long long* h_flagbuf = nullptr;  // pinned, N_FLAGS per slot
@@ -340,8 +356,11 @@ void launch_kernel(sk_server* srv) {
   cudaFuncSetAttribute(k_serve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int grid = srv->ctx->sm_count * SERVE_MINB - SERVE_RESERVE_CTAS;
   if (grid < 1) grid = 1;
+  // the previous instance has ended (stream order): clear its busy count and
+  // exit flag, but not the host's stop word
+  cudaMemsetAsync(srv->d_ctl + CTL_BUSY, 0, (CTL_WORDS - CTL_BUSY) * sizeof(int), srv->s_kernel);
   k_serve<<<grid, TPB32, smem, srv->s_kernel>>>(
-      srv->d_desc, srv->d_claim, srv->n_slots, srv->d_stop, srv->d_done,
+      srv->d_desc, srv->d_claim, srv->n_slots, srv->d_ctl, srv->d_done,
       (unsigned long long)srv->cfg.idle_exit_us * 1000ull);
   cudaEventRecord(srv->kernel_done, srv->s_kernel);
   srv->kernel_launched = true;
@@ -501,7 +520,7 @@ void scheduler(sk_server* srv) {
 void free_server(sk_server* srv) {
   if (srv->d_desc) cudaFree(srv->d_desc);
   if (srv->d_claim) cudaFree(srv->d_claim);
-  if (srv->d_stop) cudaFree(srv->d_stop);
+  if (srv->d_ctl) cudaFree(srv->d_ctl);
   if (srv->h_done) cudaFreeHost(srv->h_done);
   if (srv->h_flagbuf) cudaFreeHost(srv->h_flagbuf);
   if (srv->h_stop_one) cudaFreeHost(srv->h_stop_one);
@@ -569,7 +588,7 @@ int serve_create(sk_ctx* ctx, const sk_serve_cfg* cfg_in, sk_server** out) {
   ok(cudaStreamCreateWithFlags(&srv->s_copy, cudaStreamNonBlocking));
   ok(cudaMalloc(&srv->d_desc, MAX_SLOTS * sizeof(SlotDesc)));
   ok(cudaMalloc(&srv->d_claim, MAX_SLOTS * sizeof(SlotClaim)));
-  ok(cudaMalloc(&srv->d_stop, sizeof(int)));
+  ok(cudaMalloc(&srv->d_ctl, CTL_WORDS * sizeof(int)));
   ok(cudaHostAlloc(&srv->h_done, MAX_SLOTS * sizeof(unsigned), cudaHostAllocMapped));
   ok(cudaHostAlloc(&srv->h_flagbuf, (size_t)srv->n_slots * PIN_WORDS * sizeof(unsigned long long),
                    cudaHostAllocDefault));
@@ -585,7 +604,7 @@ int serve_create(sk_ctx* ctx, const sk_serve_cfg* cfg_in, sk_server** out) {
     ok(cudaHostGetDevicePointer((void**)&srv->d_done, srv->h_done, 0));
     ok(cudaMemset(srv->d_desc, 0, MAX_SLOTS * sizeof(SlotDesc)));
     ok(cudaMemset(srv->d_claim, 0, MAX_SLOTS * sizeof(SlotClaim)));
-    ok(cudaMemset(srv->d_stop, 0, sizeof(int)));
+    ok(cudaMemset(srv->d_ctl, 0, CTL_WORDS * sizeof(int)));
   }
   if (e != cudaSuccess) {
     ctx->err = std::string("serve_create: ") + cudaGetErrorString(e);
@@ -627,6 +646,7 @@ int serve_submit(sk_server* srv, const sk_request* q, uint64_t* ticket) {
   s.n_delta = q->n_delta;
   s.mu = q->mu;
   s.copy_inputs = true;
+  s.narrow_prep = true;
   s.n_chunks = choose_chunks(SK_FP32C, N, M, srv->ctx->sm_count);
   const int n_tb = (int)(align_up((size_t)M, TGT_CTA32) / SERVE_TGT_CTA);
   r->footprint = request_footprint(s, n_tb);
@@ -710,7 +730,8 @@ void serve_destroy(sk_server* srv) {
   srv->shutting_down = true;
   if (srv->thr.joinable()) srv->thr.join();
   cudaSetDevice(srv->ctx->device);
-  cudaMemcpyAsync(srv->d_stop, srv->h_stop_one, sizeof(int), cudaMemcpyHostToDevice, srv->s_ctl);
+  cudaMemcpyAsync(srv->d_ctl + CTL_STOP, srv->h_stop_one, sizeof(int), cudaMemcpyHostToDevice,
+                  srv->s_ctl);
   cudaStreamSynchronize(srv->s_ctl);
   cudaStreamSynchronize(srv->s_kernel);
   cudaDeviceSynchronize();
