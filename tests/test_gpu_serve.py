@@ -146,6 +146,28 @@ def test_poll_modes_invalid_requests_and_relaunch(ctx):
         sk.serve_destroy(srv)
 
 
+def test_exits_and_relaunches_racing_with_arrivals(ctx):
+    """A 300 us idle limit with arrival gaps of 0-2 ms: the persistent kernel
+    leaves and is relaunched many times, often while requests are being
+    published. Its CTAs leave together (an exit word), so no request is lost
+    or left to a partial kernel, and every result is the standalone one."""
+    reqs = mixed_requests(24, m_choices=(9, 17, 33, 49), seed=59)
+    refs = [sk.stokes_sl_eval(ctx, sk.SK_FP32C, sk.SK_HOST, *r) for r in reqs]
+    rng = np.random.default_rng(59)
+    srv = sk.serve_create(ctx, max_slots=4, idle_exit_us=300)
+    try:
+        tickets = []
+        for r in reqs:
+            tickets.append(submit_retry(srv, *r))
+            time.sleep(float(rng.uniform(0.0, 0.002)))
+        for t, r, ref in zip(tickets, reqs, refs):
+            code, u, _ = sk.serve_poll(srv, t, r[3].shape[0], timeout_us=30_000_000)
+            assert code == sk.SK_OK
+            assert np.array_equal(u, ref)
+    finally:
+        sk.serve_destroy(srv)
+
+
 def test_destroy_drains_pending_requests(ctx):
     reqs = mixed_requests(8, seed=53)
     srv = sk.serve_create(ctx, max_slots=2)
