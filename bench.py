@@ -46,6 +46,8 @@ SM_MAX_MHZ = 2070.0
 FP32_PEAK_TFLOPS = 2 * 128 * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12  # 80.55
 FP64_PEAK_TFLOPS = 1.25  # nominal dense FP64 of GB300
 CPU_SAMPLE_TARGETS = 4096
+SERVE_ORACLE_REQUESTS = 50   # served results checked against the oracle ...
+SERVE_ORACLE_TARGETS = 256   # ... on this many seeded targets each
 REF_STEP_TARGETS = 512
 
 
@@ -384,9 +386,10 @@ def build_serving_mix(n=SERVE_REQUESTS):
     return out
 
 
-def run_serving(sk, h, reqs, arrivals=None):
+def run_serving(sk, h, reqs, arrivals=None, keep=()):
     """Serve reqs (all at once if arrivals is None, else at those times in s).
-    Returns (wall seconds, latencies in ms, interactions)."""
+    Returns (wall seconds, latencies in ms, interactions); the results of the
+    requests whose indices are in keep go to run_serving.kept."""
     import collections
     srv = sk.serve_create(h, max_slots=32)
     n = len(reqs)
@@ -394,6 +397,8 @@ def run_serving(sk, h, reqs, arrivals=None):
     phases = []
     inter = 0
     outstanding = collections.OrderedDict()
+    kept = {}
+    keep = set(keep)
     nxt = 0
     t0 = time.perf_counter()
     while nxt < n or outstanding:
@@ -412,11 +417,13 @@ def run_serving(sk, h, reqs, arrivals=None):
         progressed = False
         for tk in list(outstanding):
             i, late_ms = outstanding[tk]
-            code, _, st = sk.serve_poll(srv, tk, reqs[i][3].shape[0], timeout_us=0)
+            code, u, st = sk.serve_poll(srv, tk, reqs[i][3].shape[0], timeout_us=0)
             if code == sk.SK_EAGAIN:
                 continue
             if code != sk.SK_OK:
                 raise RuntimeError(f"served request failed: {code}")
+            if i in keep:
+                kept[i] = u
             lat[i] = late_ms + (st["ready_us"] - st["submit_us"]) * 1e-3
             phases.append((st["admit_us"] - st["submit_us"], st["publish_us"] - st["admit_us"],
                            st["done_us"] - st["publish_us"], st["ready_us"] - st["done_us"]))
@@ -430,20 +437,50 @@ def run_serving(sk, h, reqs, arrivals=None):
     ph = np.mean(np.array(phases), axis=0) * 1e-3
     run_serving.last_phases_ms = {"queue": ph[0], "prepare": ph[1], "device": ph[2],
                                   "copy_back": ph[3]}
+    run_serving.kept = kept
     return wall, lat, inter
+
+
+def serving_oracle_check(reqs, check, kept, per_request=SERVE_ORACLE_TARGETS):
+    """The served results of a seeded subsample of requests against the oracle
+    on seeded targets of each: relative L2 per request and over all, and the
+    oracle's own throughput on that sample (the CPU baseline of the mix)."""
+    import oracle
+    rng = np.random.default_rng(8)
+    errs, num, den, pairs, secs = [], 0.0, 0.0, 0, 0.0
+    for i in check:
+        X, W, F, Y, D, n_active = reqs[i]
+        tsel = rng.choice(Y.shape[0], min(per_request, Y.shape[0]), replace=False)
+        t0 = time.perf_counter()
+        ref = oracle.sl(X, W, F, Y[tsel], D, 1.0)
+        secs += time.perf_counter() - t0
+        pairs += len(tsel) * n_active
+        d = kept[int(i)][tsel] - ref
+        errs.append(float(np.linalg.norm(d) / np.linalg.norm(ref)))
+        num += float(np.sum(d * d))
+        den += float(np.sum(ref * ref))
+    return {"requests": len(check), "targets_per_request": per_request,
+            "rel_l2_vs_oracle": float(np.sqrt(num / den)), "max_request_rel_l2": max(errs),
+            "cpu_oracle": {"value": pairs / secs / 1e9, "unit": UNIT,
+                           "cores": oracle.max_threads(), "seconds": secs,
+                           "sample": f"{len(check)} seeded requests x {per_request} seeded "
+                                     "targets x all active sources, FP64, OpenMP"}}
 
 
 def serving_bench(sk, h, reqs):
     n = len(reqs)
     run_serving(sk, h, reqs[:64])  # warm-up
-    wall, lat, inter = run_serving(sk, h, reqs)
+    check = np.random.default_rng(7).choice(n, SERVE_ORACLE_REQUESTS, replace=False)
+    wall, lat, inter = run_serving(sk, h, reqs, keep=check)
     cap = n / wall
+    oracle_check = serving_oracle_check(reqs, check, run_serving.kept)
     res = {"requests": n, "mix": "ellipsoid (axes U[0.5,1]) or rotated Evans-Fung cell, "
                                  "N = 6n^2 log-uniform in [1536, 98304], SH density, delta=2h",
            "saturated": {"req_per_s": cap, "ginter_per_s": inter / wall / 1e9,
                          "wall_s": wall, "p50_ms": float(np.percentile(lat, 50)),
                          "p99_ms": float(np.percentile(lat, 99)),
-                         "mean_phase_ms": run_serving.last_phases_ms}}
+                         "mean_phase_ms": run_serving.last_phases_ms},
+           "oracle_check": oracle_check}
     for frac in SERVE_LOADS:
         rng = np.random.default_rng(int(frac * 1000))
         arr = np.cumsum(rng.exponential(1.0 / (frac * cap), size=n))
@@ -691,31 +728,88 @@ def extras(sk, h, w, X, W, F, Y, D, out, u_fp32, stream, dev, torch, serve_futur
     def td(a):
         return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)
 
-    RX, RW, RN, RQ, RY, RD = (td(a) for a in (rs.X, rs.w, rs.n, rw.q, rw.targets, rw.delta))
+    RX, RW, RN, RQ, RF, RY, RD = (td(a) for a in (rs.X, rs.w, rs.n, rw.q, rw.f, rw.targets,
+                                                  rw.delta))
     rout = torch.empty((rw.targets.shape[0], 3), dtype=torch.float64, device=dev)
     ridx = np.random.default_rng(5).choice(rs.N, 2048, replace=False)
-    dref = oracle.dl(rs.X, rs.w, rs.n, rw.q, rw.targets[ridx], rw.delta)
     rinter = rw.targets.shape[0] * rs.n_active
-    dl = {}
-    for prec, name in ((sk.SK_FP32C, "fp32c"), (sk.SK_FP64, "fp64")):
-        for _ in range(2):
-            sk.stokes_dl_eval(h, prec, sk.SK_DEVICE, RX, RW, RN, RQ, RY, RD, u_out=rout,
+    t0 = time.perf_counter()
+    dref = oracle.dl(rs.X, rs.w, rs.n, rw.q, rw.targets[ridx], rw.delta)
+    t_dl = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    sref = oracle.sl(rs.X, rs.w, rw.f, rw.targets[ridx], rw.delta, rw.mu)
+    t_sl = time.perf_counter() - t0
+
+    def timed_c2(layer_eval, ref):
+        r = {}
+        for prec, name in ((sk.SK_FP32C, "fp32c"), (sk.SK_FP64, "fp64")):
+            for _ in range(2):
+                layer_eval(prec)
+            torch.cuda.synchronize(dev)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            reps = 5
+            for _ in range(reps):
+                layer_eval(prec)
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            ms = a.elapsed_time(b) / reps
+            r[name] = {"value": rinter / (ms * 1e-3) / 1e9, "ms": ms,
+                       "rel_l2_vs_oracle": rel_l2(rout.cpu().numpy()[ridx], ref)}
+        return r
+
+    dl = timed_c2(lambda prec: sk.stokes_dl_eval(h, prec, sk.SK_DEVICE, RX, RW, RN, RQ, RY, RD,
+                                                 u_out=rout, stream=stream), dref)
+    sl = timed_c2(lambda prec: sk.stokes_sl_eval(h, prec, sk.SK_DEVICE, RX, RW, RF, RY, RD,
+                                                 rw.mu, u_out=rout, stream=stream), sref)
+    sample = f"{len(ridx)} seeded node targets x all {rs.n_active} active sources, FP64, OpenMP"
+    res["dl_rbc_m65"] = {"workload": f"rotated Evans-Fung cell m=65 N={rs.N} "
+                                     f"(N_s={rs.n_active}), double layer, delta=2h",
+                         "interactions": rinter, "flops_per_interaction": FLOPS_DL, **dl,
+                         "cpu_oracle": {"value": len(ridx) * rs.n_active / t_dl / 1e9,
+                                        "unit": UNIT, "cores": oracle.max_threads(),
+                                        "sample": sample, "seconds": t_dl}}
+    res["sl_rbc_m65"] = {"workload": f"rotated Evans-Fung cell m=65 N={rs.N} "
+                                     f"(N_s={rs.n_active}), single layer, delta=2h",
+                         "interactions": rinter, "flops_per_interaction": FLOPS_SL, **sl,
+                         "cpu_oracle": {"value": len(ridx) * rs.n_active / t_sl / 1e9,
+                                        "unit": UNIT, "cores": oracle.max_threads(),
+                                        "sample": sample, "seconds": t_sl}}
+    # C1: unit sphere m = 19 with a noisy density, FP64 (and FP32C), all targets vs the oracle
+    cw = ci.sphere_noise_workload()
+    cs = cw.surface
+    CX, CW, CF, CY, CD = (td(a) for a in (cs.X, cs.w, cw.f, cw.targets, cw.delta))
+    cout = torch.empty((cw.targets.shape[0], 3), dtype=torch.float64, device=dev)
+    t0 = time.perf_counter()
+    cref = oracle.sl(cs.X, cs.w, cw.f, cw.targets, cw.delta, cw.mu)
+    t_c1 = time.perf_counter() - t0
+    cinter = cw.targets.shape[0] * cs.n_active
+    c1 = {}
+    for prec, name in ((sk.SK_FP64, "fp64"), (sk.SK_FP32C, "fp32c")):
+        for _ in range(3):
+            sk.stokes_sl_eval(h, prec, sk.SK_DEVICE, CX, CW, CF, CY, CD, cw.mu, u_out=cout,
                               stream=stream)
         torch.cuda.synchronize(dev)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        reps = 5
+        reps = 20
         for _ in range(reps):
-            sk.stokes_dl_eval(h, prec, sk.SK_DEVICE, RX, RW, RN, RQ, RY, RD, u_out=rout,
+            sk.stokes_sl_eval(h, prec, sk.SK_DEVICE, CX, CW, CF, CY, CD, cw.mu, u_out=cout,
                               stream=stream)
         b.record(stream)
         torch.cuda.synchronize(dev)
         ms = a.elapsed_time(b) / reps
-        dl[name] = {"value": rinter / (ms * 1e-3) / 1e9, "ms": ms,
-                    "rel_l2_vs_oracle": rel_l2(rout.cpu().numpy()[ridx], dref)}
-    res["dl_rbc_m65"] = {"workload": f"rotated Evans-Fung cell m=65 N={rs.N} "
-                                     f"(N_s={rs.n_active}), double layer, delta=2h",
-                         "interactions": rinter, "flops_per_interaction": FLOPS_DL, **dl}
+        c1[name] = {"value": cinter / (ms * 1e-3) / 1e9, "ms": ms,
+                    "rel_l2_vs_oracle": rel_l2(cout.cpu().numpy(), cref)}
+    res["sl_sphere_m19"] = {"workload": f"unit sphere m=19 N={cs.N} (N_s={cs.n_active}), "
+                                        "f = (1,0,0) + N(0, 0.1^2), single layer, delta=2h, "
+                                        "targets = nodes (launch-bound at this size)",
+                            "interactions": cinter, **c1,
+                            "cpu_oracle": {"value": cinter / t_c1 / 1e9, "unit": UNIT,
+                                           "cores": oracle.max_threads(),
+                                           "sample": "all targets, FP64, OpenMP",
+                                           "seconds": t_c1}}
+
     # double layer at a size that fills the GPU: ellipsoid m=193 (221,184 nodes)
     try:
         ew = ci.ellipsoid_hires_workload(m=193, n_probes=0, seed=3300)

@@ -59,6 +59,7 @@ void carve_eval_buffers(Bump& bp, const EvalShape& s, EvalBufs& b) {
   b.M_pad = (int64_t)align_up((size_t)s.M, fp32 ? TGT_CTA32 : TGT_CTA64);
   b.n_chunks = s.n_chunks;
   b.pair_np = pair32_np(s.M);
+  b.threads64 = s.threads64;
   const int64_t nsort = s.N > s.M ? s.N : s.M;
   b.sort_blocks = sort_grid_blocks(nsort > 0 ? nsort : 1);
   if (s.copy_inputs) {
@@ -136,6 +137,24 @@ int choose_chunks(int precision, int64_t N, int64_t M, int sm_count) {
     }
   }
   return best;
+}
+
+// The FP64 pipe issues a warp instruction per scheduler only every few dozen
+// cycles, so about one warp per scheduler keeps it busy: for small problems
+// the limit is how many SMs get work at all. When TPB64-thread CTAs cannot
+// fill four waves even at the largest chunk count, the FP64 kernel runs
+// TPB64_SMALL-thread CTAs (4x more target blocks) with one source tile per
+// chunk. (Measured at 1944 x 1344: 32 CTAs left 120 SMs idle.)
+void choose_decomposition(EvalShape& s, int sm_count) {
+  s.n_chunks = choose_chunks(s.precision, s.N, s.M, sm_count);
+  s.threads64 = TPB64;
+  if (s.precision != SK_FP64) return;
+  const int64_t n_tb = (int64_t)align_up((size_t)(s.M > 0 ? s.M : 1), TGT_CTA64) / TGT_CTA64;
+  const int64_t slots = (int64_t)sm_count * 2;  // resident TPB64-thread CTAs
+  if (n_tb * s.n_chunks >= 4 * slots) return;
+  const int64_t tiles = (int64_t)align_up((size_t)(s.N > 0 ? s.N : 1), TILE64) / TILE64;
+  s.threads64 = TPB64_SMALL;
+  s.n_chunks = (int)(tiles < 64 ? tiles : 64);
 }
 
 double layer_scale(const EvalShape& s) {
@@ -382,7 +401,7 @@ int eval_entry(sk_ctx* ctx, int layer, int precision, int mem, int64_t N, const 
   s.n_delta = n_delta;
   s.mu = mu;
   s.copy_inputs = mem == SK_HOST;
-  s.n_chunks = choose_chunks(precision, N, M, ctx->sm_count);
+  choose_decomposition(s, ctx->sm_count);
   const size_t need = eval_workspace_bytes(s);
   int rc = ensure_workspace(ctx, need);
   if (rc != SK_OK) return rc;

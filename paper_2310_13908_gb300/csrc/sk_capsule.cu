@@ -213,7 +213,7 @@ EvalShape capsule_shape(const sk_capsule* c) {
     s.N = c->N;
     s.n_delta = c->n_delta;
   }
-  s.n_chunks = choose_chunks(c->precision, s.N, s.M, c->ctx->sm_count);
+  choose_decomposition(s, c->ctx->sm_count);
   return s;
 }
 

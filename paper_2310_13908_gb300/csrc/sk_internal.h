@@ -125,6 +125,7 @@ struct EvalBufs {
   int64_t N = 0, M = 0, N_pad = 0, M_pad = 0;
   int n_chunks = 1;
   int pair_np = 2;  // FP32 pair kernel: f32x2 target pairs per lane (1 or 2)
+  int threads64 = TPB64;  // FP64 pair kernel: threads per CTA
   int sort_blocks = 0;
 };
 
@@ -173,6 +174,10 @@ struct sk_ctx {
 
 namespace sk {
 
+// CTA size of the FP64 pair kernel for problems too small to fill the GPU
+// with TPB64-thread CTAs (TPL64 targets per lane in both)
+constexpr int TPB64_SMALL = 64;
+
 // Shape of one evaluation.
 struct EvalShape {
   int layer = LAYER_SL;
@@ -184,6 +189,7 @@ struct EvalShape {
   // preparation runs beside the persistent serving kernel, which leaves each
   // SM room for 256-thread blocks only: every preparation launch keeps to that
   bool narrow_prep = false;
+  int threads64 = TPB64;  // CTA size of the FP64 pair kernel (TPB64 or TPB64_SMALL)
 };
 
 // sk_api.cu
@@ -193,6 +199,8 @@ int ensure_workspace(sk_ctx* ctx, size_t need);
 size_t eval_workspace_bytes(const EvalShape& s);
 void carve_eval_buffers(Bump& bp, const EvalShape& s, EvalBufs& b);
 int choose_chunks(int precision, int64_t N, int64_t M, int sm_count);
+// n_chunks (and, for FP64, the pair kernel's CTA size) of an evaluation shape
+void choose_decomposition(EvalShape& s, int sm_count);
 double layer_scale(const EvalShape& s);  // 1/(8 pi mu) or -6/(8 pi)
 int enqueue_prep(const EvalShape& s, const EvalBufs& b, double rho_T, double rho_c,
                  cudaStream_t st);

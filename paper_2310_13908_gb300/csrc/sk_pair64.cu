@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(TPB64, 2)
   const int k0 = (int)((long long)ch * n_tiles / n_chunks);
   const int k1 = (int)((long long)(ch + 1) * n_tiles / n_chunks);
 
-  const int64_t wbase = (int64_t)tb * TGT_CTA64 + wid * TGT_WARP64;
+  const int64_t wbase = (int64_t)tb * (blockDim.x * TPL64) + wid * TGT_WARP64;
   double tx[2], ty[2], tz[2], invd[2], rc2[2];
   float blo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, bhi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
   float rc2max = -1.f, amax = 0.f;
@@ -258,15 +258,17 @@ __global__ void k_finish64(const int* __restrict__ perm, int64_t M, int64_t M_pa
 }  // namespace
 
 void launch_pair64(int layer, const EvalBufs& b, double /*scale*/, cudaStream_t st) {
-  const unsigned grid = (unsigned)((b.M_pad / TGT_CTA64) * b.n_chunks);
+  // M_pad is a multiple of TGT_CTA64, hence of the smaller CTA's targets too
+  const int tpb = b.threads64;
+  const unsigned grid = (unsigned)((b.M_pad / ((int64_t)tpb * TPL64)) * b.n_chunks);
   if (layer == LAYER_SL) {
     const size_t smem = 2 * TILE64 * 2 * sizeof(double4_32a);
-    k_pair64<LAYER_SL><<<grid, TPB64, smem, st>>>(b.src64, b.nrm64, b.segbox, b.meta, b.tgt64,
-                                                   b.M_pad, b.n_chunks, b.part, b.flags);
+    k_pair64<LAYER_SL><<<grid, tpb, smem, st>>>(b.src64, b.nrm64, b.segbox, b.meta, b.tgt64,
+                                                 b.M_pad, b.n_chunks, b.part, b.flags);
   } else {
     const size_t smem = 2 * TILE64 * 3 * sizeof(double4_32a);
-    k_pair64<LAYER_DL><<<grid, TPB64, smem, st>>>(b.src64, b.nrm64, b.segbox, b.meta, b.tgt64,
-                                                   b.M_pad, b.n_chunks, b.part, b.flags);
+    k_pair64<LAYER_DL><<<grid, tpb, smem, st>>>(b.src64, b.nrm64, b.segbox, b.meta, b.tgt64,
+                                                 b.M_pad, b.n_chunks, b.part, b.flags);
   }
 }
 
