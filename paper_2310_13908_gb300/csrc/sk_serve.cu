@@ -319,6 +319,7 @@ struct sk_server {
   std::vector<sk::Slot> slots;
   std::mutex mu;
   std::condition_variable cv_done;
+  std::condition_variable cv_work;  // wakes an idle scheduler: a submit or shutdown
   std::deque<sk::Req*> queue;
   std::map<uint64_t, sk::Req*> reqs;
   std::thread thr;
@@ -425,16 +426,16 @@ void publish(sk_server* srv, int slot) {
   *word = ((unsigned long long)(unsigned)(d.n_tb * d.n_chunks) << 32);
   cudaMemcpyAsync(srv->d_desc + slot, sl.h_flags + PIN_DESC, sizeof(d), cudaMemcpyHostToDevice,
                   srv->s_ctl);
+  // stream order lands the descriptor before the claim word; the pinned block
+  // is rewritten only by this slot's next publish, after this request is done
   cudaMemcpyAsync(&srv->d_claim[slot].word, word, sizeof(*word), cudaMemcpyHostToDevice,
                   srv->s_ctl);
-  cudaStreamSynchronize(srv->s_ctl);
   sl.state = SlotState::Running;
   sl.req->st.publish_us = now_us(srv);
 }
 
 void scheduler(sk_server* srv) {
   cudaSetDevice(srv->ctx->device);
-  int idle_spins = 0;
   while (true) {
     bool progress = false;
     {
@@ -507,12 +508,18 @@ void scheduler(sk_server* srv) {
       srv->cv_done.notify_all();
       break;
     }
-    if (progress) {
-      idle_spins = 0;
-    } else if (++idle_spins > 64) {
-      std::this_thread::sleep_for(std::chrono::microseconds(20));
-    } else {
+    // While a request is in flight the thread only yields: every state change
+    // it waits for (preparation done, done flag, copy done) is noticed within
+    // microseconds. With nothing in flight it sleeps until a submit (or
+    // shutdown) wakes it.
+    bool in_flight = false;
+    for (const auto& sl : srv->slots) in_flight |= sl.state != SlotState::Free;
+    if (progress || in_flight) {
       std::this_thread::yield();
+    } else {
+      std::unique_lock<std::mutex> lk(srv->mu);
+      if (srv->queue.empty() && !srv->shutting_down)
+        srv->cv_work.wait_for(lk, std::chrono::milliseconds(10));
     }
   }
 }
@@ -694,6 +701,7 @@ int serve_submit(sk_server* srv, const sk_request* q, uint64_t* ticket) {
   srv->reqs[r->ticket] = r;
   srv->queue.push_back(r);
   *ticket = r->ticket;
+  srv->cv_work.notify_one();
   return SK_OK;
 }
 
@@ -727,7 +735,11 @@ int serve_poll(sk_server* srv, uint64_t ticket, double* u_out, sk_req_stats* st,
 
 void serve_destroy(sk_server* srv) {
   if (!srv) return;
-  srv->shutting_down = true;
+  {
+    std::unique_lock<std::mutex> lk(srv->mu);
+    srv->shutting_down = true;
+    srv->cv_work.notify_one();
+  }
   if (srv->thr.joinable()) srv->thr.join();
   cudaSetDevice(srv->ctx->device);
   cudaMemcpyAsync(srv->d_ctl + CTL_STOP, srv->h_stop_one, sizeof(int), cudaMemcpyHostToDevice,
