@@ -60,6 +60,10 @@ def parse_args():
     ap.add_argument("--m", type=int, default=257, help="grid order (default 257)")
     ap.add_argument("--probes", type=int, default=100_000)
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--layer", choices=["sl", "dl"], default="sl",
+                    help="timed step: single layer (default) or double layer (q = the SH "
+                         "density); extras run only for the default sl/fp32c step")
+    ap.add_argument("--precision", choices=["fp32c", "fp64"], default="fp32c")
     return ap.parse_args()
 
 
@@ -73,11 +77,12 @@ def workload(m, n_probes, rank=0):
     return ci.ellipsoid_hires_workload(m=m, n_probes=n_probes, seed=3000 + 17 * rank)
 
 
-def workload_name(w):
+def workload_name(w, layer="sl"):
     s = w.surface
+    kind = "single layer, delta=2h, mu=1" if layer == "sl" else \
+        "double layer (q = the SH density), delta=2h"
     return (f"ellipsoid(1,0.8,0.5) m={s.m}: N={s.N} nodes (N_s={s.n_active} active) + "
-            f"{w.targets.shape[0] - s.N} exterior probes (0.1h-5h), single layer, "
-            f"delta=2h, mu=1")
+            f"{w.targets.shape[0] - s.N} exterior probes (0.1h-5h), {kind}")
 
 
 def sample_targets(w, n, seed=1234):
@@ -253,7 +258,8 @@ def main():
         pg = dist
 
     serve_future = None
-    if rank == 0 and world == 1 and not args.no_extras:
+    default_step = args.layer == "sl" and args.precision == "fp32c"
+    if rank == 0 and world == 1 and not args.no_extras and default_step:
         import concurrent.futures
         serve_future = concurrent.futures.ThreadPoolExecutor(1).submit(build_serving_mix)
     w = workload(args.m, args.probes, rank)
@@ -268,6 +274,9 @@ def main():
         return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)
 
     X, W, F, Y, D = (tdev(a) for a in (s.X, s.w, w.f, w.targets, w.delta))
+    dl = args.layer == "dl"
+    NRM = tdev(s.n) if dl else None
+    prec_main = sk.SK_FP64 if args.precision == "fp64" else sk.SK_FP32C
     out = torch.empty((M, 3), dtype=torch.float64, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
 
@@ -276,9 +285,13 @@ def main():
     sk.sk_set_profiling(h, True)
     stream = torch.cuda.current_stream(dev)
 
-    def step(prec=sk.SK_FP32C, delta=D):
-        sk.stokes_sl_eval(h, prec, sk.SK_DEVICE, X, W, F, Y, delta, 1.0, u_out=out,
-                          stream=stream)
+    def step(prec=prec_main, delta=D):
+        if dl:
+            sk.stokes_dl_eval(h, prec, sk.SK_DEVICE, X, W, NRM, F, Y, delta, u_out=out,
+                              stream=stream)
+        else:
+            sk.stokes_sl_eval(h, prec, sk.SK_DEVICE, X, W, F, Y, delta, 1.0, u_out=out,
+                              stream=stream)
 
     for _ in range(args.warmup):
         step()
@@ -312,13 +325,18 @@ def main():
     stats = sk.sk_last_eval_stats(h)
 
     pair_avg = float(np.mean(pair_ms))
-    achieved = FLOPS_SL * inter / (pair_avg * 1e-3) / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
-                "traffic": traffic_from_profile(),
-                "kernel": "k_pair32<SLayer>", "pair_ms": pair_avg,
-                "flops_per_interaction": FLOPS_SL,
-                "peak_basis": "2 x 128 FP32 lanes x 152 SMs x 2070 MHz (max SM clock)"}
+    flops = FLOPS_DL if dl else FLOPS_SL
+    fp64 = prec_main == sk.SK_FP64
+    peak = FP64_PEAK_TFLOPS if fp64 else FP32_PEAK_TFLOPS
+    achieved = flops * inter / (pair_avg * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": traffic_from_profile() if default_step else None,
+                "kernel": {(False, False): "k_pair32<SLayer>", (True, False): "k_pair32<DLayer>",
+                           (False, True): "k_pair64<SL>", (True, True): "k_pair64<DL>"}[(dl, fp64)],
+                "pair_ms": pair_avg, "flops_per_interaction": flops,
+                "peak_basis": "nominal dense FP64 of GB300" if fp64 else
+                              "2 x 128 FP32 lanes x 152 SMs x 2070 MHz (max SM clock)"}
 
     # ---- end to end through the C ABI with pinned host buffers (SK_HOST, synchronous)
     def pinned(a):
@@ -328,29 +346,40 @@ def main():
 
     hX, hW, hF, hY, hD = (pinned(np.ascontiguousarray(a, dtype=np.float64))
                           for a in (s.X, s.w, w.f, w.targets, w.delta))
+    hN = pinned(np.ascontiguousarray(s.n, dtype=np.float64)) if dl else None
     hU = pinned(np.zeros((M, 3)))
+
+    def host_step():
+        if dl:
+            sk.stokes_dl_eval(h, prec_main, sk.SK_HOST, hX, hW, hN, hF, hY, hD, u_out=hU)
+        else:
+            sk.stokes_sl_eval(h, prec_main, sk.SK_HOST, hX, hW, hF, hY, hD, 1.0, u_out=hU)
+
     e2e_steps = max(3, min(args.steps, 10))
     for _ in range(2):
-        sk.stokes_sl_eval(h, sk.SK_FP32C, sk.SK_HOST, hX, hW, hF, hY, hD, 1.0, u_out=hU)
+        host_step()
     e2e_t = []
     for _ in range(e2e_steps):
         flush.zero_()
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        sk.stokes_sl_eval(h, sk.SK_FP32C, sk.SK_HOST, hX, hW, hF, hY, hD, 1.0, u_out=hU)
+        host_step()
         e2e_t.append(time.perf_counter() - t0)
     e2e_step = max_over_ranks(np.mean(e2e_t), pg, dev)
-    h2d = (hX.nbytes + hW.nbytes + hF.nbytes + hY.nbytes + hD.nbytes)
+    h2d = (hX.nbytes + hW.nbytes + hF.nbytes + hY.nbytes + hD.nbytes +
+           (hN.nbytes if dl else 0))
     e2e = {"value": job_throughput(world, inter, e2e_step), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
            "d2h_bytes_per_step": int(hU.nbytes), "ms_per_step": e2e_step * 1e3,
-           "path": "stokes_sl_eval(SK_FP32C, SK_HOST), pinned host buffers, synchronous"}
+           "path": f"stokes_{args.layer}_eval(SK_{args.precision.upper()}, SK_HOST), pinned host "
+                   "buffers, synchronous"}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 pairs + f64 near/final", "data": "synthetic",
-            "config": {"workload": workload_name(w), "targets": M, "sources_active": Ns,
-                       "interactions_per_step": inter, "precision": "SK_FP32C",
+            "dtype": "f64" if fp64 else "f32 pairs + f64 near/final", "data": "synthetic",
+            "config": {"workload": workload_name(w, args.layer), "targets": M,
+                       "sources_active": Ns, "interactions_per_step": inter,
+                       "precision": f"SK_{args.precision.upper()}",
                        "rho_T": 0.5, "rho_c": 5.0,
                        "l2": "flushed between timed steps (256 MB write); inputs 58 MB",
                        "parallelism": f"replicas x{world} (independent workloads)"},
@@ -359,7 +388,7 @@ def main():
             "near_pairs_per_step": stats["near_pairs"],
             "overflow_targets": stats["overflow_targets"]}
 
-    if rank == 0 and world == 1 and not args.no_extras:
+    if rank == 0 and world == 1 and not args.no_extras and default_step:
         line.update(extras(sk, h, w, X, W, F, Y, D, out, u_fp32, stream, dev, torch,
                            serve_future))
     if rank == 0:
