@@ -310,3 +310,34 @@ def test_stats_near_pairs_match_independent_count(ctx, rbc):
     n = cKDTree(s.X[act]).query_ball_point(w.targets, r=0.5 * w.delta[0], return_length=True)
     assert abs(st["near_pairs"] - n.sum()) <= 1e-3 * n.sum()
     assert st["overflow_targets"] == 0
+
+
+@pytest.mark.parametrize("layer", ["sl", "dl"])
+def test_target_pairs_per_lane_boundary(ctx, layer):
+    """M = 131,072 runs one f32x2 target pair per lane (3 CTAs/SM), M = 131,073
+    two (2 CTAs/SM). Both match the oracle on sampled targets, and the shared
+    targets agree across the two tilings up to the FP64 merge of chunk
+    partials (the chunk counts differ)."""
+    rng = np.random.default_rng(61)
+    s = ci.make_surface(ci.Ellipsoid(1.0, 0.8, 0.5), 65)
+    dens = ci.sh_density(s.x0, rng, lmax=6)
+    probes, _ = ci.exterior_probes(ci.Ellipsoid(1.0, 0.8, 0.5), 131073 - s.N, s.h, rng)
+    Y = np.concatenate([s.X, probes])
+    delta = np.array([2.0 * s.h])
+    idx = rng.choice(131072, 384, replace=False)
+    if layer == "sl":
+        ref = oracle.sl(s.X, s.w, dens, Y[idx], delta, 1.0)
+    else:
+        ref = oracle.dl(s.X, s.w, s.n, dens, Y[idx], delta)
+    outs = []
+    for M in (131072, 131073):
+        if layer == "sl":
+            u = sk.stokes_sl_eval(ctx, sk.SK_FP32C, sk.SK_DEVICE, to_dev(s.X), to_dev(s.w),
+                                  to_dev(dens), to_dev(Y[:M]), to_dev(delta), 1.0)
+        else:
+            u = sk.stokes_dl_eval(ctx, sk.SK_FP32C, sk.SK_DEVICE, to_dev(s.X), to_dev(s.w),
+                                  to_dev(s.n), to_dev(dens), to_dev(Y[:M]), to_dev(delta))
+        u = u.cpu().numpy()
+        assert_close(u[idx], ref, sk.SK_FP32C)
+        outs.append(u)
+    assert rel_l2(outs[1][:131072], outs[0]) < 1e-12
