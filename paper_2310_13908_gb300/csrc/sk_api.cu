@@ -2,6 +2,7 @@
 // the launch sequence of one evaluation.
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 
@@ -173,7 +174,8 @@ int enqueue_prep(const EvalShape& s, const EvalBufs& b, double rho_T, double rho
                  cudaStream_t st) {
   const bool fp32 = s.precision == SK_FP32C;
   const double scale = layer_scale(s);
-  constexpr int SORT_LAUNCHES = 3 + 4 * 3;  // bbox (2) + keys + 4 radix passes x 3
+  // bbox (2) + keys + 4 radix passes x 3, or the single-block sort
+  const int SORT_LAUNCHES = b.sort_blocks <= s.small_sort_blocks ? 1 : 3 + 4 * 3;
   int launches = 0;
   cudaMemsetAsync(b.flags, 0, N_FLAGS * sizeof(unsigned long long), st);
   cudaMemsetAsync(b.meta, 0, N_META * sizeof(int), st);
@@ -182,7 +184,8 @@ int enqueue_prep(const EvalShape& s, const EvalBufs& b, double rho_T, double rho
   launches += 1;
   if (s.N > 0) {
     launch_sort_points(b.src_xyz, b.src_w, s.N, b.keys_a, b.keys_b, b.vals_a, b.vals_b, b.hist,
-                       b.bbox_part, b.bbox, b.meta + META_NS, b.sort_blocks, s.narrow_prep, st);
+                       b.bbox_part, b.bbox, b.meta + META_NS, b.sort_blocks, s.narrow_prep,
+                       s.small_sort_blocks, st);
     if (fp32)
       launch_pack_sources32(s.layer, b, scale, st);
     else
@@ -190,7 +193,8 @@ int enqueue_prep(const EvalShape& s, const EvalBufs& b, double rho_T, double rho
     launches += SORT_LAUNCHES + 1;
   }
   launch_sort_points(b.tgt_xyz, nullptr, s.M, b.keys_a, b.keys_b, b.vals_a, b.vals_b, b.hist,
-                     b.bbox_part, b.bbox, b.meta + META_SCRATCH, b.sort_blocks, s.narrow_prep, st);
+                     b.bbox_part, b.bbox, b.meta + META_SCRATCH, b.sort_blocks, s.narrow_prep,
+                     s.small_sort_blocks, st);
   launches += SORT_LAUNCHES;
   if (fp32)
     launch_pack_targets32(b, s.n_delta, rho_T, rho_c, st);
@@ -271,6 +275,12 @@ int sk_create(sk_ctx** out, int device, size_t workspace_bytes) {
   }
   std::memset(ctx->h_flags, 0, 256);
   ctx->last_stream = ctx->stream;
+  ctx->small_sort_blocks = SMALL_SORT_BLOCKS;
+  if (const char* v = std::getenv("SK_SMALL_SORT_BLOCKS")) {
+    char* end = nullptr;
+    const long k = std::strtol(v, &end, 10);
+    if (end != v && *end == '\0' && k >= 0 && k <= 1024) ctx->small_sort_blocks = (int)k;
+  }
   *out = ctx;
   return SK_OK;
 }
@@ -401,6 +411,7 @@ int eval_entry(sk_ctx* ctx, int layer, int precision, int mem, int64_t N, const 
   s.n_delta = n_delta;
   s.mu = mu;
   s.copy_inputs = mem == SK_HOST;
+  s.small_sort_blocks = ctx->small_sort_blocks;
   choose_decomposition(s, ctx->sm_count);
   const size_t need = eval_workspace_bytes(s);
   int rc = ensure_workspace(ctx, need);

@@ -22,11 +22,15 @@ constexpr int BBOX_BLOCKS = 128;
 constexpr unsigned FULL = 0xffffffffu;
 
 // ---- bounding box of the (active) points -----------------------------------
-__global__ void k_bbox_partial(const double* __restrict__ xyz, const double* __restrict__ w,
-                               int64_t n, float* __restrict__ part) {
+// Min/max over points i = first, first + stride, ... of this block, reduced
+// over the block; threads 0..5 return (lo x, y, z, hi x, y, z) in *out.
+// (Min and max do not depend on the grouping, so one block or many give the
+// same box.)
+__device__ void bbox_block(const double* __restrict__ xyz, const double* __restrict__ w,
+                           int64_t n, int64_t first, int64_t stride, float (*s)[RS_THREADS],
+                           float* out) {
   float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t i = first; i < n; i += stride) {
     if (w && w[i] == 0.0) continue;
     for (int c = 0; c < 3; ++c) {
       float v = (float)xyz[3 * i + c];
@@ -34,7 +38,6 @@ __global__ void k_bbox_partial(const double* __restrict__ xyz, const double* __r
       hi[c] = fmaxf(hi[c], v);
     }
   }
-  __shared__ float s[6][RS_THREADS];
   for (int c = 0; c < 3; ++c) {
     s[c][threadIdx.x] = lo[c];
     s[3 + c][threadIdx.x] = hi[c];
@@ -49,7 +52,16 @@ __global__ void k_bbox_partial(const double* __restrict__ xyz, const double* __r
     }
     __syncthreads();
   }
-  if (threadIdx.x < 6) part[blockIdx.x * 6 + threadIdx.x] = s[threadIdx.x][0];
+  if (threadIdx.x < 6) *out = s[threadIdx.x][0];
+}
+
+__global__ void k_bbox_partial(const double* __restrict__ xyz, const double* __restrict__ w,
+                               int64_t n, float* __restrict__ part) {
+  __shared__ float s[6][RS_THREADS];
+  float v;
+  bbox_block(xyz, w, n, blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
+             (int64_t)gridDim.x * blockDim.x, s, &v);
+  if (threadIdx.x < 6) part[blockIdx.x * 6 + threadIdx.x] = v;
 }
 
 __global__ void k_bbox_final(const float* __restrict__ part, int nblk, float* __restrict__ bbox) {
@@ -70,6 +82,26 @@ __device__ __forceinline__ uint32_t spread3(uint32_t v) {
   return v;
 }
 
+// Morton key of point i (0xffffffff for a zero-weight source); true if active.
+__device__ __forceinline__ bool morton_key(const double* __restrict__ xyz,
+                                           const double* __restrict__ w, int64_t i,
+                                           const float* bbox, uint32_t* key) {
+  const bool active = !(w && w[i] == 0.0);
+  *key = 0xffffffffu;
+  if (active) {
+    float ext = fmaxf(fmaxf(bbox[3] - bbox[0], bbox[4] - bbox[1]), bbox[5] - bbox[2]);
+    float sc = ext > 0.f ? 1023.0f / ext : 0.f;
+    uint32_t q[3];
+    for (int c = 0; c < 3; ++c) {
+      float v = ((float)xyz[3 * i + c] - bbox[c]) * sc;
+      v = fminf(fmaxf(v, 0.f), 1023.f);
+      q[c] = (uint32_t)v;
+    }
+    *key = spread3(q[0]) | (spread3(q[1]) << 1) | (spread3(q[2]) << 2);
+  }
+  return active;
+}
+
 __global__ void k_morton_keys(const double* __restrict__ xyz, const double* __restrict__ w,
                               int64_t n, const float* __restrict__ bbox,
                               uint32_t* __restrict__ keys, int* __restrict__ vals,
@@ -77,19 +109,8 @@ __global__ void k_morton_keys(const double* __restrict__ xyz, const double* __re
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   bool active = false;
   if (i < n) {
-    active = !(w && w[i] == 0.0);
-    uint32_t key = 0xffffffffu;
-    if (active) {
-      float ext = fmaxf(fmaxf(bbox[3] - bbox[0], bbox[4] - bbox[1]), bbox[5] - bbox[2]);
-      float sc = ext > 0.f ? 1023.0f / ext : 0.f;
-      uint32_t q[3];
-      for (int c = 0; c < 3; ++c) {
-        float v = ((float)xyz[3 * i + c] - bbox[c]) * sc;
-        v = fminf(fmaxf(v, 0.f), 1023.f);
-        q[c] = (uint32_t)v;
-      }
-      key = spread3(q[0]) | (spread3(q[1]) << 1) | (spread3(q[2]) << 2);
-    }
+    uint32_t key;
+    active = morton_key(xyz, w, i, bbox, &key);
     keys[i] = key;
     vals[i] = (int)i;
   }
@@ -98,27 +119,32 @@ __global__ void k_morton_keys(const double* __restrict__ xyz, const double* __re
 }
 
 // ---- radix sort: histogram, scan, stable scatter ----------------------------
-__global__ void k_rs_hist(const uint32_t* __restrict__ keys, int n, int shift,
-                          uint32_t* __restrict__ hist) {
-  __shared__ uint32_t h[256];
+// Digit counts of tile blk (of nblk) into column blk of hist[digit][nblk].
+__device__ void rs_hist_tile(const uint32_t* __restrict__ keys, int n, int shift,
+                             uint32_t* __restrict__ hist, int blk, int nblk, uint32_t* h) {
   h[threadIdx.x] = 0;
   __syncthreads();
-  int base = blockIdx.x * RS_TILE;
+  int base = blk * RS_TILE;
   for (int r = 0; r < RS_ITEMS; ++r) {
     int i = base + r * RS_THREADS + threadIdx.x;
     if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
   }
   __syncthreads();
-  hist[threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];
+  hist[threadIdx.x * nblk + blk] = h[threadIdx.x];
 }
 
-// Exclusive scan of `total` counts, one block of 1024 threads: each thread
-// sums its own contiguous run, one block scan of the run totals gives every
-// run its offset, and the thread rewrites its run (exact integer sums).
+__global__ void k_rs_hist(const uint32_t* __restrict__ keys, int n, int shift,
+                          uint32_t* __restrict__ hist) {
+  __shared__ uint32_t h[256];
+  rs_hist_tile(keys, n, shift, hist, blockIdx.x, gridDim.x, h);
+}
+
+// Exclusive scan of `total` counts by one block of THREADS threads: each
+// thread sums its own contiguous run, one block scan of the run totals gives
+// every run its offset, and the thread rewrites its run (exact integer sums).
 template <int THREADS>
-__global__ void __launch_bounds__(THREADS) k_rs_scan(uint32_t* __restrict__ a, int total) {
+__device__ void rs_scan_block(uint32_t* __restrict__ a, int total, uint32_t* warp_sums) {
   static_assert(THREADS % 32 == 0 && THREADS <= 1024, "one block of whole warps");
-  __shared__ uint32_t warp_sums[32];
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
   const int K = (total + THREADS - 1) / THREADS;
   const int b = min(t * K, total), e = min(b + K, total);
@@ -148,15 +174,21 @@ __global__ void __launch_bounds__(THREADS) k_rs_scan(uint32_t* __restrict__ a, i
   }
 }
 
-__global__ void k_rs_scatter(const uint32_t* __restrict__ kin, const int* __restrict__ vin,
-                             uint32_t* __restrict__ kout, int* __restrict__ vout, int n, int shift,
-                             const uint32_t* __restrict__ offs) {
-  __shared__ uint32_t base_d[256];
-  __shared__ uint32_t wcnt[RS_THREADS / 32][256];
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS) k_rs_scan(uint32_t* __restrict__ a, int total) {
+  __shared__ uint32_t warp_sums[32];
+  rs_scan_block<THREADS>(a, total, warp_sums);
+}
+
+// Stable scatter of tile blk (of nblk) to the offsets of column blk of offs.
+__device__ void rs_scatter_tile(const uint32_t* __restrict__ kin, const int* __restrict__ vin,
+                                uint32_t* __restrict__ kout, int* __restrict__ vout, int n,
+                                int shift, const uint32_t* __restrict__ offs, int blk, int nblk,
+                                uint32_t* base_d, uint32_t (*wcnt)[256]) {
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  base_d[tid] = offs[tid * gridDim.x + blockIdx.x];
+  base_d[tid] = offs[tid * nblk + blk];
   const unsigned lt = (1u << lane) - 1u;
-  const int base = blockIdx.x * RS_TILE;
+  const int base = blk * RS_TILE;
   for (int r = 0; r < RS_ITEMS; ++r) {
     for (int w = 0; w < RS_THREADS / 32; ++w) wcnt[w][tid] = 0;
     __syncthreads();
@@ -181,6 +213,64 @@ __global__ void k_rs_scatter(const uint32_t* __restrict__ kin, const int* __rest
     base_d[tid] += add;
     __syncthreads();
   }
+}
+
+__global__ void k_rs_scatter(const uint32_t* __restrict__ kin, const int* __restrict__ vin,
+                             uint32_t* __restrict__ kout, int* __restrict__ vout, int n, int shift,
+                             const uint32_t* __restrict__ offs) {
+  __shared__ uint32_t base_d[256];
+  __shared__ uint32_t wcnt[RS_THREADS / 32][256];
+  rs_scatter_tile(kin, vin, kout, vout, n, shift, offs, blockIdx.x, gridDim.x, base_d, wcnt);
+}
+
+// The whole ordering of a small point set in one block of RS_THREADS threads:
+// box, Morton keys and the four radix passes, tile by tile, with the same
+// device code as the multi-block launches, so the order is the same. Saves
+// fourteen launches (and their gaps) per point set.
+__global__ void __launch_bounds__(RS_THREADS)
+    k_sort_small(const double* __restrict__ xyz, const double* __restrict__ w, int64_t n,
+                 uint32_t* __restrict__ keys_a, uint32_t* __restrict__ keys_b,
+                 int* __restrict__ vals_a, int* __restrict__ vals_b, uint32_t* __restrict__ hist,
+                 float* __restrict__ bbox, int* __restrict__ count_out, int nblk) {
+  __shared__ float sbox[6][RS_THREADS];
+  __shared__ float box[6];
+  __shared__ uint32_t h[256];
+  __shared__ uint32_t warp_sums[32];
+  __shared__ uint32_t base_d[256];
+  __shared__ uint32_t wcnt[RS_THREADS / 32][256];
+  __shared__ int active_total;
+  const int tid = threadIdx.x;
+  float v;
+  bbox_block(xyz, w, n, tid, RS_THREADS, sbox, &v);
+  if (tid < 6) {
+    box[tid] = v;
+    bbox[tid] = v;
+  }
+  if (tid == 0) active_total = 0;
+  __syncthreads();
+  int act = 0;
+  for (int64_t i = tid; i < n; i += RS_THREADS) {
+    uint32_t key;
+    act += morton_key(xyz, w, i, box, &key) ? 1 : 0;
+    keys_a[i] = key;
+    vals_a[i] = (int)i;
+  }
+  atomicAdd(&active_total, act);
+  uint32_t *ka = keys_a, *kb = keys_b;
+  int *va = vals_a, *vb = vals_b;
+  for (int shift = 0; shift < 32; shift += 8) {
+    __syncthreads();  // the keys (or the previous pass's scatter) are complete
+    for (int b = 0; b < nblk; ++b) rs_hist_tile(ka, (int)n, shift, hist, b, nblk, h);
+    __syncthreads();
+    rs_scan_block<RS_THREADS>(hist, 256 * nblk, warp_sums);
+    __syncthreads();
+    for (int b = 0; b < nblk; ++b)
+      rs_scatter_tile(ka, va, kb, vb, (int)n, shift, hist, b, nblk, base_d, wcnt);
+    uint32_t* tk = ka; ka = kb; kb = tk;
+    int* tv = va; va = vb; vb = tv;
+  }
+  __syncthreads();
+  if (tid == 0) atomicAdd(count_out, active_total);
 }
 
 // ---- packing ----------------------------------------------------------------
@@ -333,8 +423,13 @@ int sort_grid_blocks(int64_t n) { return (int)((n + RS_TILE - 1) / RS_TILE); }
 void launch_sort_points(const double* xyz, const double* w, int64_t n, uint32_t* keys_a,
                         uint32_t* keys_b, int* vals_a, int* vals_b, uint32_t* hist,
                         float* bbox_part, float* bbox, int* count_out, int sort_blocks,
-                        bool narrow, cudaStream_t st) {
+                        bool narrow, int small_max_blocks, cudaStream_t st) {
   if (n <= 0) return;
+  if (sort_blocks <= small_max_blocks) {
+    k_sort_small<<<1, RS_THREADS, 0, st>>>(xyz, w, n, keys_a, keys_b, vals_a, vals_b, hist, bbox,
+                                           count_out, sort_blocks);
+    return;  // four passes: the sorted data is in keys_a / vals_a
+  }
   k_bbox_partial<<<BBOX_BLOCKS, RS_THREADS, 0, st>>>(xyz, w, n, bbox_part);
   k_bbox_final<<<1, 32, 0, st>>>(bbox_part, BBOX_BLOCKS, bbox);
   k_morton_keys<<<blocks_for(n, 256), 256, 0, st>>>(xyz, w, n, bbox, keys_a, vals_a, count_out);

@@ -341,3 +341,45 @@ def test_target_pairs_per_lane_boundary(ctx, layer):
         assert_close(u[idx], ref, sk.SK_FP32C)
         outs.append(u)
     assert rel_l2(outs[1][:131072], outs[0]) < 1e-12
+
+
+def test_single_block_sort_matches_multi_block_sort(ctx):
+    """Small point sets are ordered by one single-block kernel, larger ones by
+    fifteen launches; both run the same per-tile code, so the sorted order,
+    and hence every result, is the same bit for bit. A second context with the
+    single-block path turned off (SK_SMALL_SORT_BLOCKS=0) gives the reference;
+    sizes cover 1, ragged tiles, the 4-tile limit and zero-weight sources."""
+    import os
+    old = os.environ.get("SK_SMALL_SORT_BLOCKS")
+    os.environ["SK_SMALL_SORT_BLOCKS"] = "0"
+    try:
+        multi = sk.Context(0)
+    finally:
+        if old is None:
+            del os.environ["SK_SMALL_SORT_BLOCKS"]
+        else:
+            os.environ["SK_SMALL_SORT_BLOCKS"] = old
+    rng = np.random.default_rng(67)
+    s = ci.make_surface(ci.Ellipsoid(1.0, 0.8, 0.6), 38)   # N = 8214 > 4 tiles of 2048
+    f = rng.standard_normal((s.N, 3))
+    try:
+        for n_src, n_tgt in ((1, 1), (33, 2047), (2048, 2049), (4095, 6000), (8192, 8192),
+                             (s.N, 3000)):
+            src = rng.choice(s.N, n_src, replace=False)
+            w = s.w[src].copy()
+            w[rng.random(n_src) < 0.2] = 0.0
+            Y = s.X[rng.choice(s.N, n_tgt, replace=False)] + 0.01 * rng.standard_normal((n_tgt, 3))
+            for prec in PRECS:
+                a = sk.stokes_sl_eval(ctx, prec, sk.SK_HOST, s.X[src], w, f[src], Y, 2 * s.h)
+                b = sk.stokes_sl_eval(multi.handle, prec, sk.SK_HOST, s.X[src], w, f[src], Y,
+                                      2 * s.h)
+                assert np.array_equal(a, b), (n_src, n_tgt, prec)
+                c = sk.stokes_dl_eval(ctx, prec, sk.SK_HOST, s.X[src], w, s.n[src], f[src], Y,
+                                      2 * s.h)
+                d = sk.stokes_dl_eval(multi.handle, prec, sk.SK_HOST, s.X[src], w, s.n[src],
+                                      f[src], Y, 2 * s.h)
+                assert np.array_equal(c, d), (n_src, n_tgt, prec)
+        st = sk.sk_last_eval_stats(multi.handle)
+        assert st["kernel_launches"] > 0
+    finally:
+        multi.close()
