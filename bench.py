@@ -870,6 +870,18 @@ def extras(sk, h, w, X, W, F, Y, D, out, u_fp32, stream, dev, torch, serve_futur
     except Exception as e:
         res["dl_ellipsoid_m193"] = {"error": repr(e)}
     try:
+        pk = sk.sk_probe_peaks(h)
+        res["peaks_probe"] = {
+            "ffma2_tflops": pk["ffma2_tflops"], "dfma_tflops": pk["dfma_tflops"],
+            "far_pairs_per_s": pk["far_pairs_per_s"],
+            "far_loop_ceiling_tflops": pk["far_pairs_per_s"] * FLOPS_SL / 1e12,
+            "note": "microbenchmarks (sk_probe_peaks): FFMA2 and DFMA over full occupancy; "
+                    "the single-layer far pair loop with sources in shared memory at the C3 "
+                    "kernel's shape (2 f32x2 pairs per lane, 2 CTAs/SM). The roofline peak "
+                    "stays the unit-count figure."}
+    except Exception as e:
+        res["peaks_probe"] = {"error": repr(e)}
+    try:
         res["capsule_skalak_m129"] = capsule_bench(sk, h, torch, dev)
     except Exception as e:
         res["capsule_skalak_m129"] = {"error": repr(e)}

@@ -100,6 +100,27 @@ typedef struct {
 } sk_eval_stats;
 int sk_last_eval_stats(const sk_ctx* ctx, sk_eval_stats* out);
 
+/* Throughput ceilings measured on the context's device by three
+ * microbenchmarks with fixed trip counts (about 0.1 s in all):
+ *   ffma2_tflops     packed FP32 FMA (FFMA2) over full occupancy, 4 flops per
+ *                    instruction and lane;
+ *   dfma_tflops      FP64 FMA, 2 flops per FMA;
+ *   far_pairs_per_s  the single-layer far-field pair (Sec. 3.4 kernel with
+ *                    s1 = s2 = 1) as the FP32C pair kernel runs it for large
+ *                    problems (two f32x2 target pairs per lane, two CTAs per
+ *                    SM), with sources in shared memory: the ceiling of the
+ *                    pair loop without global traffic, near/far tests or
+ *                    compensated merges.
+ * Blocks until done; runs on the context's stream. SK_EINVAL for NULL
+ * arguments, SK_ECUDA if a launch fails. */
+typedef struct {
+  double ffma2_tflops;
+  double dfma_tflops;
+  double far_pairs_per_s;
+  int32_t sm_count;
+} sk_peaks;
+int sk_probe_peaks(sk_ctx* ctx, sk_peaks* out);
+
 /* Profiling: enable = 1 records CUDA events on the evaluation's stream around
  * the pair kernel and around the whole evaluation (see sk_eval_stats). */
 int sk_set_profiling(sk_ctx* ctx, int enable);

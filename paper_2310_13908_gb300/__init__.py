@@ -42,6 +42,11 @@ class SkError(RuntimeError):
         self.code = code
 
 
+class sk_peaks(ctypes.Structure):
+    _fields_ = [("ffma2_tflops", ctypes.c_double), ("dfma_tflops", ctypes.c_double),
+                ("far_pairs_per_s", ctypes.c_double), ("sm_count", ctypes.c_int32)]
+
+
 class sk_eval_stats(ctypes.Structure):
     _fields_ = [("n_src_active", ctypes.c_int64), ("n_tgt", ctypes.c_int64),
                 ("near_pairs", ctypes.c_int64), ("overflow_targets", ctypes.c_int64),
@@ -62,6 +67,8 @@ def _declare(lib):
     lib.sk_set_fp32c_thresholds.restype = _int
     lib.sk_last_eval_stats.argtypes = [_vp, ctypes.POINTER(sk_eval_stats)]
     lib.sk_last_eval_stats.restype = _int
+    lib.sk_probe_peaks.argtypes = [_vp, ctypes.POINTER(sk_peaks)]
+    lib.sk_probe_peaks.restype = _int
     lib.sk_set_profiling.argtypes = [_vp, _int]
     lib.sk_set_profiling.restype = _int
     lib.stokes_sl_eval.argtypes = [_vp, _int, _int, _i64, _vp, _vp, _vp, _i64, _vp, _vp, _i64,
@@ -146,6 +153,13 @@ def sk_set_fp32c_thresholds(ctx, rho_T: float, rho_c: float) -> None:
 
 def sk_set_profiling(ctx, enable: bool) -> None:
     _check(ctx, load().sk_set_profiling(ctx, 1 if enable else 0))
+
+
+def sk_probe_peaks(ctx) -> dict:
+    """Measured FFMA2 / DFMA throughput and the far-field pair-loop ceiling."""
+    p = sk_peaks()
+    _check(ctx, load().sk_probe_peaks(ctx, ctypes.byref(p)))
+    return {f[0]: getattr(p, f[0]) for f in p._fields_}
 
 
 def sk_last_eval_stats(ctx) -> dict:
