@@ -76,7 +76,7 @@ void carve_eval_buffers(Bump& bp, const EvalShape& s, EvalBufs& b) {
   b.keys_b = bp.take<uint32_t>(nsort);
   b.vals_a = bp.take<int>(nsort);
   b.vals_b = bp.take<int>(nsort);
-  b.hist = bp.take<uint32_t>(256 * (size_t)b.sort_blocks);
+  b.hist = bp.take<uint32_t>(256 * (size_t)b.sort_blocks + 256);  // + the 256 row totals
   b.bbox_part = bp.take<float>(128 * 6);
   b.bbox = bp.take<float>(8);
   b.meta = bp.take<int>(N_META);
@@ -174,7 +174,7 @@ int enqueue_prep(const EvalShape& s, const EvalBufs& b, double rho_T, double rho
                  cudaStream_t st) {
   const bool fp32 = s.precision == SK_FP32C;
   const double scale = layer_scale(s);
-  // bbox (2) + keys + 4 radix passes x 3, or the single-block sort
+  // bbox (2) + keys + 4 radix passes x 3 (hist, row scan, scatter), or the single-block sort
   const int SORT_LAUNCHES = b.sort_blocks <= s.small_sort_blocks ? 1 : 3 + 4 * 3;
   int launches = 0;
   cudaMemsetAsync(b.flags, 0, N_FLAGS * sizeof(unsigned long long), st);
@@ -184,7 +184,7 @@ int enqueue_prep(const EvalShape& s, const EvalBufs& b, double rho_T, double rho
   launches += 1;
   if (s.N > 0) {
     launch_sort_points(b.src_xyz, b.src_w, s.N, b.keys_a, b.keys_b, b.vals_a, b.vals_b, b.hist,
-                       b.bbox_part, b.bbox, b.meta + META_NS, b.sort_blocks, s.narrow_prep,
+                       b.bbox_part, b.bbox, b.meta + META_NS, b.sort_blocks,
                        s.small_sort_blocks, st);
     if (fp32)
       launch_pack_sources32(s.layer, b, scale, st);
@@ -193,7 +193,7 @@ int enqueue_prep(const EvalShape& s, const EvalBufs& b, double rho_T, double rho
     launches += SORT_LAUNCHES + 1;
   }
   launch_sort_points(b.tgt_xyz, nullptr, s.M, b.keys_a, b.keys_b, b.vals_a, b.vals_b, b.hist,
-                     b.bbox_part, b.bbox, b.meta + META_SCRATCH, b.sort_blocks, s.narrow_prep,
+                     b.bbox_part, b.bbox, b.meta + META_SCRATCH, b.sort_blocks,
                      s.small_sort_blocks, st);
   launches += SORT_LAUNCHES;
   if (fp32)

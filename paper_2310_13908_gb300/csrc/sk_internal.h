@@ -102,7 +102,7 @@ struct EvalBufs {
   uint32_t* keys_b = nullptr;
   int* vals_a = nullptr;
   int* vals_b = nullptr;
-  uint32_t* hist = nullptr;
+  uint32_t* hist = nullptr;       // [256][sort_blocks] digit counts, then 256 row totals
   float* bbox_part = nullptr;
   float* bbox = nullptr;
   // prepared sources / targets
@@ -192,9 +192,6 @@ struct EvalShape {
   double mu = 1.0;
   bool copy_inputs = false;  // inputs/outputs live in the workspace (host-memory calls)
   int n_chunks = 1;
-  // preparation runs beside the persistent serving kernel, which leaves each
-  // SM room for 256-thread blocks only: every preparation launch keeps to that
-  bool narrow_prep = false;
   int threads64 = TPB64;  // CTA size of the FP64 pair kernel (TPB64 or TPB64_SMALL)
   // point sets of at most this many radix-sort tiles are ordered by one
   // single-block kernel instead of fifteen launches (0: never)
@@ -222,7 +219,7 @@ int enqueue_eval(const EvalShape& s, const EvalBufs& b, double rho_T, double rho
 void launch_sort_points(const double* xyz, const double* w, int64_t n, uint32_t* keys_a,
                         uint32_t* keys_b, int* vals_a, int* vals_b, uint32_t* hist,
                         float* bbox_part, float* bbox, int* count_out, int sort_blocks,
-                        bool narrow, int small_max_blocks, cudaStream_t st);
+                        int small_max_blocks, cudaStream_t st);
 void launch_pack_sources32(int layer, const EvalBufs& b, double scale, cudaStream_t st);
 void launch_pack_sources64(int layer, const EvalBufs& b, double scale, cudaStream_t st);
 void launch_pack_targets32(const EvalBufs& b, int64_t n_delta, double rho_T, double rho_c,

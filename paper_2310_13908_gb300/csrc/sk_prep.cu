@@ -174,19 +174,63 @@ __device__ void rs_scan_block(uint32_t* __restrict__ a, int total, uint32_t* war
   }
 }
 
-template <int THREADS>
-__global__ void __launch_bounds__(THREADS) k_rs_scan(uint32_t* __restrict__ a, int total) {
-  __shared__ uint32_t warp_sums[32];
-  rs_scan_block<THREADS>(a, total, warp_sums);
+// Inclusive scan of one value per thread over a block of RS_THREADS threads;
+// *total gets the block's sum. Ends with the block synchronized, so the
+// warp_sums scratch can be reused at once.
+__device__ __forceinline__ uint32_t block_scan_incl(uint32_t v, uint32_t* warp_sums,
+                                                   uint32_t* total) {
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  uint32_t x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(FULL, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_sums[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    uint32_t s = lane < RS_THREADS / 32 ? warp_sums[lane] : 0u;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(FULL, s, o);
+      if (lane >= o) s += y;
+    }
+    if (lane < RS_THREADS / 32) warp_sums[lane] = s;  // inclusive over warps
+  }
+  __syncthreads();
+  const uint32_t r = (wid > 0 ? warp_sums[wid - 1] : 0u) + x;
+  *total = warp_sums[RS_THREADS / 32 - 1];
+  __syncthreads();
+  return r;
 }
 
-// Stable scatter of tile blk (of nblk) to the offsets of column blk of offs.
+// Per digit d = blockIdx.x (one block per digit): exclusive scan, in place,
+// of row d of hist[256][nblk] (contiguous, so the loads are coalesced), and
+// the row's total into tot[d]. With the exclusive scan of tot (done by each
+// scatter block), offset(d, b) = sum of tot below d + row prefix (d, b): the
+// same integers as one scan of the whole flattened array.
+__global__ void __launch_bounds__(RS_THREADS) k_rs_rowscan(uint32_t* __restrict__ hist, int nblk,
+                                                           uint32_t* __restrict__ tot) {
+  __shared__ uint32_t warp_sums[RS_THREADS / 32];
+  uint32_t* row = hist + (size_t)blockIdx.x * nblk;
+  uint32_t carry = 0;
+  for (int base = 0; base < nblk; base += RS_THREADS) {
+    const int i = base + threadIdx.x;
+    const uint32_t v = i < nblk ? row[i] : 0u;
+    uint32_t sum;
+    const uint32_t incl = block_scan_incl(v, warp_sums, &sum);
+    if (i < nblk) row[i] = carry + incl - v;
+    carry += sum;
+  }
+  if (threadIdx.x == 0) tot[blockIdx.x] = carry;
+}
+
+// Stable scatter of tile blk (of nblk) to the offsets of column blk of offs,
+// plus digit_base (this thread's digit) when offs holds row prefixes only.
 __device__ void rs_scatter_tile(const uint32_t* __restrict__ kin, const int* __restrict__ vin,
                                 uint32_t* __restrict__ kout, int* __restrict__ vout, int n,
-                                int shift, const uint32_t* __restrict__ offs, int blk, int nblk,
-                                uint32_t* base_d, uint32_t (*wcnt)[256]) {
+                                int shift, const uint32_t* __restrict__ offs, uint32_t digit_base,
+                                int blk, int nblk, uint32_t* base_d, uint32_t (*wcnt)[256]) {
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  base_d[tid] = offs[tid * nblk + blk];
+  base_d[tid] = offs[tid * nblk + blk] + digit_base;
   const unsigned lt = (1u << lane) - 1u;
   const int base = blk * RS_TILE;
   for (int r = 0; r < RS_ITEMS; ++r) {
@@ -215,12 +259,20 @@ __device__ void rs_scatter_tile(const uint32_t* __restrict__ kin, const int* __r
   }
 }
 
-__global__ void k_rs_scatter(const uint32_t* __restrict__ kin, const int* __restrict__ vin,
-                             uint32_t* __restrict__ kout, int* __restrict__ vout, int n, int shift,
-                             const uint32_t* __restrict__ offs) {
+// offs: row prefixes from k_rs_rowscan; tot: the rows' totals.
+__global__ void __launch_bounds__(RS_THREADS)
+    k_rs_scatter(const uint32_t* __restrict__ kin, const int* __restrict__ vin,
+                 uint32_t* __restrict__ kout, int* __restrict__ vout, int n, int shift,
+                 const uint32_t* __restrict__ offs, const uint32_t* __restrict__ tot) {
+  static_assert(RS_THREADS == 256, "one thread per digit");
   __shared__ uint32_t base_d[256];
   __shared__ uint32_t wcnt[RS_THREADS / 32][256];
-  rs_scatter_tile(kin, vin, kout, vout, n, shift, offs, blockIdx.x, gridDim.x, base_d, wcnt);
+  __shared__ uint32_t warp_sums[RS_THREADS / 32];
+  const uint32_t t = tot[threadIdx.x];
+  uint32_t all;
+  const uint32_t digit_base = block_scan_incl(t, warp_sums, &all) - t;
+  rs_scatter_tile(kin, vin, kout, vout, n, shift, offs, digit_base, blockIdx.x, gridDim.x, base_d,
+                  wcnt);
 }
 
 // The whole ordering of a small point set in one block of RS_THREADS threads:
@@ -265,7 +317,7 @@ __global__ void __launch_bounds__(RS_THREADS)
     rs_scan_block<RS_THREADS>(hist, 256 * nblk, warp_sums);
     __syncthreads();
     for (int b = 0; b < nblk; ++b)
-      rs_scatter_tile(ka, va, kb, vb, (int)n, shift, hist, b, nblk, base_d, wcnt);
+      rs_scatter_tile(ka, va, kb, vb, (int)n, shift, hist, 0u, b, nblk, base_d, wcnt);
     uint32_t* tk = ka; ka = kb; kb = tk;
     int* tv = va; va = vb; vb = tv;
   }
@@ -423,7 +475,7 @@ int sort_grid_blocks(int64_t n) { return (int)((n + RS_TILE - 1) / RS_TILE); }
 void launch_sort_points(const double* xyz, const double* w, int64_t n, uint32_t* keys_a,
                         uint32_t* keys_b, int* vals_a, int* vals_b, uint32_t* hist,
                         float* bbox_part, float* bbox, int* count_out, int sort_blocks,
-                        bool narrow, int small_max_blocks, cudaStream_t st) {
+                        int small_max_blocks, cudaStream_t st) {
   if (n <= 0) return;
   if (sort_blocks <= small_max_blocks) {
     k_sort_small<<<1, RS_THREADS, 0, st>>>(xyz, w, n, keys_a, keys_b, vals_a, vals_b, hist, bbox,
@@ -433,15 +485,13 @@ void launch_sort_points(const double* xyz, const double* w, int64_t n, uint32_t*
   k_bbox_partial<<<BBOX_BLOCKS, RS_THREADS, 0, st>>>(xyz, w, n, bbox_part);
   k_bbox_final<<<1, 32, 0, st>>>(bbox_part, BBOX_BLOCKS, bbox);
   k_morton_keys<<<blocks_for(n, 256), 256, 0, st>>>(xyz, w, n, bbox, keys_a, vals_a, count_out);
+  uint32_t* tot = hist + 256 * (size_t)sort_blocks;  // row totals (hist holds 256 more words)
   uint32_t *ka = keys_a, *kb = keys_b;
   int *va = vals_a, *vb = vals_b;
   for (int shift = 0; shift < 32; shift += 8) {
     k_rs_hist<<<sort_blocks, RS_THREADS, 0, st>>>(ka, (int)n, shift, hist);
-    if (narrow)
-      k_rs_scan<RS_THREADS><<<1, RS_THREADS, 0, st>>>(hist, 256 * sort_blocks);
-    else
-      k_rs_scan<1024><<<1, 1024, 0, st>>>(hist, 256 * sort_blocks);
-    k_rs_scatter<<<sort_blocks, RS_THREADS, 0, st>>>(ka, va, kb, vb, (int)n, shift, hist);
+    k_rs_rowscan<<<256, RS_THREADS, 0, st>>>(hist, sort_blocks, tot);
+    k_rs_scatter<<<sort_blocks, RS_THREADS, 0, st>>>(ka, va, kb, vb, (int)n, shift, hist, tot);
     uint32_t* tk = ka; ka = kb; kb = tk;
     int* tv = va; va = vb; vb = tv;
   }
