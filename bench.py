@@ -64,6 +64,9 @@ def parse_args():
                     help="timed step: single layer (default) or double layer (q = the SH "
                          "density); extras run only for the default sl/fp32c step")
     ap.add_argument("--precision", choices=["fp32c", "fp64"], default="fp32c")
+    ap.add_argument("--membrane-only", action="store_true",
+                    help="time only the Skalak membrane force on the stress-free ellipsoid "
+                         "(0.9, 1, 1) of grid order --m, and print that line")
     return ap.parse_args()
 
 
@@ -245,6 +248,8 @@ def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.membrane_only:
+        return membrane_only(args)
     rank, world, local = dist_env()
     import torch
     import paper_2310_13908_gb300 as sk
@@ -519,6 +524,35 @@ def serving_bench(sk, h, reqs):
                                "ginter_per_s": inter / wall / 1e9, "wall_s": wall,
                                "mean_phase_ms": run_serving.last_phases_ms}
     return res
+
+
+def membrane_only(args, Es=2.0, ED=20.0, reps=10):
+    """membrane_force (overset FD derivatives + Skalak tension + divergence,
+    FP64) on a deformed ellipsoid (0.9, 1, 1) of order args.m, device memory,
+    CUDA events; one JSON line."""
+    import torch
+    import capsule_inputs as ci
+    import paper_2310_13908_gb300 as sk
+    dev = torch.device("cuda", 0)
+    ref = ci.make_surface(ci.Ellipsoid(0.9, 1.0, 1.0), args.m)
+    Xd = torch.as_tensor(ref.X * np.array([1.02, 0.99, 1.0]), device=dev)
+    Xr = torch.as_tensor(ref.X, device=dev)
+    with sk.Context(0) as c:
+        for _ in range(max(args.warmup, 1)):
+            sk.membrane_force(c.handle, args.m, sk.SK_DEVICE, Xd, Xr, Es, ED)
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            sk.membrane_force(c.handle, args.m, sk.SK_DEVICE, Xd, Xr, Es, ED)
+        b.record()
+        torch.cuda.synchronize(dev)
+    print(json.dumps({"metric": "membrane_force_ms", "value": a.elapsed_time(b) / reps,
+                      "unit": "ms", "higher_is_better": False,
+                      "config": {"workload": f"ellipsoid(0.9,1,1) m={args.m} (N={ref.N}) "
+                                             f"stretched (1.02, 0.99, 1), Es={Es}, ED={ED}, FP64"}}),
+          flush=True)
+    return 0
 
 
 def capsule_bench(sk, h, torch, dev, m=129, steps=100, dt=5e-4, Es=2.0, ED=20.0):

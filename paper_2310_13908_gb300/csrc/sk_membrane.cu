@@ -51,7 +51,7 @@ struct MembraneOp {
   int* btap_ptr = nullptr;     // [N + 1]
   int* btap_cell = nullptr;
   double* btap_w = nullptr;    // [taps][13]: basis[8], psi, dtau1/du, dtau2/du, dtau1/dv, dtau2/dv
-  double* thomas = nullptr;    // [2 n]: c' and 1/den of the reduced slope system
+  double* thomas = nullptr;    // slope-solve table (see k_slopes): c', 1/den, run products, 3/h 1/den
   // scratch for up to MEM_FMAX fields
   double *g = nullptr, *sg = nullptr;    // values, spline data [3][F][N] (u, v, uv slopes)
   double* ext = nullptr;                 // [F][6][E][E]
@@ -179,88 +179,112 @@ int h_cell_basis(int p, int n, double h, double u, double v, double basis[8]) {
 // Device kernels.
 inline unsigned blocks_of(int64_t n) { return (unsigned)((n + 255) / 256); }
 
-// Not-a-knot cubic-spline slopes, one warp per grid line. Lines: for dir 0
-// the u-lines (fixed k, stride n), for dir 1 the v-lines (fixed j). With
-// uniform spacing the end conditions read s0 + 2 s1 = (-5 g0 + 4 g1 + g2)/2h
-// and 2 s_{n-2} + s_{n-1} = (5 g_{n-1} - 4 g_{n-2} - g_{n-3})/2h; eliminating
-// s0 and s_{n-1} leaves a diagonally dominant tridiagonal system in
-// s1..s_{n-2} whose factorization (thomas: c'_q, 1/den_q) is shared by all
-// lines. Both sweeps of the solve are affine recurrences,
-//   forward   d_q = -(1/den_q) d_{q-1} + rhs_q / den_q,
+// Not-a-knot cubic-spline slopes, SLOPE_LPL lanes per grid line. Lines: for
+// dir 0 the u-lines (fixed k, stride n), for dir 1 the v-lines (fixed j).
+// With uniform spacing the end conditions read s0 + 2 s1 = (-5 g0 + 4 g1 +
+// g2)/2h and 2 s_{n-2} + s_{n-1} = (5 g_{n-1} - 4 g_{n-2} - g_{n-3})/2h;
+// eliminating s0 and s_{n-1} leaves a diagonally dominant tridiagonal system
+// in s1..s_{n-2} whose factorization (c'_q, 1/den_q) is shared by all lines.
+// Both sweeps of the solve are affine recurrences,
+//   forward   d_q = -(1/den_q) d_{q-1} + v_q,   v_q = rhs_q / den_q,
 //   backward  s_q = -c'_q s_{q+1} + d_q,
-// each with |multiplier| <= 1/2. Each lane composes the maps of its own run
-// of consecutive terms, a warp scan of the lane aggregates (composition
-// (a2, b2) o (a1, b1) = (a2 a1, a2 b1 + b2)) gives every lane its incoming
-// value, and the lane then replays its run.
-__device__ __forceinline__ void affine_scan(double& a, double& b, int lane) {
+// each with |multiplier| <= 1/2. Each lane takes a run of consecutive terms
+// and composes their maps ((a2, b2) o (a1, b1) = (a2 a1, a2 b1 + b2)); the
+// product of a run's multipliers does not depend on the data and comes from
+// the table. A scan over the line's lanes gives each lane its incoming value,
+// and the lane replays its run. v_q is computed once (stored in s, then
+// overwritten by d_q and s_q).
+// L lanes per line (8, 16 or 32): fewer lanes cost fewer scan steps, more
+// lanes give short lines and small grids enough threads (slope_lanes). Table (thomas): [c' (n) | 1/den (n) |
+// 3/h * 1/den (n) | for L = 8, 16, 32: forward then backward run products (L
+// each)].
+constexpr int SLOPE_LPL_MIN = 8, SLOPE_LPL_MAX = 32;
+__host__ __device__ constexpr int slope_products_offset(int n, int L) {
+  return 3 * n + 2 * (L - SLOPE_LPL_MIN);  // L = 8: 0, 16: 16, 32: 48
+}
+constexpr int SLOPE_TABLE_EXTRA = 2 * (8 + 16 + 32);
+constexpr int SLOPE_TPB = 128;
+
+template <int L>
+__device__ __forceinline__ void affine_scan_lines(double& a, double& b, int sub) {
 #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const double pa = __shfl_up_sync(0xffffffffu, a, o);
-    const double pb = __shfl_up_sync(0xffffffffu, b, o);
-    if (lane >= o) {
-      b = a * pb + b;
+  for (int o = 1; o < L; o <<= 1) {
+    const double pa = __shfl_up_sync(0xffffffffu, a, o, L);
+    const double pb = __shfl_up_sync(0xffffffffu, b, o, L);
+    if (sub >= o) {
+      b = fma(a, pb, b);
       a = a * pa;
     }
   }
 }
 
-__global__ void k_slopes(const double* __restrict__ g, double* __restrict__ s, int64_t n_lines,
-                         int n, int dir, double ih, const double* __restrict__ thomas) {
-  const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (t >= n_lines) return;  // whole warps leave together
-  const int64_t fp = t / n;
-  const int r = (int)(t % n);
+template <int L>
+__global__ void __launch_bounds__(SLOPE_TPB)
+    k_slopes(const double* __restrict__ g, double* __restrict__ s, int64_t n_lines, int n,
+             int dir, double ih, const double* __restrict__ thomas) {
+  const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / L;
+  const int sub = threadIdx.x % L;
+  // lanes past the last line compute a copy of it (every lane takes part in
+  // the shuffles) and store nothing
+  const bool live = t < n_lines;
+  const int64_t line = live ? t : n_lines - 1;
+  const int64_t fp = line / n;
+  const int r = (int)(line % n);
   const int64_t base = fp * n * n + (dir == 0 ? r : (int64_t)r * n);
   const int64_t st = dir == 0 ? n : 1;
   const double* cp = thomas;
   const double* iden = thomas + n;
-  const double i2h = 0.5 * ih, i3h = 3.0 * ih;
-  const double r0 = (-5.0 * g[base] + 4.0 * g[base + st] + g[base + 2 * st]) * i2h;
-  const double rN =
-      (5.0 * g[base + (n - 1) * st] - 4.0 * g[base + (n - 2) * st] - g[base + (n - 3) * st]) *
-      i2h;
-  const int K = (n - 2 + 31) / 32;          // terms per lane
-  const int qa = 1 + lane * K;              // this lane's run [qa, qb) of q = 1..n-2
+  const double* i3d = thomas + 2 * n;
+  const double* afw = thomas + slope_products_offset(n, L);
+  const double* abw = afw + L;
+  const double i2h = 0.5 * ih;
+  const int K = (n - 2 + L - 1) / L;  // terms per lane
+  const int qa = 1 + sub * K;         // this lane's run [qa, qb) of q = 1..n-2
   const int qb = min(qa + K, n - 1);
+  double c1 = 0.0, cN = 0.0;          // end-condition terms of v_1 and v_{n-2}
+  if (qa == 1)
+    c1 = (-5.0 * g[base] + 4.0 * g[base + st] + g[base + 2 * st]) * i2h * iden[1];
+  if (qa < qb && qb == n - 1)
+    cN = (5.0 * g[base + (n - 1) * st] - 4.0 * g[base + (n - 2) * st] - g[base + (n - 3) * st]) *
+         i2h * iden[n - 2];
   // forward sweep
-  double A = 1.0, B = 0.0;
+  double B = 0.0;
   for (int q = qa; q < qb; ++q) {
-    const double rhs = i3h * (g[base + (q + 1) * st] - g[base + (q - 1) * st]) -
-                       (q == 1 ? r0 : 0.0) - (q == n - 2 ? rN : 0.0);
-    const double a = q == 1 ? 0.0 : -iden[q];
-    B = a * B + rhs * iden[q];
-    A = a * A;
+    const double cq = q == 1 ? c1 : (q == n - 2 ? cN : 0.0);
+    const double v = fma(i3d[q], g[base + (q + 1) * st] - g[base + (q - 1) * st], -cq);
+    B = fma(q == 1 ? 0.0 : -iden[q], B, v);
+    if (live) s[base + q * st] = v;
   }
-  affine_scan(A, B, lane);
-  double x = __shfl_up_sync(0xffffffffu, B, 1);
-  if (lane == 0) x = 0.0;
+  double A = afw[sub];
+  affine_scan_lines<L>(A, B, sub);
+  double x = __shfl_up_sync(0xffffffffu, B, 1, L);
+  if (sub == 0) x = 0.0;
   for (int q = qa; q < qb; ++q) {
-    const double rhs = i3h * (g[base + (q + 1) * st] - g[base + (q - 1) * st]) -
-                       (q == 1 ? r0 : 0.0) - (q == n - 2 ? rN : 0.0);
-    x = (q == 1 ? 0.0 : -iden[q]) * x + rhs * iden[q];
-    s[base + q * st] = x;
+    x = fma(q == 1 ? 0.0 : -iden[q], x, s[base + q * st]);
+    if (live) s[base + q * st] = x;
   }
   __syncwarp();
   // backward sweep over p = 1..n-2, q = n-1-p (s_{n-2} = d_{n-2})
-  A = 1.0;
   B = 0.0;
   for (int p = qa; p < qb; ++p) {
     const int q = n - 1 - p;
-    const double a = q == n - 2 ? 0.0 : -cp[q];
-    B = a * B + s[base + q * st];
-    A = a * A;
+    B = fma(q == n - 2 ? 0.0 : -cp[q], B, s[base + q * st]);
   }
-  affine_scan(A, B, lane);
-  x = __shfl_up_sync(0xffffffffu, B, 1);
-  if (lane == 0) x = 0.0;
+  A = abw[sub];
+  affine_scan_lines<L>(A, B, sub);
+  x = __shfl_up_sync(0xffffffffu, B, 1, L);
+  if (sub == 0) x = 0.0;
   for (int p = qa; p < qb; ++p) {
     const int q = n - 1 - p;
-    x = (q == n - 2 ? 0.0 : -cp[q]) * x + s[base + q * st];
-    s[base + q * st] = x;
+    x = fma(q == n - 2 ? 0.0 : -cp[q], x, s[base + q * st]);
+    if (live) s[base + q * st] = x;
   }
   __syncwarp();
-  if (lane == 0) {
+  if (sub == 0 && live) {
+    const double r0 = (-5.0 * g[base] + 4.0 * g[base + st] + g[base + 2 * st]) * i2h;
+    const double rN =
+        (5.0 * g[base + (n - 1) * st] - 4.0 * g[base + (n - 2) * st] - g[base + (n - 3) * st]) *
+        i2h;
     s[base] = r0 - 2.0 * s[base + st];
     s[base + (n - 1) * st] = rN - 2.0 * s[base + (n - 2) * st];
   }
@@ -685,8 +709,9 @@ int build_op(int m, MembraneOp** out, std::string& err) {
         bptr.push_back((int)bcell.size());
       }
   // factorization of the reduced slope system: rows q = 1..n-2 with
-  // (sub, diag, super) = (-, 2, 1), (1, 4, 1) ..., (1, 2, -)
-  std::vector<double> th(2 * n, 0.0);
+  // (sub, diag, super) = (-, 2, 1), (1, 4, 1) ..., (1, 2, -); then the
+  // 3/h * 1/den and the products of each lane run's multipliers (k_slopes)
+  std::vector<double> th(3 * n + SLOPE_TABLE_EXTRA, 0.0);
   for (int q = 1; q <= n - 2; ++q) {
     const double b = (q == 1 || q == n - 2) ? 2.0 : 4.0;
     const double a = q == 1 ? 0.0 : 1.0;
@@ -694,6 +719,24 @@ int build_op(int m, MembraneOp** out, std::string& err) {
     const double den = b - a * (q > 1 ? th[q - 1] : 0.0);
     th[q] = c / den;
     th[n + q] = 1.0 / den;
+  }
+  {
+    const double i3h = 3.0 / h;
+    for (int q = 1; q <= n - 2; ++q) th[2 * n + q] = i3h * th[n + q];
+    for (int L = SLOPE_LPL_MIN; L <= SLOPE_LPL_MAX; L *= 2) {
+      const int K = (n - 2 + L - 1) / L, off = slope_products_offset(n, L);
+      for (int r = 0; r < L; ++r) {
+        const int qa = 1 + r * K, qb = std::min(qa + K, n - 1);
+        double pf = 1.0, pb = 1.0;
+        for (int q = qa; q < qb; ++q) pf *= q == 1 ? 0.0 : -th[n + q];
+        for (int p = qa; p < qb; ++p) {
+          const int q = n - 1 - p;
+          pb *= q == n - 2 ? 0.0 : -th[q];
+        }
+        th[off + r] = pf;
+        th[off + L + r] = pb;
+      }
+    }
   }
   cudaError_t e = cudaSuccess;
   auto ok = [&](cudaError_t x) {
@@ -786,14 +829,35 @@ int ensure_upsampling(MembraneOp* op, std::string& err) {
   return SK_OK;
 }
 
+#ifndef SK_SLOPE_LANES
+#define SK_SLOPE_LANES 0  // 0: by size (below); 8, 16 or 32: fixed
+#endif
+// Lanes per line by line length n, as measured for the membrane force (8 /
+// 16 / 32 lanes): m = 65: 0.54 / 0.46 / 0.50 ms; m = 129: 1.00 / 0.95 /
+// 1.09 ms; m = 257: 2.71 / 3.24 / 2.97 ms (32 lanes was the earlier kernel's
+// layout: 0.55, 1.30, 3.62 ms with its redundant arithmetic).
+inline int slope_lanes(int n) {
+  if (SK_SLOPE_LANES) return SK_SLOPE_LANES;
+  return n <= 160 ? 16 : 8;
+}
+
 // Spline data (u, v, uv slopes) of F fields in `val` into `sd` ([3][F][N]).
 void enqueue_splines(const MembraneOp& op, int F, const double* val, double* sd, cudaStream_t st) {
   const int64_t plane = (int64_t)F * op.N;
   const int64_t lines = (int64_t)F * 6 * op.n;
-  const unsigned nb = blocks_of(32 * lines);  // one warp per line
-  k_slopes<<<nb, 256, 0, st>>>(val, sd, lines, op.n, 0, op.ih, op.thomas);
-  k_slopes<<<nb, 256, 0, st>>>(val, sd + plane, lines, op.n, 1, op.ih, op.thomas);
-  k_slopes<<<nb, 256, 0, st>>>(sd, sd + 2 * plane, lines, op.n, 1, op.ih, op.thomas);
+  const int L = slope_lanes(op.n);
+  const unsigned nb = (unsigned)((L * lines + SLOPE_TPB - 1) / SLOPE_TPB);
+  auto run = [&](const double* in, double* out, int dir) {
+    if (L == 8)
+      k_slopes<8><<<nb, SLOPE_TPB, 0, st>>>(in, out, lines, op.n, dir, op.ih, op.thomas);
+    else if (L == 16)
+      k_slopes<16><<<nb, SLOPE_TPB, 0, st>>>(in, out, lines, op.n, dir, op.ih, op.thomas);
+    else
+      k_slopes<32><<<nb, SLOPE_TPB, 0, st>>>(in, out, lines, op.n, dir, op.ih, op.thomas);
+  };
+  run(val, sd, 0);
+  run(val, sd + plane, 1);
+  run(sd, sd + 2 * plane, 1);
 }
 
 }  // namespace
