@@ -60,10 +60,10 @@ typedef struct sk_ctx sk_ctx;
  * context grow its device workspace on demand; > 0 preallocates exactly
  * that much and never grows it (calls needing more return SK_ENOMEM).
  * The context owns one CUDA stream and its workspace. *out is set to NULL
- * on failure. The environment variable SK_SMALL_SORT_BLOCKS (an integer
- * 0..1024, read here) sets the largest point set, in radix tiles of 2048
- * points, that is ordered by the single-block sort (default 4; 0: always the
- * multi-block sort); results do not depend on it. */
+ * on failure. The environment variable SK_SMALL_SORT_POINTS (an integer
+ * 0..2^24, read here) sets the largest point set that is ordered by the
+ * single-block sort (default 3072; 0: always the multi-block sort); results
+ * do not depend on it. */
 int sk_create(sk_ctx** out, int device, size_t workspace_bytes);
 
 /* Release the context, its stream and workspace. NULL is ignored. */

@@ -175,7 +175,7 @@ int enqueue_prep(const EvalShape& s, const EvalBufs& b, double rho_T, double rho
   const bool fp32 = s.precision == SK_FP32C;
   const double scale = layer_scale(s);
   // bbox (2) + keys + 4 radix passes x 3 (hist, row scan, scatter), or the single-block sort
-  const int SORT_LAUNCHES = b.sort_blocks <= s.small_sort_blocks ? 1 : 3 + 4 * 3;
+  auto sort_launches = [&](int64_t n) { return n <= s.small_sort_points ? 1 : 3 + 4 * 3; };
   int launches = 0;
   cudaMemsetAsync(b.flags, 0, N_FLAGS * sizeof(unsigned long long), st);
   cudaMemsetAsync(b.meta, 0, N_META * sizeof(int), st);
@@ -184,18 +184,16 @@ int enqueue_prep(const EvalShape& s, const EvalBufs& b, double rho_T, double rho
   launches += 1;
   if (s.N > 0) {
     launch_sort_points(b.src_xyz, b.src_w, s.N, b.keys_a, b.keys_b, b.vals_a, b.vals_b, b.hist,
-                       b.bbox_part, b.bbox, b.meta + META_NS, b.sort_blocks,
-                       s.small_sort_blocks, st);
+                       b.bbox_part, b.bbox, b.meta + META_NS, s.small_sort_points, st);
     if (fp32)
       launch_pack_sources32(s.layer, b, scale, st);
     else
       launch_pack_sources64(s.layer, b, scale, st);
-    launches += SORT_LAUNCHES + 1;
+    launches += sort_launches(s.N) + 1;
   }
   launch_sort_points(b.tgt_xyz, nullptr, s.M, b.keys_a, b.keys_b, b.vals_a, b.vals_b, b.hist,
-                     b.bbox_part, b.bbox, b.meta + META_SCRATCH, b.sort_blocks,
-                     s.small_sort_blocks, st);
-  launches += SORT_LAUNCHES;
+                     b.bbox_part, b.bbox, b.meta + META_SCRATCH, s.small_sort_points, st);
+  launches += sort_launches(s.M);
   if (fp32)
     launch_pack_targets32(b, s.n_delta, rho_T, rho_c, st);
   else
@@ -275,11 +273,11 @@ int sk_create(sk_ctx** out, int device, size_t workspace_bytes) {
   }
   std::memset(ctx->h_flags, 0, 256);
   ctx->last_stream = ctx->stream;
-  ctx->small_sort_blocks = SMALL_SORT_BLOCKS;
-  if (const char* v = std::getenv("SK_SMALL_SORT_BLOCKS")) {
+  ctx->small_sort_points = SMALL_SORT_POINTS;
+  if (const char* v = std::getenv("SK_SMALL_SORT_POINTS")) {
     char* end = nullptr;
-    const long k = std::strtol(v, &end, 10);
-    if (end != v && *end == '\0' && k >= 0 && k <= 1024) ctx->small_sort_blocks = (int)k;
+    const long long k = std::strtoll(v, &end, 10);
+    if (end != v && *end == '\0' && k >= 0 && k <= (1LL << 24)) ctx->small_sort_points = k;
   }
   *out = ctx;
   return SK_OK;
@@ -411,7 +409,7 @@ int eval_entry(sk_ctx* ctx, int layer, int precision, int mem, int64_t N, const 
   s.n_delta = n_delta;
   s.mu = mu;
   s.copy_inputs = mem == SK_HOST;
-  s.small_sort_blocks = ctx->small_sort_blocks;
+  s.small_sort_points = ctx->small_sort_points;
   choose_decomposition(s, ctx->sm_count);
   const size_t need = eval_workspace_bytes(s);
   int rc = ensure_workspace(ctx, need);

@@ -213,7 +213,7 @@ EvalShape capsule_shape(const sk_capsule* c) {
     s.N = c->N;
     s.n_delta = c->n_delta;
   }
-  s.small_sort_blocks = c->ctx->small_sort_blocks;
+  s.small_sort_points = c->ctx->small_sort_points;
   choose_decomposition(s, c->ctx->sm_count);
   return s;
 }

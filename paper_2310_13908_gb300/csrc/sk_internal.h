@@ -165,7 +165,7 @@ struct sk_ctx {
   double rho_T = 0.5;
   double rho_c = 5.0;
   bool profile = false;
-  int small_sort_blocks = 0;  // single-block sort limit (sk::SMALL_SORT_BLOCKS unless overridden)
+  int64_t small_sort_points = 0;  // single-block sort limit (sk::SMALL_SORT_POINTS unless overridden)
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // eval begin, pair begin/end, eval end
   sk_eval_stats stats{};
   std::vector<std::pair<int, sk::MembraneOp*>> membrane_ops;  // derivative operators by m
@@ -175,10 +175,12 @@ struct sk_ctx {
 
 namespace sk {
 
-// Largest point set (in radix-sort tiles of 2048 points) ordered by the
-// single-block sort by default; SK_SMALL_SORT_BLOCKS in the environment of
-// sk_create overrides it per context (0 turns it off)
-constexpr int SMALL_SORT_BLOCKS = 4;
+// Largest point set ordered by the single-block sort by default;
+// SK_SMALL_SORT_POINTS in the environment of sk_create overrides it per
+// context (0 turns it off). Measured: one block costs ~24 us more per extra
+// 1024-point tile than the fifteen multi-block launches, and saves ~30 us at
+// two tiles, so the break-even is near three tiles.
+constexpr int64_t SMALL_SORT_POINTS = 3072;
 
 // CTA size of the FP64 pair kernel for problems too small to fill the GPU
 // with TPB64-thread CTAs (TPL64 targets per lane in both)
@@ -193,9 +195,9 @@ struct EvalShape {
   bool copy_inputs = false;  // inputs/outputs live in the workspace (host-memory calls)
   int n_chunks = 1;
   int threads64 = TPB64;  // CTA size of the FP64 pair kernel (TPB64 or TPB64_SMALL)
-  // point sets of at most this many radix-sort tiles are ordered by one
-  // single-block kernel instead of fifteen launches (0: never)
-  int small_sort_blocks = SMALL_SORT_BLOCKS;
+  // point sets of at most this many points are ordered by one single-block
+  // kernel instead of fifteen launches (0: never)
+  int64_t small_sort_points = SMALL_SORT_POINTS;
 };
 
 // sk_api.cu
@@ -218,8 +220,8 @@ int enqueue_eval(const EvalShape& s, const EvalBufs& b, double rho_T, double rho
 // launchers (sk_prep.cu)
 void launch_sort_points(const double* xyz, const double* w, int64_t n, uint32_t* keys_a,
                         uint32_t* keys_b, int* vals_a, int* vals_b, uint32_t* hist,
-                        float* bbox_part, float* bbox, int* count_out, int sort_blocks,
-                        int small_max_blocks, cudaStream_t st);
+                        float* bbox_part, float* bbox, int* count_out, int64_t small_max_points,
+                        cudaStream_t st);
 void launch_pack_sources32(int layer, const EvalBufs& b, double scale, cudaStream_t st);
 void launch_pack_sources64(int layer, const EvalBufs& b, double scale, cudaStream_t st);
 void launch_pack_targets32(const EvalBufs& b, int64_t n_delta, double rho_T, double rho_c,

@@ -15,8 +15,11 @@ namespace sk {
 
 namespace {
 
+#ifndef SK_RS_ITEMS
+#define SK_RS_ITEMS 4
+#endif
 constexpr int RS_THREADS = 256;
-constexpr int RS_ITEMS = 8;
+constexpr int RS_ITEMS = SK_RS_ITEMS;  // keys per thread and radix tile
 constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
 constexpr int BBOX_BLOCKS = 128;
 constexpr unsigned FULL = 0xffffffffu;
@@ -64,12 +67,18 @@ __global__ void k_bbox_partial(const double* __restrict__ xyz, const double* __r
   if (threadIdx.x < 6) part[blockIdx.x * 6 + threadIdx.x] = v;
 }
 
+// One warp per box component (6 warps): lanes stride over the partial boxes,
+// then a shuffle reduction.
 __global__ void k_bbox_final(const float* __restrict__ part, int nblk, float* __restrict__ bbox) {
-  int c = threadIdx.x;
-  if (c >= 6) return;
+  const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (c >= 6) return;  // whole warps
   float v = c < 3 ? FLT_MAX : -FLT_MAX;
-  for (int b = 0; b < nblk; ++b) v = c < 3 ? fminf(v, part[b * 6 + c]) : fmaxf(v, part[b * 6 + c]);
-  bbox[c] = v;
+  for (int b = lane; b < nblk; b += 32) v = c < 3 ? fminf(v, part[b * 6 + c]) : fmaxf(v, part[b * 6 + c]);
+  for (int o = 16; o > 0; o >>= 1) {
+    const float w = __shfl_xor_sync(FULL, v, o);
+    v = c < 3 ? fminf(v, w) : fmaxf(v, w);
+  }
+  if (lane == 0) bbox[c] = v;
 }
 
 // Spread the low 10 bits of v so that bit i lands at bit 3i.
@@ -474,16 +483,19 @@ int sort_grid_blocks(int64_t n) { return (int)((n + RS_TILE - 1) / RS_TILE); }
 
 void launch_sort_points(const double* xyz, const double* w, int64_t n, uint32_t* keys_a,
                         uint32_t* keys_b, int* vals_a, int* vals_b, uint32_t* hist,
-                        float* bbox_part, float* bbox, int* count_out, int sort_blocks,
-                        int small_max_blocks, cudaStream_t st) {
+                        float* bbox_part, float* bbox, int* count_out, int64_t small_max_points,
+                        cudaStream_t st) {
   if (n <= 0) return;
-  if (sort_blocks <= small_max_blocks) {
+  // tiles of this point set (at most the sort_grid_blocks the buffers hold);
+  // the stable order does not depend on the tiling or on the path
+  const int sort_blocks = sort_grid_blocks(n);
+  if (n <= small_max_points) {
     k_sort_small<<<1, RS_THREADS, 0, st>>>(xyz, w, n, keys_a, keys_b, vals_a, vals_b, hist, bbox,
                                            count_out, sort_blocks);
     return;  // four passes: the sorted data is in keys_a / vals_a
   }
   k_bbox_partial<<<BBOX_BLOCKS, RS_THREADS, 0, st>>>(xyz, w, n, bbox_part);
-  k_bbox_final<<<1, 32, 0, st>>>(bbox_part, BBOX_BLOCKS, bbox);
+  k_bbox_final<<<1, 6 * 32, 0, st>>>(bbox_part, BBOX_BLOCKS, bbox);
   k_morton_keys<<<blocks_for(n, 256), 256, 0, st>>>(xyz, w, n, bbox, keys_a, vals_a, count_out);
   uint32_t* tot = hist + 256 * (size_t)sort_blocks;  // row totals (hist holds 256 more words)
   uint32_t *ka = keys_a, *kb = keys_b;

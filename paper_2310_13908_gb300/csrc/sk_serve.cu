@@ -653,7 +653,7 @@ int serve_submit(sk_server* srv, const sk_request* q, uint64_t* ticket) {
   s.n_delta = q->n_delta;
   s.mu = q->mu;
   s.copy_inputs = true;
-  s.small_sort_blocks = srv->ctx->small_sort_blocks;
+  s.small_sort_points = srv->ctx->small_sort_points;
   s.n_chunks = choose_chunks(SK_FP32C, N, M, srv->ctx->sm_count);
   const int n_tb = (int)(align_up((size_t)M, TGT_CTA32) / SERVE_TGT_CTA);
   r->footprint = request_footprint(s, n_tb);

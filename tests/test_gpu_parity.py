@@ -347,23 +347,25 @@ def test_single_block_sort_matches_multi_block_sort(ctx):
     """Small point sets are ordered by one single-block kernel, larger ones by
     fifteen launches; both run the same per-tile code, so the sorted order,
     and hence every result, is the same bit for bit. A second context with the
-    single-block path turned off (SK_SMALL_SORT_BLOCKS=0) gives the reference;
-    sizes cover 1, ragged tiles, the 4-tile limit and zero-weight sources."""
+    single-block path turned off (SK_SMALL_SORT_POINTS=0) gives the reference;
+    sizes cover 1, ragged tiles, both sides of the point limit and zero-weight
+    sources."""
     import os
-    old = os.environ.get("SK_SMALL_SORT_BLOCKS")
-    os.environ["SK_SMALL_SORT_BLOCKS"] = "0"
+    old = os.environ.get("SK_SMALL_SORT_POINTS")
+    os.environ["SK_SMALL_SORT_POINTS"] = "0"
     try:
         multi = sk.Context(0)
     finally:
         if old is None:
-            del os.environ["SK_SMALL_SORT_BLOCKS"]
+            del os.environ["SK_SMALL_SORT_POINTS"]
         else:
-            os.environ["SK_SMALL_SORT_BLOCKS"] = old
+            os.environ["SK_SMALL_SORT_POINTS"] = old
     rng = np.random.default_rng(67)
-    s = ci.make_surface(ci.Ellipsoid(1.0, 0.8, 0.6), 38)   # N = 8214 > 4 tiles of 2048
+    s = ci.make_surface(ci.Ellipsoid(1.0, 0.8, 0.6), 38)   # N = 8214
     f = rng.standard_normal((s.N, 3))
     try:
-        for n_src, n_tgt in ((1, 1), (33, 2047), (2048, 2049), (4095, 6000), (8192, 8192),
+        for n_src, n_tgt in ((1, 1), (33, 2047), (2048, 2049), (3072, 3073), (4095, 6000),
+                             (8192, 8192),
                              (s.N, 3000)):
             src = rng.choice(s.N, n_src, replace=False)
             w = s.w[src].copy()
