@@ -501,6 +501,27 @@ def serving_oracle_check(reqs, check, kept, per_request=SERVE_ORACLE_TARGETS):
                                      "targets x all active sources, FP64, OpenMP"}}
 
 
+def one_at_a_time(sk, h, reqs):
+    """The same requests evaluated one by one (stokes_sl_eval, device memory,
+    profiling on): the baseline continuous batching is measured against."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    tot = pair = whole = 0.0
+    for X, W, F, Y, D, _ in reqs:
+        args = [torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)
+                for a in (X, W, F, Y, D)]
+        out = torch.empty((Y.shape[0], 3), dtype=torch.float64, device=dev)
+        sk.stokes_sl_eval(h, sk.SK_FP32C, sk.SK_DEVICE, *args, 1.0, u_out=out)
+        st = sk.sk_last_eval_stats(h)
+        tot += Y.shape[0] * st["n_src_active"]
+        pair += st["pair_ms"]
+        whole += st["eval_ms"]
+    return {"ginter_per_s_whole_evals": tot / (whole * 1e-3) / 1e9,
+            "ginter_per_s_pair_kernel_only": tot / (pair * 1e-3) / 1e9,
+            "note": "device time of each evaluation, one after another (the first "
+                    "evaluation of each shape, cold)"}
+
+
 def serving_bench(sk, h, reqs):
     n = len(reqs)
     run_serving(sk, h, reqs[:64])  # warm-up
@@ -514,7 +535,8 @@ def serving_bench(sk, h, reqs):
                          "wall_s": wall, "p50_ms": float(np.percentile(lat, 50)),
                          "p99_ms": float(np.percentile(lat, 99)),
                          "mean_phase_ms": run_serving.last_phases_ms},
-           "oracle_check": oracle_check}
+           "oracle_check": oracle_check,
+           "one_at_a_time": one_at_a_time(sk, h, reqs)}
     for frac in SERVE_LOADS:
         rng = np.random.default_rng(int(frac * 1000))
         arr = np.cumsum(rng.exponential(1.0 / (frac * cap), size=n))
