@@ -179,7 +179,7 @@ int h_cell_basis(int p, int n, double h, double u, double v, double basis[8]) {
 // Device kernels.
 inline unsigned blocks_of(int64_t n) { return (unsigned)((n + 255) / 256); }
 
-// Not-a-knot cubic-spline slopes, SLOPE_LPL lanes per grid line. Lines: for
+// Not-a-knot cubic-spline slopes, L lanes per grid line. Lines: for
 // dir 0 the u-lines (fixed k, stride n), for dir 1 the v-lines (fixed j).
 // With uniform spacing the end conditions read s0 + 2 s1 = (-5 g0 + 4 g1 +
 // g2)/2h and 2 s_{n-2} + s_{n-1} = (5 g_{n-1} - 4 g_{n-2} - g_{n-3})/2h;
@@ -194,10 +194,10 @@ inline unsigned blocks_of(int64_t n) { return (unsigned)((n + 255) / 256); }
 // the table. A scan over the line's lanes gives each lane its incoming value,
 // and the lane replays its run. v_q is computed once (stored in s, then
 // overwritten by d_q and s_q).
-// L lanes per line (8, 16 or 32): fewer lanes cost fewer scan steps, more
-// lanes give short lines and small grids enough threads (slope_lanes). Table (thomas): [c' (n) | 1/den (n) |
-// 3/h * 1/den (n) | for L = 8, 16, 32: forward then backward run products (L
-// each)].
+// L = 8, 16 or 32 lanes per line: fewer lanes cost fewer scan steps, more
+// lanes give short lines and small grids enough threads (slope_lanes).
+// Table (thomas): [c' (n) | 1/den (n) | 3/h * 1/den (n) | for L = 8, 16, 32:
+// forward then backward run products (L each)].
 constexpr int SLOPE_LPL_MIN = 8, SLOPE_LPL_MAX = 32;
 __host__ __device__ constexpr int slope_products_offset(int n, int L) {
   return 3 * n + 2 * (L - SLOPE_LPL_MIN);  // L = 8: 0, 16: 16, 32: 48
