@@ -23,6 +23,8 @@
 // of Eq. tensor from the closed-form invariants of V^2 (tr V^2 and
 // det = (W / W_r)^2); f = div_gamma Lambda column by column.
 #include <algorithm>
+#include <cstdlib>
+#include <cstring>
 #include <cmath>
 #include <new>
 #include <thread>
@@ -36,6 +38,7 @@ constexpr int MEM_FMAX = 9;  // fields per pass (Lambda has 6, positions 3)
 
 struct MembraneOp {
   int m = 0, n = 0, E = 0;  // E = m + 5: extended grid (indices -2..m+2)
+  bool slope_staging = true;  // stage slope-solve lines in shared memory when they fit
   int64_t N = 0;
   double h = 0.0, ih = 0.0;
   int G = 0;  // ghost points used by the stencils, per field
@@ -203,7 +206,7 @@ __host__ __device__ constexpr int slope_products_offset(int n, int L) {
   return 3 * n + 2 * (L - SLOPE_LPL_MIN);  // L = 8: 0, 16: 16, 32: 48
 }
 constexpr int SLOPE_TABLE_EXTRA = 2 * (8 + 16 + 32);
-constexpr int SLOPE_TPB = 128;
+constexpr int SLOPE_LINES = 8;  // grid lines per CTA
 
 template <int L>
 __device__ __forceinline__ void affine_scan_lines(double& a, double& b, int sub) {
@@ -218,20 +221,36 @@ __device__ __forceinline__ void affine_scan_lines(double& a, double& b, int sub)
   }
 }
 
-template <int L>
-__global__ void __launch_bounds__(SLOPE_TPB)
-    k_slopes(const double* __restrict__ g, double* __restrict__ s, int64_t n_lines, int n,
-             int dir, double ih, const double* __restrict__ thomas) {
-  const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / L;
-  const int sub = threadIdx.x % L;
-  // lanes past the last line compute a copy of it (every lane takes part in
-  // the shuffles) and store nothing
-  const bool live = t < n_lines;
-  const int64_t line = live ? t : n_lines - 1;
+// Padded shared-memory index of term q of a line: one spare double per 8, so
+// that the run starts of 16 lanes (stride K = 8) fall in distinct banks.
+__device__ __forceinline__ int spad(int q) { return q + (q >> 3); }
+
+// First node of grid line `line` (patch-field fp = line / n, index r):
+// u-lines (dir 0) start at column r, v-lines (dir 1) at row r.
+__device__ __forceinline__ int64_t slope_line_base(int64_t line, int n, int dir) {
   const int64_t fp = line / n;
   const int r = (int)(line % n);
-  const int64_t base = fp * n * n + (dir == 0 ? r : (int64_t)r * n);
-  const int64_t st = dir == 0 ? n : 1;
+  return fp * n * n + (dir == 0 ? r : (int64_t)r * n);
+}
+
+// Term q of one line: staged in shared memory (padded) or in global memory
+// (stride st).
+struct StagedLine {
+  double* p;
+  __device__ __forceinline__ double& operator[](int q) const { return p[spad(q)]; }
+};
+struct GlobalLine {
+  double* p;
+  int64_t st;
+  __device__ __forceinline__ double& operator[](int q) const { return p[q * st]; }
+};
+
+// Both sweeps of one line by its L lanes; g: values, s: output slopes (also
+// the scratch of v and d). `live` lanes store; the others only take part in
+// the shuffles.
+template <int L, class Acc>
+__device__ __forceinline__ void slope_sweeps(const Acc& g, const Acc& s, bool live, int n, int sub,
+                                             double ih, const double* __restrict__ thomas) {
   const double* cp = thomas;
   const double* iden = thomas + n;
   const double* i3d = thomas + 2 * n;
@@ -241,34 +260,31 @@ __global__ void __launch_bounds__(SLOPE_TPB)
   const int K = (n - 2 + L - 1) / L;  // terms per lane
   const int qa = 1 + sub * K;         // this lane's run [qa, qb) of q = 1..n-2
   const int qb = min(qa + K, n - 1);
-  double c1 = 0.0, cN = 0.0;          // end-condition terms of v_1 and v_{n-2}
-  if (qa == 1)
-    c1 = (-5.0 * g[base] + 4.0 * g[base + st] + g[base + 2 * st]) * i2h * iden[1];
-  if (qa < qb && qb == n - 1)
-    cN = (5.0 * g[base + (n - 1) * st] - 4.0 * g[base + (n - 2) * st] - g[base + (n - 3) * st]) *
-         i2h * iden[n - 2];
+  const double r0 = (-5.0 * g[0] + 4.0 * g[1] + g[2]) * i2h;
+  const double rN = (5.0 * g[n - 1] - 4.0 * g[n - 2] - g[n - 3]) * i2h;
+  const double c1 = r0 * iden[1], cN = rN * iden[n - 2];  // end-condition terms of v_1, v_{n-2}
   // forward sweep
   double B = 0.0;
   for (int q = qa; q < qb; ++q) {
     const double cq = q == 1 ? c1 : (q == n - 2 ? cN : 0.0);
-    const double v = fma(i3d[q], g[base + (q + 1) * st] - g[base + (q - 1) * st], -cq);
+    const double v = fma(i3d[q], g[q + 1] - g[q - 1], -cq);
     B = fma(q == 1 ? 0.0 : -iden[q], B, v);
-    if (live) s[base + q * st] = v;
+    if (live) s[q] = v;
   }
   double A = afw[sub];
   affine_scan_lines<L>(A, B, sub);
   double x = __shfl_up_sync(0xffffffffu, B, 1, L);
   if (sub == 0) x = 0.0;
   for (int q = qa; q < qb; ++q) {
-    x = fma(q == 1 ? 0.0 : -iden[q], x, s[base + q * st]);
-    if (live) s[base + q * st] = x;
+    x = fma(q == 1 ? 0.0 : -iden[q], x, s[q]);
+    if (live) s[q] = x;
   }
   __syncwarp();
   // backward sweep over p = 1..n-2, q = n-1-p (s_{n-2} = d_{n-2})
   B = 0.0;
   for (int p = qa; p < qb; ++p) {
     const int q = n - 1 - p;
-    B = fma(q == n - 2 ? 0.0 : -cp[q], B, s[base + q * st]);
+    B = fma(q == n - 2 ? 0.0 : -cp[q], B, s[q]);
   }
   A = abw[sub];
   affine_scan_lines<L>(A, B, sub);
@@ -276,17 +292,61 @@ __global__ void __launch_bounds__(SLOPE_TPB)
   if (sub == 0) x = 0.0;
   for (int p = qa; p < qb; ++p) {
     const int q = n - 1 - p;
-    x = fma(q == n - 2 ? 0.0 : -cp[q], x, s[base + q * st]);
-    if (live) s[base + q * st] = x;
+    x = fma(q == n - 2 ? 0.0 : -cp[q], x, s[q]);
+    if (live) s[q] = x;
   }
   __syncwarp();
   if (sub == 0 && live) {
-    const double r0 = (-5.0 * g[base] + 4.0 * g[base + st] + g[base + 2 * st]) * i2h;
-    const double rN =
-        (5.0 * g[base + (n - 1) * st] - 4.0 * g[base + (n - 2) * st] - g[base + (n - 3) * st]) *
-        i2h;
-    s[base] = r0 - 2.0 * s[base + st];
-    s[base + (n - 1) * st] = rN - 2.0 * s[base + (n - 2) * st];
+    s[0] = r0 - 2.0 * s[1];
+    s[n - 1] = rN - 2.0 * s[n - 2];
+  }
+}
+
+// SLOPE_LINES lines per CTA (8 L threads). Staged: the lines' values and
+// slopes sit in shared memory (dynamic, 2 x SLOPE_LINES x spad(n) doubles),
+// loaded and stored coalesced (for dir 0 the CTA's lines are adjacent
+// columns). Unstaged (long lines): the sweeps work in global memory.
+template <int L, bool STAGED>
+__global__ void __launch_bounds__(SLOPE_LINES * L)
+    k_slopes(const double* __restrict__ g, double* __restrict__ s, int64_t n_lines, int n,
+             int dir, double ih, const double* __restrict__ thomas) {
+  constexpr int T = SLOPE_LINES * L;
+  const int tid = threadIdx.x, l = tid / L, sub = tid % L;
+  const int64_t line0 = (int64_t)blockIdx.x * SLOPE_LINES;
+  const int64_t st = dir == 0 ? n : 1;
+  if (!STAGED) {
+    // lanes past the last line compute a copy of it and store nothing
+    const bool live = line0 + l < n_lines;
+    const int64_t b = slope_line_base(live ? line0 + l : n_lines - 1, n, dir);
+    slope_sweeps<L>(GlobalLine{const_cast<double*>(g) + b, st}, GlobalLine{s + b, st}, live, n, sub,
+                    ih, thomas);
+    return;
+  }
+  extern __shared__ double sm_lines[];
+  __shared__ int64_t base_sh[SLOPE_LINES];  // first node of each line (-1: past the last)
+  const int stride = spad(n);
+  double* gsh = sm_lines;
+  double* ssh = sm_lines + SLOPE_LINES * stride;
+  if (tid < SLOPE_LINES)
+    base_sh[tid] = line0 + tid < n_lines ? slope_line_base(line0 + tid, n, dir) : -1;
+  __syncthreads();
+  // coalesced load: for dir 0 the line index runs fastest (adjacent columns),
+  // for dir 1 the term index (contiguous rows)
+  for (int idx = tid; idx < SLOPE_LINES * n; idx += T) {
+    const int li = dir == 0 ? idx % SLOPE_LINES : idx / n;
+    const int q = dir == 0 ? idx / SLOPE_LINES : idx % n;
+    const int64_t b = base_sh[li];
+    if (b >= 0) gsh[li * stride + spad(q)] = g[b + q * st];
+  }
+  __syncthreads();
+  slope_sweeps<L>(StagedLine{gsh + l * stride}, StagedLine{ssh + l * stride}, true, n, sub, ih,
+                  thomas);
+  __syncthreads();
+  for (int idx = tid; idx < SLOPE_LINES * n; idx += T) {
+    const int li = dir == 0 ? idx % SLOPE_LINES : idx / n;
+    const int q = dir == 0 ? idx / SLOPE_LINES : idx % n;
+    const int64_t b = base_sh[li];
+    if (b >= 0) s[b + q * st] = ssh[li * stride + spad(q)];
   }
 }
 
@@ -846,14 +906,28 @@ void enqueue_splines(const MembraneOp& op, int F, const double* val, double* sd,
   const int64_t plane = (int64_t)F * op.N;
   const int64_t lines = (int64_t)F * 6 * op.n;
   const int L = slope_lanes(op.n);
-  const unsigned nb = (unsigned)((L * lines + SLOPE_TPB - 1) / SLOPE_TPB);
+  const unsigned nb = (unsigned)((lines + SLOPE_LINES - 1) / SLOPE_LINES);
+  // staged lines: 2 arrays x SLOPE_LINES lines x spad(n) doubles, within the
+  // default 48 KB of dynamic shared memory (lines up to n = 341)
+  const size_t smem = 2 * (size_t)SLOPE_LINES * (op.n + (op.n >> 3)) * sizeof(double);
+  const bool staged = op.slope_staging && smem <= 48 * 1024;
   auto run = [&](const double* in, double* out, int dir) {
-    if (L == 8)
-      k_slopes<8><<<nb, SLOPE_TPB, 0, st>>>(in, out, lines, op.n, dir, op.ih, op.thomas);
-    else if (L == 16)
-      k_slopes<16><<<nb, SLOPE_TPB, 0, st>>>(in, out, lines, op.n, dir, op.ih, op.thomas);
-    else
-      k_slopes<32><<<nb, SLOPE_TPB, 0, st>>>(in, out, lines, op.n, dir, op.ih, op.thomas);
+    const unsigned T = (unsigned)(SLOPE_LINES * L);
+    if (staged) {
+      if (L == 8)
+        k_slopes<8, true><<<nb, T, smem, st>>>(in, out, lines, op.n, dir, op.ih, op.thomas);
+      else if (L == 16)
+        k_slopes<16, true><<<nb, T, smem, st>>>(in, out, lines, op.n, dir, op.ih, op.thomas);
+      else
+        k_slopes<32, true><<<nb, T, smem, st>>>(in, out, lines, op.n, dir, op.ih, op.thomas);
+    } else {
+      if (L == 8)
+        k_slopes<8, false><<<nb, T, 0, st>>>(in, out, lines, op.n, dir, op.ih, op.thomas);
+      else if (L == 16)
+        k_slopes<16, false><<<nb, T, 0, st>>>(in, out, lines, op.n, dir, op.ih, op.thomas);
+      else
+        k_slopes<32, false><<<nb, T, 0, st>>>(in, out, lines, op.n, dir, op.ih, op.thomas);
+    }
   };
   run(val, sd, 0);
   run(val, sd + plane, 1);
@@ -949,6 +1023,9 @@ int membrane_op(sk_ctx* ctx, int m, MembraneOp** out) {
   MembraneOp* op = nullptr;
   const int rc = build_op(m, &op, ctx->err);
   if (rc != SK_OK) return rc;
+  // SK_SLOPE_STAGING=0 in the environment keeps the slope solves in global
+  // memory (same arithmetic, same results: a test compares the two)
+  if (const char* v = std::getenv("SK_SLOPE_STAGING")) op->slope_staging = std::strcmp(v, "0") != 0;
   ctx->membrane_ops.push_back({m, op});
   *out = op;
   return SK_OK;

@@ -205,3 +205,29 @@ def test_rkf45_errors_and_step_bound(ctx):
         assert e.value.code == sk.SK_EINVAL
     finally:
         cap.close()
+
+
+def test_slope_solves_staged_and_in_global_memory_agree(ctx):
+    """The spline slope solves stage grid lines in shared memory when they
+    fit (n <= 341) and otherwise run in global memory; the arithmetic is the
+    same, so a context with staging turned off (SK_SLOPE_STAGING=0) gives the
+    same derivatives bit for bit, for both line lengths with 16 and 8 lanes."""
+    import os
+    old = os.environ.get("SK_SLOPE_STAGING")
+    os.environ["SK_SLOPE_STAGING"] = "0"
+    try:
+        plain = sk.Context(0)
+    finally:
+        if old is None:
+            del os.environ["SK_SLOPE_STAGING"]
+        else:
+            os.environ["SK_SLOPE_STAGING"] = old
+    try:
+        for m in (21, 193):   # 16 and 8 lanes per line
+            s = ci.make_surface(ci.Ellipsoid(0.9, 1.0, 0.8), m)
+            fields = np.concatenate([deformed(s), s.X ** 2], axis=1)
+            a = sk.surface_derivatives(ctx, m, sk.SK_HOST, fields)
+            b = sk.surface_derivatives(plain.handle, m, sk.SK_HOST, fields)
+            assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]), m
+    finally:
+        plain.close()
