@@ -94,3 +94,11 @@ def test_membrane_entry_points_reject_null_context(lib):
                                         None, None) == sk.SK_EINVAL
     assert lib.stokes_sl_eval_fmm(None, sk.SK_HOST, 1, None, None, None, 1, None, None, 1, 1.0, 1,
                                   None, 1, 4, None, None) == sk.SK_EINVAL
+
+
+def test_probe_and_stats_entry_points_reject_null_arguments(lib):
+    assert lib.sk_probe_peaks(None, None) == sk.SK_EINVAL
+    assert lib.sk_last_eval_stats(None, None) == sk.SK_EINVAL
+    assert lib.sk_set_profiling(None, 1) == sk.SK_EINVAL
+    assert lib.capsule_set_upsampling(None, 4) == sk.SK_EINVAL
+    assert lib.capsule_shape_moments(None, None) == sk.SK_EINVAL
