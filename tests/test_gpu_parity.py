@@ -169,15 +169,30 @@ def test_fp32c_far_from_origin(ctx, layer):
 
 @pytest.mark.parametrize("prec", PRECS, ids=PREC_ID.get)
 def test_ragged_sizes_and_per_target_delta(ctx, prec):
+    """Single and double layer at ragged sizes (1 target, 1 source, partial
+    tiles and target blocks) with one delta per target. The double layer takes
+    a smooth (SH) density: with random densities on a sparse random source
+    subset a few near pairs dominate each on-surface target, and there (x - y).n
+    cancels to O(r^2), which FP32 differences carry only to ~1e-6 relative, so
+    the sum does not average those errors away."""
     rng = np.random.default_rng(9)
     s = ci.make_surface(ci.Ellipsoid(1.0, 0.7, 0.6), 21)
     f = rng.standard_normal((s.N, 3))
+    q = ci.sh_density(s.x0, np.random.default_rng(19), lmax=6)
     for n_src, n_tgt in ((1, 1), (7, 33), (257, 1), (300, 1025), (s.N, 1023), (s.N, 2049)):
         src = rng.choice(s.N, n_src, replace=False)
         Y = np.concatenate([s.X, s.X + 0.03 * s.n])[rng.choice(2 * s.N, n_tgt, replace=False)]
         delta = rng.uniform(0.5, 3.0, n_tgt) * s.h
         u = sk.stokes_sl_eval(ctx, prec, sk.SK_HOST, s.X[src], s.w[src], f[src], Y, delta, 1.3)
         ref = oracle.sl(s.X[src], s.w[src], f[src], Y, delta, 1.3)
+        if np.abs(ref).max() == 0:
+            assert np.all(u == 0)
+        else:
+            assert_close(u, ref, prec)
+        # the double layer with the same per-target delta
+        u = sk.stokes_dl_eval(ctx, prec, sk.SK_HOST, s.X[src], s.w[src], s.n[src], q[src], Y,
+                              delta)
+        ref = oracle.dl(s.X[src], s.w[src], s.n[src], q[src], Y, delta)
         if np.abs(ref).max() == 0:
             assert np.all(u == 0)
         else:

@@ -96,6 +96,31 @@ def test_same_result_alone_and_in_the_mix(ctx):
         sk.serve_destroy(srv)
 
 
+def test_per_target_delta_requests_match_standalone(ctx):
+    """Requests with one delta per target (n_delta = M, e.g. delta* of each
+    target's patch) are served like scalar-delta ones: bit for bit the
+    standalone result, alone and mixed with scalar-delta requests."""
+    rng = np.random.default_rng(71)
+    reqs = []
+    for r in mixed_requests(6, m_choices=(9, 17, 33), seed=71):
+        X, W, F, Y, D = r
+        reqs.append((X, W, F, Y, D[0] * rng.uniform(0.5, 2.0, Y.shape[0])))
+        reqs.append(r)
+    refs = [sk.stokes_sl_eval(ctx, sk.SK_FP32C, sk.SK_HOST, *r) for r in reqs]
+    srv = sk.serve_create(ctx, max_slots=4)
+    try:
+        tickets = [submit_retry(srv, *r) for r in reqs]
+        for t, r, ref in zip(tickets, reqs, refs):
+            code, u, _ = sk.serve_poll(srv, t, r[3].shape[0], timeout_us=30_000_000)
+            assert code == sk.SK_OK
+            assert np.array_equal(u, ref)
+    finally:
+        sk.serve_destroy(srv)
+    for r, ref in list(zip(reqs, refs))[:2]:
+        o = oracle.sl(*r)
+        assert np.linalg.norm(ref - o) / np.linalg.norm(o) <= 1e-6
+
+
 def test_busy_queue_and_too_large_request(ctx):
     w = ci.rbc_workload()
     s = w.surface
