@@ -211,15 +211,17 @@ PAIR32_SOURCES = ("sk_pair32.cuh", "sk_pair32.cu", "sk_series.cuh")
 
 def pair32_source_hash():
     """Hash of what shapes the FP32 pair kernel's launch: its own sources, the
-    chunk policy (choose_chunks in sk_api.cu) and the work-decomposition
-    constants of sk_internal.h (up to the Bump allocator)."""
+    chunk and decomposition policy (choose_chunks, choose_decomposition in
+    sk_api.cu) and the work-decomposition constants of sk_internal.h (up to
+    the Bump allocator)."""
     csrc = os.path.join(ROOT, "paper_2310_13908_gb300", "csrc")
     h = hashlib.sha256()
     for name in PAIR32_SOURCES:
         h.update(open(os.path.join(csrc, name), "rb").read())
     api = open(os.path.join(csrc, "sk_api.cu")).read()
-    i = api.index("int choose_chunks(")
-    h.update(api[i:api.index("\n}\n", i)].encode())
+    for fn in ("int choose_chunks(", "void choose_decomposition("):
+        i = api.index(fn)
+        h.update(api[i:api.index("\n}\n", i)].encode())
     hdr = open(os.path.join(csrc, "sk_internal.h")).read()
     h.update(hdr[hdr.index("namespace sk {"):hdr.index("// Bump allocator")].encode())
     return h.hexdigest()
@@ -337,8 +339,11 @@ def main():
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic_from_profile() if default_step else None,
-                "kernel": {(False, False): "k_pair32<SLayer>", (True, False): "k_pair32<DLayer>",
-                           (False, True): "k_pair64<SL>", (True, True): "k_pair64<DL>"}[(dl, fp64)],
+                "kernel": ({(False, False): "k_pair32<SLayer>", (True, False): "k_pair32<DLayer>",
+                            (False, True): "k_pair64<SL>", (True, True): "k_pair64<DL>"}[(dl, fp64)]
+                           .replace("k_pair32", "k_pair32_fused" if stats["finish_fused"]
+                                    else "k_pair32")),
+                "kernel_includes_finish": bool(stats["finish_fused"]),
                 "pair_ms": pair_avg, "flops_per_interaction": flops,
                 "peak_basis": "nominal dense FP64 of GB300" if fp64 else
                               "2 x 128 FP32 lanes x 152 SMs x 2070 MHz (max SM clock)"}

@@ -95,8 +95,12 @@ typedef struct {
   int64_t kernel_launches;   /* CUDA kernels the evaluation launched */
   int32_t n_chunks;          /* source chunks per target block (split of the source sum) */
   int32_t precision;         /* SK_FP64 or SK_FP32C */
-  double pair_ms;            /* device time of the pair kernel (profiling on), else -1 */
+  double pair_ms;            /* device time of the pair kernel (profiling on), else -1; when
+                                finish_fused, it includes the FP64 finish of the target blocks */
   double eval_ms;            /* device time of the whole evaluation (profiling on), else -1 */
+  int32_t finish_fused;      /* SK_FP32C: 1 if the pair kernel finished the target blocks
+                                itself (grids of >= 2 target blocks per SM), 0 if separate
+                                finish kernels followed */
 } sk_eval_stats;
 int sk_last_eval_stats(const sk_ctx* ctx, sk_eval_stats* out);
 

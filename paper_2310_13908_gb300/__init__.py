@@ -52,7 +52,7 @@ class sk_eval_stats(ctypes.Structure):
                 ("near_pairs", ctypes.c_int64), ("overflow_targets", ctypes.c_int64),
                 ("kernel_launches", ctypes.c_int64), ("n_chunks", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("pair_ms", ctypes.c_double),
-                ("eval_ms", ctypes.c_double)]
+                ("eval_ms", ctypes.c_double), ("finish_fused", ctypes.c_int32)]
 
 
 def _declare(lib):

@@ -61,6 +61,7 @@ void carve_eval_buffers(Bump& bp, const EvalShape& s, EvalBufs& b) {
   b.n_chunks = s.n_chunks;
   b.pair_np = pair32_np(s.M);
   b.threads64 = s.threads64;
+  b.fuse_finish = fp32 && s.fuse_finish;
   const int64_t nsort = s.N > s.M ? s.N : s.M;
   b.sort_blocks = sort_grid_blocks(nsort > 0 ? nsort : 1);
   if (s.copy_inputs) {
@@ -94,6 +95,7 @@ void carve_eval_buffers(Bump& bp, const EvalShape& s, EvalBufs& b) {
   b.part = bp.take<double>((size_t)s.n_chunks * b.M_pad * 3);
   if (fp32) {
     b.near_cnt = bp.take<int>(b.M_pad);
+    b.tb_done = bp.take<int>(b.M_pad / 512 + 1);  // blocks of >= 512 targets
     b.near_idx = bp.take<int>((size_t)b.M_pad * NEAR_K);
     b.near_ovf = bp.take<double>((size_t)b.M_pad * 3);
   }
@@ -149,6 +151,17 @@ int choose_chunks(int precision, int64_t N, int64_t M, int sm_count) {
 void choose_decomposition(EvalShape& s, int sm_count) {
   s.n_chunks = choose_chunks(s.precision, s.N, s.M, sm_count);
   s.threads64 = TPB64;
+  if (s.precision == SK_FP32C) {
+    // The finish of a target block runs on the CTA that completes it: with at
+    // least two blocks per SM those finishes overlap the pair work, and only
+    // the last ones form a tail (measured: C3, 482 blocks: -1.5% per
+    // evaluation; C2, 48 blocks: +25%, so smaller grids keep the finish
+    // kernels).
+    const int64_t tgt_cta = (int64_t)TPB32 * 2 * pair32_np(s.M);
+    s.fuse_finish = (int64_t)align_up((size_t)(s.M > 0 ? s.M : 1), tgt_cta) / tgt_cta >=
+                    2 * (int64_t)sm_count;
+    return;
+  }
   if (s.precision != SK_FP64) return;
   const int64_t n_tb = (int64_t)align_up((size_t)(s.M > 0 ? s.M : 1), TGT_CTA64) / TGT_CTA64;
   const int64_t slots = (int64_t)sm_count * 2;  // resident TPB64-thread CTAs
@@ -179,7 +192,10 @@ int enqueue_prep(const EvalShape& s, const EvalBufs& b, double rho_T, double rho
   int launches = 0;
   cudaMemsetAsync(b.flags, 0, N_FLAGS * sizeof(unsigned long long), st);
   cudaMemsetAsync(b.meta, 0, N_META * sizeof(int), st);
-  if (fp32) cudaMemsetAsync(b.near_cnt, 0, b.M_pad * sizeof(int), st);
+  if (fp32) {
+    cudaMemsetAsync(b.near_cnt, 0, b.M_pad * sizeof(int), st);
+    cudaMemsetAsync(b.tb_done, 0, (b.M_pad / 512 + 1) * sizeof(int), st);
+  }
   k_check_delta<<<(unsigned)((s.n_delta + 255) / 256), 256, 0, st>>>(b.delta, s.n_delta, b.flags);
   launches += 1;
   if (s.N > 0) {
@@ -209,15 +225,12 @@ int enqueue_eval(const EvalShape& s, const EvalBufs& b, double rho_T, double rho
   if (ev) cudaEventRecord(ev[0], st);
   int launches = enqueue_prep(s, b, rho_T, rho_c, st);
   if (ev) cudaEventRecord(ev[1], st);
-  if (fp32)
-    launch_pair32(s.layer, b, rho_T, st);
-  else
-    launch_pair64(s.layer, b, scale, st);
-  if (ev) cudaEventRecord(ev[2], st);
   if (fp32) {
-    launch_finish32(s.layer, b, s.n_delta, scale, rho_T, st);
-    launches += 1 + 2;
+    launch_pair32(s.layer, b, rho_T, scale, st, ev ? ev[2] : nullptr);  // with the finish
+    launches += b.fuse_finish ? 1 : 3;
   } else {
+    launch_pair64(s.layer, b, scale, st);
+    if (ev) cudaEventRecord(ev[2], st);
     launch_finish64(b, st);
     launches += 1 + 1;
   }
@@ -450,6 +463,7 @@ int eval_entry(sk_ctx* ctx, int layer, int precision, int mem, int64_t N, const 
   ctx->stats = sk_eval_stats{};
   ctx->stats.n_tgt = M;
   ctx->stats.n_chunks = s.n_chunks;
+  ctx->stats.finish_fused = b.fuse_finish ? 1 : 0;
   ctx->stats.kernel_launches = launches;
   ctx->stats.precision = precision;
   if (stream_v) return SK_OK;

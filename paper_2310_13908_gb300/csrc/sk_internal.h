@@ -118,6 +118,7 @@ struct EvalBufs {
   // accumulation
   double* part = nullptr;         // [n_chunks][M_pad][3]
   int* near_cnt = nullptr;        // [M_pad]
+  int* tb_done = nullptr;         // [M_pad / 512 + 1] chunks done per target block (FP32C)
   int* near_idx = nullptr;        // [M_pad][NEAR_K]
   double* near_ovf = nullptr;     // [M_pad][3]
   unsigned long long* flags = nullptr;
@@ -125,6 +126,7 @@ struct EvalBufs {
   int64_t N = 0, M = 0, N_pad = 0, M_pad = 0;
   int n_chunks = 1;
   int pair_np = 2;  // FP32 pair kernel: f32x2 target pairs per lane (1 or 2)
+  bool fuse_finish = false;  // FP32C: the pair kernel finishes the target blocks
   int threads64 = TPB64;  // FP64 pair kernel: threads per CTA
   int sort_blocks = 0;
 };
@@ -195,6 +197,7 @@ struct EvalShape {
   bool copy_inputs = false;  // inputs/outputs live in the workspace (host-memory calls)
   int n_chunks = 1;
   int threads64 = TPB64;  // CTA size of the FP64 pair kernel (TPB64 or TPB64_SMALL)
+  bool fuse_finish = false;  // FP32C: finish target blocks inside the pair kernel
   // point sets of at most this many points are ordered by one single-block
   // kernel instead of fifteen launches (0: never)
   int64_t small_sort_points = SMALL_SORT_POINTS;
@@ -230,9 +233,12 @@ void launch_pack_targets64(const EvalBufs& b, int64_t n_delta, cudaStream_t st);
 int sort_grid_blocks(int64_t n);
 
 // launchers (sk_pair32.cu / sk_pair64.cu)
-void launch_pair32(int layer, const EvalBufs& b, double rho_T, cudaStream_t st);
-void launch_finish32(int layer, const EvalBufs& b, int64_t n_delta, double scale,
-                     double rho_T, cudaStream_t st);
+// FP32C pair sums and the finish of every target block (overflow rescans,
+// FP64 near sums, chunk merge, output write): fused into the pair kernel when
+// b.fuse_finish, else two more launches. pair_end (optional) is recorded
+// after the pair kernel, before any finish launch.
+void launch_pair32(int layer, const EvalBufs& b, double rho_T, double scale, cudaStream_t st,
+                   cudaEvent_t pair_end = nullptr);
 void launch_pair64(int layer, const EvalBufs& b, double scale, cudaStream_t st);
 void launch_finish64(const EvalBufs& b, cudaStream_t st);
 

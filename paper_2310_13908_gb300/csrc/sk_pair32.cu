@@ -7,14 +7,41 @@ namespace {
 
 using namespace p32;
 
+// One work item (target block tb, source chunk ch) per CTA. In the fused
+// kernel (many target blocks) the CTA that completes a block's last chunk
+// finishes that block (FP64 near sums, chunk merge): that FP64 work then runs
+// beside other CTAs' FP32 pair work instead of in kernels of its own. With
+// few blocks a block's finish on one CTA would become the tail, so the plain
+// kernel is followed by the finish kernels below.
 template <class L, int NP, int MINB>
-__global__ void __launch_bounds__(TPB32, MINB)
-    k_pair32(PairArgs a) {
+__global__ void __launch_bounds__(TPB32, MINB) k_pair32(PairArgs a) {
   extern __shared__ __align__(128) float4 sm[];
   __shared__ PipeSmem<pair_stages<L, NP>()> ps;
   if (threadIdx.x == 0) ps.initialized = 0;
   const int tb = blockIdx.x / a.n_chunks, ch = blockIdx.x % a.n_chunks;
   pair_item<L, NP>(a, tb, ch, sm, ps);
+}
+
+template <class L, int NP, int MINB>
+__global__ void __launch_bounds__(TPB32, MINB)
+    k_pair32_fused(PairArgs a, OverflowArgs oa, FinishArgs fa, int* __restrict__ tb_done,
+                   int64_t M) {
+  extern __shared__ __align__(128) float4 sm[];
+  __shared__ PipeSmem<pair_stages<L, NP>()> ps;
+  __shared__ int s_last;
+  if (threadIdx.x == 0) ps.initialized = 0;
+  const int tb = blockIdx.x / a.n_chunks, ch = blockIdx.x % a.n_chunks;
+  pair_item<L, NP>(a, tb, ch, sm, ps);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();  // this chunk's partials and near-list entries before the count
+    s_last = atomicAdd(&tb_done[tb], 1) == a.n_chunks - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  constexpr int TB = TPB32 * 2 * NP;  // targets per block
+  finish_block<L>(oa, fa, M, (int64_t)tb * TB, TB);
 }
 
 template <class L>
@@ -38,46 +65,45 @@ __global__ void __launch_bounds__(128) k_finish32(FinishArgs a, int64_t M) {
 }  // namespace
 
 template <class L, int NP>
-void launch_pair32_t(const EvalBufs& b, float rho_lo, float rho_hi, cudaStream_t st) {
+void launch_pair32_t(const EvalBufs& b, float rho_lo, float rho_hi, double scale, cudaStream_t st,
+                     cudaEvent_t pair_end) {
   constexpr int MINB = NP == 2 ? PAIR32_MINB_NP2 : PAIR32_MINB_NP1;
   const unsigned grid = (unsigned)((b.M_pad / (TPB32 * 2 * NP)) * b.n_chunks);
   const size_t smem = pair_smem_bytes<L, NP>();
-  cudaFuncSetAttribute(k_pair32<L, NP, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)smem);
   PairArgs a{b.srcF,  b.segbox,   b.src_orig, b.meta,     b.tgtF,  b.tgt64, b.M_pad,
              b.n_chunks, b.part, b.near_cnt, b.near_idx, b.flags, rho_lo, rho_hi};
-  k_pair32<L, NP, MINB><<<grid, TPB32, smem, st>>>(a);
-}
-
-void launch_pair32(int layer, const EvalBufs& b, double rho_T, cudaStream_t st) {
-  const float rho_lo = (float)rho_T, rho_hi = 8.0f;
-  if (layer == LAYER_SL) {
-    if (b.pair_np == 2)
-      launch_pair32_t<SLayer, 2>(b, rho_lo, rho_hi, st);
-    else
-      launch_pair32_t<SLayer, 1>(b, rho_lo, rho_hi, st);
-  } else {
-    if (b.pair_np == 2)
-      launch_pair32_t<DLayer, 2>(b, rho_lo, rho_hi, st);
-    else
-      launch_pair32_t<DLayer, 1>(b, rho_lo, rho_hi, st);
-  }
-}
-
-void launch_finish32(int layer, const EvalBufs& b, int64_t /*n_delta*/, double scale,
-                     double /*rho_T*/, cudaStream_t st) {
-  const unsigned go = (unsigned)((b.M * 32 + 255) / 256);
-  const unsigned gf = (unsigned)((b.M + 127) / 128);
   OverflowArgs oa{b.srcF, b.segbox, b.src_orig, b.meta,  b.tgtF,  b.tgt64,     b.near_cnt,
                   b.src_xyz, b.src_w, b.dens,   b.nrm, scale, b.flags, b.near_ovf};
   FinishArgs fa{b.tgt64, b.tgt_perm, b.M_pad, b.n_chunks, b.part, b.near_cnt, b.near_idx,
                 b.near_ovf, b.src_xyz, b.src_w, b.dens, b.nrm, scale, b.u, b.flags};
-  if (layer == LAYER_SL) {
-    k_overflow32<SLayer><<<go, 256, 0, st>>>(oa, b.M);
-    k_finish32<SLayer><<<gf, 128, 0, st>>>(fa, b.M);
+  if (b.fuse_finish) {
+    cudaFuncSetAttribute(k_pair32_fused<L, NP, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    k_pair32_fused<L, NP, MINB><<<grid, TPB32, smem, st>>>(a, oa, fa, b.tb_done, b.M);
+    if (pair_end) cudaEventRecord(pair_end, st);
   } else {
-    k_overflow32<DLayer><<<go, 256, 0, st>>>(oa, b.M);
-    k_finish32<DLayer><<<gf, 128, 0, st>>>(fa, b.M);
+    cudaFuncSetAttribute(k_pair32<L, NP, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    k_pair32<L, NP, MINB><<<grid, TPB32, smem, st>>>(a);
+    if (pair_end) cudaEventRecord(pair_end, st);
+    k_overflow32<L><<<(unsigned)((b.M * 32 + 255) / 256), 256, 0, st>>>(oa, b.M);
+    k_finish32<L><<<(unsigned)((b.M + 127) / 128), 128, 0, st>>>(fa, b.M);
+  }
+}
+
+void launch_pair32(int layer, const EvalBufs& b, double rho_T, double scale, cudaStream_t st,
+                   cudaEvent_t pair_end) {
+  const float rho_lo = (float)rho_T, rho_hi = 8.0f;
+  if (layer == LAYER_SL) {
+    if (b.pair_np == 2)
+      launch_pair32_t<SLayer, 2>(b, rho_lo, rho_hi, scale, st, pair_end);
+    else
+      launch_pair32_t<SLayer, 1>(b, rho_lo, rho_hi, scale, st, pair_end);
+  } else {
+    if (b.pair_np == 2)
+      launch_pair32_t<DLayer, 2>(b, rho_lo, rho_hi, scale, st, pair_end);
+    else
+      launch_pair32_t<DLayer, 1>(b, rho_lo, rho_hi, scale, st, pair_end);
   }
 }
 

@@ -751,5 +751,26 @@ __device__ __forceinline__ int finish_target(const FinishArgs& a, int64_t t) {
   return cnt;
 }
 
+// Finish targets t0 .. t0 + nt - 1 (of M real ones) of a target block whose
+// chunks are all done: overflow rescans (if any list overflowed), FP64 near
+// sums and chunk merge, and the near-pair count. Run by a whole CTA; kept out
+// of line so that the pair loop's register allocation does not carry it.
+template <class L>
+__device__ __noinline__ void finish_block(const OverflowArgs& oa, const FinishArgs& fa, int64_t M,
+                                          int64_t t0, int nt) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  if (*(volatile const unsigned long long*)&fa.flags[FLAG_OVERFLOW] != 0ull) {
+    for (int i = wid; i < nt; i += nw)
+      if (t0 + i < M) overflow_target<L>(oa, t0 + i);
+    __syncthreads();
+    __threadfence_block();
+  }
+  int cnt = 0;
+  for (int i = tid; i < nt; i += blockDim.x)
+    if (t0 + i < M) cnt += finish_target<L>(fa, t0 + i);
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(FULL, cnt, o);
+  if (lane == 0 && cnt) atomicAdd(fa.flags + FLAG_NEAR_PAIRS, (unsigned long long)cnt);
+}
+
 }  // namespace p32
 }  // namespace sk

@@ -79,25 +79,6 @@ __device__ __forceinline__ unsigned long long gtimer() {
   return t;
 }
 
-// Finish target block tb of a request (cold path, kept out of line so the
-// pair loop's register allocation does not carry it): overflow rescans,
-// FP64 near sums and chunk merge, near-pair count.
-__device__ __noinline__ void finish_block(const SlotDesc& d, int tb) {
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int64_t t0 = (int64_t)tb * SERVE_TGT_CTA;
-  if (*(volatile const unsigned long long*)&d.pa.flags[FLAG_OVERFLOW] != 0ull) {
-    for (int i = wid; i < SERVE_TGT_CTA; i += TPB32 / 32)
-      if (t0 + i < d.M) overflow_target<SLayer>(d.oa, t0 + i);
-    __syncthreads();
-    __threadfence_block();
-  }
-  int cnt = 0;
-  for (int i = tid; i < SERVE_TGT_CTA; i += TPB32)
-    if (t0 + i < d.M) cnt += finish_target<SLayer>(d.fa, t0 + i);
-  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-  if (lane == 0 && cnt) atomicAdd(d.fa.flags + FLAG_NEAR_PAIRS, (unsigned long long)cnt);
-}
-
 __global__ void __launch_bounds__(TPB32, SERVE_MINB)
     k_serve(const SlotDesc* __restrict__ desc, SlotClaim* __restrict__ claim, int n_slots,
             int* __restrict__ ctl, unsigned* __restrict__ done_host,
@@ -197,7 +178,7 @@ __global__ void __launch_bounds__(TPB32, SERVE_MINB)
     if (s_finish) {
       // last chunk of this target block: finish the block's targets
       __threadfence();
-      finish_block(d, tb);
+      finish_block<SLayer>(d.oa, d.fa, d.M, (int64_t)tb * SERVE_TGT_CTA, SERVE_TGT_CTA);
       __syncthreads();
       if (tid == 0) {
         __threadfence();
