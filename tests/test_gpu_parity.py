@@ -48,6 +48,15 @@ def to_dev(a):
     return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda")
 
 
+def expected_fused(M):
+    """Whether an SK_FP32C evaluation with M targets finishes its target
+    blocks inside the pair kernel: at least 2 blocks (1024 targets above
+    131,072 targets, else 512) per SM."""
+    per_block = 1024 if M > 131072 else 512
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    return -(-M // per_block) >= 2 * sms
+
+
 PRECS = [sk.SK_FP64, sk.SK_FP32C]
 PREC_ID = {sk.SK_FP64: "fp64", sk.SK_FP32C: "fp32c"}
 
@@ -90,6 +99,8 @@ def test_sl_rbc(ctx, rbc, prec):
     s = w.surface
     u = sk.stokes_sl_eval(ctx, prec, sk.SK_HOST, s.X, s.w, w.f, w.targets, w.delta, w.mu)
     assert_close(u, ref, prec)
+    if prec == sk.SK_FP32C:  # 48 target blocks: separate finish kernels
+        assert sk.sk_last_eval_stats(ctx)["finish_fused"] == expected_fused(w.targets.shape[0])
 
 
 @pytest.mark.parametrize("prec", PRECS, ids=PREC_ID.get)
@@ -112,6 +123,8 @@ def test_sl_ellipsoid_full_size_sampled(ctx, ellipsoid_full, prec):
     s = w.surface
     u = sk.stokes_sl_eval(ctx, prec, sk.SK_DEVICE, to_dev(s.X), to_dev(s.w), to_dev(w.f),
                           to_dev(w.targets), to_dev(w.delta), w.mu).cpu().numpy()
+    if prec == sk.SK_FP32C:  # 482 target blocks: the pair kernel finishes them
+        assert sk.sk_last_eval_stats(ctx)["finish_fused"] == expected_fused(w.targets.shape[0])
     rng = np.random.default_rng(77)
     M = w.targets.shape[0]
     idx = np.concatenate([rng.choice(w.n_on_surface, 384, replace=False),
@@ -142,6 +155,8 @@ def test_dl_fp32c_large_grids(ctx, shape, m):
     delta = 2 * s.h
     u = sk.stokes_dl_eval(ctx, sk.SK_FP32C, sk.SK_DEVICE, to_dev(s.X), to_dev(s.w), to_dev(s.n),
                           to_dev(q), to_dev(s.X), to_dev(np.array([delta]))).cpu().numpy()
+    # sphere m = 257: 384 blocks, fused finish; ellipsoid m = 193: 216, separate
+    assert sk.sk_last_eval_stats(ctx)["finish_fused"] == expected_fused(s.N)
     idx = np.random.default_rng(6).choice(s.N, 384, replace=False)
     ref = oracle.dl(s.X, s.w, s.n, q, s.X[idx], delta)
     e = assert_close(u[idx], ref, sk.SK_FP32C)
