@@ -275,7 +275,10 @@ void capsule_destroy(sk_capsule* c);
  * operator depends only on m and is built on first use and kept in ctx.
  * mem selects host or device pointers; stream as for stokes_sl_eval (device
  * memory with a stream: asynchronous, buffers must stay valid until it
- * completes). */
+ * completes). The spline slope solves stage their grid lines in shared memory
+ * when they fit (m <= 342); SK_SLOPE_STAGING=0 in the environment when the
+ * operator is built keeps them in global memory (same arithmetic, same
+ * results). */
 
 /* u- and v-derivatives of n_fields functions g [N][n_fields] on the surface
  * (values at the nodes; each node's derivatives are in its own patch's (u, v))
