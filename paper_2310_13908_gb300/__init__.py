@@ -190,8 +190,15 @@ def _ptr(a, mem: int, shape_tail, name: str):
         return a.data_ptr(), n
     arr = np.ascontiguousarray(a, dtype=np.float64)
     if shape_tail:
-        arr = arr.reshape((-1,) + tuple(shape_tail))
+        tail = tuple(shape_tail)
+        if (arr.ndim >= 2 and tuple(arr.shape[1:]) != tail) or \
+                (arr.ndim <= 1 and arr.size % int(np.prod(tail)) != 0):
+            raise ValueError(f"{name}: expected shape (n, {', '.join(map(str, tail))}), "
+                             f"got {arr.shape}")
+        arr = arr.reshape((-1,) + tail)
     else:
+        if arr.ndim > 1:
+            raise ValueError(f"{name}: expected a vector, got shape {arr.shape}")
         arr = arr.reshape(-1)
     return arr, arr.shape[0]
 

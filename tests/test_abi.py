@@ -5,6 +5,7 @@ import glob
 import os
 import re
 
+import numpy as np
 import pytest
 
 import paper_2310_13908_gb300 as sk
@@ -102,3 +103,14 @@ def test_probe_and_stats_entry_points_reject_null_arguments(lib):
     assert lib.sk_set_profiling(None, 1) == sk.SK_EINVAL
     assert lib.capsule_set_upsampling(None, 4) == sk.SK_EINVAL
     assert lib.capsule_shape_moments(None, None) == sk.SK_EINVAL
+
+
+def test_host_arrays_with_the_wrong_shape_are_rejected(lib):
+    # checked in the binding, before any CUDA call
+    X = np.zeros((12, 4))          # 48 values: would reshape to (16, 3) silently
+    with pytest.raises(ValueError, match="src_xyz"):
+        sk.stokes_sl_eval(None, sk.SK_FP32C, sk.SK_HOST, X, np.ones(12), np.ones((12, 3)),
+                          np.zeros((2, 3)), 0.1)
+    with pytest.raises(ValueError, match="src_w"):
+        sk.stokes_sl_eval(None, sk.SK_FP32C, sk.SK_HOST, np.zeros((12, 3)), np.ones((12, 2)),
+                          np.ones((12, 3)), np.zeros((2, 3)), 0.1)
