@@ -68,3 +68,20 @@ def test_reference_arm_other_ranks_exit_without_work(monkeypatch):
         m, probes, warmup, steps = 17, 10, 1, 1
 
     assert bench.run_reference(A) == 0
+
+
+def test_traffic_is_reported_only_for_the_profiled_sources(monkeypatch):
+    """bench.py takes the pair kernel's DRAM traffic from the committed ncu
+    summary only while the hash of the kernel sources matches the one the
+    summary was taken on; any other source state reports null."""
+    import bench
+    committed = bench.traffic_from_profile()
+    text = open(os.path.join(bench.ROOT, "profiles", "pair32_dram_traffic.txt")).read()
+    recorded = [l.split(":", 1)[1].strip() for l in text.splitlines()
+                if l.startswith("source_sha256:")][0]
+    monkeypatch.setattr(bench, "pair32_source_hash", lambda: recorded)
+    assert bench.traffic_from_profile() == float(
+        [l.split(":", 1)[1] for l in text.splitlines() if l.startswith("dram_bytes_per_launch")][0])
+    monkeypatch.setattr(bench, "pair32_source_hash", lambda: "0" * 64)
+    assert bench.traffic_from_profile() is None
+    assert committed is None or committed > 0
