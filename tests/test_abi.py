@@ -114,3 +114,18 @@ def test_host_arrays_with_the_wrong_shape_are_rejected(lib):
     with pytest.raises(ValueError, match="src_w"):
         sk.stokes_sl_eval(None, sk.SK_FP32C, sk.SK_HOST, np.zeros((12, 3)), np.ones((12, 2)),
                           np.ones((12, 3)), np.zeros((2, 3)), 0.1)
+
+
+def test_header_is_plain_c(tmp_path):
+    """include/stokesreg.h is a C ABI: it compiles as C99 (no C++ in it)."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc") or shutil.which("cc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use.c"
+    src.write_text('#include "stokesreg.h"\nint main(void) { return sk_version() > 0 ? 0 : 1; }\n')
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-fsyntax-only",
+                        "-I", inc, str(src)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
