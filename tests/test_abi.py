@@ -129,3 +129,34 @@ def test_header_is_plain_c(tmp_path):
     r = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-fsyntax-only",
                         "-I", inc, str(src)], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def test_c_program_links_and_runs(tmp_path):
+    """A plain C program built against the header links with libstokesreg.so
+    alone and runs: sk_create returns SK_OK on a GPU, SK_ECUDA (with a message)
+    where there is no CUDA driver."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc") or shutil.which("cc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    libdir = os.path.dirname(sk.LIB_PATH)
+    src = tmp_path / "use.c"
+    src.write_text(
+        '#include <stdio.h>\n#include "stokesreg.h"\n'
+        "int main(void) {\n"
+        "  sk_ctx* ctx = NULL;\n"
+        "  int rc = sk_create(&ctx, 0, 0);\n"
+        '  printf("%d %s\\n", rc, rc == SK_OK ? "" : sk_last_error(NULL));\n'
+        "  if (rc == SK_OK) sk_destroy(ctx);\n"
+        "  return 0;\n}\n")
+    exe = tmp_path / "use"
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(root, "include"),
+                        str(src), "-L", libdir, "-lstokesreg", f"-Wl,-rpath,{libdir}", "-o",
+                        str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr
+    code = int(r.stdout.split()[0])
+    assert code in (sk.SK_OK, sk.SK_ECUDA), r.stdout
