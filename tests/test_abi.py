@@ -131,7 +131,7 @@ def test_header_is_plain_c(tmp_path):
     assert r.returncode == 0, r.stderr
 
 
-def test_c_program_links_and_runs(tmp_path):
+def test_c_program_links_and_runs(lib, tmp_path):
     """A plain C program built against the header links with libstokesreg.so
     alone and runs: sk_create returns SK_OK on a GPU, SK_ECUDA (with a message)
     where there is no CUDA driver."""
