@@ -37,17 +37,20 @@ _int = ctypes.c_int
 
 
 class SkError(RuntimeError):
+    """A library call returned a status other than SK_OK; .code holds it."""
     def __init__(self, code: int, message: str):
         super().__init__(f"{_NAMES.get(code, code)}: {message}")
         self.code = code
 
 
 class sk_peaks(ctypes.Structure):
+    """sk_peaks of stokesreg.h: measured FFMA2 / DFMA throughput and far-pair rate."""
     _fields_ = [("ffma2_tflops", ctypes.c_double), ("dfma_tflops", ctypes.c_double),
                 ("far_pairs_per_s", ctypes.c_double), ("sm_count", ctypes.c_int32)]
 
 
 class sk_eval_stats(ctypes.Structure):
+    """sk_eval_stats of stokesreg.h: counters of the most recent evaluation."""
     _fields_ = [("n_src_active", ctypes.c_int64), ("n_tgt", ctypes.c_int64),
                 ("near_pairs", ctypes.c_int64), ("overflow_targets", ctypes.c_int64),
                 ("kernel_launches", ctypes.c_int64), ("n_chunks", ctypes.c_int32),
@@ -127,10 +130,12 @@ def _check(ctx, code):
 
 
 def sk_version() -> int:
+    """Library version as an integer (100 for 0.1.0)."""
     return load().sk_version()
 
 
 def sk_create(device: int = 0, workspace_bytes: int = 0):
+    """Create a context on a CUDA device; workspace_bytes = 0 grows it on demand."""
     h = _vp()
     code = load().sk_create(ctypes.byref(h), int(device), int(workspace_bytes))
     if code != SK_OK:
@@ -139,19 +144,23 @@ def sk_create(device: int = 0, workspace_bytes: int = 0):
 
 
 def sk_destroy(ctx) -> None:
+    """Release the context, its stream and workspace (None is ignored)."""
     if ctx:
         load().sk_destroy(ctx)
 
 
 def sk_last_error(ctx) -> str:
+    """Message of the last failure on ctx (or of sk_create when ctx is None)."""
     return load().sk_last_error(ctx).decode()
 
 
 def sk_set_fp32c_thresholds(ctx, rho_T: float, rho_c: float) -> None:
+    """SK_FP32C regime thresholds: FP64 series below rho_T, plain kernel from rho_c."""
     _check(ctx, load().sk_set_fp32c_thresholds(ctx, float(rho_T), float(rho_c)))
 
 
 def sk_set_profiling(ctx, enable: bool) -> None:
+    """Record device times of the pair kernel and of whole evaluations (stats)."""
     _check(ctx, load().sk_set_profiling(ctx, 1 if enable else 0))
 
 
@@ -163,6 +172,7 @@ def sk_probe_peaks(ctx) -> dict:
 
 
 def sk_last_eval_stats(ctx) -> dict:
+    """Counters of the most recent evaluation on ctx (waits for it to finish)."""
     st = sk_eval_stats()
     _check(ctx, load().sk_last_eval_stats(ctx, ctypes.byref(st)))
     return {f[0]: getattr(st, f[0]) for f in st._fields_}
@@ -374,6 +384,7 @@ SK_FLOW_NONE, SK_FLOW_SHEAR, SK_FLOW_POISEUILLE = 0, 1, 2
 
 
 class sk_flow(ctypes.Structure):
+    """sk_flow of stokesreg.h: background flow (kind, rate, alpha, R0)."""
     _fields_ = [("kind", ctypes.c_int32), ("rate", ctypes.c_double), ("alpha", ctypes.c_double),
                 ("R0", ctypes.c_double)]
 
@@ -449,18 +460,21 @@ class Capsule:
 
 
 class sk_serve_cfg(ctypes.Structure):
+    """sk_serve_cfg of stokesreg.h: server limits (0 selects the default)."""
     _fields_ = [("max_slots", ctypes.c_int32), ("queue_capacity", ctypes.c_int32),
                 ("hbm_budget_bytes", ctypes.c_size_t), ("idle_exit_us", ctypes.c_int64),
                 ("host_staging_bytes", ctypes.c_size_t)]
 
 
 class sk_request(ctypes.Structure):
+    """sk_request of stokesreg.h: one single-layer request (host arrays)."""
     _fields_ = [("n_src", ctypes.c_int64), ("src_xyz", _vp), ("src_w", _vp), ("f", _vp),
                 ("n_tgt", ctypes.c_int64), ("tgt_xyz", _vp), ("delta", _vp),
                 ("n_delta", ctypes.c_int64), ("mu", ctypes.c_double)]
 
 
 class sk_req_stats(ctypes.Structure):
+    """sk_req_stats of stokesreg.h: phase timestamps and sizes of a served request."""
     _fields_ = [("submit_us", ctypes.c_double), ("admit_us", ctypes.c_double),
                 ("publish_us", ctypes.c_double), ("done_us", ctypes.c_double),
                 ("ready_us", ctypes.c_double), ("interactions", ctypes.c_int64),
@@ -505,6 +519,7 @@ def serve_poll(srv, ticket: int, n_tgt: int, timeout_us: int = -1):
 
 
 def serve_destroy(srv) -> None:
+    """Finish the queued work and free the server."""
     if srv:
         load().serve_destroy(srv)
 
