@@ -85,3 +85,18 @@ def test_traffic_is_reported_only_for_the_profiled_sources(monkeypatch):
     monkeypatch.setattr(bench, "pair32_source_hash", lambda: "0" * 64)
     assert bench.traffic_from_profile() is None
     assert committed is None or committed > 0
+
+
+def test_clock_summary_of_nvidia_smi_lines():
+    # index, sm, max sm, power, active mask, hw_slowdown, hw_thermal, sw_thermal, sw_power_cap
+    lines = ["0, 2070, 2070, 950.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n",
+             "0, 1980, 2070, 1390.5, 0x0000000000000004, Not Active, Not Active, Not Active, Active\n",
+             "0, 2070, 2070, 1200.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n",
+             "0, [N/A], 2070, [N/A], [N/A], [N/A], [N/A], [N/A], [N/A]\n",
+             "garbled\n"]
+    c = bench.clock_summary(lines)
+    assert c == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 4}
+    hot = lines[:1] + ["0, 1500, 2070, 800.0, 0x48, Active, Active, Not Active, Not Active\n"]
+    assert bench.clock_summary(hot)["reasons"] == ["hw_slowdown", "hw_thermal_slowdown"]
+    assert bench.clock_summary(hot)["sm_mhz"] == 1785.0
+    assert bench.clock_summary([]) is None and bench.clock_summary(["x, y\n"]) is None
