@@ -398,6 +398,10 @@ def main():
             "dtype": "f64" if fp64 else "f32 pairs + f64 near/final", "data": "synthetic",
             "config": {"workload": workload_name(w, args.layer), "targets": M,
                        "sources_active": Ns, "interactions_per_step": inter,
+                       "sources_total": int(s.X.shape[0]),
+                       "interactions_dense_per_step": int(M * s.X.shape[0]),
+                       "interactions_basis": "value counts targets x active sources (w != 0); "
+                                             "the dense count includes the zero-weight nodes",
                        "precision": f"SK_{args.precision.upper()}",
                        "rho_T": 0.5, "rho_c": 5.0,
                        "l2": "flushed between timed steps (256 MB write); inputs 58 MB",
