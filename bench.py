@@ -45,7 +45,7 @@ SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 FP32_PEAK_TFLOPS = 2 * 128 * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12  # 80.55
 FP64_PEAK_TFLOPS = 1.25  # nominal dense FP64 of GB300
-CPU_SAMPLE_TARGETS = 4096
+CPU_SAMPLE_TARGETS = 24576  # about 10 s of the oracle on 16 host cores
 SERVE_ORACLE_REQUESTS = 50   # served results checked against the oracle ...
 SERVE_ORACLE_TARGETS = 256   # ... on this many seeded targets each
 REF_STEP_TARGETS = 512
