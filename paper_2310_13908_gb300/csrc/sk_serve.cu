@@ -35,6 +35,7 @@
 #include <vector>
 
 #include "sk_pair32.cuh"
+#include "sk_range_alloc.h"
 
 namespace sk {
 namespace {
@@ -191,48 +192,6 @@ __global__ void __launch_bounds__(TPB32, SERVE_MINB)
     if (tid == 0) atomicSub(&ctl[CTL_BUSY], 1);
   }
 }
-
-// First-fit allocator over [0, size) in 256-byte units.
-class RangeAlloc {
- public:
-  void reset(size_t size) {
-    free_.clear();
-    free_[0] = size;
-  }
-  bool alloc(size_t n, size_t* off) {
-    n = align_up(n ? n : 1, 256);
-    for (auto it = free_.begin(); it != free_.end(); ++it) {
-      if (it->second >= n) {
-        *off = it->first;
-        const size_t rest = it->second - n;
-        const size_t start = it->first + n;
-        free_.erase(it);
-        if (rest) free_[start] = rest;
-        return true;
-      }
-    }
-    return false;
-  }
-  void release(size_t off, size_t n) {
-    n = align_up(n ? n : 1, 256);
-    auto it = free_.emplace(off, n).first;
-    auto nx = std::next(it);
-    if (nx != free_.end() && it->first + it->second == nx->first) {
-      it->second += nx->second;
-      free_.erase(nx);
-    }
-    if (it != free_.begin()) {
-      auto pv = std::prev(it);
-      if (pv->first + pv->second == it->first) {
-        pv->second += it->second;
-        free_.erase(it);
-      }
-    }
-  }
-
- private:
-  std::map<size_t, size_t> free_;
-};
 
 using Clock = std::chrono::steady_clock;
 
