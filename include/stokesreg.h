@@ -54,6 +54,7 @@ extern "C" {
 #define SK_HOST   0  /* all array arguments are host pointers */
 #define SK_DEVICE 1  /* all array arguments are device pointers on the context's device */
 
+/* ---- context (library infrastructure: the paper defines no API) --------- */
 typedef struct sk_ctx sk_ctx;
 
 /* Create a context on CUDA device `device`. workspace_bytes = 0 lets the
@@ -152,7 +153,9 @@ int stokes_sl_eval(sk_ctx* ctx, int precision, int mem,
                    const double* delta, int64_t n_delta,
                    double mu, double* u_out, void* cuda_stream);
 
-/* Regularized double layer (stresslet), same conventions as stokes_sl_eval.
+/* Regularized double layer (stresslet), same conventions as stokes_sl_eval:
+ * the sum D(x) of the file header, the regularized stresslet that the paper
+ * cites in Sec. 1, Limitations (ii), with the smoothing factor s3.
  *   src_n  [n_src][3] unit normals n at the nodes (orientation sets the sign)
  *   q      [n_src][3] double-layer density q
  * No viscosity argument: the stresslet is viscosity-free. For a constant q on
@@ -238,7 +241,7 @@ int capsule_integrate_rkf45(sk_capsule* c, double t_end, double* dt_inout, doubl
 int capsule_set_membrane(sk_capsule* c, const double* X_ref, double Es, double ED);
 
 /* Evaluate the single layer of every step on the four-times upsampled grid
- * (factor 4, as stokes_sl_eval_upsampled; W from the derivative scheme at
+ * (Sec. 3.4, "Upsampling"; factor 4, as stokes_sl_eval_upsampled; W from the derivative scheme at
  * the current nodes; delta_u per patch replaces delta) or on the nodes
  * themselves (factor 1, the default). Needs m >= 6 for factor 4.
  * Errors: SK_EINVAL, SK_ENOMEM, SK_ECUDA. */
@@ -259,7 +262,8 @@ int capsule_area_volume(sk_capsule* c, double* area, double* volume);
  * Errors: SK_EINVAL, SK_ENOMEM, SK_ECUDA. */
 int capsule_shape_moments(sk_capsule* c, double* out);
 
-/* Copy the current node positions [N][3] to host memory. */
+/* Copy the current node positions [N][3] to host memory, in the node order of
+ * capsule_create (patch, then u index, then v index; Sec. 3.2, Eq. grid). */
 int capsule_get(sk_capsule* c, double* X_out);
 
 /* Release the capsule. NULL is ignored. */
@@ -404,8 +408,9 @@ int serve_poll(sk_server* srv, uint64_t ticket, double* u_out, sk_req_stats* st,
  * free the server. Results that were never polled are discarded. */
 void serve_destroy(sk_server* srv);
 
-/* Single layer without any memory allocation (the paper has no counterpart:
- * this is a service for callers that cannot allocate).
+/* Single layer (Sec. 3.4, Eq. regstokes) without any memory allocation (the
+ * allocation-free call has no counterpart in the paper: it is a service for
+ * callers that cannot allocate).
  *
  * Who needs it: code that runs under a fixed device-memory budget owned by
  * a framework allocator, where a library's own cudaMalloc could fail or
