@@ -40,6 +40,28 @@ def test_header_declares_the_boundary():
         assert required in names
 
 
+def test_every_entry_point_cites_its_passage():
+    """Each declaration's own comment, or the header comment of its section,
+    cites the paper (Sec., Eq., Table, Appendix) or states that the paper has
+    no counterpart (library infrastructure)."""
+    cite = re.compile(r"Sec\.|Eq\.|Table|Appendix|defines no API|no counterpart")
+    decl = re.compile(r"^(?:int|void|const char\*)\s+\**(\w+)\s*\(", re.M)
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        body = text[text.index("#ifndef"):]
+        sections = [m.start() for m in re.finditer(r"/\* ---- ", body)]
+        prev_end, seen = 0, set()
+        for m in decl.finditer(body):
+            own = body[prev_end:m.start()]
+            starts = [p for p in sections if p <= m.start()]
+            head = body[starts[-1]:body.index("*/", starts[-1]) + 2] if starts else ""
+            assert cite.search(own) or cite.search(head), f"{os.path.basename(h)}: {m.group(1)}"
+            prev_end = body.index(";", m.start()) + 1
+            seen.add(m.group(1))
+        # every declared function was checked
+        assert seen == set(declared_functions())
+
+
 def test_every_declared_symbol_is_exported(lib):
     missing = [n for n in declared_functions() if not hasattr(lib, n)]
     assert not missing, missing
