@@ -81,8 +81,11 @@ int sk_version(void);
  *   rho_T: pairs with r/delta below it are evaluated in FP64 by power series
  *          (Sec. 3.4: s1/r and s2/r^3 are smooth at r = 0). 0 < rho_T <= 2.
  *   rho_c: pairs with r/delta at or above it use s1 = s2 = s3 = 1, the plain
- *          Stokeslet/stresslet; the omitted terms are below 6e-8 of the pair's
- *          value at rho_c = 5. rho_T < rho_c <= 8.
+ *          Stokeslet/stresslet. The omitted fraction of a pair's value is
+ *          largest at r/delta = rho_c: at rho_c = 5 it is 1.2e-9 (s1) and
+ *          5.6e-8 (s2) for the single layer, and 8.9e-7 (s3) for the double
+ *          layer; at rho_c = 5.5 it is 4.9e-10 (s2) and 9.5e-9 (s3).
+ *          rho_T < rho_c <= 8.
  * Returns SK_EINVAL outside those ranges. */
 int sk_set_fp32c_thresholds(sk_ctx* ctx, double rho_T, double rho_c);
 

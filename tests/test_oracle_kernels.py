@@ -81,3 +81,25 @@ def test_continuity_across_series_switch():
         lo = oracle.kernel_factor(which, [np.nextafter(1.0, 0.0)])[0]
         hi = oracle.kernel_factor(which, [1.0])[0]
         assert abs(lo / hi - 1) < 1e-14
+
+
+def test_far_cutoff_tails_at_the_default_rho_c():
+    """The plain Stokeslet/stresslet used at r/delta >= rho_c omits 1 - s_i,
+    largest at rho_c. The library documents these fractions for rho_c = 5
+    (its default) and 5.5: 1.2e-9 (s1), 5.6e-8 (s2), 8.9e-7 (s3) at 5;
+    4.9e-10 (s2), 9.5e-9 (s3) at 5.5; each falls monotonically beyond."""
+    tail = {i: 1.0 - oracle.smoothing(i, [5.0, 5.5, 6.0]) for i in (1, 2, 3)}
+    assert tail[1][0] == pytest.approx(1.18e-9, rel=0.01)
+    assert tail[2][0] == pytest.approx(5.62e-8, rel=0.01)
+    assert tail[3][0] == pytest.approx(8.94e-7, rel=0.01)
+    assert tail[2][1] == pytest.approx(4.88e-10, rel=0.01)
+    assert tail[3][1] == pytest.approx(9.48e-9, rel=0.01)
+    for i in (1, 2, 3):
+        assert tail[i][0] > tail[i][1] > tail[i][2] > 0
+    # the leading behaviour: 1 - s_i ~ c p^(2i+1) e^{-p^2} / sqrt(pi) with
+    # c = 4/3, 8/3, 16/9 (the top term of each polynomial times p); erfc p is
+    # smaller by a factor ~ p^(2i+2)
+    p = 5.0
+    for i, c in ((1, 4 / 3), (2, 8 / 3), (3, 16 / 9)):
+        lead = c * p ** (2 * i + 1) * math.exp(-p * p) / SQPI
+        assert tail[i][0] == pytest.approx(lead, rel=0.2)
