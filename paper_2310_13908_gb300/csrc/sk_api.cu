@@ -316,7 +316,7 @@ const char* sk_last_error(const sk_ctx* ctx) { return ctx ? ctx->err.c_str() : g
 int sk_set_fp32c_thresholds(sk_ctx* ctx, double rho_T, double rho_c) {
   if (!ctx) return SK_EINVAL;
   if (!(rho_T > 0.0 && rho_T <= 2.0 && rho_c > rho_T && rho_c <= 8.0))
-    return fail(ctx, SK_EINVAL, "sk_set_fp32c_thresholds: need 0 < rho_T <= 2, rho_T < rho_c <= 8%s");
+    return fail(ctx, SK_EINVAL, "sk_set_fp32c_thresholds: need 0 < rho_T <= 2, rho_T < rho_c <= 8");
   ctx->rho_T = rho_T;
   ctx->rho_c = rho_c;
   return SK_OK;
