@@ -422,9 +422,11 @@ void serve_destroy(sk_server* srv);
  * call creates no context or stream and calls no cudaMalloc, cudaFree or
  * other allocating routine.
  *
- * It computes exactly what stokes_sl_eval(ctx, SK_FP32C, SK_DEVICE, ...)
- * computes, with the default thresholds rho_T = 0.5, rho_c = 5, on the
- * calling thread's current CUDA device. All arrays are device pointers on
+ * It computes what stokes_sl_eval(ctx, SK_FP32C, SK_DEVICE, ...) computes,
+ * with the default thresholds rho_T = 0.5, rho_c = 5, on the calling
+ * thread's current CUDA device: bit for bit while the scratch holds the
+ * context call's split of the source sum; otherwise the sum is split into
+ * fewer chunks and the chunk merge may differ in the last bits (~1e-16). All arrays are device pointers on
  * that device, with the layout of stokes_sl_eval; the caller owns them.
  *
  * Scratch: one static device array of 32 MiB inside the library, shared by
