@@ -26,6 +26,10 @@
  *   - Functions return a status (SK_OK = 0 on success) and never throw; the
  *     message of the last failure is sk_last_error(ctx).
  *   - A context is not thread-safe: one host thread at a time.
+ *   - Calls on one context share its device workspace and its cached
+ *     operators' scratch, so its asynchronous calls must not overlap on the
+ *     GPU: enqueue them on one stream (or order their streams with events).
+ *     Growing the workspace synchronizes the device first.
  */
 #ifndef STOKESREG_H
 #define STOKESREG_H
