@@ -355,7 +355,10 @@ int stokes_sl_eval_fmm(sk_ctx* ctx, int mem, int64_t n_src, const double* src_xy
  * The server owns a host scheduler thread, four CUDA streams, an HBM arena,
  * a slot table and a mapped host page; it uses the context's device and
  * thresholds. One server per context at a time. serve_submit and serve_poll
- * may be called from any host thread. */
+ * may be called from any host thread. The server's arena is separate from the
+ * context workspace; a standalone call on the same context that has to grow
+ * the workspace synchronizes the device, and so waits until the persistent
+ * kernel has run out of work and exited. */
 typedef struct sk_server sk_server;
 
 typedef struct {
