@@ -100,3 +100,28 @@ def test_clock_summary_of_nvidia_smi_lines():
     assert bench.clock_summary(hot)["reasons"] == ["hw_slowdown", "hw_thermal_slowdown"]
     assert bench.clock_summary(hot)["sm_mhz"] == 1785.0
     assert bench.clock_summary([]) is None and bench.clock_summary(["x, y\n"]) is None
+
+
+def test_reference_arm_prints_the_contract_line(monkeypatch, capsys):
+    """The reference arm (the oracle on the host cores) prints one JSON line
+    with the keys of the benchmark contract, its own CPU-baseline record and a
+    host-only e2e record (no device copies)."""
+    import json
+
+    monkeypatch.setenv("RANK", "0")
+    monkeypatch.setenv("WORLD_SIZE", "1")
+
+    class A:
+        m, probes, warmup, steps = 17, 10, 0, 1
+
+    bench.run_reference(A)
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+                "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["value"] > 0 and line["steps"] == 1
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+    assert line["unit"] == bench.UNIT and line["metric"] == bench.METRIC
