@@ -74,3 +74,23 @@ def test_fmm_converges_to_the_direct_sum():
         u = fmm.sl_fmm(s.X, s.w, f, tgt, delta, 1.0, c0, 8, p)
         errs.append(np.linalg.norm(u - ref) / np.linalg.norm(ref))
     assert errs[2] < 1e-5 and errs[2] < errs[1] < errs[0], errs
+
+
+def test_clusters_within_seven_delta_are_summed_directly():
+    """delta = 0.5 on an ellipsoid with 20 clusters: 41% of the (target,
+    cluster) pairs lie outside the check cube, but all lie within 7 delta of
+    the cluster cube, where the regularized kernel differs from the plain one;
+    so every cluster is summed directly and the FMM is the direct sum."""
+    s = ci.make_surface(ci.Ellipsoid(1.0, 0.8, 0.5), 16)
+    f = ci.sh_density(s.x0, np.random.default_rng(4), lmax=6)
+    act = np.flatnonzero(s.w)
+    c0 = s.X[act[:: len(act) // 20][:20]]
+    tgt = s.X[::5]
+    _, lab = fmm.kmeans(s.X[act], c0, 8)
+    cen, a = fmm.boxes(s.X[act], lab, 20)
+    outside = np.mean([(np.abs(tgt - cen[j]).max(axis=1) >= fmm.R_CHECK * a[j]).mean()
+                       for j in range(20)])
+    assert outside > 0.3
+    u = fmm.sl_fmm(s.X, s.w, f, tgt, 0.5, 1.0, c0, 8, 6)
+    ref = oracle.sl(s.X, s.w, f, tgt, 0.5)
+    assert np.allclose(u, ref, rtol=1e-13, atol=1e-13 * np.abs(ref).max())
