@@ -221,13 +221,13 @@ PAIR32_SOURCES = ("sk_pair32.cuh", "sk_pair32.cu", "sk_series.cuh")
 def pair32_source_hash():
     """Hash of what shapes the FP32 pair kernel's launch: its own sources, the
     chunk and decomposition policy (choose_chunks, choose_decomposition in
-    sk_api.cu) and the work-decomposition constants of sk_internal.h (up to
+    sk_decomp.h) and the work-decomposition constants of sk_internal.h (up to
     the Bump allocator)."""
     csrc = os.path.join(ROOT, "paper_2310_13908_gb300", "csrc")
     h = hashlib.sha256()
     for name in PAIR32_SOURCES:
         h.update(open(os.path.join(csrc, name), "rb").read())
-    api = open(os.path.join(csrc, "sk_api.cu")).read()
+    api = open(os.path.join(csrc, "sk_decomp.h")).read()
     for fn in ("int choose_chunks(", "void choose_decomposition("):
         i = api.index(fn)
         h.update(api[i:api.index("\n}\n", i)].encode())

@@ -14,6 +14,7 @@
 #include <cstring>
 #include <new>
 
+#include "sk_decomp.h"
 #include "sk_internal.h"
 
 struct sk_capsule {

@@ -209,9 +209,7 @@ struct EvalShape {
 int ensure_workspace(sk_ctx* ctx, size_t need);
 size_t eval_workspace_bytes(const EvalShape& s);
 void carve_eval_buffers(Bump& bp, const EvalShape& s, EvalBufs& b);
-int choose_chunks(int precision, int64_t N, int64_t M, int sm_count);
-// n_chunks (and, for FP64, the pair kernel's CTA size) of an evaluation shape
-void choose_decomposition(EvalShape& s, int sm_count);
+// choose_chunks and choose_decomposition (the split into work items): sk_decomp.h
 double layer_scale(const EvalShape& s);  // 1/(8 pi mu) or -6/(8 pi)
 int enqueue_prep(const EvalShape& s, const EvalBufs& b, double rho_T, double rho_c,
                  cudaStream_t st);

@@ -11,6 +11,7 @@
 // no counterpart of this entry point.
 #include <mutex>
 
+#include "sk_decomp.h"
 #include "sk_internal.h"
 
 namespace {

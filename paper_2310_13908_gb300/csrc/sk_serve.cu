@@ -34,6 +34,7 @@
 #include <thread>
 #include <vector>
 
+#include "sk_decomp.h"
 #include "sk_pair32.cuh"
 #include "sk_range_alloc.h"
 
