@@ -15,7 +15,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CSRC = os.path.join(ROOT, "paper_2310_13908_gb300", "csrc")
 SMS = 152  # GB300
 
-DRIVER = r"""
+PROGRAM = r"""
 #include <cstdio>
 #include "sk_decomp.h"
 // stdin: "precision N M sm_count" per line; stdout: "n_chunks threads64 fuse_finish np"
@@ -53,9 +53,9 @@ def decompose(tmp_path_factory):
     if cxx is None or inc is None:
         pytest.skip("needs a host C++ compiler and the CUDA headers")
     d = tmp_path_factory.mktemp("decomp")
-    (d / "driver.cpp").write_text(DRIVER)
-    exe = d / "driver"
-    subprocess.run([cxx, "-std=c++17", "-O1", "-I", CSRC, "-I", inc, str(d / "driver.cpp"), "-o",
+    (d / "program.cpp").write_text(PROGRAM)
+    exe = d / "program"
+    subprocess.run([cxx, "-std=c++17", "-O1", "-I", CSRC, "-I", inc, str(d / "program.cpp"), "-o",
                     str(exe)], check=True)
 
     def run(cases):

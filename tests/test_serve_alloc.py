@@ -15,7 +15,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "paper_2310_13908_gb300", "csrc", "sk_range_alloc.h")
 UNIT = 256
 
-DRIVER = r"""
+PROGRAM = r"""
 #include <cstdio>
 #include "sk_range_alloc.h"
 // stdin: "Z size" reset, "A n" alloc (prints offset or -1), "R off n" release,
@@ -44,14 +44,14 @@ int main() {
 
 
 @pytest.fixture(scope="module")
-def driver(tmp_path_factory):
+def program(tmp_path_factory):
     cxx = shutil.which("g++") or shutil.which("c++")
     if cxx is None:
         pytest.skip("no host C++ compiler")
     d = tmp_path_factory.mktemp("range_alloc")
-    src = d / "driver.cpp"
-    src.write_text(DRIVER)
-    exe = d / "driver"
+    src = d / "program.cpp"
+    src.write_text(PROGRAM)
+    exe = d / "program"
     subprocess.run([cxx, "-std=c++17", "-O1", "-I", os.path.dirname(HEADER), str(src), "-o",
                     str(exe)], check=True)
 
@@ -101,8 +101,8 @@ def _parse_ranges(line):
     return [tuple(int(v) for v in tok.split(":")) for tok in line.split()]
 
 
-def test_first_fit_offsets_and_coalescing(driver):
-    out = driver(["Z 4096", "A 1", "A 256", "A 257", "A 0", "F", "R 256 256", "A 300", "A 200",
+def test_first_fit_offsets_and_coalescing(program):
+    out = program(["Z 4096", "A 1", "A 256", "A 257", "A 0", "F", "R 256 256", "A 300", "A 200",
                   "F", "R 0 1", "R 1024 1", "R 512 257", "F", "A 4096", "A 1"])
     # 1 and 256 bytes take one unit each, 257 takes two, 0 takes one
     assert out[:4] == ["0", "256", "512", "1024"]
@@ -116,7 +116,7 @@ def test_first_fit_offsets_and_coalescing(driver):
 
 
 @pytest.mark.parametrize("seed", [0, 1, 2])
-def test_random_sequences_match_the_bitmap_model(driver, seed):
+def test_random_sequences_match_the_bitmap_model(program, seed):
     rng = np.random.default_rng(seed)
     size = 64 * UNIT
     model = BitmapModel(size)
@@ -136,7 +136,7 @@ def test_random_sequences_match_the_bitmap_model(driver, seed):
         if rng.random() < 0.1:
             cmds.append("F")
             expect.append(model.ranges())
-    got = driver(cmds)
+    got = program(cmds)
     assert len(got) == len(expect)
     for g, e in zip(got, expect):
         if isinstance(e, list):
@@ -146,4 +146,4 @@ def test_random_sequences_match_the_bitmap_model(driver, seed):
     # releasing every live block restores the whole range
     for off, n in live:
         cmds.append(f"R {off} {n}")
-    assert _parse_ranges(driver(cmds + ["F"])[-1]) == [(0, size)]
+    assert _parse_ranges(program(cmds + ["F"])[-1]) == [(0, size)]
