@@ -85,6 +85,7 @@ void carve_eval_buffers(Bump& bp, const EvalShape& s, EvalBufs& b) {
   b.src_orig = bp.take<int>(b.N_pad);
   if (fp32) {
     b.srcF = bp.take<float4>((size_t)b.N_pad * (dl ? V_DL : V_SL));
+    if (dl) b.srcLo = bp.take<float4>(b.N_pad);
   } else {
     b.src64 = bp.take<double4_32a>((size_t)b.N_pad * 2);
     if (dl) b.nrm64 = bp.take<double4_32a>(b.N_pad);

@@ -109,6 +109,7 @@ struct EvalBufs {
   int* meta = nullptr;
   int* src_orig = nullptr;        // packed source -> original index (-1: padding)
   float4* srcF = nullptr;         // FP32 packed sources
+  float4* srcLo = nullptr;        // double layer, FP32C: residual (y - c) - fl32(y - c) per source
   double4_32a* src64 = nullptr;       // FP64 packed sources (pos, density)
   double4_32a* nrm64 = nullptr;       // FP64 packed normals (double layer)
   float4* segbox = nullptr;       // per segment: lo, hi

@@ -71,7 +71,7 @@ void launch_pair32_t(const EvalBufs& b, float rho_lo, float rho_hi, double scale
   const unsigned grid = (unsigned)((b.M_pad / (TPB32 * 2 * NP)) * b.n_chunks);
   const size_t smem = pair_smem_bytes<L, NP>();
   PairArgs a{b.srcF,  b.segbox,   b.src_orig, b.meta,     b.tgtF,  b.tgt64, b.M_pad,
-             b.n_chunks, b.part, b.near_cnt, b.near_idx, b.flags, rho_lo, rho_hi};
+             b.n_chunks, b.part, b.near_cnt, b.near_idx, b.flags, rho_lo, rho_hi, b.srcLo};
   OverflowArgs oa{b.srcF, b.segbox, b.src_orig, b.meta,  b.tgtF,  b.tgt64,     b.near_cnt,
                   b.src_xyz, b.src_w, b.dens,   b.nrm, scale, b.flags, b.near_ovf};
   FinishArgs fa{b.tgt64, b.tgt_perm, b.M_pad, b.n_chunks, b.part, b.near_cnt, b.near_idx,

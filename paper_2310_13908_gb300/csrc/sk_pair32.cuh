@@ -121,6 +121,22 @@ __device__ __forceinline__ float2 shift_to_segment2(float2 hi, float2 lo, float 
   return __fadd2_rn(__ffma2_rn(make_float2(c, c), make_float2(-1.f, -1.f), hi), lo);
 }
 
+// Rounding error of s = fl(a + b), exactly (Knuth's TwoSum).
+__device__ __forceinline__ float2 two_sum_err2(float2 a, float2 b, float2 s) {
+  const float2 bp = sub2(s, a);
+  const float2 ap = sub2(s, bp);
+  return add2(sub2(a, ap), sub2(b, bp));
+}
+
+// What shift_to_segment2 dropped: (hi + lo - c) - t for t = its result, to
+// FP32 rounding of this small residual. With the source's residual (srcLo) it
+// turns the FP32 difference of a pair into the exact one.
+__device__ __forceinline__ float2 shift_residual2(float2 hi, float2 lo, float c, float2 t) {
+  const float2 nc = make_float2(-c, -c);
+  const float2 a = add2(hi, nc);  // fl(hi - c), the first rounding of shift_to_segment2
+  return add2(two_sum_err2(hi, nc, a), two_sum_err2(a, lo, t));
+}
+
 // Margin added to rho_c delta in the segment-versus-warp box test: the boxes
 // hold absolute FP32 coordinates, while pair distances come from frame-
 // relative coordinates; the two differ by a few FP32 roundings of the
@@ -145,6 +161,8 @@ __device__ __forceinline__ void near_append(int64_t t, int jo, int* __restrict__
 struct SLayer {
   static constexpr int V = V_SL;
   static constexpr int STAGES = 4;
+  // no exact differences needed: the Stokeslet has no cancelling factor
+  static constexpr bool kExactNear = false;
   struct Src {
     float2 nx, ny, nz, gx, gy, gz;
   };
@@ -186,6 +204,11 @@ struct SLayer {
 struct DLayer {
   static constexpr int V = V_DL;
   static constexpr int STAGES = 3;
+  // (x - y) . n cancels to O(r^2) on the surface: pairs inside rho_c delta take
+  // the exact difference (FP32 residuals of the frame shifts added back),
+  // which FP32 rounding of |x - c| and |y - c| would otherwise swamp when the
+  // segment spans more than a few delta (sparse or irregular sources)
+  static constexpr bool kExactNear = true;
   struct Src {
     float2 nx, ny, nz, qx, qy, qz, mx, my, mz;  // m: surface normal
   };
@@ -233,15 +256,19 @@ __device__ __forceinline__ void pair_d(const Tgt2& T, float2 nx, float2 ny, floa
   r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
 }
 
-// Slow path of one target pair for one source: regime per lane component.
+// Slow path of one target pair for one source: regime per lane component,
+// decided on the FP32 difference r2 (the test of the far loop and of the
+// overflow rescan). rho and the kernel use (dx, dy, dz) and r2k, which equal
+// the FP32 difference and r2 except where pair_general corrected them.
 template <class L>
-__device__ __forceinline__ void pair_general(const typename L::Src& S, const Tgt2& T, float2 dx,
-                                             float2 dy, float2 dz, float2 r2, float2* U,
-                                             int64_t t0, int64_t t1, const int* src_orig_j,
-                                             int* near_cnt, int* near_idx,
-                                             unsigned long long* flags, float rho_lo,
-                                             float rho_hi) {
-  float2 ri = make_float2(rsq(r2.x), rsq(r2.y));
+__device__ __forceinline__ void pair_general_regimes(const typename L::Src& S, const Tgt2& T,
+                                                     float2 dx, float2 dy, float2 dz, float2 r2,
+                                                     float2 r2k, float2* U, int64_t t0,
+                                                     int64_t t1, const int* src_orig_j,
+                                                     int* near_cnt, int* near_idx,
+                                                     unsigned long long* flags, float rho_lo,
+                                                     float rho_hi) {
+  float2 ri = make_float2(rsq(r2k.x), rsq(r2k.y));
   float2 sa = make_float2(1.f, 1.f), sb = make_float2(1.f, 1.f);
   // component x
   {
@@ -251,7 +278,7 @@ __device__ __forceinline__ void pair_general(const typename L::Src& S, const Tgt
       near_append(t0, *src_orig_j, near_cnt, near_idx, flags);
       ri.x = 0.f;
     }
-    float rho = fminf(fmaxf(r2.x * ri.x * T.idl.x, rho_lo), rho_hi);
+    float rho = fminf(fmaxf(r2k.x * ri.x * T.idl.x, rho_lo), rho_hi);
     float a, b;
     L::smooth(rho, a, b);
     if (in) {
@@ -266,7 +293,7 @@ __device__ __forceinline__ void pair_general(const typename L::Src& S, const Tgt
       near_append(t1, *src_orig_j, near_cnt, near_idx, flags);
       ri.y = 0.f;
     }
-    float rho = fminf(fmaxf(r2.y * ri.y * T.idl.y, rho_lo), rho_hi);
+    float rho = fminf(fmaxf(r2k.y * ri.y * T.idl.y, rho_lo), rho_hi);
     float a, b;
     L::smooth(rho, a, b);
     if (in) {
@@ -275,6 +302,35 @@ __device__ __forceinline__ void pair_general(const typename L::Src& S, const Tgt
     }
   }
   L::general(S, dx, dy, dz, ri, sa, sb, U);
+}
+
+// For L::kExactNear, (cx, cy, cz) is the residual that makes the FP32
+// difference exact: pairs with rho_T <= rho < rho_c take the corrected
+// difference; the others keep the FP32 one, so a pair at or beyond rho_c
+// still reproduces the far formula bit for bit.
+template <class L>
+__device__ __forceinline__ void pair_general(const typename L::Src& S, const Tgt2& T, float2 dx,
+                                             float2 dy, float2 dz, float2 r2, float2* U,
+                                             int64_t t0, int64_t t1, const int* src_orig_j,
+                                             int* near_cnt, int* near_idx,
+                                             unsigned long long* flags, float rho_lo,
+                                             float rho_hi, float2 cx = float2{},
+                                             float2 cy = float2{}, float2 cz = float2{}) {
+  if constexpr (L::kExactNear) {
+    const bool in0 = r2.x >= T.rt2.x && r2.x < T.rc2.x;
+    const bool in1 = r2.y >= T.rt2.y && r2.y < T.rc2.y;
+    const float2 ex = add2(dx, cx), ey = add2(dy, cy), ez = add2(dz, cz);
+    const float2 er2 = fma2(ez, ez, fma2(ey, ey, mul2(ex, ex)));
+    dx = make_float2(in0 ? ex.x : dx.x, in1 ? ex.y : dx.y);
+    dy = make_float2(in0 ? ey.x : dy.x, in1 ? ey.y : dy.y);
+    dz = make_float2(in0 ? ez.x : dz.x, in1 ? ez.y : dz.y);
+    const float2 r2k = make_float2(in0 ? er2.x : r2.x, in1 ? er2.y : r2.y);
+    pair_general_regimes<L>(S, T, dx, dy, dz, r2, r2k, U, t0, t1, src_orig_j, near_cnt,
+                            near_idx, flags, rho_lo, rho_hi);
+  } else {
+    pair_general_regimes<L>(S, T, dx, dy, dz, r2, r2, U, t0, t1, src_orig_j, near_cnt, near_idx,
+                            flags, rho_lo, rho_hi);
+  }
 }
 
 __device__ __forceinline__ void two_sum_merge(float2* U, float2* HI, float2* LO) {
@@ -307,6 +363,9 @@ __host__ __device__ constexpr int pair_stages() {
   return NP == 1 ? L::STAGES - 1 : L::STAGES;
 }
 constexpr int TGT_SLOTS = 5;
+// A segment is wide for a target when its frame's half extent exceeds this
+// many of the target's delta (see pair_item's general branch).
+constexpr float WIDE_FRAME = 4.0f;
 template <class L, int NP>
 constexpr size_t pair_smem_bytes() {
   return (size_t)pair_stages<L, NP>() * TILE * L::V * sizeof(float4) +
@@ -339,6 +398,7 @@ struct PairArgs {
   int* near_idx;
   unsigned long long* flags;
   float rho_lo, rho_hi;
+  const float4* srcLo = nullptr;  // double layer: residuals of the packed positions
 };
 
 // One work item: target block tb (TPB32 * 2 * NP sorted targets) against
@@ -476,6 +536,7 @@ __device__ __forceinline__ bool pair_item(const PairArgs& a, int tb, int ch, flo
       const float4* S = sm + buf * TILE * V;
       bool nb = false;
       float csx = 0.f, csy = 0.f, csz = 0.f;  // lane s < TILE_SEGS: segment s's frame
+      float chs = 0.f;                        // ... and the half extent of its box
       if (lane < TILE_SEGS) {
         const float4 lo = segbox[2 * ((size_t)k * TILE_SEGS + lane)];
         const float4 hi = segbox[2 * ((size_t)k * TILE_SEGS + lane) + 1];
@@ -486,22 +547,22 @@ __device__ __forceinline__ bool pair_item(const PairArgs& a, int tb, int ch, flo
         csx = frame_mid(lo.x, hi.x);
         csy = frame_mid(lo.y, hi.y);
         csz = frame_mid(lo.z, hi.z);
+        if constexpr (L::kExactNear)
+          chs = 0.5f * fmaxf(fmaxf(hi.x - lo.x, hi.y - lo.y), hi.z - lo.z);
       }
       const unsigned nm = __ballot_sync(FULL, nb);
 #pragma unroll 1
       for (int s = 0; s < TILE_SEGS; ++s) {
         const float4* SS = S + s * SEG * V;
-        {
-          const float sx = __shfl_sync(FULL, csx, s), sy = __shfl_sync(FULL, csy, s),
-                      sz = __shfl_sync(FULL, csz, s);
+        const float sx = __shfl_sync(FULL, csx, s), sy = __shfl_sync(FULL, csy, s),
+                    sz = __shfl_sync(FULL, csz, s);
 #pragma unroll
-          for (int p = 0; p < NP; ++p) {
-            const float4 hx = ts[(p * TGT_SLOTS) * TPB32], hy = ts[(p * TGT_SLOTS + 1) * TPB32],
-                         hz = ts[(p * TGT_SLOTS + 2) * TPB32];
-            T[p].x = shift_to_segment2(lo2(hx), hi2(hx), sx);
-            T[p].y = shift_to_segment2(lo2(hy), hi2(hy), sy);
-            T[p].z = shift_to_segment2(lo2(hz), hi2(hz), sz);
-          }
+        for (int p = 0; p < NP; ++p) {
+          const float4 hx = ts[(p * TGT_SLOTS) * TPB32], hy = ts[(p * TGT_SLOTS + 1) * TPB32],
+                       hz = ts[(p * TGT_SLOTS + 2) * TPB32];
+          T[p].x = shift_to_segment2(lo2(hx), hi2(hx), sx);
+          T[p].y = shift_to_segment2(lo2(hy), hi2(hy), sy);
+          T[p].z = shift_to_segment2(lo2(hz), hi2(hz), sz);
         }
         if (!((nm >> s) & 1u)) {
 #pragma unroll kFarUnroll
@@ -523,25 +584,81 @@ __device__ __forceinline__ bool pair_item(const PairArgs& a, int tb, int ch, flo
             T[p].rc2 = hi2(q);
             T[p].rt2 = lo2(r);
           }
+          // Exact differences (L::kExactNear) where the segment is wide for a
+          // target: its frame half extent above WIDE_FRAME target deltas, so
+          // that FP32 rounding of |x - c| and |y - c| could swamp an O(r^2)
+          // (x - y) . n. Decided per target and segment, so a target's result
+          // does not depend on the warp it landed in.
+          bool wide = false;
+          const float hs = __shfl_sync(FULL, chs, s);
+          if constexpr (L::kExactNear) {
+#pragma unroll
+            for (int p = 0; p < NP; ++p)
+              wide |= (hs * T[p].idl.x > WIDE_FRAME) | (hs * T[p].idl.y > WIDE_FRAME);
+            wide = __any_sync(FULL, wide);
+          }
+          if (!wide) {
 #pragma unroll 1
-          for (int j = 0; j < SEG; ++j) {
-            const typename L::Src src = L::load(SS + j * V);
-            float2 dx[NP], dy[NP], dz[NP], r2[NP];
-            bool any = false;
+            for (int j = 0; j < SEG; ++j) {
+              const typename L::Src src = L::load(SS + j * V);
+              float2 dx[NP], dy[NP], dz[NP], r2[NP];
+              bool any = false;
 #pragma unroll
-            for (int p = 0; p < NP; ++p) {
-              pair_d(T[p], src.nx, src.ny, src.nz, dx[p], dy[p], dz[p], r2[p]);
-              any |= (r2[p].x < T[p].rc2.x) | (r2[p].y < T[p].rc2.y);
+              for (int p = 0; p < NP; ++p) {
+                pair_d(T[p], src.nx, src.ny, src.nz, dx[p], dy[p], dz[p], r2[p]);
+                any |= (r2[p].x < T[p].rc2.x) | (r2[p].y < T[p].rc2.y);
+              }
+              if (__any_sync(FULL, any)) {
+#pragma unroll
+                for (int p = 0; p < NP; ++p)
+                  pair_general<L>(src, T[p], dx[p], dy[p], dz[p], r2[p], U[p], wbase + 64 * p,
+                                  wbase + 64 * p + 32, orig + j, near_cnt, near_idx, flags,
+                                  rho_lo, rho_hi);
+              } else {
+#pragma unroll
+                for (int p = 0; p < NP; ++p) L::far(src, dx[p], dy[p], dz[p], r2[p], U[p]);
+              }
             }
-            if (__any_sync(FULL, any)) {
+          } else if constexpr (L::kExactNear) {
+            // lane j holds source j's residual; the targets' frame-shift
+            // residuals are recomputed per source from the (hi, lo) column
+            const float4 ylo = a.srcLo[(size_t)k * TILE + s * SEG + lane];
+#pragma unroll 1
+            for (int j = 0; j < SEG; ++j) {
+              const typename L::Src src = L::load(SS + j * V);
+              float2 dx[NP], dy[NP], dz[NP], r2[NP];
+              bool any = false;
 #pragma unroll
-              for (int p = 0; p < NP; ++p)
-                pair_general<L>(src, T[p], dx[p], dy[p], dz[p], r2[p], U[p], wbase + 64 * p,
-                                wbase + 64 * p + 32, orig + j, near_cnt, near_idx, flags, rho_lo,
-                                rho_hi);
-            } else {
+              for (int p = 0; p < NP; ++p) {
+                pair_d(T[p], src.nx, src.ny, src.nz, dx[p], dy[p], dz[p], r2[p]);
+                any |= (r2[p].x < T[p].rc2.x) | (r2[p].y < T[p].rc2.y);
+              }
+              if (__any_sync(FULL, any)) {
+                const float lx = __shfl_sync(FULL, ylo.x, j), ly = __shfl_sync(FULL, ylo.y, j),
+                            lz = __shfl_sync(FULL, ylo.z, j);
 #pragma unroll
-              for (int p = 0; p < NP; ++p) L::far(src, dx[p], dy[p], dz[p], r2[p], U[p]);
+                for (int p = 0; p < NP; ++p) {
+                  const float4 hx = ts[(p * TGT_SLOTS) * TPB32],
+                               hy = ts[(p * TGT_SLOTS + 1) * TPB32],
+                               hz = ts[(p * TGT_SLOTS + 2) * TPB32];
+                  const float2 wd = make_float2(hs * T[p].idl.x > WIDE_FRAME ? 1.f : 0.f,
+                                                hs * T[p].idl.y > WIDE_FRAME ? 1.f : 0.f);
+                  // residual of the pair (target's minus source's), zero where
+                  // the segment is not wide for that target
+                  pair_general<L>(src, T[p], dx[p], dy[p], dz[p], r2[p], U[p], wbase + 64 * p,
+                                  wbase + 64 * p + 32, orig + j, near_cnt, near_idx, flags,
+                                  rho_lo, rho_hi,
+                                  mul2(wd, sub2(shift_residual2(lo2(hx), hi2(hx), sx, T[p].x),
+                                                make_float2(lx, lx))),
+                                  mul2(wd, sub2(shift_residual2(lo2(hy), hi2(hy), sy, T[p].y),
+                                                make_float2(ly, ly))),
+                                  mul2(wd, sub2(shift_residual2(lo2(hz), hi2(hz), sz, T[p].z),
+                                                make_float2(lz, lz))));
+                }
+              } else {
+#pragma unroll
+                for (int p = 0; p < NP; ++p) L::far(src, dx[p], dy[p], dz[p], r2[p], U[p]);
+              }
             }
           }
         }

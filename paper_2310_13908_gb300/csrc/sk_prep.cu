@@ -361,13 +361,17 @@ constexpr float PAD_POS = 1.0e15f;  // padding sources sit far away with zero de
 // to the segment's frame (frame_mid of its box; padding keeps PAD_POS):
 //   single layer: {-x,-x,-y,-y} {-z,-z,gx,gx} {gy,gy,gz,gz},  g = w f scale
 //   double layer: {-x,-x,-y,-y} {-z,-z,qx,qx} {qy,qy,qz,qz} {nx,nx,ny,ny} {nz,nz,0,0},
-//                 q = w q_in scale
+//                 q = w q_in scale; and, in srcLo, the FP32 residuals of the
+//                 frame-relative position, (y - c) - fl32(y - c) per axis, from
+//                 which the stresslet forms exact differences for pairs inside
+//                 rho_c delta
 template <int LAYER>
 __global__ void k_pack_src32(const double* __restrict__ xyz, const double* __restrict__ w,
                              const double* __restrict__ dens, const double* __restrict__ nrm,
                              const int* __restrict__ sorted, int* __restrict__ meta,
                              int64_t N_pad, double scale, float4* __restrict__ srcF,
-                             int* __restrict__ src_orig, float4* __restrict__ segbox) {
+                             float4* __restrict__ srcLo, int* __restrict__ src_orig,
+                             float4* __restrict__ segbox) {
   constexpr int V = LAYER == LAYER_SL ? V_SL : V_DL;
   const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int Ns = meta[META_NS];
@@ -386,10 +390,15 @@ __global__ void k_pack_src32(const double* __restrict__ xyz, const double* __res
   // relative to the segment's frame, differenced in FP64
   const float3 c = warp_box(real, x, y, z, segbox + 2 * (s / SEG));
   float d0 = 0.f, d1 = 0.f, d2 = 0.f, n0 = 0.f, n1 = 0.f, n2 = 0.f;
+  float4 res = make_float4(0.f, 0.f, 0.f, 0.f);
   if (real) {
-    x = (float)(xyz[3 * j] - (double)c.x);
-    y = (float)(xyz[3 * j + 1] - (double)c.y);
-    z = (float)(xyz[3 * j + 2] - (double)c.z);
+    const double rx = xyz[3 * j] - (double)c.x, ry = xyz[3 * j + 1] - (double)c.y,
+                 rz = xyz[3 * j + 2] - (double)c.z;
+    x = (float)rx;
+    y = (float)ry;
+    z = (float)rz;
+    res = make_float4((float)(rx - (double)x), (float)(ry - (double)y), (float)(rz - (double)z),
+                      0.f);
     const double ws = w[j] * scale;
     d0 = (float)(ws * dens[3 * j]);
     d1 = (float)(ws * dens[3 * j + 1]);
@@ -407,6 +416,7 @@ __global__ void k_pack_src32(const double* __restrict__ xyz, const double* __res
   if (LAYER == LAYER_DL) {
     o[3] = make_float4(n0, n0, n1, n1);
     o[4] = make_float4(n2, n2, 0.f, 0.f);
+    srcLo[s] = res;
   }
   src_orig[s] = j;
 }
@@ -514,10 +524,12 @@ void launch_pack_sources32(int layer, const EvalBufs& b, double scale, cudaStrea
   unsigned g = blocks_for(b.N_pad, 256);
   if (layer == LAYER_SL)
     k_pack_src32<LAYER_SL><<<g, 256, 0, st>>>(b.src_xyz, b.src_w, b.dens, b.nrm, b.vals_a, b.meta,
-                                              b.N_pad, scale, b.srcF, b.src_orig, b.segbox);
+                                              b.N_pad, scale, b.srcF, nullptr, b.src_orig,
+                                              b.segbox);
   else
     k_pack_src32<LAYER_DL><<<g, 256, 0, st>>>(b.src_xyz, b.src_w, b.dens, b.nrm, b.vals_a, b.meta,
-                                              b.N_pad, scale, b.srcF, b.src_orig, b.segbox);
+                                              b.N_pad, scale, b.srcF, b.srcLo, b.src_orig,
+                                              b.segbox);
 }
 
 void launch_pack_sources64(int layer, const EvalBufs& b, double scale, cudaStream_t st) {

@@ -134,6 +134,33 @@ def test_sl_ellipsoid_full_size_sampled(ctx, ellipsoid_full, prec):
     assert np.all(np.isfinite(u))
 
 
+@pytest.mark.parametrize("prec", PRECS, ids=PREC_ID.get)
+def test_sl_ellipsoid_full_size_delta_3h(ctx, ellipsoid_full, prec):
+    """The headline workload at its widest regularization, delta = 3h: up to
+    ~64 near pairs per target (rho < rho_T) against 96 list slots, and the
+    exterior probes closest to the surface (~0.1h, nearly all of their pairs
+    inside rho_c delta) among the sampled targets."""
+    from scipy.spatial import cKDTree
+    w = ellipsoid_full
+    s = w.surface
+    delta = np.array([3.0 * s.h])
+    u = sk.stokes_sl_eval(ctx, prec, sk.SK_DEVICE, to_dev(s.X), to_dev(s.w), to_dev(w.f),
+                          to_dev(w.targets), to_dev(delta), w.mu).cpu().numpy()
+    st = sk.sk_last_eval_stats(ctx)
+    if prec == sk.SK_FP32C:
+        assert st["overflow_targets"] == 0
+    rng = np.random.default_rng(78)
+    M, n_on = w.targets.shape[0], w.n_on_surface
+    dist, _ = cKDTree(s.X).query(w.targets[n_on:])
+    closest = n_on + np.argsort(dist)[:64]          # probes at ~0.1h
+    idx = np.concatenate([rng.choice(n_on, 320, replace=False), closest,
+                          n_on + rng.choice(M - n_on, 128, replace=False)])
+    ref = oracle.sl(s.X, s.w, w.f, w.targets[idx], delta, w.mu)
+    assert_close(u[idx], ref, prec)
+    assert_close(u[closest], ref[320:384], prec)
+    assert np.all(np.isfinite(u))
+
+
 def test_dl_ellipsoid_sampled_with_probes(ctx):
     w = ci.ellipsoid_hires_workload(m=129, n_probes=20000, seed=3100)
     s = w.surface
@@ -185,15 +212,15 @@ def test_fp32c_far_from_origin(ctx, layer):
 @pytest.mark.parametrize("prec", PRECS, ids=PREC_ID.get)
 def test_ragged_sizes_and_per_target_delta(ctx, prec):
     """Single and double layer at ragged sizes (1 target, 1 source, partial
-    tiles and target blocks) with one delta per target. The double layer takes
-    a smooth (SH) density: with random densities on a sparse random source
-    subset a few near pairs dominate each on-surface target, and there (x - y).n
-    cancels to O(r^2), which FP32 differences carry only to ~1e-6 relative, so
-    the sum does not average those errors away."""
+    tiles and target blocks) with one delta per target and random densities
+    on random source subsets. On the surface (x - y).n cancels to O(r^2), and
+    on a sparse subset the 32 sources of a segment span many delta: the
+    double layer's FP32 path forms exact differences for pairs inside rho_c,
+    so the error stays at the level of the smooth cases."""
     rng = np.random.default_rng(9)
     s = ci.make_surface(ci.Ellipsoid(1.0, 0.7, 0.6), 21)
     f = rng.standard_normal((s.N, 3))
-    q = ci.sh_density(s.x0, np.random.default_rng(19), lmax=6)
+    q = np.random.default_rng(19).standard_normal((s.N, 3))
     for n_src, n_tgt in ((1, 1), (7, 33), (257, 1), (300, 1025), (s.N, 1023), (s.N, 2049)):
         src = rng.choice(s.N, n_src, replace=False)
         Y = np.concatenate([s.X, s.X + 0.03 * s.n])[rng.choice(2 * s.N, n_tgt, replace=False)]
