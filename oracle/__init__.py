@@ -83,6 +83,8 @@ class Oracle:
         for name in ("oracle_s1", "oracle_s2", "oracle_s3"):
             getattr(lib, name).argtypes = [ctypes.c_double]
             getattr(lib, name).restype = ctypes.c_double
+        lib.oracle_plain_stokeslet.argtypes = [i64, _dp, _dp, i64, _dp, _dp, ctypes.c_int]
+        lib.oracle_plain_stokeslet.restype = ctypes.c_int
         lib.oracle_max_threads.argtypes = []
         lib.oracle_max_threads.restype = ctypes.c_int
         self.lib = lib
@@ -124,6 +126,20 @@ class Oracle:
             raise ValueError("oracle_dl rejected its arguments")
         return out
 
+    def plain_stokeslet(self, src_xyz, g, tgt_xyz, threads: int = 0) -> np.ndarray:
+        """Plain Stokeslet sum without 1/(8 pi mu): sum g/r + (g . d) d / r^3, (M, 3)."""
+        X = _c(src_xyz, (-1, 3))
+        n = X.shape[0]
+        g = _c(g, (n, 3))
+        Y = _c(tgt_xyz, (-1, 3))
+        M = Y.shape[0]
+        out = np.zeros((M, 3))
+        rc = self.lib.oracle_plain_stokeslet(n, _ptr(X), _ptr(g), M, _ptr(Y), _ptr(out),
+                                             int(threads))
+        if rc != 0:
+            raise ValueError("oracle_plain_stokeslet rejected its arguments")
+        return out
+
     def kernel_factor(self, which: int, rho, branch: str = "auto") -> np.ndarray:
         """s1(p)/p (which=1), s2(p)/p^3 (which=2) or s3(p)/p^5 (which=3).
 
@@ -161,6 +177,10 @@ def sl(*args, **kwargs):
 
 def dl(*args, **kwargs):
     return default().dl(*args, **kwargs)
+
+
+def plain_stokeslet(*args, **kwargs):
+    return default().plain_stokeslet(*args, **kwargs)
 
 
 def kernel_factor(*args, **kwargs):

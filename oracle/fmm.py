@@ -6,61 +6,68 @@ Steps, in the paper's order:
   2. per cluster, an enclosing cube carrying equivalent sources on a regular
      grid of its surface, and a larger check cube; the equivalent densities
      reproduce, on the check surface, the potential of the cluster's points;
-  3. a target takes the equivalent sources of the clusters that are far from
-     it and the direct (regularized) sum over the points of the others.
+  3. box against box: the points of a box take the direct (regularized) sum
+     over the points of the neighbouring boxes and the equivalent sources of
+     the non-neighbouring ones.
 
 Readings (the paper gives no more detail):
   * Sources with zero weight are dropped first (they contribute exactly 0).
   * k-means: Lloyd iterations from caller-given initial centres; a point
-    goes to its nearest centre (lowest index on ties); a centre moves to the
-    mean of its points (an empty cluster keeps its centre); the clusters are
-    those of the final assignment to the final centres.
-  * The cluster cube: centre = midpoint of the points' bounding box, half
-    width a = half the largest extent. Equivalent cube: half width 1.05 a;
-    check cube: 2.95 a (the radii of the kernel-independent FMM the paper
-    builds on). Surface grids: p points per edge (6p^2 - 12p + 8).
+    goes to its nearest centre, by the squared distance (dx^2 + dy^2) + dz^2
+    (lowest index on ties); a centre moves to the mean of its points (an
+    empty cluster keeps its centre); the clusters are those of the final
+    assignment to the final centres.
+  * Source boxes: the cube of a cluster has its centre at the midpoint of
+    the points' bounding box and half width a = half the largest extent.
+    Equivalent cube: half width 1.05 a; check cube: 2.95 a (the radii of the
+    kernel-independent FMM the paper builds on). Surface grids: p points per
+    edge (6p^2 - 12p + 8).
   * Equivalent densities: Tikhonov-regularized least squares,
     min |K phi - u_check|^2 + alpha^2 |phi|^2 with alpha = 1e-8 |K|_F, K the
     plain-Stokeslet matrix from equivalent to check points. (A truncated
     pseudo-inverse does no better here; this one scales exactly with the
     cube size, phi(a) = a phi(1).)
-  * Far: the target lies outside the check cube and at least 7 delta from
-    the cluster cube, so the regularized kernel of every source in the
-    cluster equals the plain one to double precision. As the paper decides
-    box against box, targets are taken in groups of GROUP consecutive
-    indices: a group uses a cluster's equivalent sources only when the
-    cluster is far for every target of the group.
+  * Target boxes: the targets need not be nodes (off-surface probes), so
+    each target joins the box of its nearest final centre, by the same rule
+    as the points; a target box is the bounding box of its targets, with the
+    largest delta among them.
+  * Neighbouring boxes: source cluster j is a neighbour of target box i
+    unless the whole target box lies outside j's check cube (where the
+    equivalent sources reproduce the cluster's potential) and at least
+    7 delta_i from j's cube (where the regularized kernel of every source of
+    the cluster equals the plain one to double precision).
 """
 
 from __future__ import annotations
 
 import numpy as np
 
+from . import plain_stokeslet
 from . import sl as oracle_sl
 
 R_EQUIV = 1.05
 R_CHECK = 2.95
 RHO_FAR = 7.0
 TIKHONOV = 1e-8
-GROUP = 32
+
+
+def nearest_centre(points: np.ndarray, c: np.ndarray) -> np.ndarray:
+    """Index of the nearest centre of every point (lowest index on ties)."""
+    d = points[:, None, :] - c[None, :, :]
+    d2 = (d[..., 0] * d[..., 0] + d[..., 1] * d[..., 1]) + d[..., 2] * d[..., 2]
+    return np.argmin(d2, axis=1)   # first minimum: lowest index on ties
 
 
 def kmeans(points: np.ndarray, centers0: np.ndarray, iters: int):
     """Lloyd iterations; returns (centers, labels of the final assignment)."""
     c = np.array(centers0, dtype=np.float64, copy=True)
-
-    def assign(c):
-        d = points[:, None, :] - c[None, :, :]
-        d2 = (d[..., 0] * d[..., 0] + d[..., 1] * d[..., 1]) + d[..., 2] * d[..., 2]
-        return np.argmin(d2, axis=1)   # first minimum: lowest index on ties
-
     for _ in range(iters):
-        lab = assign(c)
+        lab = nearest_centre(points, c)
         for j in range(len(c)):
             sel = lab == j
             if np.any(sel):
                 c[j] = points[sel].mean(axis=0)
-    return c, assign(c)
+    return c, nearest_centre(points, c)
 
 
 def cube_surface(p: int) -> np.ndarray:
@@ -116,36 +123,72 @@ def equivalent_densities(points, weights, f, labels, cen, a, p):
     return eq_pts, eq_den
 
 
-def sl_fmm(src, w, f, tgt, delta, mu, centers0, iters, p):
-    """S[f] at the targets by the single-level FMM."""
+def neighbours(lo, hi, delta_i, cen, a):
+    """Neighbour flags of one target box [lo, hi] (largest delta delta_i)
+    against every source cluster cube (cen, a): True where the direct sum
+    is required."""
+    outside_check = np.any((lo[None] > cen + R_CHECK * a[:, None]) |
+                           (hi[None] < cen - R_CHECK * a[:, None]), axis=1)
+    g = np.maximum(np.maximum(lo[None] - (cen + a[:, None]), (cen - a[:, None]) - hi[None]), 0.0)
+    gap2 = (g[:, 0] * g[:, 0] + g[:, 1] * g[:, 1]) + g[:, 2] * g[:, 2]
+    far = outside_check & (gap2 >= (RHO_FAR * delta_i) * (RHO_FAR * delta_i))
+    return ~far
+
+
+def far_field(T, E, phi):
+    """Plain Stokeslet sum (without 1/(8 pi mu)) of equivalent sources E with
+    densities phi at the points T: sum_e phi_e / r + (phi_e . d) d / r^3."""
+    return plain_stokeslet(E, phi, T)
+
+
+def plan(src, w, tgt, delta, centers0, iters):
+    """The FMM's discrete decisions: active sources, k-means centres and
+    labels, cluster cubes, target boxes and the neighbour matrix
+    near[i, j] (target box i, source cluster j)."""
     src = np.asarray(src, np.float64)
     tgt = np.asarray(tgt, np.float64)
     w = np.asarray(w, np.float64)
-    f = np.asarray(f, np.float64)
     delta = np.broadcast_to(np.asarray(delta, np.float64), (len(tgt),))
     act = w != 0.0           # zero weights contribute exactly nothing
-    src, w, f = src[act], w[act], f[act]
     k = len(centers0)
-    _, labels = kmeans(src, centers0, iters)
-    cen, a = boxes(src, labels, k)
+    centers, labels = kmeans(src[act], centers0, iters)
+    cen, a = boxes(src[act], labels, k)
+    tlab = nearest_centre(tgt, centers)
+    near = np.zeros((k, k), dtype=bool)
+    for i in range(k):
+        ti = np.flatnonzero(tlab == i)
+        if len(ti):
+            T = tgt[ti]
+            near[i] = neighbours(T.min(axis=0), T.max(axis=0), float(delta[ti].max()), cen, a)
+    return {"act": act, "centers": centers, "labels": labels, "cen": cen, "a": a,
+            "tlab": tlab, "near": near, "delta": delta}
+
+
+def sl_fmm(src, w, f, tgt, delta, mu, centers0, iters, p):
+    """S[f] at the targets by the single-level FMM."""
+    pl = plan(src, w, tgt, delta, centers0, iters)
+    act, labels, cen, a, tlab, near = (pl[x] for x in ("act", "labels", "cen", "a", "tlab",
+                                                       "near"))
+    delta = pl["delta"]
+    src = np.asarray(src, np.float64)[act]
+    w = np.asarray(w, np.float64)[act]
+    f = np.asarray(f, np.float64)[act]
+    tgt = np.asarray(tgt, np.float64)
+    k = len(cen)
     eq_pts, eq_den = equivalent_densities(src, w, f, labels, cen, a, p)
     u = np.zeros((len(tgt), 3))
     scale = 1.0 / (8.0 * np.pi * mu)
-    for j in range(k):
-        sel = labels == j
-        if not np.any(sel):
+    for i in range(k):
+        ti = np.flatnonzero(tlab == i)
+        if len(ti) == 0:
             continue
-        rel = np.abs(tgt - cen[j])
-        outside_check = rel.max(axis=1) >= R_CHECK * a[j]
-        g = np.maximum(rel - a[j], 0.0)
-        gap2 = (g[:, 0] * g[:, 0] + g[:, 1] * g[:, 1]) + g[:, 2] * g[:, 2]
-        far_t = outside_check & (gap2 >= (RHO_FAR * delta) * (RHO_FAR * delta))
-        far = np.empty_like(far_t)
-        for g0 in range(0, len(tgt), GROUP):
-            far[g0:g0 + GROUP] = np.all(far_t[g0:g0 + GROUP])
-        if np.any(far):
-            u[far] += scale * (stokeslet_matrix(tgt[far], eq_pts[j]) @ eq_den[j].ravel()).reshape(-1, 3)
-        near = ~far
-        if np.any(near):
-            u[near] += oracle_sl(src[sel], w[sel], f[sel], tgt[near], delta[near], mu)
+        T = tgt[ti]
+        far_j = [j for j in range(k) if not near[i, j] and np.any(labels == j)]
+        sel = near[i][labels]           # the points of the neighbouring clusters
+        if np.any(sel):
+            u[ti] += oracle_sl(src[sel], w[sel], f[sel], T, delta[ti], mu)
+        if far_j:
+            E = np.concatenate([eq_pts[j] for j in far_j])
+            phi = np.concatenate([eq_den[j] for j in far_j])
+            u[ti] += scale * far_field(T, E, phi)
     return u

@@ -223,3 +223,35 @@ int oracle_dl(int64_t n_src, const double* src_xyz, const double* w, const doubl
   }
   return 0;
 }
+
+/* Plain (unregularized) Stokeslet sum of Sec. 2.2 without the 1/(8 pi mu)
+ * factor: v(x) = sum_y [ g_y / r + (g_y . d) d / r^3 ], d = x - y, for
+ * targets away from every source (r > 0). The single-level FMM's equivalent
+ * sources (Sec. 5) act through this kernel. Neumaier sums in input order.
+ * Returns 0, or -1 on invalid arguments. */
+int oracle_plain_stokeslet(int64_t n_src, const double* src_xyz, const double* g,
+                           int64_t n_tgt, const double* tgt_xyz, double* v_out, int n_threads) {
+  if (n_src < 0 || n_tgt < 0) return -1;
+#ifdef _OPENMP
+  int nt = n_threads > 0 ? n_threads : omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 8) num_threads(nt)
+#endif
+  for (int64_t t = 0; t < n_tgt; ++t) {
+    const double x0 = tgt_xyz[3 * t], x1 = tgt_xyz[3 * t + 1], x2 = tgt_xyz[3 * t + 2];
+    double s[3] = {0.0, 0.0, 0.0}, c[3] = {0.0, 0.0, 0.0};
+    for (int64_t j = 0; j < n_src; ++j) {
+      const double d0 = x0 - src_xyz[3 * j], d1 = x1 - src_xyz[3 * j + 1], d2 = x2 - src_xyz[3 * j + 2];
+      const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+      const double r = sqrt(r2);
+      const double g0 = g[3 * j], g1 = g[3 * j + 1], g2 = g[3 * j + 2];
+      const double gd = (g0 * d0 + g1 * d1 + g2 * d2) / (r2 * r);
+      nsum_add(&s[0], &c[0], g0 / r + gd * d0);
+      nsum_add(&s[1], &c[1], g1 / r + gd * d1);
+      nsum_add(&s[2], &c[2], g2 / r + gd * d2);
+    }
+    v_out[3 * t] = s[0] + c[0];
+    v_out[3 * t + 1] = s[1] + c[1];
+    v_out[3 * t + 2] = s[2] + c[2];
+  }
+  return 0;
+}

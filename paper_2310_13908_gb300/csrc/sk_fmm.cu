@@ -9,11 +9,13 @@
 //      the 2.95 a cube; equivalent densities phi solve, in the Tikhonov
 //      sense, K phi = u_check (plain Stokeslet), u_check being the cluster's
 //      potential at the check points;
-//   3. a group of 32 consecutive targets takes a cluster's equivalent
-//      sources when every target lies outside the check cube and at least
-//      7 delta from the cluster cube (the regularized kernel then equals the
-//      plain one to double precision), else the direct regularized sum over
-//      the cluster's points.
+//   3. box against box: each target joins the box of its nearest final
+//      centre (a target box is the bounding box of its targets, with their
+//      largest delta); the box takes a cluster's equivalent sources when it
+//      lies wholly outside the cluster's check cube and at least 7 delta
+//      from the cluster cube (the regularized kernel then equals the plain
+//      one to double precision), else the direct regularized sum over the
+//      cluster's points (neighbouring boxes).
 // The Tikhonov operator P1 = (K1^T K1 + alpha^2 I)^{-1} K1^T of the unit cube
 // (alpha = 1e-8 |K1|_F) is built once per p on the host by Householder QR of
 // [K1; alpha I]; K scales like 1/a, so phi = a P1 u_check for a cube of half
@@ -158,7 +160,7 @@ __global__ void k_km_assign(const double* __restrict__ X, const double* __restri
                             const double* __restrict__ C, int k, int* __restrict__ lab) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= N) return;
-  if (w[i] == 0.0) {
+  if (w && w[i] == 0.0) {
     lab[i] = -1;
     return;
   }
@@ -282,6 +284,69 @@ __global__ void k_km_box(const double* __restrict__ X, const int* __restrict__ o
   }
 }
 
+// block per target box: bounding box of its targets and their largest delta
+__global__ void k_tgt_box(const double* __restrict__ Y, const double* __restrict__ delta,
+                          int64_t n_delta, const int* __restrict__ off,
+                          const int* __restrict__ list, double* __restrict__ tbox) {
+  __shared__ double s[7][FMM_TPB];
+  const int c = blockIdx.x, t = threadIdx.x;
+  double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  double dmax = 0.0;
+  for (int q = off[c] + t; q < off[c + 1]; q += FMM_TPB) {
+    const int i = list[q];
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = fmin(lo[a], Y[3 * i + a]);
+      hi[a] = fmax(hi[a], Y[3 * i + a]);
+    }
+    dmax = fmax(dmax, delta[n_delta == 1 ? 0 : i]);
+  }
+  for (int a = 0; a < 3; ++a) {
+    s[a][t] = lo[a];
+    s[3 + a][t] = hi[a];
+  }
+  s[6][t] = dmax;
+  __syncthreads();
+  for (int o = FMM_TPB / 2; o > 0; o >>= 1) {
+    if (t < o) {
+      for (int a = 0; a < 3; ++a) {
+        s[a][t] = fmin(s[a][t], s[a][t + o]);
+        s[3 + a][t] = fmax(s[3 + a][t], s[3 + a][t + o]);
+      }
+      s[6][t] = fmax(s[6][t], s[6][t + o]);
+    }
+    __syncthreads();
+  }
+  if (t < 7) tbox[8 * c + t] = s[t][0];
+}
+
+// One thread per (target box i, source cluster j): near[i k + j] = 1 when
+// the cluster is a neighbour of the box (direct sum), 0 when the box lies
+// wholly outside the cluster's check cube and at least RHO_FAR delta_i from
+// its cube. Plain IEEE operations (no contraction), as the definition reads.
+__global__ void k_fmm_neighbours(const double* __restrict__ tbox, const int* __restrict__ toff,
+                                 const double* __restrict__ box, const int* __restrict__ off,
+                                 int k, unsigned char* __restrict__ near) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= (int64_t)k * k) return;
+  const int i = (int)(q / k), j = (int)(q % k);
+  if (toff[i + 1] == toff[i] || off[j + 1] == off[j]) {
+    near[q] = 0;  // an empty box or cluster contributes nothing either way
+    return;
+  }
+  const double* tb = tbox + 8 * i;
+  const double a = box[4 * j + 3], ca = __dmul_rn(R_CHECK, a);
+  bool outside = false;
+  double g2 = 0.0;
+  for (int ax = 0; ax < 3; ++ax) {
+    const double c = box[4 * j + ax], lo = tb[ax], hi = tb[3 + ax];
+    outside |= (lo > __dadd_rn(c, ca)) || (hi < __dsub_rn(c, ca));
+    const double g = fmax(fmax(__dsub_rn(lo, __dadd_rn(c, a)), __dsub_rn(__dsub_rn(c, a), hi)), 0.0);
+    g2 = ax == 0 ? __dmul_rn(g, g) : __dadd_rn(g2, __dmul_rn(g, g));
+  }
+  const double rf = __dmul_rn(RHO_FAR, tb[6]);
+  near[q] = (outside && g2 >= __dmul_rn(rf, rf)) ? 0 : 1;
+}
+
 // block per cluster: potential of its points (plain Stokeslet, w f) at the
 // check points, then phi = a P1 u_check
 __global__ void k_fmm_upward(const double* __restrict__ X, const double* __restrict__ w,
@@ -321,33 +386,31 @@ __global__ void k_fmm_upward(const double* __restrict__ X, const double* __restr
   }
 }
 
-// One thread per target, one warp per group of 32 consecutive targets: a
-// group takes a cluster's equivalent sources only when the cluster is far
-// for every target of the group (box-against-box, as the paper decides),
-// else the direct regularized sum over the cluster's points; beyond 7 delta
-// the regularized pair is the plain Stokeslet.
+// One thread per target, targets in box order (tlist), so a warp's targets
+// share their box's decisions: a far cluster through its equivalent
+// sources, a neighbouring one by the direct regularized sum over its points
+// (beyond 7 delta the regularized pair is the plain Stokeslet).
 __global__ void k_fmm_eval(const double* __restrict__ Y, const double* __restrict__ delta,
                            int64_t n_delta, int64_t M, int k, const double* __restrict__ box,
                            const int* __restrict__ off, const int* __restrict__ list,
+                           const int* __restrict__ tlab, const int* __restrict__ tlist,
+                           const unsigned char* __restrict__ near,
                            const double* __restrict__ unit, int Np, const double* __restrict__ phi,
                            const double* __restrict__ X, const double* __restrict__ w,
                            const double* __restrict__ f, double scale, double* __restrict__ u) {
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const bool live = t < M;
-  const int64_t tt = live ? t : M - 1;
-  const double x = Y[3 * tt], y = Y[3 * tt + 1], z = Y[3 * tt + 2];
-  const double d = delta[n_delta == 1 ? 0 : tt], invd = 1.0 / d;
-  const double rf = RHO_FAR * d, rf2 = __dmul_rn(rf, rf);
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= M) return;
+  const int t = tlist[q];
+  const int bi = tlab[t];
+  const double x = Y[3 * t], y = Y[3 * t + 1], z = Y[3 * t + 2];
+  const double d = delta[n_delta == 1 ? 0 : t], invd = 1.0 / d;
+  const double rf = RHO_FAR * d, rf2 = rf * rf;
   double fx0 = 0.0, fx1 = 0.0, fx2 = 0.0;  // far, without 1/(8 pi mu)
   double n0 = 0.0, n1 = 0.0, n2 = 0.0;     // near
   for (int c = 0; c < k; ++c) {
     if (off[c + 1] == off[c]) continue;
     const double cx = box[4 * c], cy = box[4 * c + 1], cz = box[4 * c + 2], a = box[4 * c + 3];
-    const double rx = fabs(x - cx), ry = fabs(y - cy), rz = fabs(z - cz);
-    const double gx = fmax(rx - a, 0.0), gy = fmax(ry - a, 0.0), gz = fmax(rz - a, 0.0);
-    const double gap2 = __dadd_rn(__dadd_rn(__dmul_rn(gx, gx), __dmul_rn(gy, gy)), __dmul_rn(gz, gz));
-    const bool far = !live || (fmax(rx, fmax(ry, rz)) >= R_CHECK * a && gap2 >= rf2);
-    if (__all_sync(0xffffffffu, far)) {
+    if (!near[(int64_t)bi * k + c]) {
       const double* ph = phi + (int64_t)c * 3 * Np;
       for (int j = 0; j < Np; ++j) {
         const double dx = x - (cx + R_EQUIV * a * unit[3 * j]);
@@ -362,8 +425,8 @@ __global__ void k_fmm_eval(const double* __restrict__ Y, const double* __restric
         fx2 += pz * ir + pd * dz;
       }
     } else {
-      for (int q = off[c]; q < off[c + 1]; ++q) {
-        const int i = list[q];
+      for (int qq = off[c]; qq < off[c + 1]; ++qq) {
+        const int i = list[qq];
         const double dx = x - X[3 * i], dy = y - X[3 * i + 1], dz = z - X[3 * i + 2];
         const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
         if (r2 >= rf2) {  // s1 = s2 = 1 to double precision
@@ -381,11 +444,9 @@ __global__ void k_fmm_eval(const double* __restrict__ Y, const double* __restric
       }
     }
   }
-  if (live) {
-    u[3 * t] = scale * fx0 + n0;
-    u[3 * t + 1] = scale * fx1 + n1;
-    u[3 * t + 2] = scale * fx2 + n2;
-  }
+  u[3 * t] = scale * fx0 + n0;
+  u[3 * t + 1] = scale * fx1 + n1;
+  u[3 * t + 2] = scale * fx2 + n2;
 }
 
 }  // namespace
@@ -450,7 +511,9 @@ int stokes_sl_eval_fmm(sk_ctx* ctx, int mem, int64_t n_src, const double* src_xy
   struct Carve {
     double *tX = nullptr, *tW = nullptr, *tF = nullptr, *tY = nullptr, *tD = nullptr, *U = nullptr;
     int *lab = nullptr, *count = nullptr, *offs = nullptr, *list = nullptr;
-    double *C = nullptr, *box = nullptr, *ucheck = nullptr, *phi = nullptr;
+    int *tlab = nullptr, *tcount = nullptr, *toffs = nullptr, *tlist = nullptr;
+    double *C = nullptr, *box = nullptr, *tbox = nullptr, *ucheck = nullptr, *phi = nullptr;
+    unsigned char* near = nullptr;
   };
   auto carve = [&](Bump& b, Carve& c) {
     if (mem == SK_HOST) {
@@ -465,8 +528,14 @@ int stokes_sl_eval_fmm(sk_ctx* ctx, int mem, int64_t n_src, const double* src_xy
     c.count = b.take<int>(k);
     c.offs = b.take<int>(k + 1);
     c.list = b.take<int>(n_src);
+    c.tlab = b.take<int>(n_tgt);
+    c.tcount = b.take<int>(k);
+    c.toffs = b.take<int>(k + 1);
+    c.tlist = b.take<int>(n_tgt);
     c.C = b.take<double>(3 * (size_t)k);
     c.box = b.take<double>(4 * (size_t)k);
+    c.tbox = b.take<double>(8 * (size_t)k);
+    c.near = b.take<unsigned char>((size_t)k * k);
     c.ucheck = b.take<double>((size_t)k * n3);
     c.phi = b.take<double>((size_t)k * n3);
   };
@@ -514,9 +583,18 @@ int stokes_sl_eval_fmm(sk_ctx* ctx, int mem, int64_t n_src, const double* src_xy
   k_km_box<<<k, FMM_TPB, 0, st>>>(X, offs, list, box);
   k_fmm_upward<<<k, FMM_TPB, 0, st>>>(X, W, F, offs, list, box, op->unit, op->Np, op->P1, ucheck,
                                       phi);
+  // target boxes: nearest final centre, ordered lists, boxes, neighbour matrix
+  k_km_assign<<<nblk(n_tgt), FMM_TPB, 0, st>>>(Y, nullptr, n_tgt, C, k, cv.tlab);
+  k_km_update<<<k, FMM_TPB, 0, st>>>(Y, cv.tlab, n_tgt, C, cv.tcount, 0);
+  k_km_offsets<<<1, 32, 0, st>>>(cv.tcount, k, cv.toffs);
+  k_km_list<<<k, FMM_TPB, 0, st>>>(cv.tlab, n_tgt, cv.toffs, cv.tlist);
+  k_tgt_box<<<k, FMM_TPB, 0, st>>>(Y, D, n_delta, cv.toffs, cv.tlist, cv.tbox);
+  k_fmm_neighbours<<<nblk((int64_t)k * k), FMM_TPB, 0, st>>>(cv.tbox, cv.toffs, box, offs, k,
+                                                              cv.near);
   const double scale = 1.0 / (8.0 * PI_CONST * mu);
-  k_fmm_eval<<<nblk(n_tgt, 128), 128, 0, st>>>(Y, D, n_delta, n_tgt, k, box, offs, list, op->unit,
-                                               op->Np, phi, X, W, F, scale, U);
+  k_fmm_eval<<<nblk(n_tgt, 128), 128, 0, st>>>(Y, D, n_delta, n_tgt, k, box, offs, list, cv.tlab,
+                                               cv.tlist, cv.near, op->unit, op->Np, phi, X, W, F,
+                                               scale, U);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess && mem == SK_HOST)
     e = cudaMemcpyAsync(u_out, U, 3 * n_tgt * sizeof(double), cudaMemcpyDeviceToHost, st);

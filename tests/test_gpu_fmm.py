@@ -1,11 +1,12 @@
-"""Single-level FMM (Sec. 5) on the GPU against the oracle's FMM (same
-algorithm and decisions; independent implementations of the Tikhonov solve,
-the sums and k-means) and against the direct FP64 evaluation."""
+"""Single-level FMM (Sec. 5) on the GPU against the oracle's FMM (the same
+algorithm and box-against-box decisions; independent implementations of the
+Tikhonov solve, the sums and k-means) and against the oracle's direct sum."""
 
 import numpy as np
 import pytest
 
 import capsule_inputs as ci
+import oracle
 from oracle import fmm
 
 sk = pytest.importorskip("paper_2310_13908_gb300")
@@ -43,22 +44,43 @@ def test_fmm_matches_oracle_fmm(ctx, p):
     assert rel(u, ref) < 1e-8, rel(u, ref)
 
 
-def test_all_near_equals_direct_fp64(ctx):
+def test_fmm_with_probes_and_per_target_delta_matches_oracle_fmm(ctx):
+    """Off-surface probes join the boxes of their nearest centres; per-target
+    delta makes the box's largest delta decide its neighbours."""
+    rng = np.random.default_rng(8)
+    shape = ci.Ellipsoid(1.0, 0.8, 0.5)
+    s = ci.make_surface(shape, 24)
+    f = ci.sh_density(s.x0, rng, lmax=6)
+    probes, _ = ci.exterior_probes(shape, 400, s.h, rng)
+    tgt = np.concatenate([s.X[::4], probes])
+    delta = rng.uniform(0.01, 0.03, len(tgt))
+    c0 = seeds(s, 30)
+    pl = fmm.plan(s.X, s.w, tgt, delta, c0, 8)
+    assert 0.2 < pl["near"].mean() < 0.9     # both kinds of box pairs occur
+    u = sk.stokes_sl_eval_fmm(ctx, sk.SK_HOST, s.X, s.w, f, tgt, delta, 0.9, c0, 8, 6)
+    ref = fmm.sl_fmm(s.X, s.w, f, tgt, delta, 0.9, c0, 8, 6)
+    assert rel(u, ref) < 1e-8, rel(u, ref)
+
+
+def test_all_near_equals_the_direct_sum(ctx):
     s = ci.make_surface(ci.Sphere(1.0), 12)
     f = ci.sh_density(s.x0, np.random.default_rng(4), lmax=4)
     u = sk.stokes_sl_eval_fmm(ctx, sk.SK_HOST, s.X, s.w, f, s.X, 10.0, 1.0, seeds(s, 8), 4, 4)
-    d = sk.stokes_sl_eval(ctx, sk.SK_FP64, sk.SK_HOST, s.X, s.w, f, s.X, 10.0, 1.0)
-    assert rel(u, d) < 1e-13
+    assert rel(u, fmm.sl_fmm(s.X, s.w, f, s.X, 10.0, 1.0, seeds(s, 8), 4, 4)) < 1e-13
+    assert rel(u, oracle.sl(s.X, s.w, f, s.X, 10.0, 1.0)) < 1e-13
 
 
-def test_fmm_against_direct_at_larger_size_and_device_memory(ctx):
+def test_fmm_at_larger_size_and_device_memory(ctx):
     s = ci.make_surface(ci.Ellipsoid(1.0, 0.8, 0.5), 65)
     f = ci.sh_density(s.x0, np.random.default_rng(5), lmax=8)
     delta = 2 * s.h
+    c0 = seeds(s, 100)
     t = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda")
     u = sk.stokes_sl_eval_fmm(ctx, sk.SK_DEVICE, t(s.X), t(s.w), t(f), t(s.X),
-                              t(np.array([delta])), 1.0, t(seeds(s, 100)), 10, 6).cpu().numpy()
-    d = sk.stokes_sl_eval(ctx, sk.SK_FP64, sk.SK_HOST, s.X, s.w, f, s.X, delta, 1.0)
+                              t(np.array([delta])), 1.0, t(c0), 10, 6).cpu().numpy()
+    ref = fmm.sl_fmm(s.X, s.w, f, s.X, delta, 1.0, c0, 10, 6)
+    assert rel(u, ref) < 1e-8, rel(u, ref)
+    d = oracle.sl(s.X, s.w, f, s.X, delta, 1.0)
     assert rel(u, d) < 1e-5, rel(u, d)
 
 

@@ -6,7 +6,12 @@
 * one cluster's equivalent sources reproduce its plain-Stokeslet potential
   outside the check cube, with an error that falls quickly with p;
 * with every cluster near (huge delta), the FMM is the direct sum;
-* on an ellipsoid, the FMM approaches the direct regularized sum as p grows.
+* on an ellipsoid, the FMM approaches the direct regularized sum as p grows;
+* the plain Stokeslet of the far field has its closed form;
+* the neighbour rule is box against box (Sec. 5, step 3), checked against
+  an independent computation of box distances, and every far (box, cluster)
+  pair is valid for each of its targets: outside the check cube and at least
+  7 delta (the target's own) from the cluster cube.
 """
 
 import numpy as np
@@ -94,3 +99,62 @@ def test_clusters_within_seven_delta_are_summed_directly():
     u = fmm.sl_fmm(s.X, s.w, f, tgt, 0.5, 1.0, c0, 8, 6)
     ref = oracle.sl(s.X, s.w, f, tgt, 0.5)
     assert np.allclose(u, ref, rtol=1e-13, atol=1e-13 * np.abs(ref).max())
+
+
+def test_plain_stokeslet_closed_form():
+    """One source g = (1, 2, -1) at the origin, target at (0, 0, 10) and at
+    (3, 4, 0): v = g / r + (g . d) d / r^3 (Sec. 2.2), written out."""
+    g = np.array([[1.0, 2.0, -1.0]])
+    v = oracle.plain_stokeslet(np.zeros((1, 3)), g, [[0.0, 0.0, 10.0], [3.0, 4.0, 0.0]])
+    assert np.allclose(v[0], [0.1, 0.2, -0.1 - 0.1], rtol=1e-15)
+    assert np.allclose(v[1], [0.2 + 11 * 3 / 125, 0.4 + 11 * 4 / 125, -0.2], rtol=1e-15)
+    # and the regularized sum far from the sources (rho >= 100) is the plain one
+    rng = np.random.default_rng(6)
+    X = rng.uniform(-0.5, 0.5, (40, 3))
+    w = rng.uniform(0.5, 1.0, 40)
+    f = rng.standard_normal((40, 3))
+    Y = rng.uniform(2.0, 3.0, (10, 3))
+    ref = oracle.sl(X, w, f, Y, 0.01, 1.0) * 8 * np.pi
+    assert np.allclose(oracle.plain_stokeslet(X, w[:, None] * f, Y), ref, rtol=1e-13)
+
+
+def fmm_case(m=16, k=20, n_probes=300, seed=9):
+    """Ellipsoid nodes plus near exterior probes, one delta per target."""
+    rng = np.random.default_rng(seed)
+    shape = ci.Ellipsoid(1.0, 0.8, 0.5)
+    s = ci.make_surface(shape, m)
+    probes, _ = ci.exterior_probes(shape, n_probes, s.h, rng)
+    tgt = np.concatenate([s.X[::2], probes])
+    delta = rng.uniform(0.05, 0.15, len(tgt))
+    act = np.flatnonzero(s.w)
+    c0 = s.X[act[:: len(act) // k][:k]]
+    return s, tgt, delta, c0
+
+
+def test_neighbour_rule_is_box_against_box():
+    s, tgt, delta, c0 = fmm_case()
+    pl = fmm.plan(s.X, s.w, tgt, delta, c0, 8)
+    cen, a, tlab, near, cent = pl["cen"], pl["a"], pl["tlab"], pl["near"], pl["centers"]
+    # targets join their nearest final centre
+    dist = np.linalg.norm(tgt[:, None] - cent[None], axis=-1)
+    assert np.array_equal(tlab, np.argmin(dist, axis=1))
+    counts = np.bincount(pl["labels"], minlength=len(cen))
+    n_far = 0
+    for i in np.unique(tlab):
+        ti = np.flatnonzero(tlab == i)
+        T = tgt[ti]
+        bc, bh = 0.5 * (T.min(0) + T.max(0)), 0.5 * (T.max(0) - T.min(0))
+        for j in np.flatnonzero(counts):
+            sep = np.abs(bc - cen[j]) - bh            # per axis, box centre to box edge
+            outside_check = np.any(sep > fmm.R_CHECK * a[j])
+            gap = np.linalg.norm(np.maximum(sep - a[j], 0.0))
+            far = outside_check and gap >= fmm.RHO_FAR * delta[ti].max()
+            assert near[i, j] == (not far), (i, j)
+            if far:
+                n_far += 1
+                # valid for every target of the box, with its own delta
+                rel = np.abs(T - cen[j])
+                assert np.all(rel.max(axis=1) > fmm.R_CHECK * a[j])
+                g = np.linalg.norm(np.maximum(rel - a[j], 0.0), axis=1)
+                assert np.all(g >= fmm.RHO_FAR * delta[ti])
+    assert n_far > 0 and not near.all()

@@ -13,45 +13,46 @@ import capsule_inputs as ci
 import oracle
 import test_oracle_fmm as pins
 from oracle import fmm
-from oracle import sl as oracle_sl
 
-def _sl_fmm_variant(scale_far=True, gap=True, group=np.all):
-    """sl_fmm with one of its decisions changed."""
+def _neighbours_variant(centre_only=False, gap=True, gap_from_centre=False):
+    """oracle/fmm.py's neighbour rule with one of its decisions changed."""
 
-    def sl_fmm(src, w, f, tgt, delta, mu, centers0, iters, p):
-        src, tgt = np.asarray(src, np.float64), np.asarray(tgt, np.float64)
-        w, f = np.asarray(w, np.float64), np.asarray(f, np.float64)
-        delta = np.broadcast_to(np.asarray(delta, np.float64), (len(tgt),))
-        act = w != 0.0
-        src, w, f = src[act], w[act], f[act]
-        k = len(centers0)
-        _, labels = fmm.kmeans(src, centers0, iters)
-        cen, a = fmm.boxes(src, labels, k)
-        eq_pts, eq_den = fmm.equivalent_densities(src, w, f, labels, cen, a, p)
-        u = np.zeros((len(tgt), 3))
-        scale = 1.0 / (8.0 * np.pi * mu)
-        for j in range(k):
-            sel = labels == j
-            if not np.any(sel):
-                continue
-            rel = np.abs(tgt - cen[j])
-            far_t = rel.max(axis=1) >= fmm.R_CHECK * a[j]
-            if gap:
-                g = np.maximum(rel - a[j], 0.0)
-                far_t &= (g * g).sum(axis=1) >= (fmm.RHO_FAR * delta) ** 2
-            far = np.empty_like(far_t)
-            for g0 in range(0, len(tgt), fmm.GROUP):
-                far[g0:g0 + fmm.GROUP] = group(far_t[g0:g0 + fmm.GROUP])
-            if np.any(far):
-                s = scale if scale_far else 1.0
-                u[far] += s * (fmm.stokeslet_matrix(tgt[far], eq_pts[j])
-                               @ eq_den[j].ravel()).reshape(-1, 3)
-            near = ~far
-            if np.any(near):
-                u[near] += oracle_sl(src[sel], w[sel], f[sel], tgt[near], delta[near], mu)
-        return u
+    def neighbours(lo, hi, delta_i, cen, a):
+        if centre_only:   # the box's centre instead of the whole box
+            lo = hi = 0.5 * (lo + hi)
+        outside_check = np.any((lo[None] > cen + fmm.R_CHECK * a[:, None]) |
+                               (hi[None] < cen - fmm.R_CHECK * a[:, None]), axis=1)
+        half = 0.0 if gap_from_centre else a[:, None]
+        g = np.maximum(np.maximum(lo[None] - (cen + half), (cen - half) - hi[None]), 0.0)
+        gap2 = (g * g).sum(axis=1)
+        far = outside_check
+        if gap:
+            far = far & (gap2 >= (fmm.RHO_FAR * delta_i) ** 2)
+        return ~far
 
-    return sl_fmm
+    return neighbours
+
+
+def _plan_with_smallest_delta(src, w, tgt, delta, centers0, iters):
+    """plan() with the smallest delta of a target box instead of the largest."""
+    delta = np.broadcast_to(np.asarray(delta, np.float64), (len(tgt),))
+    pl = _PLAN(src, w, tgt, delta, centers0, iters)
+    tgt = np.asarray(tgt, np.float64)
+    for i in range(len(pl["cen"])):
+        ti = np.flatnonzero(pl["tlab"] == i)
+        if len(ti):
+            T = tgt[ti]
+            pl["near"][i] = fmm.neighbours(T.min(0), T.max(0), float(delta[ti].min()), pl["cen"],
+                                           pl["a"])
+    return pl
+
+
+def _far_field_without_scale(T, E, phi):
+    return 8.0 * np.pi * _FAR_FIELD(T, E, phi)   # pins use mu = 1
+
+
+_PLAN = fmm.plan
+_FAR_FIELD = fmm.far_field
 
 
 def component_major_columns(targets, sources):
@@ -73,9 +74,12 @@ def kmeans_without_updates(points, centers0, iters):
 
 
 MUTATIONS = {
-    "far_field_without_1_over_8_pi_mu": {"sl_fmm": _sl_fmm_variant(scale_far=False)},
-    "far_test_without_the_7_delta_gap": {"sl_fmm": _sl_fmm_variant(gap=False)},
-    "group_far_if_any_target_is_far": {"sl_fmm": _sl_fmm_variant(group=np.any)},
+    "far_field_without_1_over_8_pi_mu": {"far_field": _far_field_without_scale},
+    "far_test_without_the_7_delta_gap": {"neighbours": _neighbours_variant(gap=False)},
+    "far_if_the_box_centre_is_outside_the_check_cube":
+        {"neighbours": _neighbours_variant(centre_only=True)},
+    "gap_from_the_cluster_centre": {"neighbours": _neighbours_variant(gap_from_centre=True)},
+    "smallest_delta_of_the_box": {"plan": _plan_with_smallest_delta},
     "equivalent_and_check_radii_swapped": {"R_EQUIV": fmm.R_CHECK, "R_CHECK": fmm.R_EQUIV},
     "stokeslet_columns_component_major": {"stokeslet_matrix": component_major_columns},
     "kmeans_without_updates": {"kmeans": kmeans_without_updates},
@@ -94,6 +98,7 @@ def fmm_matches_direct_at_p6():
 
 
 PINS = [
+    pins.test_neighbour_rule_is_box_against_box,
     pins.test_cube_surface_grid,
     pins.test_kmeans_invariants,
     pins.test_equivalent_sources_reproduce_far_potential,
