@@ -46,6 +46,7 @@ SM_MAX_MHZ = 2070.0
 FP32_PEAK_TFLOPS = 2 * 128 * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12  # 80.55
 FP64_PEAK_TFLOPS = 1.25  # nominal dense FP64 of GB300
 CPU_SAMPLE_TARGETS = 24576  # about 10 s of the oracle on 16 host cores
+SWEEP_SAMPLE_TARGETS = 8192  # oracle check of each delta of the sweep (about 3 s each)
 SERVE_ORACLE_REQUESTS = 50   # served results checked against the oracle ...
 SERVE_ORACLE_TARGETS = 256   # ... on this many seeded targets each
 REF_STEP_TARGETS = 512
@@ -599,12 +600,15 @@ def capsule_bench(sk, h, torch, dev, m=129, steps=100, dt=5e-4, Es=2.0, ED=20.0)
     """Capsule with a Skalak membrane in shear flow: stress-free ellipsoid
     (0.9, 1, 1), Es = 2, ED = 20, shear rate 1 (Sec. 4.3 setup), m = 129,
     explicit Euler steps with f = div_gamma Lambda, weights and delta* updated
-    every step. dt = 5e-4: explicit Euler on this grid is unstable at 1e-3."""
+    every step (Sec. 3.6). Both precisions run all `steps` steps at dt and are
+    compared at the end: displacement, area and volume drift. The configured
+    dt = 1e-3 is run as written too; explicit Euler is unstable there on this
+    grid, so a sweep of dt gives the largest stable step."""
     import capsule_inputs as ci
     ref = ci.make_surface(ci.Ellipsoid(0.9, 1.0, 1.0), m)
     flow = (sk.SK_FLOW_SHEAR, 1.0, 0.0, 0.0)
     res = {"workload": f"ellipsoid(0.9,1,1) stress-free, m={m} (N={ref.N}), Es={Es}, ED={ED}, "
-                       f"shear rate 1, explicit Euler dt={dt}, delta* per step",
+                       f"shear rate 1, explicit Euler, delta* per step",
            "steps": steps, "dt": dt}
     # the membrane force alone (device memory, CUDA events)
     Xd = torch.as_tensor(ref.X * np.array([1.02, 0.99, 1.0]), device=dev)
@@ -620,64 +624,46 @@ def capsule_bench(sk, h, torch, dev, m=129, steps=100, dt=5e-4, Es=2.0, ED=20.0)
     torch.cuda.synchronize(dev)
     res["membrane_force_ms"] = a.elapsed_time(b) / 10
 
-    def run(prec, n):
+    def run(prec, n, step_dt):
         cap = sk.Capsule(h, m, ref.X, ref.w, delta=None, mu=1.0, precision=prec)
         try:
             cap.set_membrane(ref.X, Es, ED)
             A0, V0 = cap.area_volume()
-            cap.step(1, dt, None, flow)  # captures the step graph
+            cap.step(1, step_dt, None, flow)  # captures the step graph
             t0 = time.perf_counter()
-            cap.step(n, dt, None, flow)
-            ms = (time.perf_counter() - t0) * 1e3 / n
+            cap.step(n - 1, step_dt, None, flow)
+            ms = (time.perf_counter() - t0) * 1e3 / max(n - 1, 1)
             A, V = cap.area_volume()
-            return cap.positions(), {"ms_per_step": ms, "area_change": A / A0 - 1.0,
-                                     "volume_drift": V / V0 - 1.0}
+            X = cap.positions()
+            return X, {"steps": n, "dt": step_dt, "ms_per_step": ms,
+                       "area_change": A / A0 - 1.0, "volume_drift": V / V0 - 1.0,
+                       "finite": bool(np.all(np.isfinite(X))),
+                       "max_displacement": float(np.nanmax(np.linalg.norm(X - ref.X, axis=1)))}
         finally:
             cap.close()
 
-    _, res["fp32c"] = run(sk.SK_FP32C, steps)
-    X64, res["fp64"] = run(sk.SK_FP64, 10)
-    X32, _ = run(sk.SK_FP32C, 10)
-    res["fp32c_vs_fp64_after_11_steps"] = rel_l2(X32 - ref.X, X64 - ref.X)
+    X32, res["fp32c"] = run(sk.SK_FP32C, steps, dt)
+    X64, res["fp64"] = run(sk.SK_FP64, steps, dt)
+    res["fp32c_vs_fp64_at_final_step"] = {
+        "steps": steps,
+        "displacement_rel_l2": rel_l2(X32 - ref.X, X64 - ref.X),
+        "area_change_diff": res["fp32c"]["area_change"] - res["fp64"]["area_change"],
+        "volume_drift_diff": res["fp32c"]["volume_drift"] - res["fp64"]["volume_drift"]}
+    # as written: dt = 1e-3; and the stability sweep (a run counts as stable
+    # when it stays finite with |area change| below 1e-2)
+    sweep = {}
+    for sdt in (6e-4, 7e-4, 8e-4, 9e-4, 1e-3):
+        try:
+            _, r = run(sk.SK_FP32C, steps, sdt)
+            r["stable"] = bool(r["finite"] and abs(r["area_change"]) < 1e-2)
+        except sk.SkError as e:  # e.g. delta* no longer finite once the shape has blown up
+            r = {"steps": steps, "dt": sdt, "error": str(e), "stable": False}
+        sweep[f"{sdt:g}"] = r
+    res["fp32c_dt_1e-3_as_configured"] = sweep["0.001"]
+    res["dt_stability_fp32c"] = sweep
+    stable = [float(k) for k, v in sweep.items() if v["stable"]] + [dt]
+    res["largest_stable_dt_of_sweep"] = max(stable)
     return res
-
-
-# Wall clock per RKF45 time step with 4x upsampling, sphere in shear, printed
-# in Table wall_clock_sph (hardware and precision unstated): context only.
-PAPER_RKF45_STEP_S = {8: 0.61, 16: 1.26, 32: 10.10, 48: 46.46}
-
-
-def rkf45_upsampled_bench(sk, h, ms=(16, 32, 48), t_end=0.02, Es=2.0, ED=20.0):
-    """The paper's production loop (Sec. 3.6): unit sphere with a stress-free
-    Skalak membrane in shear flow (rate 1), RKF45 with relative tolerance
-    1e-6, single layer on the four-times upsampled grid, membrane force by
-    the overset finite differences. Wall clock per accepted step."""
-    import capsule_inputs as ci
-    flow = (sk.SK_FLOW_SHEAR, 1.0, 0.0, 0.0)
-    out = {"workload": f"unit sphere, Skalak Es={Es} ED={ED}, shear rate 1, RKF45 tol 1e-6, "
-                       f"4x upsampled single layer, t in [0, {t_end}]",
-           "paper_s_per_step": PAPER_RKF45_STEP_S}
-    for m in ms:
-        ref = ci.make_surface(ci.Sphere(1.0), m)
-        row = {"N": ref.N, "N_up": 6 * (4 * m - 1) ** 2}
-        for prec, name in ((sk.SK_FP32C, "fp32c"), (sk.SK_FP64, "fp64")):
-            if prec == sk.SK_FP64 and m > 32:
-                continue
-            cap = sk.Capsule(h, m, ref.X, ref.w, delta=None, mu=1.0, precision=prec)
-            try:
-                cap.set_membrane(ref.X, Es, ED)
-                cap.set_upsampling(4)
-                dt, _, _ = cap.integrate_rkf45(1e-4, 1e-4, tol=1e-6, flow=flow)  # captures
-                t0 = time.perf_counter()
-                dt, acc, rej = cap.integrate_rkf45(t_end, dt, tol=1e-6, flow=flow)
-                el = time.perf_counter() - t0
-                A, V = cap.area_volume()
-            finally:
-                cap.close()
-            row[name] = {"s_per_step": el / max(acc, 1), "accepted": acc, "rejected": rej,
-                         "final_dt": dt, "area": A, "volume": V}
-        out[f"m{m}"] = row
-    return out
 
 
 def fmm_bench(sk, h, torch, dev, m=129, k=64, p=6):
@@ -713,54 +699,6 @@ def fmm_bench(sk, h, torch, dev, m=129, k=64, p=6):
             "fmm_rel_l2_vs_direct_fp64": rel_l2(uf, u64),
             "fp32c_rel_l2_vs_direct_fp64": rel_l2(u32, u64),
             "paper_speedup_fmm_vs_direct": {"m32": 1.02, "m64": 1.57, "m96": 1.81}}
-
-
-# Relative errors at T = 0.5 against the m = 48 solution printed in Table
-# convg_full (shear: convg_shear, Poiseuille: convg_poiseuille): (A, V, J).
-PAPER_CONVERGENCE = {"shear": {8: (2e-2, 4e-2, 3e-2), 16: (2e-3, 1e-3, 2e-3), 32: (1e-4, 1e-4, 1e-4)},
-                     "poiseuille": {8: (2e-2, 4e-2, 2e-2), 16: (3e-3, 1e-3, 2e-3),
-                                    32: (2e-4, 1e-4, 1e-4)}}
-
-
-def capsule_run(sk, h, m, flow, T, precision, Es=2.0, ED=20.0, tol=1e-6):
-    """Stress-free ellipsoid (0.9, 1, 1) capsule, Skalak membrane, RKF45 with
-    the 4x upsampled single layer (Sec. 3.6) to time T; returns
-    (A, V, centroid, J, accepted, rejected, seconds)."""
-    import capsule_inputs as ci
-    ref = ci.make_surface(ci.Ellipsoid(0.9, 1.0, 1.0), m)
-    cap = sk.Capsule(h, m, ref.X, ref.w, delta=None, mu=1.0, precision=precision)
-    try:
-        cap.set_membrane(ref.X, Es, ED)
-        cap.set_upsampling(4)
-        t0 = time.perf_counter()
-        _, acc, rej = cap.integrate_rkf45(T, 1e-3, tol=tol, flow=flow)
-        el = time.perf_counter() - t0
-        A, V, c, J = cap.shape_moments()
-    finally:
-        cap.close()
-    return A, V, c, J, acc, rej, el
-
-
-def convergence_bench(sk, h, ms=(8, 16, 32), m_ref=48, T=0.5):
-    """Self-convergence of area, volume and inertia tensor at T = 0.5 (Sec. 4.2,
-    Table convg_full): Es = 2, ED = 20, shear rate 1 / Poiseuille (25 - y^2 -
-    z^2, 0, 0), RKF45 tol 1e-6, 4x upsampling; reference m = 48."""
-    flows = {"shear": (sk.SK_FLOW_SHEAR, 1.0, 0.0, 0.0),
-             "poiseuille": (sk.SK_FLOW_POISEUILLE, 0.0, 1.0, 5.0)}
-    out = {"setup": "ellipsoid (0.9, 1, 1) stress-free, Es=2, ED=20, RKF45 tol 1e-6, 4x "
-                    f"upsampled single layer (FP32C), T={T}, reference m={m_ref}; "
-                    "errors: |A - A_ref|/A_ref, |V - V_ref|/V_ref, |J - J_ref|_F/|J_ref|_F",
-           "paper": PAPER_CONVERGENCE}
-    for name, fl in flows.items():
-        Ar, Vr, _, Jr, acc, rej, el = capsule_run(sk, h, m_ref, fl, T, sk.SK_FP32C)
-        row = {f"m{m_ref}": {"accepted": acc, "rejected": rej, "seconds": el}}
-        for m in ms:
-            A, V, _, J, acc, rej, el = capsule_run(sk, h, m, fl, T, sk.SK_FP32C)
-            row[f"m{m}"] = {"eps_A": abs(A - Ar) / Ar, "eps_V": abs(V - Vr) / Vr,
-                            "eps_J": float(np.linalg.norm(J - Jr) / np.linalg.norm(Jr)),
-                            "accepted": acc, "rejected": rej, "seconds": el}
-        out[name] = row
-    return out
 
 
 def extras(sk, h, w, X, W, F, Y, D, out, u_fp32, stream, dev, torch, serve_future=None):
@@ -806,8 +744,10 @@ def extras(sk, h, w, X, W, F, Y, D, out, u_fp32, stream, dev, torch, serve_futur
                                 "kernel": "k_pair64<SL>", "pair_ms": st64["pair_ms"],
                                 "peak_basis": "nominal dense FP64 of GB300"}}
 
-    # delta sweep (FP32C), one step each
+    # delta sweep (FP32C timed, one step each), both precisions checked against
+    # the oracle on the same seeded sample of nodes and probes
     sweep = {}
+    sidx = sample_targets(w, SWEEP_SAMPLE_TARGETS, seed=4321)
     for fac in (1.5, 2.0, 3.0):
         Dd = torch.tensor([fac * s.h], dtype=torch.float64, device=dev)
         sk.stokes_sl_eval(h, sk.SK_FP32C, sk.SK_DEVICE, X, W, F, Y, Dd, 1.0, u_out=out,
@@ -820,8 +760,18 @@ def extras(sk, h, w, X, W, F, Y, D, out, u_fp32, stream, dev, torch, serve_futur
         b.record(stream)
         st = sk.sk_last_eval_stats(h)
         torch.cuda.synchronize(dev)
+        u32 = out.cpu().numpy()[sidx]
+        sk.stokes_sl_eval(h, sk.SK_FP64, sk.SK_DEVICE, X, W, F, Y, Dd, 1.0, u_out=out,
+                          stream=stream)
+        torch.cuda.synchronize(dev)
+        u64 = out.cpu().numpy()[sidx]
+        dref = oracle.sl(s.X, s.w, w.f, w.targets[sidx], fac * s.h, w.mu)
         sweep[f"{fac}h"] = {"value": inter / (a.elapsed_time(b) * 1e-3) / 1e9,
-                            "pair_ms": st["pair_ms"], "near_pairs": st["near_pairs"]}
+                            "pair_ms": st["pair_ms"], "near_pairs": st["near_pairs"],
+                            "overflow_targets": st["overflow_targets"],
+                            "rel_l2_vs_oracle": {"fp32c": rel_l2(u32, dref),
+                                                 "fp64": rel_l2(u64, dref),
+                                                 "sample_targets": int(len(sidx))}}
     res["delta_sweep_fp32c"] = sweep
 
     # double layer on the rotated Evans-Fung cell (m = 65, N = 24,576)
@@ -960,17 +910,9 @@ def extras(sk, h, w, X, W, F, Y, D, out, u_fp32, stream, dev, torch, serve_futur
     except Exception as e:
         res["capsule_skalak_m129"] = {"error": repr(e)}
     try:
-        res["capsule_rkf45_upsampled"] = rkf45_upsampled_bench(sk, h)
-    except Exception as e:
-        res["capsule_rkf45_upsampled"] = {"error": repr(e)}
-    try:
         res["fmm_m129"] = fmm_bench(sk, h, torch, dev)
     except Exception as e:
         res["fmm_m129"] = {"error": repr(e)}
-    try:
-        res["capsule_self_convergence"] = convergence_bench(sk, h)
-    except Exception as e:
-        res["capsule_self_convergence"] = {"error": repr(e)}
     if serve_future is not None:
         try:
             res["serving"] = serving_bench(sk, h, serve_future.result())

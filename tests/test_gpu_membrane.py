@@ -131,6 +131,42 @@ def test_capsule_membrane_steps_match_oracle(ctx, prec, tol):
     assert abs(A - Ao) / Ao < 1e-13 and abs(V - Vo) / Vo < 1e-13
 
 
+@pytest.fixture(scope="module")
+def config5_oracle_run():
+    """The capsule benchmark's setup (stress-free ellipsoid (0.9, 1, 1), Es = 2,
+    ED = 20, shear rate 1, explicit Euler at the configured dt = 1e-3, delta*
+    and weights per step) at m = 33, the largest grid whose oracle loop stays
+    affordable here (the NumPy membrane oracle takes minutes per step at the
+    benchmark's m = 129): 10 steps by the oracle."""
+    m, n, dt = 33, 10, 1e-3
+    ref = ci.make_surface(ci.Ellipsoid(0.9, 1.0, 1.0), m)
+    flow = (sk.SK_FLOW_SHEAR, 1.0, 0.0, 0.0)
+    Xo = oracle_membrane_euler(m, ref.X, ref.X, n, dt, flow, 1.0)
+    return m, n, dt, ref, flow, Xo
+
+
+@pytest.mark.parametrize("prec,tol", [(sk.SK_FP64, 1e-10), (sk.SK_FP32C, 2e-6)],
+                         ids=["fp64", "fp32c"])
+def test_stress_free_capsule_in_shear_matches_oracle_loop(ctx, config5_oracle_run, prec, tol):
+    m, n, dt, ref, flow, Xo = config5_oracle_run
+    cap = sk.Capsule(ctx, m, ref.X, ref.w, delta=None, mu=1.0, precision=prec)
+    try:
+        cap.set_membrane(ref.X, ES, ED)
+        A0, V0 = cap.area_volume()
+        cap.step(n, dt, None, flow)
+        X = cap.positions()
+        A, V = cap.area_volume()
+    finally:
+        cap.close()
+    err = np.linalg.norm((X - ref.X) - (Xo - ref.X)) / np.linalg.norm(Xo - ref.X)
+    assert err < tol, err
+    # area and volume drift against the oracle's, from the oracle's own functionals
+    Ao, Vo = mb.area_volume(m, Xo)
+    Ar, Vr = mb.area_volume(m, ref.X)
+    assert abs((A / A0 - 1.0) - (Ao / Ar - 1.0)) < (1e-12 if prec == sk.SK_FP64 else 1e-8)
+    assert abs((V / V0 - 1.0) - (Vo / Vr - 1.0)) < (1e-12 if prec == sk.SK_FP64 else 1e-8)
+
+
 def test_membrane_capsule_relaxes_toward_reference(ctx):
     """A deformed capsule with no background flow moves back toward its
     stress-free shape: the Skalak energy decreases step by step."""

@@ -129,16 +129,3 @@ def test_shape_moments_of_an_ellipsoid(ctx):
     assert np.linalg.norm(J - J_ex) / np.linalg.norm(J_ex) < 1e-5
     Ao, Vo = mb.area_volume(m, s.X)
     assert abs(A - Ao) / Ao < 1e-12
-
-
-def test_capsule_self_convergence_in_shear(ctx):
-    """Shortened Table convg_shear: errors against a finer run fall with m."""
-    import bench
-    flow = (sk.SK_FLOW_SHEAR, 1.0, 0.0, 0.0)
-    Ar, Vr, _, Jr, *_ = bench.capsule_run(sk, ctx, 24, flow, 0.05, sk.SK_FP64)
-    errs = {}
-    for m in (8, 12):
-        A, V, _, J, *_ = bench.capsule_run(sk, ctx, m, flow, 0.05, sk.SK_FP64)
-        errs[m] = (abs(A - Ar) / Ar, abs(V - Vr) / Vr, np.linalg.norm(J - Jr) / np.linalg.norm(Jr))
-    assert all(e12 < e8 for e8, e12 in zip(errs[8], errs[12])), errs
-    assert max(errs[12]) < 2e-3, errs
