@@ -418,9 +418,9 @@ int serve_poll(sk_server* srv, uint64_t ticket, double* u_out, sk_req_stats* st,
  * free the server. Results that were never polled are discarded. */
 void serve_destroy(sk_server* srv);
 
-/* Single layer (Sec. 3.4, Eq. regstokes) without any memory allocation (the
- * allocation-free call has no counterpart in the paper: it is a service for
- * callers that cannot allocate).
+/* The single layer of stokes_sl_eval without any memory allocation. Library
+ * infrastructure: the paper has no counterpart of this call; it is a service
+ * for callers that cannot allocate.
  *
  * Who needs it: code that runs under a fixed device-memory budget owned by
  * a framework allocator, where a library's own cudaMalloc could fail or
@@ -433,8 +433,9 @@ void serve_destroy(sk_server* srv);
  * with the default thresholds rho_T = 0.5, rho_c = 5, on the calling
  * thread's current CUDA device: bit for bit while the scratch holds the
  * context call's split of the source sum; otherwise the sum is split into
- * fewer chunks and the chunk merge may differ in the last bits (~1e-16). All arrays are device pointers on
- * that device, with the layout of stokes_sl_eval; the caller owns them.
+ * fewer chunks and the chunk merge may differ in the last bits (~1e-16).
+ * All arrays are device pointers on that device, with the layout of
+ * stokes_sl_eval; the caller owns them.
  *
  * Scratch: one static device array of 32 MiB inside the library, shared by
  * every call on a device. A GPU that loads the library's code holds it until
@@ -446,8 +447,11 @@ void serve_destroy(sk_server* srv);
  * corrupt each other's results: serialize them.
  *
  * Set-up: the first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) and caches it; make that first call before any
- * stream capture on that device.
+ * (cudaGetSymbolAddress) and caches it for the life of the process; make
+ * that first call before any stream capture on that device. A
+ * cudaDeviceReset of that device reloads the library's device code and
+ * leaves the cached address stale: do not call this function on a device
+ * after resetting it.
  *
  * cuda_stream NULL: the call runs on the legacy default stream, waits for
  * completion and reports a device-side failure (SK_ETIMEOUT, SK_EINVAL for a

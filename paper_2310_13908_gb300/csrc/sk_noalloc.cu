@@ -68,7 +68,10 @@ extern "C" int stokes_sl_eval_noalloc(int64_t n_src, const double* src_xyz, cons
   s.n_delta = n_delta;
   s.mu = mu;
   s.copy_inputs = false;
-  s.n_chunks = choose_chunks(SK_FP32C, n_src, n_tgt, sms);
+  // the decomposition of stokes_sl_eval (chunks, fused or separate finish);
+  // the single-block and multi-block sorts give the same order, so the sort
+  // limit does not matter for the result
+  choose_decomposition(s, sms);
   // fewer source chunks need less scratch; reject what does not fit at one chunk
   while (s.n_chunks > 1 && eval_workspace_bytes(s) > NOALLOC_SCRATCH_BYTES) s.n_chunks /= 2;
   if (eval_workspace_bytes(s) > NOALLOC_SCRATCH_BYTES) return SK_EINVAL;
@@ -89,7 +92,9 @@ extern "C" int stokes_sl_eval_noalloc(int64_t n_src, const double* src_xyz, cons
   b.u = u_out;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   // enqueue_eval clears the flags, counters and near-pair counts it relies on;
-  // every other scratch word is written before it is read.
+  // every other scratch word is written before it is read. cudaGetLastError
+  // reports a failure of any runtime call made since the last check on this
+  // thread: the launches, and the memsets and attribute calls among them.
   enqueue_eval(s, b, 0.5, 5.0, st);
   if (cudaGetLastError() != cudaSuccess) return SK_ECUDA;
   if (cuda_stream) return SK_OK;

@@ -182,3 +182,61 @@ def test_c_program_links_and_runs(lib, tmp_path):
     assert r.returncode == 0, r.stderr
     code = int(r.stdout.split()[0])
     assert code in (sk.SK_OK, sk.SK_ECUDA), r.stdout
+
+
+@pytest.mark.gpu
+def test_c_program_evaluates_the_self_limit(lib, tmp_path):
+    """A plain C program evaluates stokes_sl_eval through the ABI alone, in
+    both precisions, on host arrays: one source with a target on it gives the
+    r -> 0 limit of Sec. 3.4, u = w f / (8 pi mu) * 16 / (3 delta sqrt(pi)),
+    and a distant target the textbook Stokeslet of Sec. 2.2 to O(e^-rho^2)."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc") or shutil.which("cc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    libdir = os.path.dirname(sk.LIB_PATH)
+    src = tmp_path / "eval.c"
+    src.write_text(r"""
+#include <math.h>
+#include <stdio.h>
+#include "stokesreg.h"
+int main(void) {
+  sk_ctx* ctx = NULL;
+  if (sk_create(&ctx, 0, 0) != SK_OK) { printf("create %s\n", sk_last_error(NULL)); return 2; }
+  const double x[3] = {1.0, 2.0, 3.0}, w[1] = {0.7}, f[3] = {0.3, -1.2, 2.0};
+  const double y[6] = {1.0, 2.0, 3.0, 1.0, 2.0, 13.0};  /* on the node; 10 away on z */
+  const double delta = 0.2, mu = 1.5, pi = 3.14159265358979323846;
+  const int precs[2] = {SK_FP64, SK_FP32C};
+  int bad = 0;
+  for (int k = 0; k < 2; ++k) {
+    double u[6];
+    int rc = stokes_sl_eval(ctx, precs[k], SK_HOST, 1, x, w, f, 2, y, &delta, 1, mu, u, NULL);
+    if (rc != SK_OK) { printf("eval %d %s\n", rc, sk_last_error(ctx)); return 3; }
+    const double lim = 16.0 / (3.0 * delta * sqrt(pi)) * w[0] / (8.0 * pi * mu);
+    const double tol = k == 0 ? 1e-13 : 1e-12;
+    for (int c = 0; c < 3; ++c) {
+      const double ref = lim * f[c];
+      if (fabs(u[c] - ref) > tol * fabs(ref)) { printf("self %d %d %.17g %.17g\n", k, c, u[c], ref); bad = 1; }
+    }
+    /* d = (0, 0, 10): u = w / (8 pi mu) (f / r + (f . d) d / r^3) */
+    const double r = 10.0, s = w[0] / (8.0 * pi * mu);
+    const double far[3] = {s * f[0] / r, s * f[1] / r, s * (f[2] / r + f[2] * 100.0 / (r * r * r))};
+    const double tf = k == 0 ? 1e-13 : 1e-6;
+    for (int c = 0; c < 3; ++c)
+      if (fabs(u[3 + c] - far[c]) > tf * fabs(far[2])) { printf("far %d %d %.17g %.17g\n", k, c, u[3 + c], far[c]); bad = 1; }
+  }
+  sk_destroy(ctx);
+  printf("%s\n", bad ? "FAIL" : "OK");
+  return bad;
+}
+""")
+    exe = tmp_path / "eval"
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(root, "include"),
+                        str(src), "-L", libdir, "-lstokesreg", f"-Wl,-rpath,{libdir}", "-lm",
+                        "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert r.stdout.strip().endswith("OK")
