@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <cfloat>
 #include <cstddef>
 #include <cstdint>
 #include <string>
@@ -72,7 +73,41 @@ __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a -
 __device__ __forceinline__ float frame_mid(float lo, float hi) {
   return lo <= hi ? __fmul_rn(__fadd_rn(lo, hi), 0.5f) : 0.f;
 }
+
+// Writes the FP32 box of the warp's real points (lane 0) and returns its
+// midpoint frame to every lane. All 32 lanes call it (the packers run whole
+// warps over slots padded to multiples of 32).
+__device__ __forceinline__ float3 warp_box(bool real, float x, float y, float z, float4* out) {
+  constexpr float BIG = FLT_MAX;
+  float lx = real ? x : BIG, ly = real ? y : BIG, lz = real ? z : BIG;
+  float hx = real ? x : -BIG, hy = real ? y : -BIG, hz = real ? z : -BIG;
+  for (int o = 16; o > 0; o >>= 1) {
+    lx = fminf(lx, __shfl_xor_sync(0xffffffffu, lx, o));
+    ly = fminf(ly, __shfl_xor_sync(0xffffffffu, ly, o));
+    lz = fminf(lz, __shfl_xor_sync(0xffffffffu, lz, o));
+    hx = fmaxf(hx, __shfl_xor_sync(0xffffffffu, hx, o));
+    hy = fmaxf(hy, __shfl_xor_sync(0xffffffffu, hy, o));
+    hz = fmaxf(hz, __shfl_xor_sync(0xffffffffu, hz, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    out[0] = make_float4(lx, ly, lz, 0.f);
+    out[1] = make_float4(hx, hy, hz, 0.f);
+  }
+  return make_float3(frame_mid(lx, hx), frame_mid(ly, hy), frame_mid(lz, hz));
+}
+
+// Single-layer FP32 source record (duplicated lanes for f32x2 arithmetic):
+// {-x,-x,-y,-y} {-z,-z,gx,gx} {gy,gy,gz,gz}, x relative to the segment frame.
+__device__ __forceinline__ void write_sl_record(float4* o, float x, float y, float z, float g0,
+                                                float g1, float g2) {
+  o[0] = make_float4(-x, -x, -y, -y);
+  o[1] = make_float4(-z, -z, g0, g0);
+  o[2] = make_float4(g1, g1, g2, g2);
+}
 #endif
+
+// Padding sources sit this far away, with zero density.
+constexpr float PAD_POS = 1.0e15f;
 
 // Bump allocator over one device buffer; a null base only measures.
 struct Bump {
@@ -135,7 +170,10 @@ struct EvalBufs {
 // FP32 pair kernel configuration: two f32x2 target pairs per lane at two
 // CTAs per SM for large target counts, one pair per lane at three CTAs per SM
 // (more warps, smaller target blocks) otherwise.
-constexpr int64_t PAIR32_NP1_MAX_TARGETS = 131072;
+#ifndef SK_NP1_MAX_TARGETS
+#define SK_NP1_MAX_TARGETS 131072
+#endif
+constexpr int64_t PAIR32_NP1_MAX_TARGETS = SK_NP1_MAX_TARGETS;
 inline int pair32_np(int64_t M) { return M > PAIR32_NP1_MAX_TARGETS ? 2 : 1; }
 #ifndef SK_MINB_NP2
 #define SK_MINB_NP2 (512 / SK_TPB32)
@@ -224,6 +262,12 @@ void launch_sort_points(const double* xyz, const double* w, int64_t n, uint32_t*
                         uint32_t* keys_b, int* vals_a, int* vals_b, uint32_t* hist,
                         float* bbox_part, float* bbox, int* count_out, int64_t small_max_points,
                         cudaStream_t st);
+// Stable LSD radix sort of (key, value) pairs by the low `bits` bits of the
+// keys, 8 bits per pass, in the buffers of launch_sort_points (hist holds
+// 256 * sort_grid_blocks(n) + 256 words). Returns 0 when the sorted pairs are
+// in (keys_a, vals_a), 1 when they are in (keys_b, vals_b).
+int launch_sort_pairs(uint32_t* keys_a, uint32_t* keys_b, int* vals_a, int* vals_b, int64_t n,
+                      int bits, uint32_t* hist, cudaStream_t st);
 void launch_pack_sources32(int layer, const EvalBufs& b, double scale, cudaStream_t st);
 void launch_pack_sources64(int layer, const EvalBufs& b, double scale, cudaStream_t st);
 void launch_pack_targets32(const EvalBufs& b, int64_t n_delta, double rho_T, double rho_c,

@@ -401,22 +401,45 @@ struct PairArgs {
   const float4* srcLo = nullptr;  // double layer: residuals of the packed positions
 };
 
+// The source tiles of one work item: n tiles, each (first packed source,
+// segments of SEG sources, at most TILE_SEGS). With desc == nullptr they are
+// the full tiles k0 .. k0 + n - 1 of the packed array; a list serves work
+// whose tiles are scattered (the FMM's neighbouring clusters and
+// equivalent sources).
+struct TileList {
+  const int2* desc;
+  int k0, n;
+  __device__ __forceinline__ int2 tile(int it) const {
+    return desc ? desc[it] : make_int2((k0 + it) * TILE, TILE_SEGS);
+  }
+};
+
+// Tiles of source chunk ch of a direct evaluation: an even split of the
+// padded sources into a.n_chunks contiguous ranges.
+__device__ __forceinline__ TileList chunk_tiles(const PairArgs& a, int ch) {
+  const int n_tiles = a.meta[META_NS_PAD] / TILE;
+  const int k0 = (int)((long long)ch * n_tiles / a.n_chunks);
+  const int k1 = (int)((long long)(ch + 1) * n_tiles / a.n_chunks);
+  return TileList{nullptr, k0, k1 - k0};
+}
+
 // One work item: target block tb (TPB32 * 2 * NP sorted targets) against
-// source chunk ch. Writes the chunk partials of the block's targets; returns
-// false if a bounded wait expired (the flag is set, nothing is written).
+// the source tiles tl. Writes the block's partials (target t at
+// part + (t - t_sub) * 3); returns false if a bounded wait expired (the flag
+// is set, nothing is written).
 template <class L, int NP>
-__device__ __forceinline__ bool pair_item(const PairArgs& a, int tb, int ch, float4* sm,
+__device__ __forceinline__ bool pair_item(const PairArgs& a, int tb, const TileList& tl,
+                                          double* __restrict__ part, int64_t t_sub, float4* sm,
                                           PipeSmem<pair_stages<L, NP>()>& ps) {
   constexpr int V = L::V;
   constexpr int STAGES = pair_stages<L, NP>();
   constexpr int WARPS = TPB32 / 32;
-  constexpr uint32_t TILE_BYTES = TILE * V * sizeof(float4);
+  constexpr uint32_t SEG_BYTES = SEG * V * sizeof(float4);
   const float4* __restrict__ srcF = a.srcF;
   const float4* __restrict__ segbox = a.segbox;
   const int* __restrict__ src_orig = a.src_orig;
   const float4* __restrict__ tgtF = a.tgtF;
   const double4_32a* __restrict__ tgt64 = a.tgt64;
-  const int n_chunks = a.n_chunks;
   int* __restrict__ near_cnt = a.near_cnt;
   int* __restrict__ near_idx = a.near_idx;
   unsigned long long* __restrict__ flags = a.flags;
@@ -426,9 +449,7 @@ __device__ __forceinline__ bool pair_item(const PairArgs& a, int tb, int ch, flo
   int* issued = ps.issued;
 
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int n_tiles = a.meta[META_NS_PAD] / TILE;
-  const int k0 = (int)((long long)ch * n_tiles / n_chunks);
-  const int k1 = (int)((long long)(ch + 1) * n_tiles / n_chunks);
+  const int n_it = tl.n;
 
   // ---- targets of this lane: pair p holds targets (base + 64p + lane, base + 64p + 32 + lane)
   const int64_t wbase = (int64_t)tb * (TPB32 * 2 * NP) + wid * (64 * NP) + lane;
@@ -519,12 +540,15 @@ __device__ __forceinline__ bool pair_item(const PairArgs& a, int tb, int ch, flo
   __syncthreads();
   if (tid == 0) {
     for (int b = 0; b < STAGES; ++b)
-      if (k0 + b < k1) {
-        bulk_load(sm + b * TILE * V, srcF + (size_t)(k0 + b) * TILE * V, TILE_BYTES, &full[b]);
+      if (b < n_it) {
+        const int2 t = tl.tile(b);
+        bulk_load(sm + b * TILE * V, srcF + (size_t)t.x * V, t.y * SEG_BYTES, &full[b]);
         issued[b] = 1;
       }
   }
-  for (int k = k0, it = 0; k < k1; ++k, ++it) {
+  for (int it = 0; it < n_it; ++it) {
+    const int2 tile = tl.tile(it);
+    const int src0 = tile.x, nseg = tile.y;  // first packed source, segments
     const int buf = it % STAGES;
     const int use = it / STAGES;
     const bool ok = __all_sync(FULL, mbar_wait_bounded(&full[buf], (uint32_t)(use & 1)));
@@ -535,11 +559,11 @@ __device__ __forceinline__ bool pair_item(const PairArgs& a, int tb, int ch, flo
     if (warp_live) {
       const float4* S = sm + buf * TILE * V;
       bool nb = false;
-      float csx = 0.f, csy = 0.f, csz = 0.f;  // lane s < TILE_SEGS: segment s's frame
+      float csx = 0.f, csy = 0.f, csz = 0.f;  // lane s < nseg: segment s's frame
       float chs = 0.f;                        // ... and the half extent of its box
-      if (lane < TILE_SEGS) {
-        const float4 lo = segbox[2 * ((size_t)k * TILE_SEGS + lane)];
-        const float4 hi = segbox[2 * ((size_t)k * TILE_SEGS + lane) + 1];
+      if (lane < nseg) {
+        const float4 lo = segbox[2 * ((size_t)(src0 / SEG) + lane)];
+        const float4 hi = segbox[2 * ((size_t)(src0 / SEG) + lane) + 1];
         const float dx = fmaxf(0.f, fmaxf(lo.x - bhi[0], blo[0] - hi.x));
         const float dy = fmaxf(0.f, fmaxf(lo.y - bhi[1], blo[1] - hi.y));
         const float dz = fmaxf(0.f, fmaxf(lo.z - bhi[2], blo[2] - hi.z));
@@ -552,7 +576,7 @@ __device__ __forceinline__ bool pair_item(const PairArgs& a, int tb, int ch, flo
       }
       const unsigned nm = __ballot_sync(FULL, nb);
 #pragma unroll 1
-      for (int s = 0; s < TILE_SEGS; ++s) {
+      for (int s = 0; s < nseg; ++s) {
         const float4* SS = S + s * SEG * V;
         const float sx = __shfl_sync(FULL, csx, s), sy = __shfl_sync(FULL, csy, s),
                     sz = __shfl_sync(FULL, csz, s);
@@ -576,7 +600,7 @@ __device__ __forceinline__ bool pair_item(const PairArgs& a, int tb, int ch, flo
             }
           }
         } else {
-          const int* orig = src_orig + (size_t)k * TILE + s * SEG;
+          const int* orig = src_orig + (size_t)src0 + s * SEG;
 #pragma unroll
           for (int p = 0; p < NP; ++p) {
             const float4 q = ts[(p * TGT_SLOTS + 3) * TPB32], r = ts[(p * TGT_SLOTS + 4) * TPB32];
@@ -620,9 +644,10 @@ __device__ __forceinline__ bool pair_item(const PairArgs& a, int tb, int ch, flo
               }
             }
           } else if constexpr (L::kExactNear) {
-            // lane j holds source j's residual; the targets' frame-shift
-            // residuals are recomputed per source from the (hi, lo) column
-            const float4 ylo = a.srcLo[(size_t)k * TILE + s * SEG + lane];
+            // the source's residual is read per source (a broadcast load), the
+            // targets' frame-shift residuals recomputed from the (hi, lo)
+            // column: nothing extra stays live across the loop
+            const float4* __restrict__ ylo = a.srcLo + (size_t)src0 + s * SEG;
 #pragma unroll 1
             for (int j = 0; j < SEG; ++j) {
               const typename L::Src src = L::load(SS + j * V);
@@ -634,8 +659,8 @@ __device__ __forceinline__ bool pair_item(const PairArgs& a, int tb, int ch, flo
                 any |= (r2[p].x < T[p].rc2.x) | (r2[p].y < T[p].rc2.y);
               }
               if (__any_sync(FULL, any)) {
-                const float lx = __shfl_sync(FULL, ylo.x, j), ly = __shfl_sync(FULL, ylo.y, j),
-                            lz = __shfl_sync(FULL, ylo.z, j);
+                const float4 yl = ylo[j];
+                const float lx = yl.x, ly = yl.y, lz = yl.z;
 #pragma unroll
                 for (int p = 0; p < NP; ++p) {
                   const float4 hx = ts[(p * TGT_SLOTS) * TPB32],
@@ -662,7 +687,7 @@ __device__ __forceinline__ bool pair_item(const PairArgs& a, int tb, int ch, flo
             }
           }
         }
-        if ((s & 3) == 3) {
+        if ((s & 3) == 3 || s == nseg - 1) {  // at most 128 sources in plain FP32
 #pragma unroll
           for (int p = 0; p < NP; ++p) {
             if constexpr (kHiLoSmem) {
@@ -689,11 +714,11 @@ __device__ __forceinline__ bool pair_item(const PairArgs& a, int tb, int ch, flo
     if (lane == 0) {
       __threadfence_block();
       const int prev = atomicAdd(&rel[buf], 1);
-      if (prev == (use + 1) * WARPS - 1 && k + STAGES < k1) {
+      if (prev == (use + 1) * WARPS - 1 && it + STAGES < n_it) {
         __threadfence_block();
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        bulk_load(sm + buf * TILE * V, srcF + (size_t)(k + STAGES) * TILE * V, TILE_BYTES,
-                  &full[buf]);
+        const int2 t = tl.tile(it + STAGES);
+        bulk_load(sm + buf * TILE * V, srcF + (size_t)t.x * V, t.y * SEG_BYTES, &full[buf]);
         atomicAdd(&issued[buf], 1);
       }
     }
@@ -713,7 +738,7 @@ __device__ __forceinline__ bool pair_item(const PairArgs& a, int tb, int ch, flo
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int64_t t = wbase + 64 * p + 32 * h;
-      double* o = a.part + ((size_t)ch * a.M_pad + t) * 3;
+      double* o = part + (size_t)(t - t_sub) * 3;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const float2 H2 = kHiLoSmem ? acc[((p * 3 + c) * 2) * TPB32 + tid] : HI[p][c];
@@ -830,17 +855,13 @@ __device__ __forceinline__ void overflow_target(const OverflowArgs& a, int64_t t
 // Finish one sorted target: chunk partials in fixed order plus the FP64 near
 // sum (list sorted by source index, or the overflow rescan's sum); writes
 // u at the target's original index. Returns the target's near-pair count.
+// FP64 near sum of sorted target t: its list sorted by source index, or the
+// overflow rescan's sum. Returns the target's near-pair count.
 template <class L>
-__device__ __forceinline__ int finish_target(const FinishArgs& a, int64_t t) {
-  double u0 = 0, u1 = 0, u2 = 0;
-  for (int c = 0; c < a.n_chunks; ++c) {
-    const double* p = a.part + ((size_t)c * a.M_pad + t) * 3;
-    u0 += p[0];
-    u1 += p[1];
-    u2 += p[2];
-  }
+__device__ __forceinline__ int near_sum(const FinishArgs& a, int64_t t, double& n0, double& n1,
+                                        double& n2) {
   const int cnt = a.near_cnt[t];
-  double n0 = 0, n1 = 0, n2 = 0;
+  n0 = n1 = n2 = 0;
   if (cnt <= NEAR_K) {
     int li[NEAR_K];
     for (int i = 0; i < cnt; ++i) {
@@ -861,11 +882,46 @@ __device__ __forceinline__ int finish_target(const FinishArgs& a, int64_t t) {
     n1 = a.near_ovf[3 * t + 1];
     n2 = a.near_ovf[3 * t + 2];
   }
+  return cnt;
+}
+
+template <class L>
+__device__ __forceinline__ int finish_target(const FinishArgs& a, int64_t t) {
+  double u0 = 0, u1 = 0, u2 = 0;
+  for (int c = 0; c < a.n_chunks; ++c) {
+    const double* p = a.part + ((size_t)c * a.M_pad + t) * 3;
+    u0 += p[0];
+    u1 += p[1];
+    u2 += p[2];
+  }
+  double n0, n1, n2;
+  const int cnt = near_sum<L>(a, t, n0, n1, n2);
   const int j = a.perm[t];
   a.u[3 * j] = u0 + n0;
   a.u[3 * j + 1] = u1 + n1;
   a.u[3 * j + 2] = u2 + n2;
   return cnt;
+}
+
+// Drop from L2, without writing them back, the 128-byte lines lying wholly
+// inside [begin, begin + bytes): scratch that has been read for the last
+// time in this evaluation (chunk partials, near lists of a finished target
+// block). Lines only partly inside are left alone, so no other block's data
+// is touched. The calling threads (tid of n) split the lines.
+__device__ __forceinline__ void discard_l2(const void* begin, size_t bytes, int tid, int n) {
+  const size_t g = (size_t)__cvta_generic_to_global(begin);
+  const size_t a = (g + 127) & ~(size_t)127, e = (g + bytes) & ~(size_t)127;
+  for (size_t q = a + (size_t)tid * 128; q < e; q += (size_t)n * 128)
+    asm volatile("discard.global.L2 [%0], 128;" ::"l"(q) : "memory");
+}
+
+// The scratch of targets t0 .. t0 + nt - 1 after their finish: their chunk
+// partials and near lists.
+__device__ __forceinline__ void discard_block_scratch(const FinishArgs& fa, int64_t t0, int nt,
+                                                      int tid, int n) {
+  for (int c = 0; c < fa.n_chunks; ++c)
+    discard_l2(fa.part + ((size_t)c * fa.M_pad + t0) * 3, (size_t)nt * 3 * sizeof(double), tid, n);
+  discard_l2(fa.near_idx + (size_t)t0 * NEAR_K, (size_t)nt * NEAR_K * sizeof(int), tid, n);
 }
 
 // Finish targets t0 .. t0 + nt - 1 (of M real ones) of a target block whose
@@ -887,6 +943,8 @@ __device__ __noinline__ void finish_block(const OverflowArgs& oa, const FinishAr
     if (t0 + i < M) cnt += finish_target<L>(fa, t0 + i);
   for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(FULL, cnt, o);
   if (lane == 0 && cnt) atomicAdd(fa.flags + FLAG_NEAR_PAIRS, (unsigned long long)cnt);
+  __syncthreads();  // every read of the block's partials and near lists is done
+  discard_block_scratch(fa, t0, nt, tid, blockDim.x);
 }
 
 }  // namespace p32

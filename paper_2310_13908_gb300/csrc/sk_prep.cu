@@ -335,28 +335,6 @@ __global__ void __launch_bounds__(RS_THREADS)
 }
 
 // ---- packing ----------------------------------------------------------------
-// Writes the FP32 box of the warp's real points (lane 0) and returns its
-// midpoint frame to every lane.
-__device__ __forceinline__ float3 warp_box(bool real, float x, float y, float z, float4* out) {
-  float lx = real ? x : FLT_MAX, ly = real ? y : FLT_MAX, lz = real ? z : FLT_MAX;
-  float hx = real ? x : -FLT_MAX, hy = real ? y : -FLT_MAX, hz = real ? z : -FLT_MAX;
-  for (int o = 16; o > 0; o >>= 1) {
-    lx = fminf(lx, __shfl_xor_sync(FULL, lx, o));
-    ly = fminf(ly, __shfl_xor_sync(FULL, ly, o));
-    lz = fminf(lz, __shfl_xor_sync(FULL, lz, o));
-    hx = fmaxf(hx, __shfl_xor_sync(FULL, hx, o));
-    hy = fmaxf(hy, __shfl_xor_sync(FULL, hy, o));
-    hz = fmaxf(hz, __shfl_xor_sync(FULL, hz, o));
-  }
-  if ((threadIdx.x & 31) == 0) {
-    out[0] = make_float4(lx, ly, lz, 0.f);
-    out[1] = make_float4(hx, hy, hz, 0.f);
-  }
-  return make_float3(frame_mid(lx, hx), frame_mid(ly, hy), frame_mid(lz, hz));
-}
-
-constexpr float PAD_POS = 1.0e15f;  // padding sources sit far away with zero density
-
 // FP32 packed layout (duplicated lanes for f32x2 arithmetic), x, y, z relative
 // to the segment's frame (frame_mid of its box; padding keeps PAD_POS):
 //   single layer: {-x,-x,-y,-y} {-z,-z,gx,gx} {gy,gy,gz,gz},  g = w f scale
@@ -410,9 +388,7 @@ __global__ void k_pack_src32(const double* __restrict__ xyz, const double* __res
     }
   }
   float4* o = srcF + s * V;
-  o[0] = make_float4(-x, -x, -y, -y);
-  o[1] = make_float4(-z, -z, d0, d0);
-  o[2] = make_float4(d1, d1, d2, d2);
+  write_sl_record(o, x, y, z, d0, d1, d2);
   if (LAYER == LAYER_DL) {
     o[3] = make_float4(n0, n0, n1, n1);
     o[4] = make_float4(n2, n2, 0.f, 0.f);
@@ -518,6 +494,24 @@ void launch_sort_points(const double* xyz, const double* w, int64_t n, uint32_t*
     int* tv = va; va = vb; vb = tv;
   }
   // four passes: the sorted data is back in keys_a / vals_a
+}
+
+int launch_sort_pairs(uint32_t* keys_a, uint32_t* keys_b, int* vals_a, int* vals_b, int64_t n,
+                      int bits, uint32_t* hist, cudaStream_t st) {
+  if (n <= 0) return 0;
+  const int sort_blocks = sort_grid_blocks(n);
+  uint32_t* tot = hist + 256 * (size_t)sort_blocks;
+  uint32_t *ka = keys_a, *kb = keys_b;
+  int *va = vals_a, *vb = vals_b;
+  int passes = 0;
+  for (int shift = 0; shift < bits; shift += 8, ++passes) {
+    k_rs_hist<<<sort_blocks, RS_THREADS, 0, st>>>(ka, (int)n, shift, hist);
+    k_rs_rowscan<<<256, RS_THREADS, 0, st>>>(hist, sort_blocks, tot);
+    k_rs_scatter<<<sort_blocks, RS_THREADS, 0, st>>>(ka, va, kb, vb, (int)n, shift, hist, tot);
+    uint32_t* tk = ka; ka = kb; kb = tk;
+    int* tv = va; va = vb; vb = tv;
+  }
+  return passes & 1;
 }
 
 void launch_pack_sources32(int layer, const EvalBufs& b, double scale, cudaStream_t st) {

@@ -170,7 +170,8 @@ __global__ void __launch_bounds__(TPB32, SERVE_MINB)
     __syncthreads();
     const int item = s_item;
     const int tb = item / d.n_chunks, ch = item % d.n_chunks;
-    pair_item<SLayer, SERVE_NP>(d.pa, tb, ch, sm, ps);  // a timeout sets the request's flag
+    pair_item<SLayer, SERVE_NP>(d.pa, tb, chunk_tiles(d.pa, ch), d.pa.part + (size_t)ch * d.pa.M_pad * 3,
+                                0, sm, ps);  // a timeout sets the request's flag
     __syncthreads();
     if (tid == 0) {
       __threadfence();
