@@ -666,39 +666,68 @@ def capsule_bench(sk, h, torch, dev, m=129, steps=100, dt=5e-4, Es=2.0, ED=20.0)
     return res
 
 
-def fmm_bench(sk, h, torch, dev, m=129, k=64, p=6):
-    """Single-level FMM (Sec. 5, FP64) against the direct FP64 and FP32C sums:
-    ellipsoid (1, 0.8, 0.5) nodes as sources and targets, delta = 2h."""
+def fmm_bench(sk, h, torch, dev):
+    """Single-level FMM (Sec. 5) against the direct sums, on the ellipsoid
+    (1, 0.8, 0.5) at delta = 2h: nodes as sources and targets at m = 129 and
+    193, and the 4x upsampled setting of the paper's m = 96 (the 4m-th order
+    nodes as sources, the m-th order nodes as targets, delta = 2 h_fine).
+    FP32C FMM and direct FP32C are timed with CUDA events; both are checked
+    against the oracle on 1024 seeded targets; the FP64 FMM is timed at
+    m = 129 beside the direct FP64 sum."""
     import capsule_inputs as ci
-    s = ci.make_surface(ci.Ellipsoid(1.0, 0.8, 0.5), m)
-    f = ci.sh_density(s.x0, np.random.default_rng(5), lmax=8)
+    import oracle
 
     def td(a):
         return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)
 
-    X, W, F, D = td(s.X), td(s.w), td(f), td(np.array([2 * s.h]))
-    act = np.flatnonzero(s.w)
-    C0 = td(s.X[act[:: len(act) // k][:k]])
-
     def timed(fn, reps):
         fn()
         torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
         for _ in range(reps):
             u = fn()
+        b.record()
         torch.cuda.synchronize(dev)
-        return (time.perf_counter() - t0) * 1e3 / reps, u.cpu().numpy()
+        return a.elapsed_time(b) / reps, u.cpu().numpy()
 
-    t64, u64 = timed(lambda: sk.stokes_sl_eval(h, sk.SK_FP64, sk.SK_DEVICE, X, W, F, X, D, 1.0), 2)
-    t32, u32 = timed(lambda: sk.stokes_sl_eval(h, sk.SK_FP32C, sk.SK_DEVICE, X, W, F, X, D, 1.0), 5)
-    tf, uf = timed(lambda: sk.stokes_sl_eval_fmm(h, sk.SK_DEVICE, X, W, F, X, D, 1.0, C0, 10, p), 2)
-    return {"workload": f"ellipsoid(1,0.8,0.5) m={m}: N={s.N} targets x N_s={s.n_active} sources, "
-                        f"delta=2h; FMM k={k} clusters (10 Lloyd steps), p={p} "
-                        f"({6 * p * p - 12 * p + 8} equivalent points per cube)",
-            "direct_fp64_ms": t64, "direct_fp32c_ms": t32, "fmm_fp64_ms": tf,
-            "fmm_rel_l2_vs_direct_fp64": rel_l2(uf, u64),
-            "fp32c_rel_l2_vs_direct_fp64": rel_l2(u32, u64),
-            "paper_speedup_fmm_vs_direct": {"m32": 1.02, "m64": 1.57, "m96": 1.81}}
+    shape = ci.Ellipsoid(1.0, 0.8, 0.5)
+    out = {"paper_speedup_fmm_vs_direct": {"m32": 1.02, "m64": 1.57, "m96": 1.81},
+           "p": 6, "lloyd_iters": 10}
+    cases = [("m129", 129, None, (48, 64, 96)), ("m193", 193, None, (96, 128)),
+             ("up4_m96", 96, 384, (96, 128))]
+    for name, m, m_src, ks in cases:
+        tgt_s = ci.make_surface(shape, m)
+        src_s = tgt_s if m_src is None else ci.make_surface(shape, m_src)
+        f = ci.sh_density(src_s.x0, np.random.default_rng(5), lmax=8)
+        delta = 2 * src_s.h
+        X, W, F, Y, D = td(src_s.X), td(src_s.w), td(f), td(tgt_s.X), td(np.array([delta]))
+        act = np.flatnonzero(src_s.w)
+        inter = tgt_s.N * len(act)
+        t32, u32 = timed(lambda: sk.stokes_sl_eval(h, sk.SK_FP32C, sk.SK_DEVICE, X, W, F, Y, D,
+                                                   1.0), 5)
+        idx = np.random.default_rng(7).choice(tgt_s.N, 1024, replace=False)
+        ref = oracle.sl(src_s.X, src_s.w, f, tgt_s.X[idx], delta, 1.0)
+        row = {"targets": tgt_s.N, "sources_active": int(len(act)), "interactions": inter,
+               "direct_fp32c_ms": t32, "direct_fp32c_rel_l2_vs_oracle": rel_l2(u32[idx], ref)}
+        for k in ks:
+            C0 = td(src_s.X[act[:: len(act) // k][:k]])
+            tf, uf = timed(lambda: sk.stokes_sl_eval_fmm(h, sk.SK_DEVICE, X, W, F, Y, D, 1.0, C0,
+                                                         10, 6, precision=sk.SK_FP32C), 5)
+            row[f"fmm_fp32c_k{k}"] = {"ms": tf, "speedup_vs_direct_fp32c": t32 / tf,
+                                      "rel_l2_vs_oracle": rel_l2(uf[idx], ref),
+                                      "work_items": sk.sk_last_eval_stats(h)["n_chunks"]}
+        if name == "m129":
+            C0 = td(src_s.X[act[:: len(act) // 64][:64]])
+            t64, u64 = timed(lambda: sk.stokes_sl_eval(h, sk.SK_FP64, sk.SK_DEVICE, X, W, F, Y, D,
+                                                       1.0), 2)
+            tf64, uf64 = timed(lambda: sk.stokes_sl_eval_fmm(h, sk.SK_DEVICE, X, W, F, Y, D, 1.0,
+                                                             C0, 10, 6), 2)
+            row["direct_fp64_ms"] = t64
+            row["fmm_fp64_k64"] = {"ms": tf64, "speedup_vs_direct_fp64": t64 / tf64,
+                                   "rel_l2_vs_oracle": rel_l2(uf64[idx], ref)}
+        out[name] = row
+    return out
 
 
 def extras(sk, h, w, X, W, F, Y, D, out, u_fp32, stream, dev, torch, serve_future=None):
@@ -910,9 +939,9 @@ def extras(sk, h, w, X, W, F, Y, D, out, u_fp32, stream, dev, torch, serve_futur
     except Exception as e:
         res["capsule_skalak_m129"] = {"error": repr(e)}
     try:
-        res["fmm_m129"] = fmm_bench(sk, h, torch, dev)
+        res["fmm"] = fmm_bench(sk, h, torch, dev)
     except Exception as e:
-        res["fmm_m129"] = {"error": repr(e)}
+        res["fmm"] = {"error": repr(e)}
     if serve_future is not None:
         try:
             res["serving"] = serving_bench(sk, h, serve_future.result())

@@ -320,24 +320,30 @@ int stokes_sl_eval_upsampled(sk_ctx* ctx, int precision, int mem, int m, const d
                              const double* W, const double* f, double mu, double* u_out,
                              void* cuda_stream);
 
-/* Single layer by the single-level kernel-independent FMM of Sec. 5, FP64.
- * Arguments as for stokes_sl_eval (sources with zero weight are dropped),
- * plus:
+/* Single layer by the single-level kernel-independent FMM of Sec. 5.
+ * precision: SK_FP64, or SK_FP32C (the neighbouring clusters through the
+ * FP32-compensated pair sums of stokes_sl_eval, with FP64 near lists; the
+ * equivalent sources in FP32; check potentials FP32, equivalent densities
+ * FP64). Arguments otherwise as for stokes_sl_eval (sources with zero weight
+ * are dropped), plus:
  *   k           clusters (1..65536), centers0 [k][3] their initial centres
  *               (host or device per mem), lloyd_iters >= 0 k-means steps
  *   p           equivalent/check points per cube edge (3..10; 6 p^2 - 12 p + 8
  *               points per cube)
  * Clusters get a cube (half width a), equivalent sources on the 1.05 a cube
- * and check points on the 2.95 a cube; targets go in groups of 32
- * consecutive indices, and a group takes a cluster's equivalent sources when
- * every target lies outside the check cube and at least 7 delta from the
- * cluster cube, else the direct regularized sum over the cluster's points.
- * Deterministic. Errors: SK_EINVAL, SK_ENOMEM, SK_ECUDA. */
-int stokes_sl_eval_fmm(sk_ctx* ctx, int mem, int64_t n_src, const double* src_xyz,
-                       const double* src_w, const double* f, int64_t n_tgt, const double* tgt_xyz,
-                       const double* delta, int64_t n_delta, double mu, int k,
-                       const double* centers0, int lloyd_iters, int p, double* u_out,
-                       void* cuda_stream);
+ * and check points on the 2.95 a cube. Box against box (Sec. 5, step 3):
+ * each target joins the box of its nearest final centre; a target box takes
+ * a cluster's equivalent sources when it lies wholly outside the cluster's
+ * check cube and at least 7 delta (its largest) from the cluster cube, else
+ * the direct regularized sum over the cluster's points. Deterministic. The
+ * SK_FP32C path synchronizes the stream once, to plan its work items on the
+ * host, and returns after the result is complete.
+ * Errors: SK_EINVAL, SK_ENOMEM, SK_ECUDA, SK_ETIMEOUT. */
+int stokes_sl_eval_fmm(sk_ctx* ctx, int precision, int mem, int64_t n_src,
+                       const double* src_xyz, const double* src_w, const double* f,
+                       int64_t n_tgt, const double* tgt_xyz, const double* delta,
+                       int64_t n_delta, double mu, int k, const double* centers0,
+                       int lloyd_iters, int p, double* u_out, void* cuda_stream);
 
 /* ---- serving: continuous batching of single-layer requests -------------
  *

@@ -104,7 +104,7 @@ _EXTRA_DECLS: dict = {
     "surface_derivatives": ([_vp, _int, _int, _i64, _vp, _vp, _vp, _vp], _int),
     "membrane_force": ([_vp, _int, _int, _vp, _vp, _dbl, _dbl, _vp, _vp, _vp], _int),
     "stokes_sl_eval_upsampled": ([_vp, _int, _int, _int, _vp, _vp, _vp, _dbl, _vp, _vp], _int),
-    "stokes_sl_eval_fmm": ([_vp, _int, _i64, _vp, _vp, _vp, _i64, _vp, _vp, _i64, _dbl, _int, _vp,
+    "stokes_sl_eval_fmm": ([_vp, _int, _int, _i64, _vp, _vp, _vp, _i64, _vp, _vp, _i64, _dbl, _int, _vp,
                             _int, _int, _vp, _vp], _int),
     "capsule_destroy": ([_vp], None),
 }
@@ -358,8 +358,9 @@ def stokes_sl_eval_upsampled(ctx, precision: int, mem: int, m: int, X, W, f, mu:
 
 
 def stokes_sl_eval_fmm(ctx, mem: int, src_xyz, src_w, f, tgt_xyz, delta, mu: float, centers0,
-                       lloyd_iters: int = 10, p: int = 6, stream=None):
-    """Single layer by the single-level FMM of Sec. 5 (FP64). Returns u (M, 3)."""
+                       lloyd_iters: int = 10, p: int = 6, stream=None, precision: int = SK_FP64):
+    """Single layer by the single-level FMM of Sec. 5 (SK_FP64 or SK_FP32C).
+    Returns u (M, 3)."""
     lib = load()
     X, n = _ptr(src_xyz, mem, (3,), "src_xyz")
     W, nw = _ptr(src_w, mem, (), "src_w")
@@ -376,7 +377,8 @@ def stokes_sl_eval_fmm(ctx, mem: int, src_xyz, src_w, f, tgt_xyz, delta, mu: flo
                 float(mu), k, _host_ptr(C), int(lloyd_iters), int(p), _host_ptr(u)]
     else:
         args = [X, W, F, M, Y, D, nd, float(mu), k, C, int(lloyd_iters), int(p), u.data_ptr()]
-    _check(ctx, lib.stokes_sl_eval_fmm(ctx, int(mem), n, *args, _stream_handle(stream)))
+    _check(ctx, lib.stokes_sl_eval_fmm(ctx, int(precision), int(mem), n, *args,
+                                       _stream_handle(stream)))
     return u
 
 

@@ -115,8 +115,8 @@ def test_membrane_entry_points_reject_null_context(lib):
                               None) == sk.SK_EINVAL
     assert lib.stokes_sl_eval_upsampled(None, sk.SK_FP64, sk.SK_HOST, 9, None, None, None, 1.0,
                                         None, None) == sk.SK_EINVAL
-    assert lib.stokes_sl_eval_fmm(None, sk.SK_HOST, 1, None, None, None, 1, None, None, 1, 1.0, 1,
-                                  None, 1, 4, None, None) == sk.SK_EINVAL
+    assert lib.stokes_sl_eval_fmm(None, sk.SK_FP64, sk.SK_HOST, 1, None, None, None, 1, None, None,
+                                  1, 1.0, 1, None, 1, 4, None, None) == sk.SK_EINVAL
 
 
 def test_probe_and_stats_entry_points_reject_null_arguments(lib):

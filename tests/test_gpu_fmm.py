@@ -33,18 +33,28 @@ def seeds(s, k):
     return s.X[act[:: max(1, len(act) // k)][:k]].copy()
 
 
-@pytest.mark.parametrize("p", [4, 6])
-def test_fmm_matches_oracle_fmm(ctx, p):
+# against the oracle's FMM: FP64 to the rounding of the Tikhonov solve, FP32C
+# at the FP32C tolerance of the direct sums
+TOL = {sk.SK_FP64: 1e-8, sk.SK_FP32C: 1e-6}
+PRECS = [sk.SK_FP64, sk.SK_FP32C]
+PREC_ID = {sk.SK_FP64: "fp64", sk.SK_FP32C: "fp32c"}
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=PREC_ID.get)
+@pytest.mark.parametrize("p", [4, 6, 8])
+def test_fmm_matches_oracle_fmm(ctx, p, prec):
     s = ci.make_surface(ci.Ellipsoid(1.0, 0.8, 0.5), 24)
     f = ci.sh_density(s.x0, np.random.default_rng(3), lmax=6)
     c0 = seeds(s, 30)
     tgt = s.X[::3]
-    u = sk.stokes_sl_eval_fmm(ctx, sk.SK_HOST, s.X, s.w, f, tgt, 0.02, 1.2, c0, 8, p)
+    u = sk.stokes_sl_eval_fmm(ctx, sk.SK_HOST, s.X, s.w, f, tgt, 0.02, 1.2, c0, 8, p,
+                              precision=prec)
     ref = fmm.sl_fmm(s.X, s.w, f, tgt, 0.02, 1.2, c0, 8, p)
-    assert rel(u, ref) < 1e-8, rel(u, ref)
+    assert rel(u, ref) < TOL[prec], rel(u, ref)
 
 
-def test_fmm_with_probes_and_per_target_delta_matches_oracle_fmm(ctx):
+@pytest.mark.parametrize("prec", PRECS, ids=PREC_ID.get)
+def test_fmm_with_probes_and_per_target_delta_matches_oracle_fmm(ctx, prec):
     """Off-surface probes join the boxes of their nearest centres; per-target
     delta makes the box's largest delta decide its neighbours."""
     rng = np.random.default_rng(8)
@@ -57,31 +67,57 @@ def test_fmm_with_probes_and_per_target_delta_matches_oracle_fmm(ctx):
     c0 = seeds(s, 30)
     pl = fmm.plan(s.X, s.w, tgt, delta, c0, 8)
     assert 0.2 < pl["near"].mean() < 0.9     # both kinds of box pairs occur
-    u = sk.stokes_sl_eval_fmm(ctx, sk.SK_HOST, s.X, s.w, f, tgt, delta, 0.9, c0, 8, 6)
+    u = sk.stokes_sl_eval_fmm(ctx, sk.SK_HOST, s.X, s.w, f, tgt, delta, 0.9, c0, 8, 6,
+                              precision=prec)
     ref = fmm.sl_fmm(s.X, s.w, f, tgt, delta, 0.9, c0, 8, 6)
-    assert rel(u, ref) < 1e-8, rel(u, ref)
+    assert rel(u, ref) < TOL[prec], rel(u, ref)
 
 
-def test_all_near_equals_the_direct_sum(ctx):
+@pytest.mark.parametrize("prec,tol", [(sk.SK_FP64, 1e-13), (sk.SK_FP32C, 1e-6)],
+                         ids=["fp64", "fp32c"])
+def test_all_near_equals_the_direct_sum(ctx, prec, tol):
     s = ci.make_surface(ci.Sphere(1.0), 12)
     f = ci.sh_density(s.x0, np.random.default_rng(4), lmax=4)
-    u = sk.stokes_sl_eval_fmm(ctx, sk.SK_HOST, s.X, s.w, f, s.X, 10.0, 1.0, seeds(s, 8), 4, 4)
-    assert rel(u, fmm.sl_fmm(s.X, s.w, f, s.X, 10.0, 1.0, seeds(s, 8), 4, 4)) < 1e-13
-    assert rel(u, oracle.sl(s.X, s.w, f, s.X, 10.0, 1.0)) < 1e-13
+    u = sk.stokes_sl_eval_fmm(ctx, sk.SK_HOST, s.X, s.w, f, s.X, 10.0, 1.0, seeds(s, 8), 4, 4,
+                              precision=prec)
+    assert rel(u, fmm.sl_fmm(s.X, s.w, f, s.X, 10.0, 1.0, seeds(s, 8), 4, 4)) < tol
+    assert rel(u, oracle.sl(s.X, s.w, f, s.X, 10.0, 1.0)) < tol
 
 
-def test_fmm_at_larger_size_and_device_memory(ctx):
+@pytest.mark.parametrize("prec", PRECS, ids=PREC_ID.get)
+def test_fmm_at_larger_size_and_device_memory(ctx, prec):
     s = ci.make_surface(ci.Ellipsoid(1.0, 0.8, 0.5), 65)
     f = ci.sh_density(s.x0, np.random.default_rng(5), lmax=8)
     delta = 2 * s.h
     c0 = seeds(s, 100)
     t = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda")
     u = sk.stokes_sl_eval_fmm(ctx, sk.SK_DEVICE, t(s.X), t(s.w), t(f), t(s.X),
-                              t(np.array([delta])), 1.0, t(c0), 10, 6).cpu().numpy()
+                              t(np.array([delta])), 1.0, t(c0), 10, 6,
+                              precision=prec).cpu().numpy()
     ref = fmm.sl_fmm(s.X, s.w, f, s.X, delta, 1.0, c0, 10, 6)
-    assert rel(u, ref) < 1e-8, rel(u, ref)
+    assert rel(u, ref) < TOL[prec], rel(u, ref)
     d = oracle.sl(s.X, s.w, f, s.X, delta, 1.0)
     assert rel(u, d) < 1e-5, rel(u, d)
+
+
+def test_fp32c_fmm_ragged_and_degenerate(ctx):
+    """One cluster (all near), clusters left empty by k-means, zero weights,
+    a single target, and more targets than one block; the FP32C FMM against
+    the oracle's FMM."""
+    rng = np.random.default_rng(12)
+    s = ci.make_surface(ci.Ellipsoid(1.0, 0.9, 0.7), 17)
+    f = rng.standard_normal((s.N, 3))
+    w = s.w.copy()
+    w[rng.random(s.N) < 0.3] = 0.0
+    cases = [(s.X[:1], 1, 0.05), (s.X, 1, 0.05), (s.X[::2], 40, 0.03),
+             (np.concatenate([s.X, s.X + 0.02 * s.n]), 25, 0.04)]
+    for tgt, k, delta in cases:
+        c0 = s.X[np.flatnonzero(w)[:: max(1, np.count_nonzero(w) // k)][:k]].copy()
+        c0[-1] += 5.0          # a centre far away: its cluster may stay empty
+        u = sk.stokes_sl_eval_fmm(ctx, sk.SK_HOST, s.X, w, f, tgt, delta, 1.1, c0, 6, 5,
+                                  precision=sk.SK_FP32C)
+        ref = fmm.sl_fmm(s.X, w, f, tgt, delta, 1.1, c0, 6, 5)
+        assert rel(u, ref) < 1e-6, (len(tgt), k, rel(u, ref))
 
 
 def test_fmm_rejects_bad_arguments(ctx):
