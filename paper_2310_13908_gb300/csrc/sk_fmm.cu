@@ -784,8 +784,8 @@ __global__ void __launch_bounds__(TPB32, MINB)
   if (threadIdx.x == 0) ps.initialized = 0;
   constexpr int TB = TPB32 * 2 * NP;
   const int4 it = items[blockIdx.x];
-  p32::pair_item<p32::SLayer, NP>(a, it.x, p32::TileList{desc + it.y, 0, it.z},
-                                  a.part + (size_t)it.w * TB * 3, (int64_t)it.x * TB, sm, ps);
+  p32::pair_item<p32::SLayer, NP>(
+      a, it.x, p32::TileList{desc + it.y, it.z, it.w, TB, (int64_t)it.x * TB}, sm, ps);
 }
 
 // Thread per target slot: its block's item partials in item order, plus the

@@ -19,7 +19,7 @@ __global__ void __launch_bounds__(TPB32, MINB) k_pair32(PairArgs a) {
   __shared__ PipeSmem<pair_stages<L, NP>()> ps;
   if (threadIdx.x == 0) ps.initialized = 0;
   const int tb = blockIdx.x / a.n_chunks, ch = blockIdx.x % a.n_chunks;
-  pair_item<L, NP>(a, tb, chunk_tiles(a, ch), a.part + (size_t)ch * a.M_pad * 3, 0, sm, ps);
+  pair_item<L, NP>(a, tb, chunk_tiles(a, ch), sm, ps);
 }
 
 template <class L, int NP, int MINB>
@@ -31,7 +31,7 @@ __global__ void __launch_bounds__(TPB32, MINB)
   __shared__ int s_last;
   if (threadIdx.x == 0) ps.initialized = 0;
   const int tb = blockIdx.x / a.n_chunks, ch = blockIdx.x % a.n_chunks;
-  pair_item<L, NP>(a, tb, chunk_tiles(a, ch), a.part + (size_t)ch * a.M_pad * 3, 0, sm, ps);
+  pair_item<L, NP>(a, tb, chunk_tiles(a, ch), sm, ps);
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();  // this chunk's partials and near-list entries before the count

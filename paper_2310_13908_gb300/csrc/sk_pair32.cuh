@@ -345,6 +345,72 @@ __device__ __forceinline__ void two_sum_merge(float2* U, float2* HI, float2* LO)
   }
 }
 
+// per-thread target state: TGT_SLOTS float4 per f32x2 pair (see pair_smem_bytes)
+constexpr int TGT_SLOTS = 5;
+// A segment is wide for a target when its frame's half extent exceeds this
+// many of the target's delta (see pair_item's general branch).
+constexpr float WIDE_FRAME = 4.0f;
+
+// A lane's accumulators and target pairs, passed by value in and out of the
+// out-of-line exact loop below.
+template <int NP>
+struct LaneAcc {
+  float2 u[NP][3];
+};
+template <int NP>
+struct LaneTgt {
+  Tgt2 t[NP];
+};
+
+// The general loop over the 32 sources of one segment that is wide for some
+// target of the warp (L::kExactNear): pairs with rho_T <= rho < rho_c on a
+// target for which the segment is wide take the exact difference (the
+// target's frame-shift residual, recomputed from its (hi, lo) column ts, minus
+// the source's residual ylo[j]); every other pair computes what the inline
+// general loop computes, in the same order, so the accumulators come out bit
+// for bit as there. Out of line: its registers do not weigh on the pair loop,
+// and wide segments are rare on dense surfaces.
+template <class L, int NP>
+__device__ __noinline__ LaneAcc<NP> exact_segment(
+    LaneAcc<NP> acc, LaneTgt<NP> tg, const float4* SS, const float4* __restrict__ ylo,
+    const int* orig, const float4* ts, float sx, float sy, float sz, float hs, int64_t wbase,
+    int* near_cnt, int* near_idx, unsigned long long* flags, float rho_lo, float rho_hi) {
+  constexpr int V = L::V;
+#pragma unroll 1
+  for (int j = 0; j < SEG; ++j) {
+    const typename L::Src src = L::load(SS + j * V);
+    float2 dx[NP], dy[NP], dz[NP], r2[NP];
+    bool any = false;
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      pair_d(tg.t[p], src.nx, src.ny, src.nz, dx[p], dy[p], dz[p], r2[p]);
+      any |= (r2[p].x < tg.t[p].rc2.x) | (r2[p].y < tg.t[p].rc2.y);
+    }
+    if (__any_sync(FULL, any)) {
+      const float4 yl = ylo[j];
+#pragma unroll
+      for (int p = 0; p < NP; ++p) {
+        const float4 hx = ts[(p * TGT_SLOTS) * TPB32], hy = ts[(p * TGT_SLOTS + 1) * TPB32],
+                     hz = ts[(p * TGT_SLOTS + 2) * TPB32];
+        const float2 wd = make_float2(hs * tg.t[p].idl.x > WIDE_FRAME ? 1.f : 0.f,
+                                      hs * tg.t[p].idl.y > WIDE_FRAME ? 1.f : 0.f);
+        pair_general<L>(src, tg.t[p], dx[p], dy[p], dz[p], r2[p], acc.u[p], wbase + 64 * p,
+                        wbase + 64 * p + 32, orig + j, near_cnt, near_idx, flags, rho_lo, rho_hi,
+                        mul2(wd, sub2(shift_residual2(lo2(hx), hi2(hx), sx, tg.t[p].x),
+                                      make_float2(yl.x, yl.x))),
+                        mul2(wd, sub2(shift_residual2(lo2(hy), hi2(hy), sy, tg.t[p].y),
+                                      make_float2(yl.y, yl.y))),
+                        mul2(wd, sub2(shift_residual2(lo2(hz), hi2(hz), sz, tg.t[p].z),
+                                      make_float2(yl.z, yl.z))));
+      }
+    } else {
+#pragma unroll
+      for (int p = 0; p < NP; ++p) L::far(src, dx[p], dy[p], dz[p], r2[p], acc.u[p]);
+    }
+  }
+  return acc;
+}
+
 // Shared memory of a pair item: the source stages; the per-thread target
 // state (TGT_SLOTS float4 per f32x2 pair: (hi, lo) of x, y, z, then
 // (1/delta, rho_c^2 delta^2), (rho_T^2 delta^2, -)), read once per segment;
@@ -362,10 +428,7 @@ template <class L, int NP>
 __host__ __device__ constexpr int pair_stages() {
   return NP == 1 ? L::STAGES - 1 : L::STAGES;
 }
-constexpr int TGT_SLOTS = 5;
-// A segment is wide for a target when its frame's half extent exceeds this
-// many of the target's delta (see pair_item's general branch).
-constexpr float WIDE_FRAME = 4.0f;
+
 template <class L, int NP>
 constexpr size_t pair_smem_bytes() {
   return (size_t)pair_stages<L, NP>() * TILE * L::V * sizeof(float4) +
@@ -406,30 +469,54 @@ struct PairArgs {
 // the full tiles k0 .. k0 + n - 1 of the packed array; a list serves work
 // whose tiles are scattered (the FMM's neighbouring clusters and
 // equivalent sources).
+// out(a, t): where the item writes target t's partial. A list's item
+// writes its block's partials to slot * tb (t - t_sub indexes the block).
 struct TileList {
+  static constexpr bool kFull = false;  // tiles may have fewer than TILE_SEGS segments
   const int2* desc;
-  int k0, n;
+  int n;
+  int slot, tb;
+  int64_t t_sub;
+  __device__ __forceinline__ int2 tile(int it) const { return desc[it]; }
+  __device__ __forceinline__ size_t first_segment(int, int src0) const {
+    return (size_t)(src0 / SEG);
+  }
+  __device__ __forceinline__ double* out(const PairArgs& a, int64_t t) const {
+    return a.part + ((size_t)slot * tb + (size_t)(t - t_sub)) * 3;
+  }
+};
+// A contiguous range of full tiles k0 .. k0 + n - 1 of source chunk ch
+// (known to be full at compile time, so the direct evaluation's loops keep
+// their fixed shape); partials at [ch][M_pad][3].
+struct TileRange {
+  static constexpr bool kFull = true;
+  int k0, n, ch;
   __device__ __forceinline__ int2 tile(int it) const {
-    return desc ? desc[it] : make_int2((k0 + it) * TILE, TILE_SEGS);
+    return make_int2((k0 + it) * TILE, TILE_SEGS);
+  }
+  __device__ __forceinline__ size_t first_segment(int it, int) const {
+    return (size_t)(k0 + it) * TILE_SEGS;
+  }
+  __device__ __forceinline__ double* out(const PairArgs& a, int64_t t) const {
+    return a.part + ((size_t)ch * a.M_pad + t) * 3;
   }
 };
 
 // Tiles of source chunk ch of a direct evaluation: an even split of the
 // padded sources into a.n_chunks contiguous ranges.
-__device__ __forceinline__ TileList chunk_tiles(const PairArgs& a, int ch) {
+__device__ __forceinline__ TileRange chunk_tiles(const PairArgs& a, int ch) {
   const int n_tiles = a.meta[META_NS_PAD] / TILE;
   const int k0 = (int)((long long)ch * n_tiles / a.n_chunks);
   const int k1 = (int)((long long)(ch + 1) * n_tiles / a.n_chunks);
-  return TileList{nullptr, k0, k1 - k0};
+  return TileRange{k0, k1 - k0, ch};
 }
 
 // One work item: target block tb (TPB32 * 2 * NP sorted targets) against
 // the source tiles tl. Writes the block's partials (target t at
-// part + (t - t_sub) * 3); returns false if a bounded wait expired (the flag
-// is set, nothing is written).
-template <class L, int NP>
-__device__ __forceinline__ bool pair_item(const PairArgs& a, int tb, const TileList& tl,
-                                          double* __restrict__ part, int64_t t_sub, float4* sm,
+// tl.out(a, t)); returns false if a bounded wait expired (the flag is set,
+// nothing is written).
+template <class L, int NP, class TL>
+__device__ __forceinline__ bool pair_item(const PairArgs& a, int tb, const TL& tl, float4* sm,
                                           PipeSmem<pair_stages<L, NP>()>& ps) {
   constexpr int V = L::V;
   constexpr int STAGES = pair_stages<L, NP>();
@@ -541,14 +628,27 @@ __device__ __forceinline__ bool pair_item(const PairArgs& a, int tb, const TileL
   if (tid == 0) {
     for (int b = 0; b < STAGES; ++b)
       if (b < n_it) {
-        const int2 t = tl.tile(b);
-        bulk_load(sm + b * TILE * V, srcF + (size_t)t.x * V, t.y * SEG_BYTES, &full[b]);
+        if constexpr (TL::kFull) {
+          bulk_load(sm + b * TILE * V, srcF + (size_t)(tl.k0 + b) * TILE * V, TILE * V * 16u,
+                    &full[b]);
+        } else {
+          const int2 t = tl.tile(b);
+          bulk_load(sm + b * TILE * V, srcF + (size_t)t.x * V, t.y * SEG_BYTES, &full[b]);
+        }
         issued[b] = 1;
       }
   }
   for (int it = 0; it < n_it; ++it) {
-    const int2 tile = tl.tile(it);
-    const int src0 = tile.x, nseg = tile.y;  // first packed source, segments
+    // first packed source and segments of this tile
+    int src0, nseg;
+    if constexpr (TL::kFull) {
+      src0 = (tl.k0 + it) * TILE;
+      nseg = TILE_SEGS;
+    } else {
+      const int2 tile = tl.tile(it);
+      src0 = tile.x;
+      nseg = tile.y;
+    }
     const int buf = it % STAGES;
     const int use = it / STAGES;
     const bool ok = __all_sync(FULL, mbar_wait_bounded(&full[buf], (uint32_t)(use & 1)));
@@ -562,8 +662,9 @@ __device__ __forceinline__ bool pair_item(const PairArgs& a, int tb, const TileL
       float csx = 0.f, csy = 0.f, csz = 0.f;  // lane s < nseg: segment s's frame
       float chs = 0.f;                        // ... and the half extent of its box
       if (lane < nseg) {
-        const float4 lo = segbox[2 * ((size_t)(src0 / SEG) + lane)];
-        const float4 hi = segbox[2 * ((size_t)(src0 / SEG) + lane) + 1];
+        const size_t sg = tl.first_segment(it, src0);
+        const float4 lo = segbox[2 * (sg + lane)];
+        const float4 hi = segbox[2 * (sg + lane) + 1];
         const float dx = fmaxf(0.f, fmaxf(lo.x - bhi[0], blo[0] - hi.x));
         const float dy = fmaxf(0.f, fmaxf(lo.y - bhi[1], blo[1] - hi.y));
         const float dz = fmaxf(0.f, fmaxf(lo.z - bhi[2], blo[2] - hi.z));
@@ -644,50 +745,25 @@ __device__ __forceinline__ bool pair_item(const PairArgs& a, int tb, const TileL
               }
             }
           } else if constexpr (L::kExactNear) {
-            // the source's residual is read per source (a broadcast load), the
-            // targets' frame-shift residuals recomputed from the (hi, lo)
-            // column: nothing extra stays live across the loop
-            const float4* __restrict__ ylo = a.srcLo + (size_t)src0 + s * SEG;
-#pragma unroll 1
-            for (int j = 0; j < SEG; ++j) {
-              const typename L::Src src = L::load(SS + j * V);
-              float2 dx[NP], dy[NP], dz[NP], r2[NP];
-              bool any = false;
+            LaneAcc<NP> acc;
+            LaneTgt<NP> tg;
 #pragma unroll
-              for (int p = 0; p < NP; ++p) {
-                pair_d(T[p], src.nx, src.ny, src.nz, dx[p], dy[p], dz[p], r2[p]);
-                any |= (r2[p].x < T[p].rc2.x) | (r2[p].y < T[p].rc2.y);
-              }
-              if (__any_sync(FULL, any)) {
-                const float4 yl = ylo[j];
-                const float lx = yl.x, ly = yl.y, lz = yl.z;
+            for (int p = 0; p < NP; ++p) {
+              tg.t[p] = T[p];
 #pragma unroll
-                for (int p = 0; p < NP; ++p) {
-                  const float4 hx = ts[(p * TGT_SLOTS) * TPB32],
-                               hy = ts[(p * TGT_SLOTS + 1) * TPB32],
-                               hz = ts[(p * TGT_SLOTS + 2) * TPB32];
-                  const float2 wd = make_float2(hs * T[p].idl.x > WIDE_FRAME ? 1.f : 0.f,
-                                                hs * T[p].idl.y > WIDE_FRAME ? 1.f : 0.f);
-                  // residual of the pair (target's minus source's), zero where
-                  // the segment is not wide for that target
-                  pair_general<L>(src, T[p], dx[p], dy[p], dz[p], r2[p], U[p], wbase + 64 * p,
-                                  wbase + 64 * p + 32, orig + j, near_cnt, near_idx, flags,
-                                  rho_lo, rho_hi,
-                                  mul2(wd, sub2(shift_residual2(lo2(hx), hi2(hx), sx, T[p].x),
-                                                make_float2(lx, lx))),
-                                  mul2(wd, sub2(shift_residual2(lo2(hy), hi2(hy), sy, T[p].y),
-                                                make_float2(ly, ly))),
-                                  mul2(wd, sub2(shift_residual2(lo2(hz), hi2(hz), sz, T[p].z),
-                                                make_float2(lz, lz))));
-                }
-              } else {
-#pragma unroll
-                for (int p = 0; p < NP; ++p) L::far(src, dx[p], dy[p], dz[p], r2[p], U[p]);
-              }
+              for (int c = 0; c < 3; ++c) acc.u[p][c] = U[p][c];
             }
+            acc = exact_segment<L, NP>(acc, tg, SS, a.srcLo + (size_t)src0 + s * SEG,
+                                       orig, ts, sx, sy, sz, hs, wbase, near_cnt, near_idx,
+                                       flags, rho_lo, rho_hi);
+#pragma unroll
+            for (int p = 0; p < NP; ++p)
+#pragma unroll
+              for (int c = 0; c < 3; ++c) U[p][c] = acc.u[p][c];
           }
         }
-        if ((s & 3) == 3 || s == nseg - 1) {  // at most 128 sources in plain FP32
+        // at most 128 sources in plain FP32 (a full tile ends on a merge)
+        if ((s & 3) == 3 || (!TL::kFull && s == nseg - 1)) {
 #pragma unroll
           for (int p = 0; p < NP; ++p) {
             if constexpr (kHiLoSmem) {
@@ -717,8 +793,13 @@ __device__ __forceinline__ bool pair_item(const PairArgs& a, int tb, const TileL
       if (prev == (use + 1) * WARPS - 1 && it + STAGES < n_it) {
         __threadfence_block();
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        const int2 t = tl.tile(it + STAGES);
-        bulk_load(sm + buf * TILE * V, srcF + (size_t)t.x * V, t.y * SEG_BYTES, &full[buf]);
+        if constexpr (TL::kFull) {
+          bulk_load(sm + buf * TILE * V, srcF + (size_t)(tl.k0 + it + STAGES) * TILE * V,
+                    TILE * V * 16u, &full[buf]);
+        } else {
+          const int2 t = tl.tile(it + STAGES);
+          bulk_load(sm + buf * TILE * V, srcF + (size_t)t.x * V, t.y * SEG_BYTES, &full[buf]);
+        }
         atomicAdd(&issued[buf], 1);
       }
     }
@@ -738,7 +819,7 @@ __device__ __forceinline__ bool pair_item(const PairArgs& a, int tb, const TileL
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int64_t t = wbase + 64 * p + 32 * h;
-      double* o = part + (size_t)(t - t_sub) * 3;
+      double* o = tl.out(a, t);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const float2 H2 = kHiLoSmem ? acc[((p * 3 + c) * 2) * TPB32 + tid] : HI[p][c];
