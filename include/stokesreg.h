@@ -389,6 +389,22 @@ typedef struct {
   const double* delta;
   int64_t n_delta;
   double mu;
+  /* A capsule request when capsule != NULL (the fields above are then
+   * ignored): the server advances this resident capsule (capsule_create on
+   * the server's context, SK_FP32C, not upsampled) by n_steps explicit Euler
+   * steps of dt (Sec. 3.6, Eq. bi_combined) under the background flow (kind
+   * SK_FLOW_NONE for none). Each step takes the Skalak force and weights at
+   * the current nodes when the capsule has a membrane (capsule_set_membrane),
+   * else its current f, and delta* when the capsule's delta is automatic, as
+   * capsule_step does; each step's sum is served beside the other requests.
+   * The capsule's state stays in device memory across requests; the result
+   * (serve_poll's u_out) is its nodes [N][3] after the last step. One request
+   * per capsule at a time (SK_EBUSY otherwise); do not step or destroy the
+   * capsule while its request is pending. */
+  sk_capsule* capsule;
+  int32_t n_steps;
+  double dt;
+  sk_flow flow;
 } sk_request;
 
 typedef struct {

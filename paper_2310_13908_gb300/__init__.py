@@ -469,10 +469,13 @@ class sk_serve_cfg(ctypes.Structure):
 
 
 class sk_request(ctypes.Structure):
-    """sk_request of stokesreg.h: one single-layer request (host arrays)."""
+    """sk_request of stokesreg.h: one single-layer request (host arrays), or
+    Euler steps of a resident capsule (capsule != NULL)."""
     _fields_ = [("n_src", ctypes.c_int64), ("src_xyz", _vp), ("src_w", _vp), ("f", _vp),
                 ("n_tgt", ctypes.c_int64), ("tgt_xyz", _vp), ("delta", _vp),
-                ("n_delta", ctypes.c_int64), ("mu", ctypes.c_double)]
+                ("n_delta", ctypes.c_int64), ("mu", ctypes.c_double),
+                ("capsule", _vp), ("n_steps", ctypes.c_int32), ("dt", ctypes.c_double),
+                ("flow", sk_flow)]
 
 
 class sk_req_stats(ctypes.Structure):
@@ -507,6 +510,24 @@ def serve_submit(srv, src_xyz, src_w, f, tgt_xyz, delta, mu: float = 1.0) -> int
     code = load().serve_submit(srv, ctypes.byref(req), ctypes.byref(t))
     if code != SK_OK:
         raise SkError(code, "serve_submit")
+    return t.value
+
+
+def serve_submit_capsule(srv, capsule, n_steps: int, dt: float, flow=None) -> int:
+    """Queue n_steps explicit Euler steps of a resident capsule (a Capsule of
+    the server's context); serve_poll(srv, ticket, capsule.N) returns its
+    nodes after the steps. Raises SkError (SK_EBUSY: the capsule or the queue
+    is busy)."""
+    req = sk_request()
+    req.capsule = capsule.handle
+    req.n_steps = int(n_steps)
+    req.dt = float(dt)
+    if flow is not None:
+        req.flow = sk_flow(*flow)
+    t = ctypes.c_uint64()
+    code = load().serve_submit(srv, ctypes.byref(req), ctypes.byref(t))
+    if code != SK_OK:
+        raise SkError(code, "serve_submit (capsule)")
     return t.value
 
 

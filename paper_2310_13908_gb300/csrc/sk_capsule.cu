@@ -10,6 +10,7 @@
 // the update X += dt (S[f](X) + u_inf(X)). The step is captured once into a
 // CUDA graph and replayed n_steps times, so a step costs one graph launch on
 // the host.
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -60,6 +61,8 @@ struct sk_capsule {
   char* g_ws = nullptr;
   size_t g_ws_bytes = 0;
   double g_rho_T = 0.0, g_rho_c = 0.0;
+  // held by a served request (serve_submit with this capsule) until it completes
+  std::atomic<bool> served{false};
 };
 
 namespace sk {
@@ -257,6 +260,54 @@ void enqueue_velocity(sk_capsule* c, const double* P, int mode, const EvalShape&
   enqueue_eval(s, b, ctx->rho_T, ctx->rho_c, st);
   k_sticky<<<1, 32, 0, st>>>(b.flags, c->sticky);
 }
+
+}  // namespace
+
+// ---- steps run by the server (sk_serve.cu) ----------------------------------
+bool capsule_try_acquire(sk_capsule* c) {
+  bool expect = false;
+  return c->served.compare_exchange_strong(expect, true);
+}
+void capsule_release(sk_capsule* c) { c->served = false; }
+sk_ctx* capsule_ctx(const sk_capsule* c) { return c->ctx; }
+bool capsule_servable(const sk_capsule* c) { return c->precision == SK_FP32C && c->up == 1; }
+int64_t capsule_node_count(const sk_capsule* c) { return c->N; }
+EvalShape capsule_step_shape(const sk_capsule* c) { return capsule_shape(c); }
+const double* capsule_nodes(const sk_capsule* c) { return c->X; }
+const unsigned long long* capsule_sticky(const sk_capsule* c) { return c->sticky; }
+
+// The inputs of one step's single layer, enqueued on st: with a membrane the
+// weights psi W h^2 and the Skalak force at the current nodes (else the
+// capsule's f), delta* when it is automatic; b's inputs and output are
+// pointed at the capsule's arrays. The same operations as a capsule_step.
+void capsule_enqueue_step_inputs(sk_capsule* c, EvalBufs& b, cudaStream_t st) {
+  if (c->mop) enqueue_skalak(*c->mop, c->X, c->ref6, c->Es, c->ED, c->f, c->w, st);
+  if (c->auto_delta) {
+    cudaMemsetAsync(c->patch_max, 0, 8 * sizeof(unsigned long long), st);
+    k_delta_star_patch<<<blocks(c->N), 256, 0, st>>>(c->X, c->m, c->patch_max);
+    k_delta_fill<<<blocks(c->N), 256, 0, st>>>(c->patch_max, c->m, 1.0, c->delta);
+  }
+  b.src_xyz = c->X;
+  b.src_w = c->w;
+  b.dens = c->f;
+  b.delta = c->delta;
+  b.tgt_xyz = c->X;
+  b.u = c->u;
+}
+
+// After a step's sum: its flags into the capsule's sticky flags, and the
+// Euler update X += dt (u + u_inf(X)).
+void capsule_enqueue_step_update(sk_capsule* c, const unsigned long long* flags, double dt,
+                                 const sk_flow& fl, cudaStream_t st) {
+  k_sticky<<<1, 32, 0, st>>>(flags, c->sticky);
+  k_euler<<<blocks(c->N), 256, 0, st>>>(c->X, c->u, c->N, dt, fl);
+}
+
+void capsule_clear_sticky(sk_capsule* c, cudaStream_t st) {
+  cudaMemsetAsync(c->sticky, 0, N_FLAGS * sizeof(unsigned long long), st);
+}
+
+namespace {
 
 void free_capsule(sk_capsule* c) {
   if (c->exec) cudaGraphExecDestroy(c->exec);

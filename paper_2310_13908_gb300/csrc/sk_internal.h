@@ -292,6 +292,22 @@ int eval_call(sk_ctx* ctx, int layer, int precision, int mem, int64_t N, const d
               const double* txyz, const double* delta, int64_t n_delta, double mu,
               double* u_out, void* stream);
 
+// sk_capsule.cu: capsule steps run by the server. A served request holds
+// the capsule (try_acquire) until it completes; each step enqueues its sum's
+// inputs (membrane force, weights, delta*), the sum, then the update.
+bool capsule_try_acquire(sk_capsule* c);
+void capsule_release(sk_capsule* c);
+sk_ctx* capsule_ctx(const sk_capsule* c);
+bool capsule_servable(const sk_capsule* c);  // SK_FP32C, no upsampling
+int64_t capsule_node_count(const sk_capsule* c);
+EvalShape capsule_step_shape(const sk_capsule* c);
+const double* capsule_nodes(const sk_capsule* c);
+const unsigned long long* capsule_sticky(const sk_capsule* c);
+void capsule_enqueue_step_inputs(sk_capsule* c, EvalBufs& b, cudaStream_t st);
+void capsule_enqueue_step_update(sk_capsule* c, const unsigned long long* flags, double dt,
+                                 const sk_flow& fl, cudaStream_t st);
+void capsule_clear_sticky(sk_capsule* c, cudaStream_t st);
+
 // sk_fmm.cu: single-level FMM operators (cached per p in ctx)
 void free_fmm_ops(sk_ctx* ctx);
 

@@ -170,8 +170,7 @@ __global__ void __launch_bounds__(TPB32, SERVE_MINB)
     __syncthreads();
     const int item = s_item;
     const int tb = item / d.n_chunks, ch = item % d.n_chunks;
-    pair_item<SLayer, SERVE_NP>(d.pa, tb, chunk_tiles(d.pa, ch), d.pa.part + (size_t)ch * d.pa.M_pad * 3,
-                                0, sm, ps);  // a timeout sets the request's flag
+    pair_item<SLayer, SERVE_NP>(d.pa, tb, chunk_tiles(d.pa, ch), sm, ps);  // a timeout sets the request's flag
     __syncthreads();
     if (tid == 0) {
       __threadfence();
@@ -212,6 +211,11 @@ struct Req {
   int status = SK_EAGAIN;
   sk_req_stats st{};
   unsigned long long flags[N_FLAGS] = {};
+  // capsule request: Euler steps of a resident capsule
+  sk_capsule* cap = nullptr;
+  int steps = 0, steps_done = 0;
+  double dt = 0.0;
+  sk_flow flow{};
 };
 
 enum class SlotState { Free, Prep, Running, Copying };
@@ -223,7 +227,7 @@ struct Slot {
   EvalBufs b;
   int* tb_counters = nullptr;  // [n_tb + 1]
   unsigned seq = 0;
-  cudaEvent_t prep_done = nullptr, copy_done = nullptr;
+  cudaEvent_t prep_done = nullptr, copy_done = nullptr, update_done = nullptr;
   // pinned per-slot block (PIN_WORDS words): [0, 8) device flags, [8, 12)
   // meta ints, [12] claim word, [16, ...) descriptor being published
   unsigned long long* h_flags = nullptr;
@@ -309,6 +313,25 @@ void launch_kernel(sk_server* srv) {
   srv->kernel_launched = true;
 }
 
+// Capsule steps prepare on the context's stream: the membrane operator's
+// scratch is shared by every capsule of a grid order on the context, so its
+// uses (served steps of several capsules, and the caller's own capsule_step
+// or membrane_force calls) must follow one another.
+cudaStream_t capsule_stream(sk_server* srv) { return srv->ctx->stream; }
+
+// One step of a capsule request, on st: the inputs of its sum (membrane
+// force, weights, delta* at the current nodes), cleared counters and the
+// preparation kernels; the step's items are published when st reaches
+// prep_done.
+void enqueue_capsule_step(sk_server* srv, Slot& sl, cudaStream_t st) {
+  Req* r = sl.req;
+  capsule_enqueue_step_inputs(r->cap, sl.b, st);
+  const int n_tb = (int)(sl.b.M_pad / SERVE_TGT_CTA);
+  cudaMemsetAsync(sl.tb_counters, 0, (n_tb + 1) * sizeof(int), st);
+  enqueue_prep(r->shape, sl.b, srv->ctx->rho_T, srv->ctx->rho_c, st);
+  cudaEventRecord(sl.prep_done, st);
+}
+
 // Admit: bind a queued request to a free slot and its arena block, enqueue
 // the H2D copy and the preparation kernels.
 bool admit_one(sk_server* srv, Req* r, Slot& sl, int slot) {
@@ -328,6 +351,13 @@ bool admit_one(sk_server* srv, Req* r, Slot& sl, int slot) {
   sl.tb_counters = bp.take<int>(n_tb + 1);
   const EvalShape& s = r->shape;
   cudaStream_t st = srv->s_prep[slot % SERVE_PREP_STREAMS];
+  if (r->cap) {  // the first step of a capsule request: its inputs are resident
+    st = capsule_stream(srv);
+    capsule_clear_sticky(r->cap, st);
+    enqueue_capsule_step(srv, sl, st);
+    r->st.admit_us = now_us(srv);
+    return true;
+  }
   if (s.N > 0) {
     cudaMemcpyAsync((void*)b.src_xyz, r->h_xyz, 3 * s.N * sizeof(double), cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync((void*)b.src_w, r->h_w, s.N * sizeof(double), cudaMemcpyHostToDevice, st);
@@ -406,7 +436,35 @@ void scheduler(sk_server* srv) {
       }
       if (sl.state == SlotState::Running) {
         any_running = true;
-        if (*(volatile unsigned*)&srv->h_done[i] == sl.seq) {
+        if (*(volatile unsigned*)&srv->h_done[i] == sl.seq && sl.req->cap) {
+          // a capsule step's sum is done: update the nodes, then the next
+          // step, or read the nodes back after the last one
+          Req* r = sl.req;
+          cudaStream_t st = capsule_stream(srv);
+          capsule_enqueue_step_update(r->cap, sl.b.flags, r->dt, r->flow, st);
+          if (++r->steps_done < r->steps) {
+            {
+              std::unique_lock<std::mutex> lk(srv->mu);
+              sl.seq = srv->next_seq++;
+            }
+            enqueue_capsule_step(srv, sl, st);
+            sl.state = SlotState::Prep;
+          } else {
+            r->st.done_us = now_us(srv);
+            cudaEventRecord(sl.update_done, st);
+            cudaStreamWaitEvent(srv->s_copy, sl.update_done, 0);
+            cudaMemcpyAsync(r->h_u, capsule_nodes(r->cap), 3 * r->shape.M * sizeof(double),
+                            cudaMemcpyDeviceToHost, srv->s_copy);
+            cudaMemcpyAsync(sl.h_flags, capsule_sticky(r->cap),
+                            N_FLAGS * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                            srv->s_copy);
+            cudaMemcpyAsync(sl.h_flags + PIN_META, sl.b.meta, N_META * sizeof(int),
+                            cudaMemcpyDeviceToHost, srv->s_copy);
+            cudaEventRecord(sl.copy_done, srv->s_copy);
+            sl.state = SlotState::Copying;
+          }
+          progress = true;
+        } else if (*(volatile unsigned*)&srv->h_done[i] == sl.seq) {
           Req* r = sl.req;
           r->st.done_us = now_us(srv);
           cudaMemcpyAsync(r->h_u, sl.b.u, 3 * r->shape.M * sizeof(double), cudaMemcpyDeviceToHost,
@@ -429,6 +487,7 @@ void scheduler(sk_server* srv) {
                     : r->flags[FLAG_BAD_DELTA] ? SK_EINVAL : SK_OK;
         r->st.status = r->status;
         r->st.ready_us = now_us(srv);
+        if (r->cap) capsule_release(r->cap);
         srv->arena_alloc.release(sl.arena_off, sl.arena_len);
         sl.state = SlotState::Free;
         sl.req = nullptr;
@@ -478,13 +537,17 @@ void free_server(sk_server* srv) {
   for (auto& sl : srv->slots) {
     if (sl.prep_done) cudaEventDestroy(sl.prep_done);
     if (sl.copy_done) cudaEventDestroy(sl.copy_done);
+    if (sl.update_done) cudaEventDestroy(sl.update_done);
   }
   if (srv->kernel_done) cudaEventDestroy(srv->kernel_done);
   for (cudaStream_t s : {srv->s_kernel, srv->s_ctl, srv->s_copy})
     if (s) cudaStreamDestroy(s);
   for (cudaStream_t s : srv->s_prep)
     if (s) cudaStreamDestroy(s);
-  for (auto& kv : srv->reqs) delete kv.second;
+  for (auto& kv : srv->reqs) {
+    if (kv.second->cap) capsule_release(kv.second->cap);
+    delete kv.second;
+  }
   delete srv;
 }
 
@@ -548,6 +611,7 @@ int serve_create(sk_ctx* ctx, const sk_serve_cfg* cfg_in, sk_server** out) {
   for (auto& sl : srv->slots) {
     ok(cudaEventCreateWithFlags(&sl.prep_done, cudaEventDisableTiming));
     ok(cudaEventCreateWithFlags(&sl.copy_done, cudaEventDisableTiming));
+    ok(cudaEventCreateWithFlags(&sl.update_done, cudaEventDisableTiming));
   }
   if (e == cudaSuccess) {
     ok(cudaHostGetDevicePointer((void**)&srv->d_done, srv->h_done, 0));
@@ -575,9 +639,60 @@ int serve_create(sk_ctx* ctx, const sk_serve_cfg* cfg_in, sk_server** out) {
   return SK_OK;
 }
 
+namespace {
+
+// A capsule request: n_steps Euler steps of a resident capsule; the result
+// is its nodes after the last step.
+int submit_capsule(sk_server* srv, const sk_request* q, uint64_t* ticket) {
+  sk_capsule* c = q->capsule;
+  if (capsule_ctx(c) != srv->ctx || !capsule_servable(c) || q->n_steps < 1 ||
+      !(q->dt > 0.0 && q->dt < INFINITY) || q->flow.kind < SK_FLOW_NONE ||
+      q->flow.kind > SK_FLOW_POISEUILLE)
+    return SK_EINVAL;
+  Req* r = new (std::nothrow) Req();
+  if (!r) return SK_ENOMEM;
+  r->cap = c;
+  r->steps = q->n_steps;
+  r->dt = q->dt;
+  r->flow = q->flow;
+  r->shape = capsule_step_shape(c);
+  const int64_t M = r->shape.M;
+  const int n_tb = (int)(align_up((size_t)M, TGT_CTA32) / SERVE_TGT_CTA);
+  r->footprint = request_footprint(r->shape, n_tb);
+  const size_t bytes = 3 * (size_t)M * sizeof(double) + 256;
+  if (r->footprint > srv->arena_bytes || bytes > srv->stage_bytes) {
+    delete r;
+    return SK_ENOMEM;
+  }
+  std::unique_lock<std::mutex> lk(srv->mu);
+  if ((int)srv->queue.size() >= srv->cfg.queue_capacity ||
+      !srv->stage_alloc.alloc(bytes, &r->stage_off)) {
+    delete r;
+    return SK_EBUSY;
+  }
+  if (!capsule_try_acquire(c)) {  // one request per capsule at a time
+    srv->stage_alloc.release(r->stage_off, bytes);
+    delete r;
+    return SK_EBUSY;
+  }
+  r->stage_len = bytes;
+  r->h_u = reinterpret_cast<double*>(srv->stage + r->stage_off);
+  r->ticket = srv->next_ticket++;
+  r->st.submit_us = now_us(srv);
+  r->st.n_chunks = r->shape.n_chunks;
+  srv->reqs[r->ticket] = r;
+  srv->queue.push_back(r);
+  *ticket = r->ticket;
+  srv->cv_work.notify_one();
+  return SK_OK;
+}
+
+}  // namespace
+
 int serve_submit(sk_server* srv, const sk_request* q, uint64_t* ticket) {
   if (!srv || !q || !ticket) return SK_EINVAL;
   if (srv->failed) return SK_ECUDA;
+  if (q->capsule) return submit_capsule(srv, q, ticket);
   const int64_t N = q->n_src, M = q->n_tgt;
   if (N < 0 || M < 1 || N > (int64_t(1) << 30) || M > (int64_t(1) << 30)) return SK_EINVAL;
   if (N > 0 && (!q->src_xyz || !q->src_w || !q->f)) return SK_EINVAL;
@@ -666,7 +781,7 @@ int serve_poll(sk_server* srv, uint64_t ticket, double* u_out, sk_req_stats* st,
   if (status == SK_OK && u_out) std::memcpy(u_out, r->h_u, 3 * r->shape.M * sizeof(double));
   if (st) {
     *st = r->st;
-    st->interactions = r->shape.M * r->n_active;
+    st->interactions = r->shape.M * r->n_active * (r->cap ? r->steps : 1);
   }
   srv->stage_alloc.release(r->stage_off, r->stage_len);
   srv->reqs.erase(it);

@@ -201,3 +201,121 @@ def test_destroy_drains_pending_requests(ctx):
     sk.serve_destroy(srv)  # must finish the work and return
     srv = sk.serve_create(ctx)  # the context can serve again
     sk.serve_destroy(srv)
+
+
+# ---- resident capsules -------------------------------------------------------
+ES, ED = 2.0, 20.0
+
+
+def make_capsule(ctx, m=17, stretch=(1.04, 0.98, 1.0)):
+    """A capsule with a Skalak membrane on the stress-free ellipsoid
+    (0.9, 1, 1), started from a stretched shape; delta* per step."""
+    ref = ci.make_surface(ci.Ellipsoid(0.9, 1.0, 1.0), m)
+    cap = sk.Capsule(ctx, m, ref.X * np.array(stretch), ref.w, delta=None, mu=1.0,
+                     precision=sk.SK_FP32C)
+    cap.set_membrane(ref.X, ES, ED)
+    return cap
+
+
+def submit_capsule_retry(srv, cap, n, dt, flow, tries=2000):
+    for _ in range(tries):
+        try:
+            return sk.serve_submit_capsule(srv, cap, n, dt, flow)
+        except sk.SkError as e:
+            if e.code != sk.SK_EBUSY:
+                raise
+            time.sleep(0.001)
+    raise TimeoutError("server stayed busy")
+
+
+def test_served_capsule_steps_equal_capsule_step_bitwise(ctx):
+    """n Euler steps of a resident capsule served through the persistent
+    kernel leave the nodes bit for bit where capsule_step leaves an identical
+    capsule: each step's membrane force, weights, delta* and update are the
+    same operations, and each step's sum is the standalone one. The capsule's
+    state stays on the device across two requests."""
+    flow = (sk.SK_FLOW_SHEAR, 1.0, 0.0, 0.0)
+    a, b = make_capsule(ctx), make_capsule(ctx)
+    srv = sk.serve_create(ctx, max_slots=4)
+    try:
+        a.step(4, 1e-3, None, flow)
+        a.step(3, 1e-3, None, flow)
+        t = submit_capsule_retry(srv, b, 4, 1e-3, flow)
+        code, x4, st = sk.serve_poll(srv, t, b.N, timeout_us=60_000_000)
+        assert code == sk.SK_OK
+        assert st["interactions"] == 4 * b.N * np.count_nonzero(make_surface_w(17))
+        t = submit_capsule_retry(srv, b, 3, 1e-3, flow)
+        code, x7, _ = sk.serve_poll(srv, t, b.N, timeout_us=60_000_000)
+        assert code == sk.SK_OK
+    finally:
+        sk.serve_destroy(srv)
+    assert np.array_equal(x7, a.positions())
+    assert np.array_equal(x7, b.positions())
+    assert not np.array_equal(x4, x7)
+    a.close()
+    b.close()
+
+
+def make_surface_w(m):
+    return ci.make_surface(ci.Ellipsoid(0.9, 1.0, 1.0), m).w
+
+
+def test_shear_rate_sweep_in_the_mix(ctx):
+    """A parameter sweep: capsules at four shear rates and a Poiseuille flow,
+    each a multi-step request, served together with ordinary single-layer
+    requests; every capsule ends where capsule_step takes its twin, and every
+    ordinary request equals its standalone result, bit for bit."""
+    flows = [(sk.SK_FLOW_SHEAR, r, 0.0, 0.0) for r in (0.5, 1.0, 2.0, 4.0)] + \
+            [(sk.SK_FLOW_POISEUILLE, 0.0, 1.0, 5.0)]
+    twins = [make_capsule(ctx, m=13 + 4 * (i % 2)) for i in range(len(flows))]
+    served = [make_capsule(ctx, m=13 + 4 * (i % 2)) for i in range(len(flows))]
+    for cap, fl in zip(twins, flows):
+        cap.step(5, 1e-3, None, fl)
+    reqs = mixed_requests(10, seed=47)
+    refs = [sk.stokes_sl_eval(ctx, sk.SK_FP32C, sk.SK_HOST, *r) for r in reqs]
+    srv = sk.serve_create(ctx, max_slots=8)
+    try:
+        tickets = []
+        for i in range(max(len(flows), len(reqs))):
+            if i < len(flows):
+                tickets.append(("cap", i, submit_capsule_retry(srv, served[i], 5, 1e-3, flows[i])))
+            if i < len(reqs):
+                tickets.append(("req", i, submit_retry(srv, *reqs[i])))
+        for kind, i, t in tickets:
+            n = served[i].N if kind == "cap" else reqs[i][3].shape[0]
+            code, u, _ = sk.serve_poll(srv, t, n, timeout_us=60_000_000)
+            assert code == sk.SK_OK
+            if kind == "cap":
+                assert np.array_equal(u, twins[i].positions()), i
+            else:
+                assert np.array_equal(u, refs[i]), i
+    finally:
+        sk.serve_destroy(srv)
+    for c in twins + served:
+        c.close()
+
+
+def test_capsule_request_errors(ctx):
+    cap = make_capsule(ctx, m=9)
+    fp64 = sk.Capsule(ctx, 9, ci.make_surface(ci.Sphere(1.0), 9).X,
+                      ci.make_surface(ci.Sphere(1.0), 9).w, precision=sk.SK_FP64)
+    srv = sk.serve_create(ctx, max_slots=2)
+    try:
+        with pytest.raises(sk.SkError) as e:
+            sk.serve_submit_capsule(srv, fp64, 1, 1e-3)
+        assert e.value.code == sk.SK_EINVAL
+        with pytest.raises(sk.SkError) as e:
+            sk.serve_submit_capsule(srv, cap, 0, 1e-3)
+        assert e.value.code == sk.SK_EINVAL
+        t = sk.serve_submit_capsule(srv, cap, 50, 1e-3)
+        with pytest.raises(sk.SkError) as e:   # one request per capsule at a time
+            sk.serve_submit_capsule(srv, cap, 1, 1e-3)
+        assert e.value.code == sk.SK_EBUSY
+        code, _, _ = sk.serve_poll(srv, t, cap.N, timeout_us=60_000_000)
+        assert code == sk.SK_OK
+        t = sk.serve_submit_capsule(srv, cap, 1, 1e-3)   # free again
+        assert sk.serve_poll(srv, t, cap.N, timeout_us=60_000_000)[0] == sk.SK_OK
+    finally:
+        sk.serve_destroy(srv)
+    cap.close()
+    fp64.close()
