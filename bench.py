@@ -65,6 +65,11 @@ def parse_args():
                     help="timed step: single layer (default) or double layer (q = the SH "
                          "density); extras run only for the default sl/fp32c step")
     ap.add_argument("--precision", choices=["fp32c", "fp64"], default="fp32c")
+    ap.add_argument("--fmm-only", action="store_true",
+                    help="time only the single-level FMM (SK_FP32C, k = --fmm-k clusters, p = 6) "
+                         "on the ellipsoid (1, 0.8, 0.5) nodes of grid order --m, delta = 2h, "
+                         "and print that line")
+    ap.add_argument("--fmm-k", type=int, default=64)
     ap.add_argument("--membrane-only", action="store_true",
                     help="time only the Skalak membrane force on the stress-free ellipsoid "
                          "(0.9, 1, 1) of grid order --m, and print that line")
@@ -262,6 +267,8 @@ def main():
         return run_reference(args)
     if args.membrane_only:
         return membrane_only(args)
+    if args.fmm_only:
+        return fmm_only(args)
     rank, world, local = dist_env()
     import torch
     import paper_2310_13908_gb300 as sk
@@ -565,6 +572,109 @@ def serving_bench(sk, h, reqs):
                                "ginter_per_s": inter / wall / 1e9, "wall_s": wall,
                                "mean_phase_ms": run_serving.last_phases_ms}
     return res
+
+
+def capsule_sweep_bench(sk, h, m=33, rates=(0.25, 0.5, 1.0, 2.0, 4.0, 8.0, 0.5, 1.0), steps=20,
+                        dt=1e-3, Es=2.0, ED=20.0):
+    """A shear-rate sweep of resident capsules served together: each request
+    advances its capsule (stretched ellipsoid (0.9, 1, 1) with a Skalak
+    membrane, delta* per step) by `steps` Euler steps; all are submitted at
+    once. Against the same steps taken one capsule after another with
+    capsule_step. The results agree bit for bit (checked here)."""
+    import capsule_inputs as ci
+    ref = ci.make_surface(ci.Ellipsoid(0.9, 1.0, 1.0), m)
+
+    def make():
+        cap = sk.Capsule(h, m, ref.X * np.array([1.04, 0.98, 1.0]), ref.w, delta=None, mu=1.0,
+                         precision=sk.SK_FP32C)
+        cap.set_membrane(ref.X, Es, ED)
+        return cap
+
+    flows = [(sk.SK_FLOW_SHEAR, r, 0.0, 0.0) for r in rates]
+    seq = [make() for _ in flows]
+    served = [make() for _ in flows]
+    try:
+        for cap, fl in zip(seq, flows):  # warm-up (captures the step graphs)
+            cap.step(1, dt, None, fl)
+        seq2 = [make() for _ in flows]
+        t0 = time.perf_counter()
+        for cap, fl in zip(seq2, flows):
+            cap.step(steps, dt, None, fl)
+        t_seq = time.perf_counter() - t0
+        srv = sk.serve_create(h, max_slots=len(flows))
+        try:
+            warm = make()  # warm-up request
+            w = sk.serve_submit_capsule(srv, warm, 2, dt, flows[0])
+            sk.serve_poll(srv, w, warm.N, timeout_us=60_000_000)
+            warm.close()
+            t0 = time.perf_counter()
+            tickets = [sk.serve_submit_capsule(srv, c, steps, dt, fl)
+                       for c, fl in zip(served, flows)]
+            lat, same = [], True
+            for t, c, twin in zip(tickets, served, seq2):
+                code, x, st = sk.serve_poll(srv, t, c.N, timeout_us=120_000_000)
+                lat.append((st["ready_us"] - st["submit_us"]) * 1e-3)
+                same &= code == sk.SK_OK and np.array_equal(x, twin.positions())
+            t_srv = time.perf_counter() - t0
+        finally:
+            sk.serve_destroy(srv)
+        inter = len(flows) * steps * ref.N * np.count_nonzero(ref.w)
+        for c in seq2:
+            c.close()
+        return {"workload": f"{len(flows)} capsules m={m} (N={ref.N}), shear rates {list(rates)}, "
+                            f"{steps} Euler steps each, dt={dt}, Skalak Es={Es} ED={ED}",
+                "served_wall_s": t_srv, "served_ginter_per_s": inter / t_srv / 1e9,
+                "served_p50_ms": float(np.percentile(lat, 50)),
+                "served_max_ms": float(np.max(lat)),
+                "one_after_another_wall_s": t_seq,
+                "one_after_another_ginter_per_s": inter / t_seq / 1e9,
+                "bitwise_equal_to_capsule_step": bool(same)}
+    finally:
+        for c in seq + served:
+            c.close()
+
+
+def fmm_only(args, iters=10, p=6):
+    """stokes_sl_eval_fmm(SK_FP32C) on the ellipsoid (1, 0.8, 0.5) nodes of
+    order args.m (sources and targets), delta = 2h, k = args.fmm_k clusters
+    seeded from every (N_s / k)-th active node: args.warmup untimed calls,
+    then args.steps calls timed with CUDA events; one JSON line."""
+    import torch
+    import capsule_inputs as ci
+    import paper_2310_13908_gb300 as sk
+    dev = torch.device("cuda", 0)
+    s = ci.make_surface(ci.Ellipsoid(1.0, 0.8, 0.5), args.m)
+    f = ci.sh_density(s.x0, np.random.default_rng(5), lmax=8)
+
+    def td(a):
+        return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)
+
+    X, W, F, D = td(s.X), td(s.w), td(f), td(np.array([2 * s.h]))
+    act = np.flatnonzero(s.w)
+    k = args.fmm_k
+    C0 = td(s.X[act[:: len(act) // k][:k]])
+    with sk.Context(0) as c:
+        def call():
+            return sk.stokes_sl_eval_fmm(c.handle, sk.SK_DEVICE, X, W, F, X, D, 1.0, C0, iters,
+                                         p, precision=sk.SK_FP32C)
+        for _ in range(max(args.warmup, 1)):
+            call()
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(args.steps):
+            call()
+        b.record()
+        torch.cuda.synchronize(dev)
+    inter = s.N * len(act)
+    ms = a.elapsed_time(b) / args.steps
+    print(json.dumps({"metric": METRIC, "value": inter / (ms * 1e-3) / 1e9, "unit": UNIT,
+                      "ms_per_step": ms, "higher_is_better": True,
+                      "config": {"workload": f"ellipsoid(1,0.8,0.5) m={args.m} nodes (N={s.N}, "
+                                             f"N_s={len(act)}), delta=2h, single-level FMM "
+                                             f"SK_FP32C, k={k}, p={p}, {iters} Lloyd steps"}}),
+          flush=True)
+    return 0
 
 
 def membrane_only(args, Es=2.0, ED=20.0, reps=10):
@@ -947,6 +1057,10 @@ def extras(sk, h, w, X, W, F, Y, D, out, u_fp32, stream, dev, torch, serve_futur
             res["serving"] = serving_bench(sk, h, serve_future.result())
         except Exception as e:  # report, but keep the headline line
             res["serving"] = {"error": repr(e)}
+    try:
+        res["serving_capsule_sweep"] = capsule_sweep_bench(sk, h)
+    except Exception as e:
+        res["serving_capsule_sweep"] = {"error": repr(e)}
     return res
 
 
