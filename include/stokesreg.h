@@ -99,7 +99,8 @@ typedef struct {
   int64_t n_src_active;      /* sources with w != 0 (the N_s of the interaction count) */
   int64_t n_tgt;             /* targets */
   int64_t near_pairs;        /* pairs evaluated in FP64 by series (SK_FP32C) */
-  int64_t overflow_targets;  /* targets whose near pairs exceeded the list and were rescanned */
+  int64_t overflow_targets;  /* targets rescanned because their group's near-pair list
+                                overflowed (a group: the 64 or 128 targets of one warp) */
   int64_t kernel_launches;   /* CUDA kernels the evaluation launched */
   int32_t n_chunks;          /* source chunks per target block (split of the source sum) */
   int32_t precision;         /* SK_FP64 or SK_FP32C */
@@ -138,7 +139,8 @@ int sk_probe_peaks(sk_ctx* ctx, sk_peaks* out);
 int sk_set_profiling(sk_ctx* ctx, int enable);
 
 /* Regularized single layer (Sec. 3.4, Eq. regstokes; Sec. 3.3, Eq. smoothint).
- *   n_src    number of quadrature nodes N (>= 0)
+ *   n_src    number of quadrature nodes N (>= 0; at most 2^30, and at most 2^25
+ *            in SK_FP32C, whose near-pair lists hold source indices in 25 bits)
  *   src_xyz  [n_src][3] node positions y
  *   src_w    [n_src]    quadrature weights w = psi W h^2 (zero weights allowed)
  *   f        [n_src][3] density (traction) f at the nodes
@@ -207,7 +209,8 @@ typedef struct {
  *          (largest distance from a node to its grid neighbours on its patch,
  *          per patch, Eq. regparam with C = 1); otherwise [n_delta] fixed
  *          values, n_delta in {1, N}
- *   mu     viscosity > 0; precision SK_FP64 or SK_FP32C.
+ *   mu     viscosity > 0; precision SK_FP64 or SK_FP32C (SK_FP32C: at most
+ *          2^25 nodes, as for stokes_sl_eval).
  * Errors: SK_EINVAL, SK_ENOMEM, SK_ECUDA. */
 int capsule_create(sk_ctx* ctx, sk_capsule** out, int m, const double* X, const double* w,
                    const double* delta, int64_t n_delta, double mu, int precision);
@@ -250,7 +253,8 @@ int capsule_set_membrane(sk_capsule* c, const double* X_ref, double Es, double E
 /* Evaluate the single layer of every step on the four-times upsampled grid
  * (Sec. 3.4, "Upsampling"; factor 4, as stokes_sl_eval_upsampled; W from the derivative scheme at
  * the current nodes; delta_u per patch replaces delta) or on the nodes
- * themselves (factor 1, the default). Needs m >= 6 for factor 4.
+ * themselves (factor 1, the default). Needs m >= 6 for factor 4, and in
+ * SK_FP32C at most 2^25 fine nodes (6 (4m - 1)^2).
  * Errors: SK_EINVAL, SK_ENOMEM, SK_ECUDA. */
 int capsule_set_upsampling(sk_capsule* c, int factor);
 
@@ -380,7 +384,8 @@ typedef struct {
 } sk_serve_cfg;
 
 typedef struct {
-  int64_t n_src;             /* as in stokes_sl_eval; host pointers, copied by serve_submit */
+  int64_t n_src;             /* as in stokes_sl_eval (SK_FP32C: at most 2^25); host pointers,
+                                copied by serve_submit */
   const double* src_xyz;
   const double* src_w;
   const double* f;

@@ -96,9 +96,9 @@ void carve_eval_buffers(Bump& bp, const EvalShape& s, EvalBufs& b) {
   b.tgt64 = bp.take<double4_32a>(b.M_pad);
   b.part = bp.take<double>((size_t)s.n_chunks * b.M_pad * 3);
   if (fp32) {
-    b.near_cnt = bp.take<int>(b.M_pad);
+    b.near_cnt = bp.take<int>(b.M_pad / NEAR_GROUP_MIN);
     b.tb_done = bp.take<int>(b.M_pad / 512 + 1);  // blocks of >= 512 targets
-    b.near_idx = bp.take<int>((size_t)b.M_pad * NEAR_K);
+    b.near_idx = bp.take<unsigned>((size_t)b.M_pad * NEAR_K);
     b.near_ovf = bp.take<double>((size_t)b.M_pad * 3);
   }
   b.flags = bp.take<unsigned long long>(N_FLAGS);
@@ -126,7 +126,7 @@ int enqueue_prep(const EvalShape& s, const EvalBufs& b, double rho_T, double rho
   cudaMemsetAsync(b.flags, 0, N_FLAGS * sizeof(unsigned long long), st);
   cudaMemsetAsync(b.meta, 0, N_META * sizeof(int), st);
   if (fp32) {
-    cudaMemsetAsync(b.near_cnt, 0, b.M_pad * sizeof(int), st);
+    cudaMemsetAsync(b.near_cnt, 0, (b.M_pad / NEAR_GROUP_MIN) * sizeof(int), st);
     cudaMemsetAsync(b.tb_done, 0, (b.M_pad / 512 + 1) * sizeof(int), st);
   }
   k_check_delta<<<(unsigned)((s.n_delta + 255) / 256), 256, 0, st>>>(b.delta, s.n_delta, b.flags);
@@ -332,6 +332,8 @@ int eval_entry(sk_ctx* ctx, int layer, int precision, int mem, int64_t N, const 
   if (N < 0 || M < 0) return fail(ctx, SK_EINVAL, "%s: negative size", fn);
   if (N > MAX_POINTS || M > MAX_POINTS)
     return fail(ctx, SK_EINVAL, "%s: more than 2^30 sources or targets", fn);
+  if (precision == SK_FP32C && N > FP32C_MAX_SOURCES)
+    return fail(ctx, SK_EINVAL, "%s: more than 2^25 sources in SK_FP32C", fn);
   if (M == 0) return SK_OK;
   if (N > 0 && (!xyz || !w || !dens || (layer == LAYER_DL && !nrm)))
     return fail(ctx, SK_EINVAL, "%s: NULL source array", fn);

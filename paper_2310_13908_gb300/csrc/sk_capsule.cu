@@ -336,6 +336,10 @@ int capsule_create(sk_ctx* ctx, sk_capsule** out, int m, const double* X, const 
     return SK_EINVAL;
   }
   const int64_t N = 6 * (int64_t)(m - 1) * (m - 1);
+  if (precision == SK_FP32C && N > FP32C_MAX_SOURCES) {
+    ctx->err = "capsule_create: more than 2^25 nodes in SK_FP32C";
+    return SK_EINVAL;
+  }
   if (delta) {
     if (!(n_delta == 1 || n_delta == N)) {
       ctx->err = "capsule_create: n_delta must be 1 or 6 (m-1)^2";
@@ -593,6 +597,11 @@ int capsule_set_upsampling(sk_capsule* c, int factor) {
     return SK_EINVAL;
   }
   if (factor == 4) {
+    const int64_t n_up = 6 * (int64_t)(4 * c->m - 1) * (4 * c->m - 1);
+    if (c->precision == SK_FP32C && n_up > FP32C_MAX_SOURCES) {
+      ctx->err = "capsule_set_upsampling: more than 2^25 fine nodes in SK_FP32C";
+      return SK_EINVAL;
+    }
     MembraneOp* op = nullptr;
     int rc = membrane_op(ctx, c->m, &op);
     if (rc == SK_OK) rc = membrane_upsampling(ctx, op);

@@ -788,29 +788,31 @@ __global__ void __launch_bounds__(TPB32, MINB)
       a, it.x, p32::TileList{desc + it.y, it.z, it.w, TB, (int64_t)it.x * TB}, sm, ps);
 }
 
-// Thread per target slot: its block's item partials in item order, plus the
-// FP64 near sum; u at the target's original index.
-__global__ void __launch_bounds__(128) k_fmm_finish32(p32::FinishArgs fa,
-                                                      const int* __restrict__ item_first, int tb,
-                                                      int64_t n_slots) {
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  int cnt = 0;
-  if (t < n_slots && fa.perm[t] >= 0) {
-    const int64_t b = t / tb, l = t - b * tb;
-    double u0 = 0.0, u1 = 0.0, u2 = 0.0;
-    for (int it = item_first[b]; it < item_first[b + 1]; ++it) {
-      const double* p = fa.part + ((size_t)it * tb + l) * 3;
-      u0 += p[0];
-      u1 += p[1];
-      u2 += p[2];
-    }
-    double n0, n1, n2;
-    cnt = p32::near_sum<p32::SLayer>(fa, t, n0, n1, n2);
-    const int j = fa.perm[t];
-    fa.u[3 * j] = u0 + n0;
-    fa.u[3 * j + 1] = u1 + n1;
-    fa.u[3 * j + 2] = u2 + n2;
-  }
+// One CTA of G threads per target group of G targets (a thread per target):
+// each target's item partials in item order plus its FP64 near sum (the
+// near-sum scratch in dynamic shared memory); u at the target's original
+// index.
+template <int G>
+__global__ void __launch_bounds__(G)
+    k_fmm_finish32(p32::OverflowArgs oa, p32::FinishArgs fa, const int* __restrict__ item_first,
+                   int tb) {
+  extern __shared__ unsigned fsm[];
+  int cnt = p32::near_group<p32::SLayer, G>(
+      oa, fa, blockIdx.x, fsm, threadIdx.x, [&](int64_t t, double n0, double n1, double n2) {
+        const int j = fa.perm[t];
+        if (j < 0) return;
+        const int64_t b = t / tb, l = t - b * tb;
+        double u0 = 0.0, u1 = 0.0, u2 = 0.0;
+        for (int it = item_first[b]; it < item_first[b + 1]; ++it) {
+          const double* p = fa.part + ((size_t)it * tb + l) * 3;
+          u0 += p[0];
+          u1 += p[1];
+          u2 += p[2];
+        }
+        fa.u[3 * j] = u0 + n0;
+        fa.u[3 * j + 1] = u1 + n1;
+        fa.u[3 * j + 2] = u2 + n2;
+      });
   for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
   if ((threadIdx.x & 31) == 0 && cnt)
     atomicAdd(fa.flags + FLAG_NEAR_PAIRS, (unsigned long long)cnt);
@@ -881,6 +883,10 @@ int stokes_sl_eval_fmm(sk_ctx* ctx, int precision, int mem, int64_t n_src,
                "3 <= p <= 10, n_delta in {1, n_tgt}, mu > 0, mem, precision)";
     return SK_EINVAL;
   }
+  if (precision == SK_FP32C && n_src > FP32C_MAX_SOURCES) {
+    ctx->err = "stokes_sl_eval_fmm: more than 2^25 sources in SK_FP32C";
+    return SK_EINVAL;
+  }
   if (mem == SK_HOST)
     for (int64_t i = 0; i < n_delta; ++i)
       if (!(delta[i] > 0.0 && delta[i] < INFINITY)) {
@@ -932,7 +938,8 @@ int stokes_sl_eval_fmm(sk_ctx* ctx, int precision, int mem, int64_t n_src,
         *tgt_order = nullptr;
     float *bbox_part = nullptr, *bbox = nullptr;
     float4 *srcF = nullptr, *segbox = nullptr, *tgtF = nullptr;
-    int *src_orig = nullptr, *perm = nullptr, *near_cnt = nullptr, *near_idx = nullptr;
+    int *src_orig = nullptr, *perm = nullptr, *near_cnt = nullptr;
+    unsigned* near_idx = nullptr;
     double4_32a* tgt64 = nullptr;
     double *near_ovf = nullptr, *part = nullptr;
     int* plan = nullptr;  // tile_cluster, src_first, block_box, box_first, item_first, items, desc
@@ -985,8 +992,8 @@ int stokes_sl_eval_fmm(sk_ctx* ctx, int precision, int mem, int64_t n_src,
     c.tgtF = b.take<float4>((size_t)m_slots_max * 2);
     c.tgt64 = b.take<double4_32a>(m_slots_max);
     c.perm = b.take<int>(m_slots_max);
-    c.near_cnt = b.take<int>(m_slots_max);
-    c.near_idx = b.take<int>((size_t)m_slots_max * NEAR_K);
+    c.near_cnt = b.take<int>(m_slots_max / NEAR_GROUP_MIN);
+    c.near_idx = b.take<unsigned>((size_t)m_slots_max * NEAR_K);
     c.near_ovf = b.take<double>((size_t)m_slots_max * 3);
     c.part = b.take<double>((size_t)n_items_max * tb * 3);
     c.plan = b.take<int>(plan_ints);
@@ -1167,7 +1174,7 @@ int stokes_sl_eval_fmm(sk_ctx* ctx, int precision, int mem, int64_t n_src,
       meta[META_NS] = (int)near_slots;  // the overflow rescan's range
       cudaMemcpyAsync(cv.meta, meta, sizeof(meta), cudaMemcpyHostToDevice, st);
       cudaMemsetAsync(cv.flags, 0, N_FLAGS * sizeof(unsigned long long), st);
-      cudaMemsetAsync(cv.near_cnt, 0, m_slots * sizeof(int), st);
+      cudaMemsetAsync(cv.near_cnt, 0, (m_slots / NEAR_GROUP_MIN) * sizeof(int), st);
       const int* d_tc = cv.plan + o_tc;
       const int* d_sf = cv.plan + o_sf;
       const int* d_bb = cv.plan + o_bb;
@@ -1196,10 +1203,16 @@ int stokes_sl_eval_fmm(sk_ctx* ctx, int precision, int mem, int64_t n_src,
       p32::OverflowArgs oa{cv.srcF,   cv.segbox, cv.src_orig, cv.meta, cv.tgtF,  cv.tgt64,
                            cv.near_cnt, X,        W,           F,       nullptr, scale,
                            cv.flags,  cv.near_ovf};
+      oa.group = 64 * np32;
       k_fmm_overflow32<<<(unsigned)((m_slots * 32 + 255) / 256), 256, 0, st>>>(oa, m_slots);
       p32::FinishArgs fa{cv.tgt64, cv.perm, m_slots, 1, cv.part, cv.near_cnt, cv.near_idx,
                          cv.near_ovf, X, W, F, nullptr, scale, U, cv.flags};
-      k_fmm_finish32<<<(unsigned)((m_slots + 127) / 128), 128, 0, st>>>(fa, d_if, tb, m_slots);
+      fa.group = 64 * np32;
+      const size_t fsmem = (size_t)p32::near_warp_words(fa.group) * 4;
+      if (np32 == 2)
+        k_fmm_finish32<128><<<(unsigned)(m_slots / 128), 128, fsmem, st>>>(oa, fa, d_if, tb);
+      else
+        k_fmm_finish32<64><<<(unsigned)(m_slots / 64), 64, fsmem, st>>>(oa, fa, d_if, tb);
       ctx->stats = sk_eval_stats{};
       ctx->stats.n_tgt = n_tgt;
       ctx->stats.n_chunks = n_items;

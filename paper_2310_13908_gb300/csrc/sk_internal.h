@@ -30,7 +30,11 @@ constexpr int TPB64 = 256;
 constexpr int TPL64 = 2;
 constexpr int TGT_WARP64 = 32 * TPL64;
 constexpr int TGT_CTA64 = TPB64 * TPL64;
-constexpr int NEAR_K = 96;              // FP64 near-pair slots per target
+constexpr int NEAR_K = 96;              // FP64 near-pair slots per target (pooled per group)
+constexpr int NEAR_GROUP_MIN = 64;      // targets per near-list group: 64 * (f32x2 pairs per lane)
+constexpr int NEAR_SRC_BITS = 25;       // near-list entry: source index bits (the rest: target)
+// SK_FP32C lists near pairs by the source's original index in NEAR_SRC_BITS bits
+constexpr int64_t FP32C_MAX_SOURCES = int64_t(1) << NEAR_SRC_BITS;
 constexpr int RHO_C64 = 7;              // FP64 path: s_i == 1 to double precision beyond 7
 
 // layer kinds
@@ -153,9 +157,9 @@ struct EvalBufs {
   double4_32a* tgt64 = nullptr;       // FP64 sorted targets: (x, y, z, delta)
   // accumulation
   double* part = nullptr;         // [n_chunks][M_pad][3]
-  int* near_cnt = nullptr;        // [M_pad]
+  int* near_cnt = nullptr;        // [M_pad / NEAR_GROUP_MIN] entries per target group
   int* tb_done = nullptr;         // [M_pad / 512 + 1] chunks done per target block (FP32C)
-  int* near_idx = nullptr;        // [M_pad][NEAR_K]
+  unsigned* near_idx = nullptr;   // [M_pad / group][NEAR_K * group] near-pair entries
   double* near_ovf = nullptr;     // [M_pad][3]
   unsigned long long* flags = nullptr;
   // sizes

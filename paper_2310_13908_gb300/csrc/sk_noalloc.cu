@@ -52,7 +52,7 @@ extern "C" int stokes_sl_eval_noalloc(int64_t n_src, const double* src_xyz, cons
   if (!tgt_xyz || !delta || !u_out) return SK_EINVAL;
   if (!(n_delta == 1 || n_delta == n_tgt)) return SK_EINVAL;
   if (!(mu > 0.0 && mu < INFINITY)) return SK_EINVAL;
-  if (n_src > (int64_t(1) << 30) || n_tgt > (int64_t(1) << 30)) return SK_EINVAL;
+  if (n_src > FP32C_MAX_SOURCES || n_tgt > (int64_t(1) << 30)) return SK_EINVAL;
 
   int dev = -1, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES)

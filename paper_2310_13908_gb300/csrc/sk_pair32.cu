@@ -41,7 +41,10 @@ __global__ void __launch_bounds__(TPB32, MINB)
   if (!s_last) return;
   __threadfence();
   constexpr int TB = TPB32 * 2 * NP;  // targets per block
-  finish_block<L>(oa, fa, M, (int64_t)tb * TB, TB);
+  // the source stages are free now: the finish buckets the near lists there
+  static_assert(pair_smem_bytes<L, NP>() / 4 >= (size_t)(TPB32 / 32) * near_warp_words(64 * NP),
+                "finish scratch");
+  finish_block<L>(oa, fa, M, (int64_t)tb * TB, TB, reinterpret_cast<unsigned*>(sm));
 }
 
 template <class L>
@@ -52,16 +55,22 @@ __global__ void k_overflow32(OverflowArgs a, int64_t M) {
   overflow_target<L>(a, t);
 }
 
-template <class L>
-__global__ void __launch_bounds__(128) k_finish32(FinishArgs a, int64_t M) {
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  int cnt = 0;
-  if (t < M) cnt = finish_target<L>(a, t);
+// Separate finish for grids too small to fuse it: one CTA of G threads per
+// target group of G targets (a thread per target), the near-sum scratch in
+// dynamic shared memory.
+template <class L, int G>
+__global__ void __launch_bounds__(G) k_finish32(OverflowArgs oa, FinishArgs a, int64_t M) {
+  extern __shared__ unsigned fsm[];
+  const int64_t t0 = (int64_t)blockIdx.x * G;
+  int cnt = near_group<L, G>(oa, a, blockIdx.x, fsm, threadIdx.x,
+                             [&](int64_t t, double n0, double n1, double n2) {
+                               if (t < M) finish_merge(a, t, n0, n1, n2);
+                             });
   // count near pairs: one atomic per warp
   for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(FULL, cnt, o);
   if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(a.flags + FLAG_NEAR_PAIRS, (unsigned long long)cnt);
-  __syncthreads();  // this CTA's targets are finished: their scratch is dead
-  discard_block_scratch(a, (int64_t)blockIdx.x * blockDim.x, blockDim.x, threadIdx.x, blockDim.x);
+  __syncthreads();  // this group's targets are finished: their scratch is dead
+  discard_block_scratch(a, t0, G, threadIdx.x, blockDim.x);
 }
 
 }  // namespace
@@ -78,6 +87,7 @@ void launch_pair32_t(const EvalBufs& b, float rho_lo, float rho_hi, double scale
                   b.src_xyz, b.src_w, b.dens,   b.nrm, scale, b.flags, b.near_ovf};
   FinishArgs fa{b.tgt64, b.tgt_perm, b.M_pad, b.n_chunks, b.part, b.near_cnt, b.near_idx,
                 b.near_ovf, b.src_xyz, b.src_w, b.dens, b.nrm, scale, b.u, b.flags};
+  oa.group = fa.group = 64 * NP;
   if (b.fuse_finish) {
     cudaFuncSetAttribute(k_pair32_fused<L, NP, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
@@ -89,7 +99,9 @@ void launch_pair32_t(const EvalBufs& b, float rho_lo, float rho_hi, double scale
     k_pair32<L, NP, MINB><<<grid, TPB32, smem, st>>>(a);
     if (pair_end) cudaEventRecord(pair_end, st);
     k_overflow32<L><<<(unsigned)((b.M * 32 + 255) / 256), 256, 0, st>>>(oa, b.M);
-    k_finish32<L><<<(unsigned)((b.M + 127) / 128), 128, 0, st>>>(fa, b.M);
+    constexpr int G = 64 * NP;
+    const size_t fsmem = (size_t)near_warp_words(G) * sizeof(unsigned);
+    k_finish32<L, G><<<(unsigned)(b.M_pad / G), G, fsmem, st>>>(oa, fa, b.M);
   }
 }
 

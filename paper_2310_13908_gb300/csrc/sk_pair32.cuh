@@ -145,14 +145,55 @@ __device__ __forceinline__ float box_margin(float coord_max, float rc) {
   return 1.0e-6f * (coord_max + rc);
 }
 
-__device__ __forceinline__ void near_append(int64_t t, int jo, int* __restrict__ cnt,
-                                            int* __restrict__ idx,
-                                            unsigned long long* __restrict__ flags) {
-  const int slot = atomicAdd(cnt + t, 1);
-  if (slot < NEAR_K)
-    idx[t * NEAR_K + slot] = jo;
-  else if (slot == NEAR_K)
-    atomicAdd(flags + FLAG_OVERFLOW, 1ull);
+// Near pairs (rho < rho_T) are listed per target group: the 64 * NP targets
+// of one warp of the pair kernel (group g = first target / (64 * NP)). An
+// entry is (k << NEAR_SRC_BITS) | jo, k the target's place in the group and
+// jo the source's original index. The warp appends the near pairs of one
+// source together: one atomic per warp and source, and consecutive slots, so
+// the group's list fills whole 32-byte sectors. (Entries appended one by one
+// to per-target lists leave a partly written sector per target, which L2
+// completes from DRAM when the finish reads it.) near_bits holds bit 2p + h
+// for the lane's target 64p + 32h + lane. A list longer than NEAR_K * 64 * NP
+// entries keeps counting but stores no more; the group's targets then take
+// the rescan of overflow_target.
+template <int NP>
+__device__ __noinline__ void near_append_list(unsigned near_bits, int lane, int64_t g,
+                                              const int* jo_at, int* __restrict__ cnt,
+                                              unsigned* __restrict__ idx,
+                                              unsigned long long* __restrict__ flags) {
+  constexpr int CAP = NEAR_K * 64 * NP;
+  const unsigned jo = (unsigned)*jo_at;
+  const unsigned lt = (1u << lane) - 1u;
+  int total = 0;
+#pragma unroll
+  for (int b = 0; b < 2 * NP; ++b) total += __popc(__ballot_sync(FULL, (near_bits >> b) & 1u));
+  int base = 0;
+  if (lane == 0) {
+    base = atomicAdd(cnt + g, total);
+    // the group's targets will be rescanned: count them
+    if (base <= CAP && base + total > CAP) atomicAdd(flags + FLAG_OVERFLOW, 64ull * NP);
+  }
+  base = __shfl_sync(FULL, base, 0);
+  unsigned* __restrict__ list = idx + (size_t)g * CAP;
+  // slots in (bit, lane) order: the ballots again, so that no offsets stay live
+#pragma unroll
+  for (int b = 0; b < 2 * NP; ++b) {
+    const unsigned m = __ballot_sync(FULL, (near_bits >> b) & 1u);
+    const int slot = base + __popc(m & lt);
+    if (((near_bits >> b) & 1u) && slot < CAP)
+      list[slot] = ((unsigned)(64 * (b >> 1) + 32 * (b & 1) + lane) << NEAR_SRC_BITS) | jo;
+    base += __popc(m);
+  }
+}
+
+// Out of line beyond the vote: few general-path sources have a near pair,
+// and the append's registers then do not weigh on the pair loop.
+template <int NP>
+__device__ __forceinline__ void near_append_warp(unsigned near_bits, int lane, int64_t g,
+                                                 const int* jo_at, int* __restrict__ cnt,
+                                                 unsigned* __restrict__ idx,
+                                                 unsigned long long* __restrict__ flags) {
+  if (__any_sync(FULL, near_bits)) near_append_list<NP>(near_bits, lane, g, jo_at, cnt, idx, flags);
 }
 
 // ---- layer policies ---------------------------------------------------------
@@ -261,21 +302,19 @@ __device__ __forceinline__ void pair_d(const Tgt2& T, float2 nx, float2 ny, floa
 // overflow rescan). rho and the kernel use (dx, dy, dz) and r2k, which equal
 // the FP32 difference and r2 except where pair_general corrected them.
 template <class L>
-__device__ __forceinline__ void pair_general_regimes(const typename L::Src& S, const Tgt2& T,
-                                                     float2 dx, float2 dy, float2 dz, float2 r2,
-                                                     float2 r2k, float2* U, int64_t t0,
-                                                     int64_t t1, const int* src_orig_j,
-                                                     int* near_cnt, int* near_idx,
-                                                     unsigned long long* flags, float rho_lo,
-                                                     float rho_hi) {
+__device__ __forceinline__ unsigned pair_general_regimes(const typename L::Src& S, const Tgt2& T,
+                                                         float2 dx, float2 dy, float2 dz,
+                                                         float2 r2, float2 r2k, float2* U,
+                                                         float rho_lo, float rho_hi) {
   float2 ri = make_float2(rsq(r2k.x), rsq(r2k.y));
   float2 sa = make_float2(1.f, 1.f), sb = make_float2(1.f, 1.f);
+  unsigned near_bits = 0;
   // component x
   {
     const bool vn = r2.x < T.rt2.x;
     const bool in = !vn && r2.x < T.rc2.x;
     if (vn) {
-      near_append(t0, *src_orig_j, near_cnt, near_idx, flags);
+      near_bits |= 1u;
       ri.x = 0.f;
     }
     float rho = fminf(fmaxf(r2k.x * ri.x * T.idl.x, rho_lo), rho_hi);
@@ -290,7 +329,7 @@ __device__ __forceinline__ void pair_general_regimes(const typename L::Src& S, c
     const bool vn = r2.y < T.rt2.y;
     const bool in = !vn && r2.y < T.rc2.y;
     if (vn) {
-      near_append(t1, *src_orig_j, near_cnt, near_idx, flags);
+      near_bits |= 2u;
       ri.y = 0.f;
     }
     float rho = fminf(fmaxf(r2k.y * ri.y * T.idl.y, rho_lo), rho_hi);
@@ -302,20 +341,20 @@ __device__ __forceinline__ void pair_general_regimes(const typename L::Src& S, c
     }
   }
   L::general(S, dx, dy, dz, ri, sa, sb, U);
+  return near_bits;
 }
 
 // For L::kExactNear, (cx, cy, cz) is the residual that makes the FP32
 // difference exact: pairs with rho_T <= rho < rho_c take the corrected
 // difference; the others keep the FP32 one, so a pair at or beyond rho_c
 // still reproduces the far formula bit for bit.
+// Returns the pair's near bits (x component: 1, y component: 2).
 template <class L>
-__device__ __forceinline__ void pair_general(const typename L::Src& S, const Tgt2& T, float2 dx,
-                                             float2 dy, float2 dz, float2 r2, float2* U,
-                                             int64_t t0, int64_t t1, const int* src_orig_j,
-                                             int* near_cnt, int* near_idx,
-                                             unsigned long long* flags, float rho_lo,
-                                             float rho_hi, float2 cx = float2{},
-                                             float2 cy = float2{}, float2 cz = float2{}) {
+__device__ __forceinline__ unsigned pair_general(const typename L::Src& S, const Tgt2& T,
+                                                 float2 dx, float2 dy, float2 dz, float2 r2,
+                                                 float2* U, float rho_lo, float rho_hi,
+                                                 float2 cx = float2{}, float2 cy = float2{},
+                                                 float2 cz = float2{}) {
   if constexpr (L::kExactNear) {
     const bool in0 = r2.x >= T.rt2.x && r2.x < T.rc2.x;
     const bool in1 = r2.y >= T.rt2.y && r2.y < T.rc2.y;
@@ -325,11 +364,9 @@ __device__ __forceinline__ void pair_general(const typename L::Src& S, const Tgt
     dy = make_float2(in0 ? ey.x : dy.x, in1 ? ey.y : dy.y);
     dz = make_float2(in0 ? ez.x : dz.x, in1 ? ez.y : dz.y);
     const float2 r2k = make_float2(in0 ? er2.x : r2.x, in1 ? er2.y : r2.y);
-    pair_general_regimes<L>(S, T, dx, dy, dz, r2, r2k, U, t0, t1, src_orig_j, near_cnt,
-                            near_idx, flags, rho_lo, rho_hi);
+    return pair_general_regimes<L>(S, T, dx, dy, dz, r2, r2k, U, rho_lo, rho_hi);
   } else {
-    pair_general_regimes<L>(S, T, dx, dy, dz, r2, r2, U, t0, t1, src_orig_j, near_cnt, near_idx,
-                            flags, rho_lo, rho_hi);
+    return pair_general_regimes<L>(S, T, dx, dy, dz, r2, r2, U, rho_lo, rho_hi);
   }
 }
 
@@ -362,6 +399,46 @@ struct LaneTgt {
   Tgt2 t[NP];
 };
 
+// The general loop over the 32 sources of one segment near the warp's
+// targets: per source, the far formula unless some lane's pair lies inside
+// rho_c delta, then the regimes and the warp's near-pair append. Out of line:
+// its registers do not weigh on the far loop, and such segments are few (the
+// ones within rho_c delta of the warp's box).
+template <class L, int NP>
+__device__ __noinline__ LaneAcc<NP> general_segment(LaneAcc<NP> acc, LaneTgt<NP> tg,
+                                                    const float4* SS, const int* orig,
+                                                    int64_t group, int* near_cnt,
+                                                    unsigned* near_idx,
+                                                    unsigned long long* flags, float rho_lo,
+                                                    float rho_hi) {
+  constexpr int V = L::V;
+  const int lane = threadIdx.x & 31;
+#pragma unroll 1
+  for (int j = 0; j < SEG; ++j) {
+    const typename L::Src src = L::load(SS + j * V);
+    float2 dx[NP], dy[NP], dz[NP], r2[NP];
+    bool any = false;
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      pair_d(tg.t[p], src.nx, src.ny, src.nz, dx[p], dy[p], dz[p], r2[p]);
+      any |= (r2[p].x < tg.t[p].rc2.x) | (r2[p].y < tg.t[p].rc2.y);
+    }
+    if (__any_sync(FULL, any)) {
+      unsigned near_bits = 0;
+#pragma unroll
+      for (int p = 0; p < NP; ++p)
+        near_bits |= pair_general<L>(src, tg.t[p], dx[p], dy[p], dz[p], r2[p], acc.u[p], rho_lo,
+                                     rho_hi)
+                     << (2 * p);
+      near_append_warp<NP>(near_bits, lane, group, orig + j, near_cnt, near_idx, flags);
+    } else {
+#pragma unroll
+      for (int p = 0; p < NP; ++p) L::far(src, dx[p], dy[p], dz[p], r2[p], acc.u[p]);
+    }
+  }
+  return acc;
+}
+
 // The general loop over the 32 sources of one segment that is wide for some
 // target of the warp (L::kExactNear): pairs with rho_T <= rho < rho_c on a
 // target for which the segment is wide take the exact difference (the
@@ -373,9 +450,10 @@ struct LaneTgt {
 template <class L, int NP>
 __device__ __noinline__ LaneAcc<NP> exact_segment(
     LaneAcc<NP> acc, LaneTgt<NP> tg, const float4* SS, const float4* __restrict__ ylo,
-    const int* orig, const float4* ts, float sx, float sy, float sz, float hs, int64_t wbase,
-    int* near_cnt, int* near_idx, unsigned long long* flags, float rho_lo, float rho_hi) {
+    const int* orig, const float4* ts, float sx, float sy, float sz, float hs, int64_t group,
+    int* near_cnt, unsigned* near_idx, unsigned long long* flags, float rho_lo, float rho_hi) {
   constexpr int V = L::V;
+  const int lane = threadIdx.x & 31;
 #pragma unroll 1
   for (int j = 0; j < SEG; ++j) {
     const typename L::Src src = L::load(SS + j * V);
@@ -388,21 +466,24 @@ __device__ __noinline__ LaneAcc<NP> exact_segment(
     }
     if (__any_sync(FULL, any)) {
       const float4 yl = ylo[j];
+      unsigned near_bits = 0;
 #pragma unroll
       for (int p = 0; p < NP; ++p) {
         const float4 hx = ts[(p * TGT_SLOTS) * TPB32], hy = ts[(p * TGT_SLOTS + 1) * TPB32],
                      hz = ts[(p * TGT_SLOTS + 2) * TPB32];
         const float2 wd = make_float2(hs * tg.t[p].idl.x > WIDE_FRAME ? 1.f : 0.f,
                                       hs * tg.t[p].idl.y > WIDE_FRAME ? 1.f : 0.f);
-        pair_general<L>(src, tg.t[p], dx[p], dy[p], dz[p], r2[p], acc.u[p], wbase + 64 * p,
-                        wbase + 64 * p + 32, orig + j, near_cnt, near_idx, flags, rho_lo, rho_hi,
-                        mul2(wd, sub2(shift_residual2(lo2(hx), hi2(hx), sx, tg.t[p].x),
-                                      make_float2(yl.x, yl.x))),
-                        mul2(wd, sub2(shift_residual2(lo2(hy), hi2(hy), sy, tg.t[p].y),
-                                      make_float2(yl.y, yl.y))),
-                        mul2(wd, sub2(shift_residual2(lo2(hz), hi2(hz), sz, tg.t[p].z),
-                                      make_float2(yl.z, yl.z))));
+        near_bits |= pair_general<L>(
+                         src, tg.t[p], dx[p], dy[p], dz[p], r2[p], acc.u[p], rho_lo, rho_hi,
+                         mul2(wd, sub2(shift_residual2(lo2(hx), hi2(hx), sx, tg.t[p].x),
+                                       make_float2(yl.x, yl.x))),
+                         mul2(wd, sub2(shift_residual2(lo2(hy), hi2(hy), sy, tg.t[p].y),
+                                       make_float2(yl.y, yl.y))),
+                         mul2(wd, sub2(shift_residual2(lo2(hz), hi2(hz), sz, tg.t[p].z),
+                                       make_float2(yl.z, yl.z))))
+                     << (2 * p);
       }
+      near_append_warp<NP>(near_bits, lane, group, orig + j, near_cnt, near_idx, flags);
     } else {
 #pragma unroll
       for (int p = 0; p < NP; ++p) L::far(src, dx[p], dy[p], dz[p], r2[p], acc.u[p]);
@@ -457,8 +538,8 @@ struct PairArgs {
   int64_t M_pad;
   int n_chunks;
   double* part;
-  int* near_cnt;
-  int* near_idx;
+  int* near_cnt;       // per target group (64 * NP targets)
+  unsigned* near_idx;  // per target group: NEAR_K * 64 * NP entries
   unsigned long long* flags;
   float rho_lo, rho_hi;
   const float4* srcLo = nullptr;  // double layer: residuals of the packed positions
@@ -528,7 +609,7 @@ __device__ __forceinline__ bool pair_item(const PairArgs& a, int tb, const TL& t
   const float4* __restrict__ tgtF = a.tgtF;
   const double4_32a* __restrict__ tgt64 = a.tgt64;
   int* __restrict__ near_cnt = a.near_cnt;
-  int* __restrict__ near_idx = a.near_idx;
+  unsigned* __restrict__ near_idx = a.near_idx;
   unsigned long long* __restrict__ flags = a.flags;
   const float rho_lo = a.rho_lo, rho_hi = a.rho_hi;
   uint64_t* full = ps.full;
@@ -540,6 +621,8 @@ __device__ __forceinline__ bool pair_item(const PairArgs& a, int tb, const TL& t
 
   // ---- targets of this lane: pair p holds targets (base + 64p + lane, base + 64p + 32 + lane)
   const int64_t wbase = (int64_t)tb * (TPB32 * 2 * NP) + wid * (64 * NP) + lane;
+  // this warp's target group (its near-pair list)
+  const int64_t group = (int64_t)tb * (TPB32 / 32) + wid;
   // per-thread target state: [(p * TGT_SLOTS + slot) * TPB32 + tid]
   float4* const ts = sm + STAGES * TILE * V + tid;
   Tgt2 T[NP];
@@ -723,27 +806,20 @@ __device__ __forceinline__ bool pair_item(const PairArgs& a, int tb, const TL& t
             wide = __any_sync(FULL, wide);
           }
           if (!wide) {
-#pragma unroll 1
-            for (int j = 0; j < SEG; ++j) {
-              const typename L::Src src = L::load(SS + j * V);
-              float2 dx[NP], dy[NP], dz[NP], r2[NP];
-              bool any = false;
+            LaneAcc<NP> acc;
+            LaneTgt<NP> tg;
 #pragma unroll
-              for (int p = 0; p < NP; ++p) {
-                pair_d(T[p], src.nx, src.ny, src.nz, dx[p], dy[p], dz[p], r2[p]);
-                any |= (r2[p].x < T[p].rc2.x) | (r2[p].y < T[p].rc2.y);
-              }
-              if (__any_sync(FULL, any)) {
+            for (int p = 0; p < NP; ++p) {
+              tg.t[p] = T[p];
 #pragma unroll
-                for (int p = 0; p < NP; ++p)
-                  pair_general<L>(src, T[p], dx[p], dy[p], dz[p], r2[p], U[p], wbase + 64 * p,
-                                  wbase + 64 * p + 32, orig + j, near_cnt, near_idx, flags,
-                                  rho_lo, rho_hi);
-              } else {
-#pragma unroll
-                for (int p = 0; p < NP; ++p) L::far(src, dx[p], dy[p], dz[p], r2[p], U[p]);
-              }
+              for (int c = 0; c < 3; ++c) acc.u[p][c] = U[p][c];
             }
+            acc = general_segment<L, NP>(acc, tg, SS, orig, group, near_cnt, near_idx, flags,
+                                         rho_lo, rho_hi);
+#pragma unroll
+            for (int p = 0; p < NP; ++p)
+#pragma unroll
+              for (int c = 0; c < 3; ++c) U[p][c] = acc.u[p][c];
           } else if constexpr (L::kExactNear) {
             LaneAcc<NP> acc;
             LaneTgt<NP> tg;
@@ -754,7 +830,7 @@ __device__ __forceinline__ bool pair_item(const PairArgs& a, int tb, const TL& t
               for (int c = 0; c < 3; ++c) acc.u[p][c] = U[p][c];
             }
             acc = exact_segment<L, NP>(acc, tg, SS, a.srcLo + (size_t)src0 + s * SEG,
-                                       orig, ts, sx, sy, sz, hs, wbase, near_cnt, near_idx,
+                                       orig, ts, sx, sy, sz, hs, group, near_cnt, near_idx,
                                        flags, rho_lo, rho_hi);
 #pragma unroll
             for (int p = 0; p < NP; ++p)
@@ -867,7 +943,7 @@ struct OverflowArgs {
   const int* meta;
   const float4* tgtF;
   const double4_32a* tgt64;
-  const int* near_cnt;
+  const int* near_cnt;  // per target group
   const double* xyz;
   const double* w;
   const double* dens;
@@ -875,6 +951,7 @@ struct OverflowArgs {
   double scale;
   const unsigned long long* flags;
   double* near_ovf;
+  int group = 0;  // targets per group: 64 * (f32x2 pairs per lane) of the pair kernel
 };
 
 struct FinishArgs {
@@ -883,8 +960,8 @@ struct FinishArgs {
   int64_t M_pad;
   int n_chunks;
   const double* part;
-  const int* near_cnt;
-  const int* near_idx;
+  const int* near_cnt;       // per target group
+  const unsigned* near_idx;  // per target group
   const double* near_ovf;
   const double* xyz;
   const double* w;
@@ -893,15 +970,16 @@ struct FinishArgs {
   double scale;
   double* u;
   unsigned long long* flags;
+  int group = 0;  // targets per group: 64 * (f32x2 pairs per lane) of the pair kernel
 };
 
-// Target t's near list overflowed: the calling warp rescans all packed sources
-// with exactly the FP32 test of the pair kernel and sums the near pairs in
-// FP64 (fixed lane split and butterfly, so the sum is deterministic).
+// FP64 near sum of target t by a rescan of all packed sources with exactly the
+// FP32 test of the pair kernel, split over the calling warp's lanes and
+// summed by a fixed butterfly (deterministic); every lane gets the sum.
 template <class L>
-__device__ __forceinline__ void overflow_target(const OverflowArgs& a, int64_t t) {
+__device__ __forceinline__ void rescan_target(const OverflowArgs& a, int64_t t, double& u0,
+                                              double& u1, double& u2) {
   const int lane = threadIdx.x & 31;
-  if (a.near_cnt[t] <= NEAR_K) return;
   constexpr int V = L::V;
   const float rt2 = a.tgtF[2 * t + 1].y;
   const double4_32a x = a.tgt64[t];
@@ -910,7 +988,7 @@ __device__ __forceinline__ void overflow_target(const OverflowArgs& a, int64_t t
   const float lx = (float)(x.x - (double)hx), ly = (float)(x.y - (double)hy),
               lz = (float)(x.z - (double)hz);
   const int Ns = a.meta[META_NS];
-  double u0 = 0, u1 = 0, u2 = 0;
+  u0 = u1 = u2 = 0;
   for (int s = lane; s < Ns; s += 32) {
     const float4 blo = a.segbox[2 * (s / SEG)], bhi = a.segbox[2 * (s / SEG) + 1];
     const float tx = shift_to_segment(hx, lx, frame_mid(blo.x, bhi.x));
@@ -926,7 +1004,16 @@ __device__ __forceinline__ void overflow_target(const OverflowArgs& a, int64_t t
     u1 += __shfl_xor_sync(FULL, u1, o);
     u2 += __shfl_xor_sync(FULL, u2, o);
   }
-  if (lane == 0) {
+}
+
+// Target t's group list overflowed: the calling warp rescans for it and
+// stores the sum for the finish.
+template <class L>
+__device__ __forceinline__ void overflow_target(const OverflowArgs& a, int64_t t) {
+  if (a.near_cnt[t / a.group] <= NEAR_K * a.group) return;
+  double u0, u1, u2;
+  rescan_target<L>(a, t, u0, u1, u2);
+  if ((threadIdx.x & 31) == 0) {
     a.near_ovf[3 * t] = u0;
     a.near_ovf[3 * t + 1] = u1;
     a.near_ovf[3 * t + 2] = u2;
@@ -936,38 +1023,168 @@ __device__ __forceinline__ void overflow_target(const OverflowArgs& a, int64_t t
 // Finish one sorted target: chunk partials in fixed order plus the FP64 near
 // sum (list sorted by source index, or the overflow rescan's sum); writes
 // u at the target's original index. Returns the target's near-pair count.
-// FP64 near sum of sorted target t: its list sorted by source index, or the
-// overflow rescan's sum. Returns the target's near-pair count.
-template <class L>
-__device__ __forceinline__ int near_sum(const FinishArgs& a, int64_t t, double& n0, double& n1,
-                                        double& n2) {
-  const int cnt = a.near_cnt[t];
-  n0 = n1 = n2 = 0;
-  if (cnt <= NEAR_K) {
-    int li[NEAR_K];
-    for (int i = 0; i < cnt; ++i) {
-      const int v = a.near_idx[t * NEAR_K + i];
+// v[0 .. n) in ascending order, by one thread: insertion sort for short runs,
+// heapsort for long ones (a group list may hold thousands of one target's
+// entries).
+__device__ __forceinline__ void sort_entries(unsigned* v, int n) {
+  if (n <= 32) {
+    for (int i = 1; i < n; ++i) {
+      const unsigned x = v[i];
       int k = i;
-      while (k > 0 && li[k - 1] > v) {
-        li[k] = li[k - 1];
+      while (k > 0 && v[k - 1] > x) {
+        v[k] = v[k - 1];
         --k;
       }
-      li[k] = v;
+      v[k] = x;
     }
-    const double4_32a x = a.tgt64[t];
-    const double invd = 1.0 / x.w;
-    for (int i = 0; i < cnt; ++i)
-      Near64<L>::eval(x, a.xyz, a.w, a.dens, a.nrm, li[i], a.scale, invd, n0, n1, n2);
-  } else {
-    n0 = a.near_ovf[3 * t];
-    n1 = a.near_ovf[3 * t + 1];
-    n2 = a.near_ovf[3 * t + 2];
+    return;
   }
-  return cnt;
+  auto sift = [v](int root, int end) {
+    for (int c = 2 * root + 1; c < end; c = 2 * root + 1) {
+      if (c + 1 < end && v[c] < v[c + 1]) ++c;
+      if (v[root] >= v[c]) return;
+      const unsigned x = v[root];
+      v[root] = v[c];
+      v[c] = x;
+      root = c;
+    }
+  };
+  for (int i = n / 2 - 1; i >= 0; --i) sift(i, n);
+  for (int e = n - 1; e > 0; --e) {
+    const unsigned x = v[0];
+    v[0] = v[e];
+    v[e] = x;
+    sift(0, e);
+  }
 }
 
-template <class L>
-__device__ __forceinline__ int finish_target(const FinishArgs& a, int64_t t) {
+// Shared 32-bit words of one warp's near-sum scratch for groups of G targets:
+// the same in every kernel that finishes such groups, so that a target's sum
+// never depends on which kernel finished it.
+__host__ __device__ constexpr int near_warp_words(int G) { return G <= 64 ? 2048 : 3200; }
+
+// Barrier of a team of TEAM threads: one warp, or the whole CTA.
+template <int TEAM>
+__device__ __forceinline__ void team_sync() {
+  if constexpr (TEAM == 32) __syncwarp();
+  else __syncthreads();
+}
+
+// FP64 near sums of target group g (G = a.group targets) by a team of TEAM
+// threads (one warp, or a CTA of TEAM threads; tid = the thread's place in
+// it) with the shared words R[0 .. near_warp_words(G)); fin(t, n0, n1, n2)
+// then finishes target t (one thread per target). The group list is bucketed
+// by target in R, in passes over target ranges whose entries fit, and each
+// bucket sorted by source index: every target sums its near pairs in
+// ascending source order, whatever the order of the appends. The targets of
+// an overflowed group take their overflow rescan sums; a target with more
+// near pairs than R holds is rescanned here. Returns the near pairs this
+// thread counted.
+template <class L, int TEAM, class Fin>
+__device__ __forceinline__ int near_group(const OverflowArgs& oa, const FinishArgs& a, int64_t g,
+                                          unsigned* R, int tid, Fin fin) {
+  const int G = a.group, CAP = NEAR_K * G, lane = tid & 31;
+  int* const cnt = reinterpret_cast<int*>(R);  // per target: count, then fill position
+  int* const beg = cnt + G;                    // per target: first entry (exclusive scan)
+  unsigned* const ent = R + 2 * G + 1;
+  const int EW = near_warp_words(G) - (2 * G + 1);
+  const int64_t tg0 = g * G;
+  const int c = a.near_cnt[g];
+  if (c > CAP) {
+    for (int k = tid; k < G; k += TEAM) {
+      const int64_t t = tg0 + k;
+      fin(t, a.near_ovf[3 * t], a.near_ovf[3 * t + 1], a.near_ovf[3 * t + 2]);
+    }
+    return tid == 0 ? c : 0;
+  }
+  const unsigned* list = a.near_idx + (size_t)g * CAP;
+  for (int k = tid; k < G; k += TEAM) cnt[k] = 0;
+  team_sync<TEAM>();
+  for (int i = tid; i < c; i += TEAM) atomicAdd(&cnt[list[i] >> NEAR_SRC_BITS], 1);
+  team_sync<TEAM>();
+  if (tid < 32) {
+    int run = 0;
+    for (int k0 = 0; k0 < G; k0 += 32) {
+      const int v = cnt[k0 + lane];
+      int x = v;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += y;
+      }
+      beg[k0 + lane] = run + x - v;
+      run += __shfl_sync(FULL, x, 31);
+    }
+    if (lane == 0) beg[G] = run;
+  }
+  team_sync<TEAM>();
+  int pairs = 0;
+  for (int ka = 0; ka < G;) {
+    // the longest target range [ka, kb) whose entries fit (at least one target)
+    int lo = ka + 1, hi = G;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (beg[mid] - beg[ka] <= EW) lo = mid;
+      else hi = mid - 1;
+    }
+    const int kb = lo, base = beg[ka];
+    if (beg[kb] - base <= EW) {
+      for (int k = ka + tid; k < kb; k += TEAM) cnt[k] = beg[k] - base;
+      team_sync<TEAM>();
+      for (int i = tid; i < c; i += TEAM) {
+        const unsigned e = list[i];
+        const int k = (int)(e >> NEAR_SRC_BITS);
+        if (k >= ka && k < kb) ent[atomicAdd(&cnt[k], 1)] = e & ((1u << NEAR_SRC_BITS) - 1u);
+      }
+      team_sync<TEAM>();
+      for (int k = ka + tid; k < kb; k += TEAM) {
+        const int64_t t = tg0 + k;
+        const int b0 = beg[k] - base, b1 = beg[k + 1] - base;
+        sort_entries(ent + b0, b1 - b0);
+        const double4_32a x = a.tgt64[t];
+        const double invd = 1.0 / x.w;
+        double n0 = 0, n1 = 0, n2 = 0;
+        for (int i = b0; i < b1; ++i)
+          Near64<L>::eval(x, a.xyz, a.w, a.dens, a.nrm, (int)ent[i], a.scale, invd, n0, n1, n2);
+        pairs += b1 - b0;
+        fin(t, n0, n1, n2);
+      }
+    } else if (tid < 32) {
+      // target ka alone has more near pairs than R holds: the team's first
+      // warp rescans for it
+      const int64_t t = tg0 + ka;
+      double n0, n1, n2;
+      rescan_target<L>(oa, t, n0, n1, n2);
+      if (lane == 0) {
+        pairs += beg[ka + 1] - base;
+        fin(t, n0, n1, n2);
+      }
+    }
+    team_sync<TEAM>();
+    ka = kb;
+  }
+  return pairs;
+}
+
+// Near sums of targets t0 .. t0 + nt - 1 (whole groups) by the calling CTA:
+// warp w takes groups w, w + warps, ...; R holds near_warp_words(group) shared
+// words per warp.
+template <class L, class Fin>
+__device__ __forceinline__ int near_groups(const OverflowArgs& oa, const FinishArgs& a,
+                                           int64_t t0, int nt, unsigned* R, Fin fin) {
+  const int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int W = near_warp_words(a.group);
+  int pairs = 0;
+  for (int q = wid; q < nt / a.group; q += nw)
+    pairs += near_group<L, 32>(oa, a, t0 / a.group + q, R + (size_t)wid * W, threadIdx.x & 31,
+                               fin);
+  return pairs;
+}
+
+// Target t of a direct evaluation: its chunk partials in chunk order plus its
+// FP64 near sum, written at the target's original index.
+__device__ __forceinline__ void finish_merge(const FinishArgs& a, int64_t t, double n0, double n1,
+                                             double n2) {
   double u0 = 0, u1 = 0, u2 = 0;
   for (int c = 0; c < a.n_chunks; ++c) {
     const double* p = a.part + ((size_t)c * a.M_pad + t) * 3;
@@ -975,13 +1192,10 @@ __device__ __forceinline__ int finish_target(const FinishArgs& a, int64_t t) {
     u1 += p[1];
     u2 += p[2];
   }
-  double n0, n1, n2;
-  const int cnt = near_sum<L>(a, t, n0, n1, n2);
   const int j = a.perm[t];
   a.u[3 * j] = u0 + n0;
   a.u[3 * j + 1] = u1 + n1;
   a.u[3 * j + 2] = u2 + n2;
-  return cnt;
 }
 
 // Drop from L2, without writing them back, the 128-byte lines lying wholly
@@ -1007,11 +1221,12 @@ __device__ __forceinline__ void discard_block_scratch(const FinishArgs& fa, int6
 
 // Finish targets t0 .. t0 + nt - 1 (of M real ones) of a target block whose
 // chunks are all done: overflow rescans (if any list overflowed), FP64 near
-// sums and chunk merge, and the near-pair count. Run by a whole CTA; kept out
-// of line so that the pair loop's register allocation does not carry it.
+// sums and chunk merge, and the near-pair count. Run by a whole CTA, with
+// near_warp_words(group) free shared words per warp at sm; kept out of line
+// so that the pair loop's register allocation does not carry it.
 template <class L>
 __device__ __noinline__ void finish_block(const OverflowArgs& oa, const FinishArgs& fa, int64_t M,
-                                          int64_t t0, int nt) {
+                                          int64_t t0, int nt, unsigned* sm) {
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
   if (*(volatile const unsigned long long*)&fa.flags[FLAG_OVERFLOW] != 0ull) {
     for (int i = wid; i < nt; i += nw)
@@ -1019,9 +1234,9 @@ __device__ __noinline__ void finish_block(const OverflowArgs& oa, const FinishAr
     __syncthreads();
     __threadfence_block();
   }
-  int cnt = 0;
-  for (int i = tid; i < nt; i += blockDim.x)
-    if (t0 + i < M) cnt += finish_target<L>(fa, t0 + i);
+  int cnt = near_groups<L>(oa, fa, t0, nt, sm, [&](int64_t t, double n0, double n1, double n2) {
+    if (t < M) finish_merge(fa, t, n0, n1, n2);
+  });
   for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(FULL, cnt, o);
   if (lane == 0 && cnt) atomicAdd(fa.flags + FLAG_NEAR_PAIRS, (unsigned long long)cnt);
   __syncthreads();  // every read of the block's partials and near lists is done

@@ -180,7 +180,11 @@ __global__ void __launch_bounds__(TPB32, SERVE_MINB)
     if (s_finish) {
       // last chunk of this target block: finish the block's targets
       __threadfence();
-      finish_block<SLayer>(d.oa, d.fa, d.M, (int64_t)tb * SERVE_TGT_CTA, SERVE_TGT_CTA);
+      static_assert(pair_smem_bytes<SLayer, SERVE_NP>() / 4 >=
+                        (size_t)(TPB32 / 32) * near_warp_words(64 * SERVE_NP),
+                    "finish scratch");
+      finish_block<SLayer>(d.oa, d.fa, d.M, (int64_t)tb * SERVE_TGT_CTA, SERVE_TGT_CTA,
+                           reinterpret_cast<unsigned*>(sm));
       __syncthreads();
       if (tid == 0) {
         __threadfence();
@@ -386,6 +390,7 @@ void publish(sk_server* srv, int slot) {
                       b.src_xyz, b.src_w, b.dens, b.nrm, scale, b.flags, b.near_ovf};
   d.fa = FinishArgs{b.tgt64, b.tgt_perm, b.M_pad, b.n_chunks, b.part, b.near_cnt, b.near_idx,
                     b.near_ovf, b.src_xyz, b.src_w, b.dens, b.nrm, scale, b.u, b.flags};
+  d.oa.group = d.fa.group = 64 * SERVE_NP;
   d.n_tb = (int)(b.M_pad / SERVE_TGT_CTA);
   d.tb_done = sl.tb_counters;
   d.tb_finished = sl.tb_counters + d.n_tb;
@@ -694,7 +699,7 @@ int serve_submit(sk_server* srv, const sk_request* q, uint64_t* ticket) {
   if (srv->failed) return SK_ECUDA;
   if (q->capsule) return submit_capsule(srv, q, ticket);
   const int64_t N = q->n_src, M = q->n_tgt;
-  if (N < 0 || M < 1 || N > (int64_t(1) << 30) || M > (int64_t(1) << 30)) return SK_EINVAL;
+  if (N < 0 || M < 1 || N > FP32C_MAX_SOURCES || M > (int64_t(1) << 30)) return SK_EINVAL;
   if (N > 0 && (!q->src_xyz || !q->src_w || !q->f)) return SK_EINVAL;
   if (!q->tgt_xyz || !q->delta || !(q->n_delta == 1 || q->n_delta == M)) return SK_EINVAL;
   if (!(q->mu > 0.0 && q->mu < INFINITY)) return SK_EINVAL;

@@ -317,6 +317,51 @@ def test_near_list_overflow_rescan(ctx):
     assert_close(u, oracle.sl(s.X, s.w, f, s.X, 3 * s.h), sk.SK_FP32C)
 
 
+def _long_list_case(n_far, seed):
+    """Sphere m = 33 (3960 active nodes) with rho_T = 2: one target near all
+    of them, a list longer than a warp's near-sum scratch, so the finish
+    rescans it; one with ~300 near pairs (more than the 96 slots per target
+    of the pooled group lists, within the group's capacity; the heapsort
+    path); one with a few dozen; and n_far targets 10 away with none."""
+    s = ci.make_surface(ci.Sphere(1.0), 33)
+    rng = np.random.default_rng(seed)
+    f = rng.standard_normal((s.N, 3))
+    near = s.X[rng.choice(s.N, 3, replace=False)] * np.array([[1.0], [1.0], [1.01]])
+    far = rng.standard_normal((n_far, 3))
+    far = 10.0 * far / np.linalg.norm(far, axis=1, keepdims=True) * rng.uniform(1.0, 1.5, (n_far, 1))
+    Y = np.concatenate([near, far])
+    delta = np.concatenate([[1.0, 0.25, s.h], np.full(n_far, s.h)])
+    return s, f, Y, delta
+
+
+@pytest.mark.parametrize("n_far", [61, 320_000])
+def test_long_near_lists_without_overflow(ctx, n_far):
+    """Near lists are pooled per target group: a target may hold far more
+    than 96 near pairs as long as its group's list has room, and a target
+    with more than a warp's scratch is rescanned in the finish. 64 targets
+    run one pair per lane and the separate finish; 320,003 run two pairs per
+    lane and the finish inside the pair kernel."""
+    s, f, Y, delta = _long_list_case(n_far, 7)
+    try:
+        sk.sk_set_fp32c_thresholds(ctx, 2.0, 5.0)
+        u = sk.stokes_sl_eval(ctx, sk.SK_FP32C, sk.SK_HOST, s.X, s.w, f, Y, delta)
+        st = sk.sk_last_eval_stats(ctx)
+    finally:
+        sk.sk_set_fp32c_thresholds(ctx, 0.5, 5.0)
+    assert st["overflow_targets"] == 0
+    assert st["finish_fused"] == int(expected_fused(len(Y)))
+    pick = np.concatenate([[0, 1, 2], 3 + np.random.default_rng(8).choice(n_far, 61, replace=False)])
+    ref = oracle.sl(s.X, s.w, f, Y[pick], delta[pick])
+    assert_close(u[pick], ref, sk.SK_FP32C)
+    # the three near targets against their own sums (the far ones are small)
+    for i in range(3):
+        assert rel_l2(u[i], ref[i]) <= 1e-6
+    rho = np.linalg.norm(Y[:3, None, :] - s.X[None, s.w != 0], axis=-1) / delta[:3, None]
+    n_near = (rho < 2.0).sum(axis=1)
+    assert n_near[0] > 3000 and 96 < n_near[1] < 1900 and 0 < n_near[2] < 96
+    assert abs(st["near_pairs"] - int(n_near.sum())) <= 3  # FP32 vs FP64 at rho = 2
+
+
 @pytest.mark.parametrize("rho_T,rho_c", [(0.25, 5.0), (1.0, 5.0), (0.5, 4.5), (0.5, 6.0)])
 def test_fp32c_threshold_variants(ctx, rbc, rho_T, rho_c):
     w, ref, _ = rbc
