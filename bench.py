@@ -1057,10 +1057,12 @@ def extras(sk, h, w, X, W, F, Y, D, out, u_fp32, stream, dev, torch, serve_futur
             res["serving"] = serving_bench(sk, h, serve_future.result())
         except Exception as e:  # report, but keep the headline line
             res["serving"] = {"error": repr(e)}
-    try:
-        res["serving_capsule_sweep"] = capsule_sweep_bench(sk, h)
-    except Exception as e:
-        res["serving_capsule_sweep"] = {"error": repr(e)}
+    res["serving_capsule_sweep"] = {}
+    for m in (33, 65):
+        try:
+            res["serving_capsule_sweep"][f"m{m}"] = capsule_sweep_bench(sk, h, m=m)
+        except Exception as e:
+            res["serving_capsule_sweep"][f"m{m}"] = {"error": repr(e)}
     return res
 
 

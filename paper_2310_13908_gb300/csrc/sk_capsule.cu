@@ -279,9 +279,25 @@ const unsigned long long* capsule_sticky(const sk_capsule* c) { return c->sticky
 // The inputs of one step's single layer, enqueued on st: with a membrane the
 // weights psi W h^2 and the Skalak force at the current nodes (else the
 // capsule's f), delta* when it is automatic; b's inputs and output are
-// pointed at the capsule's arrays. The same operations as a capsule_step.
-void capsule_enqueue_step_inputs(sk_capsule* c, EvalBufs& b, cudaStream_t st) {
-  if (c->mop) enqueue_skalak(*c->mop, c->X, c->ref6, c->Es, c->ED, c->f, c->w, st);
+// pointed at the capsule's arrays. The same operations as a capsule_step, with
+// the membrane operator's scratch copy `set`, so that the steps of capsules
+// of one grid order can be prepared on different streams at once.
+int capsule_prepare_sets(sk_capsule* c, int n_sets) {
+  if (!c->mop) return SK_OK;
+  for (int i = 0; i < n_sets; ++i) {
+    MembraneOp* op = nullptr;
+    const int rc = membrane_scratch_set(c->ctx, c->mop, i, &op);
+    if (rc != SK_OK) return rc;
+  }
+  return SK_OK;
+}
+
+void capsule_enqueue_step_inputs(sk_capsule* c, EvalBufs& b, cudaStream_t st, int set) {
+  if (c->mop) {
+    MembraneOp* op = nullptr;
+    membrane_scratch_set(c->ctx, c->mop, set, &op);  // built by capsule_prepare_sets
+    enqueue_skalak(*op, c->X, c->ref6, c->Es, c->ED, c->f, c->w, st);
+  }
   if (c->auto_delta) {
     cudaMemsetAsync(c->patch_max, 0, 8 * sizeof(unsigned long long), st);
     k_delta_star_patch<<<blocks(c->N), 256, 0, st>>>(c->X, c->m, c->patch_max);

@@ -307,7 +307,10 @@ int64_t capsule_node_count(const sk_capsule* c);
 EvalShape capsule_step_shape(const sk_capsule* c);
 const double* capsule_nodes(const sk_capsule* c);
 const unsigned long long* capsule_sticky(const sk_capsule* c);
-void capsule_enqueue_step_inputs(sk_capsule* c, EvalBufs& b, cudaStream_t st);
+// set: the membrane operator's scratch copy used on st (see
+// membrane_scratch_set; capsule_prepare_sets builds them beforehand).
+int capsule_prepare_sets(sk_capsule* c, int n_sets);
+void capsule_enqueue_step_inputs(sk_capsule* c, EvalBufs& b, cudaStream_t st, int set);
 void capsule_enqueue_step_update(sk_capsule* c, const unsigned long long* flags, double dt,
                                  const sk_flow& fl, cudaStream_t st);
 void capsule_clear_sticky(sk_capsule* c, cudaStream_t st);
@@ -318,6 +321,7 @@ void free_fmm_ops(sk_ctx* ctx);
 // sk_membrane.cu: overset finite-difference derivatives and the Skalak force
 // on the six-patch grid of order m (built once per m and cached in ctx).
 int membrane_op(sk_ctx* ctx, int m, MembraneOp** out);
+int membrane_scratch_set(sk_ctx* ctx, MembraneOp* op, int i, MembraneOp** out);
 void free_membrane_ops(sk_ctx* ctx);
 int64_t membrane_nodes(const MembraneOp& op);
 // Wraw (optional): the area element W itself.

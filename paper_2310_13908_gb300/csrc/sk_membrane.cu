@@ -26,6 +26,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <cmath>
+#include <mutex>
 #include <new>
 #include <thread>
 #include <vector>
@@ -35,6 +36,7 @@
 namespace sk {
 
 constexpr int MEM_FMAX = 9;  // fields per pass (Lambda has 6, positions 3)
+constexpr int MEM_SCRATCH_SETS = 4;  // scratch copies for concurrent streams (serving)
 
 struct MembraneOp {
   int m = 0, n = 0, E = 0;  // E = m + 5: extended grid (indices -2..m+2)
@@ -73,6 +75,10 @@ struct MembraneOp {
   double *Xc = nullptr, *Wc = nullptr, *fc = nullptr, *uc = nullptr;  // coarse staging
   double* dtgt = nullptr;        // [N] delta per coarse target
   unsigned long long* pmax = nullptr;  // [8] delta_u per patch (double bits)
+  // copies that share the tables above and own their scratch, so that
+  // their kernels may run on different streams at once (built on demand)
+  MembraneOp* sets[MEM_SCRATCH_SETS] = {};
+  bool owns_tables = true;
 };
 
 namespace {
@@ -691,16 +697,43 @@ __global__ void k_delta_targets(const MembraneOp op) {
 
 void free_op(MembraneOp* op) {
   if (!op) return;
-  for (void* p : {(void*)op->ghost_dst, (void*)op->gtap_ptr, (void*)op->gtap_cell,
-                  (void*)op->gtap_w, (void*)op->psi_own, (void*)op->btap_ptr,
-                  (void*)op->btap_cell, (void*)op->btap_w, (void*)op->thomas, (void*)op->g,
-                  (void*)op->sg, (void*)op->ext, (void*)op->du, (void*)op->dv, (void*)op->sdu,
-                  (void*)op->sdv, (void*)op->gu, (void*)op->gv, (void*)op->cur_t, (void*)op->red,
-                  (void*)op->ucell1, (void*)op->ubasis1, (void*)op->psi_up, (void*)op->Xu,
-                  (void*)op->Fu, (void*)op->wu, (void*)op->Xc, (void*)op->Wc, (void*)op->fc,
-                  (void*)op->uc, (void*)op->dtgt, (void*)op->pmax})
+  for (MembraneOp* c : op->sets) free_op(c);
+  for (void* p : {(void*)op->g, (void*)op->sg, (void*)op->ext, (void*)op->du, (void*)op->dv,
+                  (void*)op->sdu, (void*)op->sdv, (void*)op->gu, (void*)op->gv, (void*)op->cur_t,
+                  (void*)op->red})
     if (p) cudaFree(p);
+  if (op->owns_tables)
+    for (void* p : {(void*)op->ghost_dst, (void*)op->gtap_ptr, (void*)op->gtap_cell,
+                    (void*)op->gtap_w, (void*)op->psi_own, (void*)op->btap_ptr,
+                    (void*)op->btap_cell, (void*)op->btap_w, (void*)op->thomas, (void*)op->ucell1,
+                    (void*)op->ubasis1, (void*)op->psi_up, (void*)op->Xu, (void*)op->Fu,
+                    (void*)op->wu, (void*)op->Xc, (void*)op->Wc, (void*)op->fc, (void*)op->uc,
+                    (void*)op->dtgt, (void*)op->pmax})
+      if (p) cudaFree(p);
   delete op;
+}
+
+// The scratch of up to MEM_FMAX fields (values, spline data, extended
+// blocks, derivatives, tangents, reduction partials).
+cudaError_t alloc_scratch(MembraneOp* op) {
+  cudaError_t e = cudaSuccess;
+  auto ok = [&](cudaError_t r) {
+    if (e == cudaSuccess) e = r;
+  };
+  const int E = op->E;
+  const size_t fn = (size_t)MEM_FMAX * op->N * sizeof(double);
+  ok(cudaMalloc(&op->g, fn));
+  ok(cudaMalloc(&op->sg, 3 * fn));
+  ok(cudaMalloc(&op->ext, (size_t)MEM_FMAX * 6 * E * E * sizeof(double)));
+  ok(cudaMalloc(&op->du, fn));
+  ok(cudaMalloc(&op->dv, fn));
+  ok(cudaMalloc(&op->sdu, 3 * fn));
+  ok(cudaMalloc(&op->sdv, 3 * fn));
+  ok(cudaMalloc(&op->gu, fn));
+  ok(cudaMalloc(&op->gv, fn));
+  ok(cudaMalloc(&op->cur_t, 6 * op->N * sizeof(double)));
+  ok(cudaMalloc(&op->red, (13 * (((size_t)op->N + 127) / 128) + 16) * sizeof(double)));
+  return e;
 }
 
 template <class T>
@@ -811,18 +844,7 @@ int build_op(int m, MembraneOp** out, std::string& err) {
   ok(upload(&op->btap_cell, bcell));
   ok(upload(&op->btap_w, bw));
   ok(upload(&op->thomas, th));
-  const size_t fn = (size_t)MEM_FMAX * op->N * sizeof(double);
-  ok(cudaMalloc(&op->g, fn));
-  ok(cudaMalloc(&op->sg, 3 * fn));
-  ok(cudaMalloc(&op->ext, (size_t)MEM_FMAX * 6 * E * E * sizeof(double)));
-  ok(cudaMalloc(&op->du, fn));
-  ok(cudaMalloc(&op->dv, fn));
-  ok(cudaMalloc(&op->sdu, 3 * fn));
-  ok(cudaMalloc(&op->sdv, 3 * fn));
-  ok(cudaMalloc(&op->gu, fn));
-  ok(cudaMalloc(&op->gv, fn));
-  ok(cudaMalloc(&op->cur_t, 6 * op->N * sizeof(double)));
-  ok(cudaMalloc(&op->red, (13 * (((size_t)op->N + 127) / 128) + 16) * sizeof(double)));
+  ok(alloc_scratch(op));
   if (e != cudaSuccess) {
     err = std::string("membrane operator: ") + cudaGetErrorString(e);
     free_op(op);
@@ -1028,6 +1050,35 @@ int membrane_op(sk_ctx* ctx, int m, MembraneOp** out) {
   if (const char* v = std::getenv("SK_SLOPE_STAGING")) op->slope_staging = std::strcmp(v, "0") != 0;
   ctx->membrane_ops.push_back({m, op});
   *out = op;
+  return SK_OK;
+}
+
+// Scratch copy i (0 <= i < MEM_SCRATCH_SETS) of op: op's tables, its own
+// scratch. Built on first use; the copies live as long as op.
+int membrane_scratch_set(sk_ctx* ctx, MembraneOp* op, int i, MembraneOp** out) {
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lk(mu);
+  if (i < 0 || i >= MEM_SCRATCH_SETS) return SK_EINVAL;
+  if (!op->sets[i]) {
+    MembraneOp* c = new (std::nothrow) MembraneOp(*op);
+    if (!c) return SK_ENOMEM;
+    c->owns_tables = false;
+    for (MembraneOp*& q : c->sets) q = nullptr;
+    c->g = c->sg = c->ext = c->du = c->dv = c->sdu = c->sdv = c->gu = c->gv = c->cur_t =
+        c->red = nullptr;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(ctx->device);
+    const cudaError_t e = alloc_scratch(c);
+    if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);
+    if (e != cudaSuccess) {
+      free_op(c);
+      ctx->err = std::string("membrane scratch: ") + cudaGetErrorString(e);
+      return e == cudaErrorMemoryAllocation ? SK_ENOMEM : SK_ECUDA;
+    }
+    op->sets[i] = c;
+  }
+  *out = op->sets[i];
   return SK_OK;
 }
 

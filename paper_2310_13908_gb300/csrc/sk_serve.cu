@@ -302,10 +302,15 @@ bool kernel_running(sk_server* srv) {
   return false;
 }
 
-void launch_kernel(sk_server* srv) {
+// capsules: some resident request is a capsule's. Its steps prepare with
+// FP64 membrane kernels between the sums, and those run only on the CTA
+// slots the persistent kernel leaves free: then the kernel leaves one slot
+// per SM (SERVE_MINB - 1 CTAs per SM) instead of SERVE_RESERVE_CTAS in all.
+void launch_kernel(sk_server* srv, bool capsules) {
   const size_t smem = pair_smem_bytes<SLayer, SERVE_NP>();
   cudaFuncSetAttribute(k_serve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  int grid = srv->ctx->sm_count * SERVE_MINB - SERVE_RESERVE_CTAS;
+  int grid = capsules ? srv->ctx->sm_count * (SERVE_MINB - 1)
+                      : srv->ctx->sm_count * SERVE_MINB - SERVE_RESERVE_CTAS;
   if (grid < 1) grid = 1;
   // the previous instance has ended (stream order): clear its busy count and
   // exit flag, but not the host's stop word
@@ -317,19 +322,19 @@ void launch_kernel(sk_server* srv) {
   srv->kernel_launched = true;
 }
 
-// Capsule steps prepare on the context's stream: the membrane operator's
-// scratch is shared by every capsule of a grid order on the context, so its
-// uses (served steps of several capsules, and the caller's own capsule_step
-// or membrane_force calls) must follow one another.
-cudaStream_t capsule_stream(sk_server* srv) { return srv->ctx->stream; }
+// A capsule request's steps run on its slot's preparation stream, with that
+// stream's scratch copy of the membrane operator: capsules of one grid order
+// in different slots prepare at the same time, and the steps of one capsule
+// follow one another on its stream.
+int capsule_set(int slot) { return slot % SERVE_PREP_STREAMS; }
 
 // One step of a capsule request, on st: the inputs of its sum (membrane
 // force, weights, delta* at the current nodes), cleared counters and the
 // preparation kernels; the step's items are published when st reaches
 // prep_done.
-void enqueue_capsule_step(sk_server* srv, Slot& sl, cudaStream_t st) {
+void enqueue_capsule_step(sk_server* srv, Slot& sl, int slot, cudaStream_t st) {
   Req* r = sl.req;
-  capsule_enqueue_step_inputs(r->cap, sl.b, st);
+  capsule_enqueue_step_inputs(r->cap, sl.b, st, capsule_set(slot));
   const int n_tb = (int)(sl.b.M_pad / SERVE_TGT_CTA);
   cudaMemsetAsync(sl.tb_counters, 0, (n_tb + 1) * sizeof(int), st);
   enqueue_prep(r->shape, sl.b, srv->ctx->rho_T, srv->ctx->rho_c, st);
@@ -356,9 +361,8 @@ bool admit_one(sk_server* srv, Req* r, Slot& sl, int slot) {
   const EvalShape& s = r->shape;
   cudaStream_t st = srv->s_prep[slot % SERVE_PREP_STREAMS];
   if (r->cap) {  // the first step of a capsule request: its inputs are resident
-    st = capsule_stream(srv);
     capsule_clear_sticky(r->cap, st);
-    enqueue_capsule_step(srv, sl, st);
+    enqueue_capsule_step(srv, sl, slot, st);
     r->st.admit_us = now_us(srv);
     return true;
   }
@@ -445,14 +449,14 @@ void scheduler(sk_server* srv) {
           // a capsule step's sum is done: update the nodes, then the next
           // step, or read the nodes back after the last one
           Req* r = sl.req;
-          cudaStream_t st = capsule_stream(srv);
+          cudaStream_t st = srv->s_prep[i % SERVE_PREP_STREAMS];
           capsule_enqueue_step_update(r->cap, sl.b.flags, r->dt, r->flow, st);
           if (++r->steps_done < r->steps) {
             {
               std::unique_lock<std::mutex> lk(srv->mu);
               sl.seq = srv->next_seq++;
             }
-            enqueue_capsule_step(srv, sl, st);
+            enqueue_capsule_step(srv, sl, i, st);
             sl.state = SlotState::Prep;
           } else {
             r->st.done_us = now_us(srv);
@@ -501,7 +505,11 @@ void scheduler(sk_server* srv) {
       }
     }
     if (any_running && !kernel_running(srv)) {
-      launch_kernel(srv);
+      bool capsules = false;
+      for (int i = 0; i < srv->n_slots; ++i)
+        capsules |= srv->slots[i].state != SlotState::Free && srv->slots[i].req &&
+                    srv->slots[i].req->cap;
+      launch_kernel(srv, capsules);
       progress = true;
     }
     const cudaError_t e = cudaGetLastError();
@@ -668,6 +676,12 @@ int submit_capsule(sk_server* srv, const sk_request* q, uint64_t* ticket) {
   if (r->footprint > srv->arena_bytes || bytes > srv->stage_bytes) {
     delete r;
     return SK_ENOMEM;
+  }
+  // the membrane operator's scratch copies of the preparation streams
+  const int rc = capsule_prepare_sets(c, SERVE_PREP_STREAMS);
+  if (rc != SK_OK) {
+    delete r;
+    return rc;
   }
   std::unique_lock<std::mutex> lk(srv->mu);
   if ((int)srv->queue.size() >= srv->cfg.queue_capacity ||
