@@ -185,8 +185,10 @@ constexpr int KM_SMEM_SUMS = 512;      // clusters whose sums a block gathers in
 // centre select the candidates: their error is below 1e-6 (d^2 + S^2), S the
 // largest coordinate magnitude of point and centres, so every centre within
 // 2^-16 (m + S^2) of the FP32 minimum m is a candidate and the FP64 minimum is
-// always among them; the FP64 distances of the candidates decide. -1 for a
-// zero-weight point. C32: FP32 centres (x, y, z, largest |coordinate|).
+// always among them. A point with a single candidate takes it (the FP64
+// minimum then is that centre); the FP64 distances decide between several,
+// in a pass that only blocks holding such points run. -1 for a zero-weight
+// point. C32: FP32 centres (x, y, z, largest |coordinate|).
 __global__ void __launch_bounds__(FMM_TPB) k_km_assign32(const double* __restrict__ X,
                                                          const double* __restrict__ w, int64_t N,
                                                          const double* __restrict__ C,
@@ -198,7 +200,8 @@ __global__ void __launch_bounds__(FMM_TPB) k_km_assign32(const double* __restric
   const int64_t ii = i < N ? i : N - 1;
   const double x = X[3 * ii], y = X[3 * ii + 1], z = X[3 * ii + 2];
   const float xf = (float)x, yf = (float)y, zf = (float)z;
-  float m32 = INFINITY, cmax = 0.f;
+  float m1 = INFINITY, m2 = INFINITY, cmax = 0.f;  // smallest, second smallest
+  int j1 = 0;
   for (int j0 = 0; j0 < k; j0 += KM_SMEM_CENTRES) {
     const int nj = min(KM_SMEM_CENTRES, k - j0);
     __syncthreads();
@@ -207,32 +210,43 @@ __global__ void __launch_bounds__(FMM_TPB) k_km_assign32(const double* __restric
     for (int j = 0; j < nj; ++j) {
       const float4 c = sc[j];
       const float dx = xf - c.x, dy = yf - c.y, dz = zf - c.z;
-      m32 = fminf(m32, dx * dx + dy * dy + dz * dz);
+      const float d = dx * dx + dy * dy + dz * dz;
+      if (d < m1) {
+        m2 = m1;
+        m1 = d;
+        j1 = j0 + j;
+      } else {
+        m2 = fminf(m2, d);
+      }
       cmax = fmaxf(cmax, c.w);
     }
   }
   const float S = fmaxf(fabsf(xf), fmaxf(fabsf(yf), fabsf(zf))) + cmax;
-  const float lim = m32 + 1.52587890625e-05f * (m32 + S * S);  // 2^-16
-  double best = INFINITY;
-  int bj = 0;
-  for (int j0 = 0; j0 < k; j0 += KM_SMEM_CENTRES) {
-    const int nj = min(KM_SMEM_CENTRES, k - j0);
-    if (k > KM_SMEM_CENTRES) {  // restage (the staged centres are the last chunk otherwise)
-      __syncthreads();
-      for (int j = threadIdx.x; j < nj; j += blockDim.x) sc[j] = C32[j0 + j];
-      __syncthreads();
-    }
-    for (int j = 0; j < nj; ++j) {
-      const float4 c = sc[j];
-      const float fx = xf - c.x, fy = yf - c.y, fz = zf - c.z;
-      if (fx * fx + fy * fy + fz * fz > lim) continue;
-      const int jj = j0 + j;
-      const double dx = x - C[3 * jj], dy = y - C[3 * jj + 1], dz = z - C[3 * jj + 2];
-      const double d2 =
-          __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-      if (d2 < best) {
-        best = d2;
-        bj = jj;
+  const float lim = m1 + 1.52587890625e-05f * (m1 + S * S);  // 2^-16
+  const bool several = m2 <= lim;
+  int bj = j1;
+  if (__syncthreads_or(several)) {
+    double best = INFINITY;
+    for (int j0 = 0; j0 < k; j0 += KM_SMEM_CENTRES) {
+      const int nj = min(KM_SMEM_CENTRES, k - j0);
+      if (k > KM_SMEM_CENTRES) {  // restage (the staged centres are the last chunk otherwise)
+        __syncthreads();
+        for (int j = threadIdx.x; j < nj; j += blockDim.x) sc[j] = C32[j0 + j];
+        __syncthreads();
+      }
+      if (!several) continue;
+      for (int j = 0; j < nj; ++j) {
+        const float4 c = sc[j];
+        const float fx = xf - c.x, fy = yf - c.y, fz = zf - c.z;
+        if (fx * fx + fy * fy + fz * fz > lim) continue;
+        const int jj = j0 + j;
+        const double dx = x - C[3 * jj], dy = y - C[3 * jj + 1], dz = z - C[3 * jj + 2];
+        const double d2 =
+            __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+        if (d2 < best) {
+          best = d2;
+          bj = jj;
+        }
       }
     }
   }
@@ -279,26 +293,36 @@ __global__ void k_km_frame_part(const double* __restrict__ X, const double* __re
 }
 
 __global__ void k_km_frame(const double* __restrict__ part, int nblk, double* __restrict__ frame) {
-  if (threadIdx.x != 0) return;
+  // one warp: lane-strided minima and maxima, then a butterfly (exact in any order)
+  const int lane = threadIdx.x & 31;
   double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-  for (int b = 0; b < nblk; ++b)
+  for (int b = lane; b < nblk; b += 32)
     for (int a = 0; a < 3; ++a) {
       lo[a] = fmin(lo[a], part[6 * b + a]);
       hi[a] = fmax(hi[a], part[6 * b + 3 + a]);
     }
+  for (int o = 16; o > 0; o >>= 1)
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = fmin(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], o));
+      hi[a] = fmax(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
+    }
+  if (threadIdx.x != 0) return;
   double ext = 0.0;
   for (int a = 0; a < 3; ++a) {
     frame[a] = lo[a] <= hi[a] ? lo[a] : 0.0;
     ext = fmax(ext, hi[a] - lo[a]);
   }
   frame[3] = (ext > 0.0 ? ext : 1.0) * 5.820766091346741e-11;  // 2^-34
+  frame[4] = 1.0 / frame[3];
 }
 
 // Exact sums of each cluster's points: every coordinate rounded to a
 // multiple of the quantum q above the box corner (at most 2^34 quanta) and
 // added in 64-bit integers, which makes the sums independent of the order of
-// the additions; point counts likewise. For k <= KM_SMEM_SUMS a block first
-// gathers its points' sums in shared memory.
+// the additions; point counts likewise. A warp first adds up the quanta of
+// its lanes that share a cluster (consecutive points mostly do), so one lane
+// per cluster and warp adds them on; for k <= KM_SMEM_SUMS a block gathers
+// those in shared memory first.
 __global__ void __launch_bounds__(FMM_TPB) k_km_sums(const double* __restrict__ X,
                                                      const int* __restrict__ lab, int64_t N,
                                                      const double* __restrict__ frame, int k,
@@ -315,18 +339,35 @@ __global__ void __launch_bounds__(FMM_TPB) k_km_sums(const double* __restrict__ 
     __syncthreads();
   }
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
   const int l = i < N ? lab[i] : -1;
+  unsigned long long q[3] = {0ull, 0ull, 0ull};
   if (l >= 0) {
-    const double inv = 1.0 / frame[3];
-    unsigned long long q[3];
+    const double inv = frame[4];
     for (int a = 0; a < 3; ++a)
       q[a] = (unsigned long long)llrint(fmax(X[3 * i + a] - frame[a], 0.0) * inv);
+  }
+  // lanes of the same cluster (points without one form their own group)
+  const unsigned grp = __match_any_sync(0xffffffffu, l);
+  unsigned long long s[3] = {0ull, 0ull, 0ull};
+  for (int r = 0; r < 32; ++r) {
+    const unsigned long long a0 = __shfl_sync(0xffffffffu, q[0], r);
+    const unsigned long long a1 = __shfl_sync(0xffffffffu, q[1], r);
+    const unsigned long long a2 = __shfl_sync(0xffffffffu, q[2], r);
+    if ((grp >> r) & 1u) {
+      s[0] += a0;
+      s[1] += a1;
+      s[2] += a2;
+    }
+  }
+  if (l >= 0 && lane == __ffs(grp) - 1) {
+    const unsigned n = (unsigned)__popc(grp);
     if (local) {
-      for (int a = 0; a < 3; ++a) atomicAdd(&ss[l][a], q[a]);
-      atomicAdd(&sn[l], 1u);
+      for (int a = 0; a < 3; ++a) atomicAdd(&ss[l][a], s[a]);
+      atomicAdd(&sn[l], n);
     } else {
-      for (int a = 0; a < 3; ++a) atomicAdd(&sums[3 * l + a], q[a]);
-      atomicAdd(&cnt[l], 1u);
+      for (int a = 0; a < 3; ++a) atomicAdd(&sums[3 * l + a], s[a]);
+      atomicAdd(&cnt[l], n);
     }
   }
   if (local) {
@@ -970,7 +1011,7 @@ int stokes_sl_eval_fmm(sk_ctx* ctx, int precision, int mem, int64_t n_src,
     c.near = b.take<unsigned char>((size_t)k * k);
     c.ucheck = b.take<double>((size_t)k * n3 * (fp32 ? FMM_CHECK_SPLIT : 1));
     c.phi = b.take<double>((size_t)k * n3);
-    c.frame = b.take<double>(4);
+    c.frame = b.take<double>(5);  // corner, quantum q, 1 / q
     c.frame_part = b.take<double>(6 * 128);
     c.C32 = b.take<float4>(k);
     c.sums = b.take<unsigned long long>(3 * (size_t)k);
