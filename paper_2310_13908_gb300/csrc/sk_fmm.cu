@@ -1192,6 +1192,23 @@ int stokes_sl_eval_fmm(sk_ctx* ctx, int precision, int mem, int64_t n_src,
     }
     item_first.push_back((int)(items.size() / 4));
     const int n_blocks = (int)(m_slots / tb), n_items = (int)(items.size() / 4);
+    {
+      // launch order: most segments first (items keep their partial slots,
+      // so the order changes nothing but the tail of the launch)
+      std::vector<int> work(n_items), order(n_items);
+      for (int q = 0; q < n_items; ++q) {
+        int nseg = 0;
+        for (int t = 0; t < items[4 * q + 2]; ++t) nseg += desc[2 * (items[4 * q + 1] + t) + 1];
+        work[q] = nseg;
+        order[q] = q;
+      }
+      std::stable_sort(order.begin(), order.end(),
+                       [&](int a, int b) { return work[a] > work[b]; });
+      std::vector<int> sorted(items.size());
+      for (int q = 0; q < n_items; ++q)
+        for (int c = 0; c < 4; ++c) sorted[4 * q + c] = items[4 * order[q] + c];
+      items.swap(sorted);
+    }
     if (n_items > 0) {
       // upload the plan: tile_cluster, src_first, block_box, box_first, item_first, items, desc
       std::vector<int> h_plan;
