@@ -19,8 +19,14 @@ namespace {
 #define SK_RS_ITEMS 4
 #endif
 constexpr int RS_THREADS = 256;
-constexpr int RS_ITEMS = SK_RS_ITEMS;  // keys per thread and radix tile
-constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
+constexpr int RS_ITEMS = SK_RS_ITEMS;  // keys per thread and radix tile (large sorts)
+// Up to RS_FINE_MAX keys, tiles of one key per thread: four times the blocks
+// for the same keys, which the short launches of mid-size sorts need.
+constexpr int64_t RS_FINE_MAX = 65536;
+inline int rs_items(int64_t n) { return n <= RS_FINE_MAX ? 1 : RS_ITEMS; }
+inline int rs_tiles(int64_t n, int items) {
+  return (int)((n + (int64_t)RS_THREADS * items - 1) / ((int64_t)RS_THREADS * items));
+}
 constexpr int BBOX_BLOCKS = 128;
 constexpr unsigned FULL = 0xffffffffu;
 
@@ -128,13 +134,15 @@ __global__ void k_morton_keys(const double* __restrict__ xyz, const double* __re
 }
 
 // ---- radix sort: histogram, scan, stable scatter ----------------------------
-// Digit counts of tile blk (of nblk) into column blk of hist[digit][nblk].
+// Digit counts of tile blk (of nblk; ITEMS keys per thread) into column blk
+// of hist[digit][nblk].
+template <int ITEMS>
 __device__ void rs_hist_tile(const uint32_t* __restrict__ keys, int n, int shift,
                              uint32_t* __restrict__ hist, int blk, int nblk, uint32_t* h) {
   h[threadIdx.x] = 0;
   __syncthreads();
-  int base = blk * RS_TILE;
-  for (int r = 0; r < RS_ITEMS; ++r) {
+  int base = blk * RS_THREADS * ITEMS;
+  for (int r = 0; r < ITEMS; ++r) {
     int i = base + r * RS_THREADS + threadIdx.x;
     if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
   }
@@ -142,10 +150,11 @@ __device__ void rs_hist_tile(const uint32_t* __restrict__ keys, int n, int shift
   hist[threadIdx.x * nblk + blk] = h[threadIdx.x];
 }
 
+template <int ITEMS>
 __global__ void k_rs_hist(const uint32_t* __restrict__ keys, int n, int shift,
                           uint32_t* __restrict__ hist) {
   __shared__ uint32_t h[256];
-  rs_hist_tile(keys, n, shift, hist, blockIdx.x, gridDim.x, h);
+  rs_hist_tile<ITEMS>(keys, n, shift, hist, blockIdx.x, gridDim.x, h);
 }
 
 // Exclusive scan of `total` counts by one block of THREADS threads: each
@@ -232,8 +241,10 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_rowscan(uint32_t* __restrict_
   if (threadIdx.x == 0) tot[blockIdx.x] = carry;
 }
 
-// Stable scatter of tile blk (of nblk) to the offsets of column blk of offs,
-// plus digit_base (this thread's digit) when offs holds row prefixes only.
+// Stable scatter of tile blk (of nblk; ITEMS keys per thread) to the offsets
+// of column blk of offs, plus digit_base (this thread's digit) when offs holds
+// row prefixes only.
+template <int ITEMS>
 __device__ void rs_scatter_tile(const uint32_t* __restrict__ kin, const int* __restrict__ vin,
                                 uint32_t* __restrict__ kout, int* __restrict__ vout, int n,
                                 int shift, const uint32_t* __restrict__ offs, uint32_t digit_base,
@@ -241,8 +252,8 @@ __device__ void rs_scatter_tile(const uint32_t* __restrict__ kin, const int* __r
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   base_d[tid] = offs[tid * nblk + blk] + digit_base;
   const unsigned lt = (1u << lane) - 1u;
-  const int base = blk * RS_TILE;
-  for (int r = 0; r < RS_ITEMS; ++r) {
+  const int base = blk * RS_THREADS * ITEMS;
+  for (int r = 0; r < ITEMS; ++r) {
     for (int w = 0; w < RS_THREADS / 32; ++w) wcnt[w][tid] = 0;
     __syncthreads();
     int i = base + r * RS_THREADS + tid;
@@ -269,6 +280,7 @@ __device__ void rs_scatter_tile(const uint32_t* __restrict__ kin, const int* __r
 }
 
 // offs: row prefixes from k_rs_rowscan; tot: the rows' totals.
+template <int ITEMS>
 __global__ void __launch_bounds__(RS_THREADS)
     k_rs_scatter(const uint32_t* __restrict__ kin, const int* __restrict__ vin,
                  uint32_t* __restrict__ kout, int* __restrict__ vout, int n, int shift,
@@ -280,8 +292,8 @@ __global__ void __launch_bounds__(RS_THREADS)
   const uint32_t t = tot[threadIdx.x];
   uint32_t all;
   const uint32_t digit_base = block_scan_incl(t, warp_sums, &all) - t;
-  rs_scatter_tile(kin, vin, kout, vout, n, shift, offs, digit_base, blockIdx.x, gridDim.x, base_d,
-                  wcnt);
+  rs_scatter_tile<ITEMS>(kin, vin, kout, vout, n, shift, offs, digit_base, blockIdx.x, gridDim.x,
+                         base_d, wcnt);
 }
 
 // The whole ordering of a small point set in one block of RS_THREADS threads:
@@ -321,12 +333,12 @@ __global__ void __launch_bounds__(RS_THREADS)
   int *va = vals_a, *vb = vals_b;
   for (int shift = 0; shift < 32; shift += 8) {
     __syncthreads();  // the keys (or the previous pass's scatter) are complete
-    for (int b = 0; b < nblk; ++b) rs_hist_tile(ka, (int)n, shift, hist, b, nblk, h);
+    for (int b = 0; b < nblk; ++b) rs_hist_tile<RS_ITEMS>(ka, (int)n, shift, hist, b, nblk, h);
     __syncthreads();
     rs_scan_block<RS_THREADS>(hist, 256 * nblk, warp_sums);
     __syncthreads();
     for (int b = 0; b < nblk; ++b)
-      rs_scatter_tile(ka, va, kb, vb, (int)n, shift, hist, 0u, b, nblk, base_d, wcnt);
+      rs_scatter_tile<RS_ITEMS>(ka, va, kb, vb, (int)n, shift, hist, 0u, b, nblk, base_d, wcnt);
     uint32_t* tk = ka; ka = kb; kb = tk;
     int* tv = va; va = vb; vb = tv;
   }
@@ -465,7 +477,29 @@ inline unsigned blocks_for(int64_t n, int tpb) { return (unsigned)((n + tpb - 1)
 
 }  // namespace
 
-int sort_grid_blocks(int64_t n) { return (int)((n + RS_TILE - 1) / RS_TILE); }
+// Blocks (tiles) whose digit counts a sort of up to n keys may need: the
+// fine tiling holds more tiles than the coarse one for the same keys.
+int sort_grid_blocks(int64_t n) {
+  const int fine = rs_tiles(n < RS_FINE_MAX ? n : RS_FINE_MAX, 1);
+  const int coarse = rs_tiles(n, RS_ITEMS);
+  return fine > coarse ? fine : coarse;
+}
+
+// One radix pass (8 bits at shift) of n keys in nblk tiles of ITEMS keys per thread.
+static void rs_pass(const uint32_t* ka, const int* va, uint32_t* kb, int* vb, int64_t n, int shift,
+             uint32_t* hist, cudaStream_t st) {
+  const int items = rs_items(n), nblk = rs_tiles(n, items);
+  uint32_t* tot = hist + 256 * (size_t)nblk;  // row totals (hist holds 256 more words)
+  if (items == 1)
+    k_rs_hist<1><<<nblk, RS_THREADS, 0, st>>>(ka, (int)n, shift, hist);
+  else
+    k_rs_hist<RS_ITEMS><<<nblk, RS_THREADS, 0, st>>>(ka, (int)n, shift, hist);
+  k_rs_rowscan<<<256, RS_THREADS, 0, st>>>(hist, nblk, tot);
+  if (items == 1)
+    k_rs_scatter<1><<<nblk, RS_THREADS, 0, st>>>(ka, va, kb, vb, (int)n, shift, hist, tot);
+  else
+    k_rs_scatter<RS_ITEMS><<<nblk, RS_THREADS, 0, st>>>(ka, va, kb, vb, (int)n, shift, hist, tot);
+}
 
 void launch_sort_points(const double* xyz, const double* w, int64_t n, uint32_t* keys_a,
                         uint32_t* keys_b, int* vals_a, int* vals_b, uint32_t* hist,
@@ -474,22 +508,18 @@ void launch_sort_points(const double* xyz, const double* w, int64_t n, uint32_t*
   if (n <= 0) return;
   // tiles of this point set (at most the sort_grid_blocks the buffers hold);
   // the stable order does not depend on the tiling or on the path
-  const int sort_blocks = sort_grid_blocks(n);
   if (n <= small_max_points) {
     k_sort_small<<<1, RS_THREADS, 0, st>>>(xyz, w, n, keys_a, keys_b, vals_a, vals_b, hist, bbox,
-                                           count_out, sort_blocks);
+                                           count_out, rs_tiles(n, RS_ITEMS));
     return;  // four passes: the sorted data is in keys_a / vals_a
   }
   k_bbox_partial<<<BBOX_BLOCKS, RS_THREADS, 0, st>>>(xyz, w, n, bbox_part);
   k_bbox_final<<<1, 6 * 32, 0, st>>>(bbox_part, BBOX_BLOCKS, bbox);
   k_morton_keys<<<blocks_for(n, 256), 256, 0, st>>>(xyz, w, n, bbox, keys_a, vals_a, count_out);
-  uint32_t* tot = hist + 256 * (size_t)sort_blocks;  // row totals (hist holds 256 more words)
   uint32_t *ka = keys_a, *kb = keys_b;
   int *va = vals_a, *vb = vals_b;
   for (int shift = 0; shift < 32; shift += 8) {
-    k_rs_hist<<<sort_blocks, RS_THREADS, 0, st>>>(ka, (int)n, shift, hist);
-    k_rs_rowscan<<<256, RS_THREADS, 0, st>>>(hist, sort_blocks, tot);
-    k_rs_scatter<<<sort_blocks, RS_THREADS, 0, st>>>(ka, va, kb, vb, (int)n, shift, hist, tot);
+    rs_pass(ka, va, kb, vb, n, shift, hist, st);
     uint32_t* tk = ka; ka = kb; kb = tk;
     int* tv = va; va = vb; vb = tv;
   }
@@ -499,15 +529,11 @@ void launch_sort_points(const double* xyz, const double* w, int64_t n, uint32_t*
 int launch_sort_pairs(uint32_t* keys_a, uint32_t* keys_b, int* vals_a, int* vals_b, int64_t n,
                       int bits, uint32_t* hist, cudaStream_t st) {
   if (n <= 0) return 0;
-  const int sort_blocks = sort_grid_blocks(n);
-  uint32_t* tot = hist + 256 * (size_t)sort_blocks;
   uint32_t *ka = keys_a, *kb = keys_b;
   int *va = vals_a, *vb = vals_b;
   int passes = 0;
   for (int shift = 0; shift < bits; shift += 8, ++passes) {
-    k_rs_hist<<<sort_blocks, RS_THREADS, 0, st>>>(ka, (int)n, shift, hist);
-    k_rs_rowscan<<<256, RS_THREADS, 0, st>>>(hist, sort_blocks, tot);
-    k_rs_scatter<<<sort_blocks, RS_THREADS, 0, st>>>(ka, va, kb, vb, (int)n, shift, hist, tot);
+    rs_pass(ka, va, kb, vb, n, shift, hist, st);
     uint32_t* tk = ka; ka = kb; kb = tk;
     int* tv = va; va = vb; vb = tv;
   }
