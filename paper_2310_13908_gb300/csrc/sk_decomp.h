@@ -30,12 +30,21 @@ inline int choose_chunks(int precision, int64_t N, int64_t M, int sm_count) {
   // Many small items balance the ragged last wave better than partial-sum
   // traffic costs (measured at 493k targets: 5 chunks 71.0 ms, 13: 69.1,
   // 29: 68.7, 45: 68.4). Take the fewest chunks that give >= 32 waves filled
-  // to >= 98%; if the problem is too small for that, the fullest waves with
-  // at least four of them.
+  // to >= 98%; if the problem is too small for that, see below (SK_FP32C),
+  // or the fullest waves with at least four of them (SK_FP64).
   auto waves_of = [&](int64_t nc) { return (double)(n_tb * nc) / (double)slots; };
   for (int64_t nc = 1; nc <= cap; ++nc) {
     const double w = waves_of(nc);
     if (w >= 32.0 && w / std::ceil(w) >= 0.98) return (int)nc;
+  }
+  // A grid that cannot fill 32 waves: SK_FP32C takes the most chunks, down to
+  // one source tile each (at most 64). Short items balance the uneven work of
+  // the general (erf/exp) path better than full waves do (measured, evaluation
+  // time by chunks: 24,576 x 15,384 single layer 38: 0.791, 57: 0.752,
+  // 64: 0.740 ms; 98,304 x 60,504: 19: 4.95, 44: 4.71, 64: 4.71 ms).
+  if (fp32) {
+    int64_t many = tiles < 64 ? tiles : 64;
+    return (int)(many < 1 ? 1 : many);
   }
   int best = (int)cap;
   double best_eff = -1.0;

@@ -77,8 +77,9 @@ def test_measured_shapes(decompose):
     c3, c2, c1_64, c1_32 = decompose([(FP32C, 393216, 493216, SMS), (FP32C, 24576, 24576, SMS),
                                       (FP64, 1944, 1944, SMS), (FP32C, 1944, 1944, SMS)])
     assert c3 == (22, 256, 1, 2) and _blocks(493216, 2) * 22 == 10604
-    # the cell at m = 65: 48 target blocks, separate finish kernels
-    assert c2[2] == 0 and _blocks(24576, 1) == 48 and c2[3] == 1
+    # the cell at m = 65: 48 target blocks, separate finish kernels; too small
+    # for 32 full waves, so the most chunks (64: measured fastest)
+    assert c2[2] == 0 and _blocks(24576, 1) == 48 and c2[3] == 1 and c2[0] == 64
     # the sphere at m = 19 in FP64: 64-thread CTAs, one 128-source tile per chunk
     assert c1_64[1] == 64 and c1_64[0] == math.ceil(1944 / 128)
     assert c1_32[2] == 0
@@ -109,12 +110,17 @@ def test_chunk_counts_fill_waves(decompose):
             cases.append((FP32C, N, M, SMS))
     for (p, N, M, sm), (nc, t64, fused, np_) in zip(cases, decompose(cases)):
         tiles = -(-max(N, 1) // 256)
-        assert 1 <= nc <= max(1, min(64, tiles // 2)), (N, M, nc)
+        many = max(1, min(64, tiles))
+        assert 1 <= nc <= many, (N, M, nc)
         slots = sm * (2 if np_ == 2 else 3)
         waves = _blocks(M, np_) * nc / slots
+        cap = max(1, min(64, tiles // 2))
         # enough work: at least 32 waves, the last one at least 98% full
-        if _blocks(M, np_) * min(64, max(1, tiles // 2)) / slots >= 40:
+        if _blocks(M, np_) * cap / slots >= 40:
             assert waves >= 32 and waves / math.ceil(waves) >= 0.98, (N, M, nc, waves)
+        # too little for 32 waves: the most chunks, down to one tile each
+        if _blocks(M, np_) * cap / slots < 32:
+            assert nc == many, (N, M, nc)
         assert t64 == 256  # the FP64 CTA size is not touched on the FP32C path
 
 
