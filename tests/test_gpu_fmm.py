@@ -100,6 +100,30 @@ def test_fmm_at_larger_size_and_device_memory(ctx, prec):
     assert rel(u, d) < 1e-5, rel(u, d)
 
 
+def test_fp32c_fmm_two_target_pairs_per_lane(ctx):
+    """More than 131,072 targets (ellipsoid m = 129 nodes and 40,000 exterior
+    probes): the FP32C FMM runs two target pairs per lane and groups of 128
+    targets. Against the FP64 FMM (same plan: FP32 rounding only) and the
+    direct oracle on sampled targets."""
+    shape = ci.Ellipsoid(1.0, 0.8, 0.5)
+    s = ci.make_surface(shape, 129)
+    rng = np.random.default_rng(21)
+    f = ci.sh_density(s.x0, rng, lmax=8)
+    probes, _ = ci.exterior_probes(shape, 40_000, s.h, rng)
+    Y = np.concatenate([s.X, probes])
+    assert Y.shape[0] > 131_072
+    delta = 2 * s.h
+    c0 = seeds(s, 64)
+    u32 = sk.stokes_sl_eval_fmm(ctx, sk.SK_HOST, s.X, s.w, f, Y, delta, 1.0, c0, 10, 6,
+                                precision=sk.SK_FP32C)
+    u64 = sk.stokes_sl_eval_fmm(ctx, sk.SK_HOST, s.X, s.w, f, Y, delta, 1.0, c0, 10, 6,
+                                precision=sk.SK_FP64)
+    assert rel(u32, u64) < 1e-6, rel(u32, u64)
+    pick = np.random.default_rng(22).choice(Y.shape[0], 256, replace=False)
+    d = oracle.sl(s.X, s.w, f, Y[pick], delta, 1.0)
+    assert rel(u32[pick], d) < 1e-5, rel(u32[pick], d)
+
+
 def test_fp32c_fmm_ragged_and_degenerate(ctx):
     """One cluster (all near), clusters left empty by k-means, zero weights,
     a single target, and more targets than one block; the FP32C FMM against

@@ -96,6 +96,44 @@ def test_same_result_alone_and_in_the_mix(ctx):
         sk.serve_destroy(srv)
 
 
+def test_large_request_alone_and_in_the_mix(ctx):
+    """Above 131,072 targets the standalone call runs two target pairs per
+    lane while the server keeps one: the served result is then the same bit
+    for bit alone and in any mix, and within FP32 rounding of the standalone
+    call and within the tolerance of the oracle."""
+    shape = ci.Ellipsoid(1.0, 0.8, 0.5)
+    s = ci.make_surface(shape, 129)
+    rng = np.random.default_rng(77)
+    f = ci.sh_density(s.x0, rng, lmax=8)
+    probes, _ = ci.exterior_probes(shape, 40_000, s.h, rng)
+    Y = np.concatenate([s.X, probes])
+    big = (s.X, s.w, f, Y, np.array([2 * s.h]))
+    assert Y.shape[0] > 131_072
+    small = mixed_requests(6, m_choices=(17, 33), seed=79)
+    srv = sk.serve_create(ctx, max_slots=4)
+    try:
+        t = submit_retry(srv, *big)
+        code, alone, _ = sk.serve_poll(srv, t, Y.shape[0], timeout_us=60_000_000)
+        assert code == sk.SK_OK
+        tickets = [(submit_retry(srv, *r), r) for r in small[:3]]
+        tickets.append((submit_retry(srv, *big), big))
+        tickets += [(submit_retry(srv, *r), r) for r in small[3:]]
+        mixed = None
+        for tk, r in tickets:
+            code, u, _ = sk.serve_poll(srv, tk, r[3].shape[0], timeout_us=60_000_000)
+            assert code == sk.SK_OK
+            if r is big:
+                mixed = u
+        assert mixed is not None and np.array_equal(mixed, alone)
+    finally:
+        sk.serve_destroy(srv)
+    ref = sk.stokes_sl_eval(ctx, sk.SK_FP32C, sk.SK_HOST, *big)
+    assert np.linalg.norm(alone - ref) / np.linalg.norm(ref) <= 1e-7
+    pick = np.random.default_rng(78).choice(Y.shape[0], 256, replace=False)
+    o = oracle.sl(s.X, s.w, f, Y[pick], 2 * s.h)
+    assert np.linalg.norm(alone[pick] - o) / np.linalg.norm(o) <= 1e-6
+
+
 def test_per_target_delta_requests_match_standalone(ctx):
     """Requests with one delta per target (n_delta = M, e.g. delta* of each
     target's patch) are served like scalar-delta ones: bit for bit the
