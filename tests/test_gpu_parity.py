@@ -317,6 +317,27 @@ def test_near_list_overflow_rescan(ctx):
     assert_close(u, oracle.sl(s.X, s.w, f, s.X, 3 * s.h), sk.SK_FP32C)
 
 
+def test_near_list_overflow_in_the_fused_finish(ctx):
+    """320,000 targets near a sphere m = 33 (3960 active nodes) with rho_T = 2
+    and delta = 0.28: ~300 near pairs per target, every group list overflows,
+    and the pair kernel's own finish (two pairs per lane, fused) rescans."""
+    s = ci.make_surface(ci.Sphere(1.0), 33)
+    rng = np.random.default_rng(9)
+    f = rng.standard_normal((s.N, 3))
+    d = rng.standard_normal((320_000, 3))
+    Y = d / np.linalg.norm(d, axis=1, keepdims=True) * rng.uniform(0.98, 1.02, (320_000, 1))
+    try:
+        sk.sk_set_fp32c_thresholds(ctx, 2.0, 5.0)
+        u = sk.stokes_sl_eval(ctx, sk.SK_FP32C, sk.SK_HOST, s.X, s.w, f, Y, 0.28)
+        st = sk.sk_last_eval_stats(ctx)
+    finally:
+        sk.sk_set_fp32c_thresholds(ctx, 0.5, 5.0)
+    assert st["finish_fused"] == 1 and expected_fused(len(Y))
+    assert st["overflow_targets"] > 0
+    pick = np.random.default_rng(10).choice(len(Y), 256, replace=False)
+    assert_close(u[pick], oracle.sl(s.X, s.w, f, Y[pick], 0.28), sk.SK_FP32C)
+
+
 def _long_list_case(n_far, seed):
     """Sphere m = 33 (3960 active nodes) with rho_T = 2: one target near all
     of them, a list longer than a warp's near-sum scratch, so the finish
