@@ -400,8 +400,10 @@ struct LaneTgt {
 };
 
 // The general loop over the 32 sources of one segment near the warp's
-// targets: per source, the far formula unless some lane's pair lies inside
-// rho_c delta, then the regimes and the warp's near-pair append. Out of line:
+// targets: per source and target pair p, the far formula unless some lane's
+// pair p lies inside rho_c delta, then the regimes (which give the far
+// formula's bits for pairs beyond rho_c, so the choice per pair changes no
+// result) and the warp's near-pair append. Out of line:
 // its registers do not weigh on the far loop, and such segments are few (the
 // ones within rho_c delta of the warp's box).
 template <class L, int NP>
@@ -417,19 +419,24 @@ __device__ __noinline__ LaneAcc<NP> general_segment(LaneAcc<NP> acc, LaneTgt<NP>
   for (int j = 0; j < SEG; ++j) {
     const typename L::Src src = L::load(SS + j * V);
     float2 dx[NP], dy[NP], dz[NP], r2[NP];
-    bool any = false;
+    unsigned inr = 0;
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
       pair_d(tg.t[p], src.nx, src.ny, src.nz, dx[p], dy[p], dz[p], r2[p]);
-      any |= (r2[p].x < tg.t[p].rc2.x) | (r2[p].y < tg.t[p].rc2.y);
+      inr |= (__any_sync(FULL, (r2[p].x < tg.t[p].rc2.x) | (r2[p].y < tg.t[p].rc2.y)) ? 1u : 0u)
+             << p;
     }
-    if (__any_sync(FULL, any)) {
+    if (inr) {
       unsigned near_bits = 0;
 #pragma unroll
-      for (int p = 0; p < NP; ++p)
-        near_bits |= pair_general<L>(src, tg.t[p], dx[p], dy[p], dz[p], r2[p], acc.u[p], rho_lo,
-                                     rho_hi)
-                     << (2 * p);
+      for (int p = 0; p < NP; ++p) {
+        if ((inr >> p) & 1u)
+          near_bits |= pair_general<L>(src, tg.t[p], dx[p], dy[p], dz[p], r2[p], acc.u[p],
+                                       rho_lo, rho_hi)
+                       << (2 * p);
+        else
+          L::far(src, dx[p], dy[p], dz[p], r2[p], acc.u[p]);
+      }
       near_append_warp<NP>(near_bits, lane, group, orig + j, near_cnt, near_idx, flags);
     } else {
 #pragma unroll
