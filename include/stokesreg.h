@@ -209,8 +209,8 @@ typedef struct {
  *          (largest distance from a node to its grid neighbours on its patch,
  *          per patch, Eq. regparam with C = 1); otherwise [n_delta] fixed
  *          values, n_delta in {1, N}
- *   mu     viscosity > 0; precision SK_FP64 or SK_FP32C (SK_FP32C: at most
- *          2^25 nodes, as for stokes_sl_eval).
+ *   mu     viscosity > 0; precision SK_FP64 or SK_FP32C (at most 2^30
+ *          nodes, SK_FP32C at most 2^25, as for stokes_sl_eval).
  * Errors: SK_EINVAL, SK_ENOMEM, SK_ECUDA. */
 int capsule_create(sk_ctx* ctx, sk_capsule** out, int m, const double* X, const double* w,
                    const double* delta, int64_t n_delta, double mu, int precision);
@@ -253,8 +253,8 @@ int capsule_set_membrane(sk_capsule* c, const double* X_ref, double Es, double E
 /* Evaluate the single layer of every step on the four-times upsampled grid
  * (Sec. 3.4, "Upsampling"; factor 4, as stokes_sl_eval_upsampled; W from the derivative scheme at
  * the current nodes; delta_u per patch replaces delta) or on the nodes
- * themselves (factor 1, the default). Needs m >= 6 for factor 4, and in
- * SK_FP32C at most 2^25 fine nodes (6 (4m - 1)^2).
+ * themselves (factor 1, the default). Needs m >= 6 for factor 4, and at
+ * most 2^30 fine nodes (6 (4m - 1)^2), in SK_FP32C at most 2^25.
  * Errors: SK_EINVAL, SK_ENOMEM, SK_ECUDA. */
 int capsule_set_upsampling(sk_capsule* c, int factor);
 

@@ -11,7 +11,6 @@
 
 namespace {
 
-constexpr int64_t MAX_POINTS = int64_t(1) << 30;
 const char* g_create_error = "";
 thread_local std::string g_create_error_buf;
 

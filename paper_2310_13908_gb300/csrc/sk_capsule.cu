@@ -356,6 +356,10 @@ int capsule_create(sk_ctx* ctx, sk_capsule** out, int m, const double* X, const 
     ctx->err = "capsule_create: more than 2^25 nodes in SK_FP32C";
     return SK_EINVAL;
   }
+  if (N > MAX_POINTS) {
+    ctx->err = "capsule_create: more than 2^30 nodes";
+    return SK_EINVAL;
+  }
   if (delta) {
     if (!(n_delta == 1 || n_delta == N)) {
       ctx->err = "capsule_create: n_delta must be 1 or 6 (m-1)^2";
@@ -616,6 +620,10 @@ int capsule_set_upsampling(sk_capsule* c, int factor) {
     const int64_t n_up = 6 * (int64_t)(4 * c->m - 1) * (4 * c->m - 1);
     if (c->precision == SK_FP32C && n_up > FP32C_MAX_SOURCES) {
       ctx->err = "capsule_set_upsampling: more than 2^25 fine nodes in SK_FP32C";
+      return SK_EINVAL;
+    }
+    if (n_up > MAX_POINTS) {
+      ctx->err = "capsule_set_upsampling: more than 2^30 fine nodes";
       return SK_EINVAL;
     }
     MembraneOp* op = nullptr;

@@ -434,7 +434,7 @@ __global__ void k_km_box(const double* __restrict__ X, const int* __restrict__ o
   const int c = blockIdx.x, t = threadIdx.x;
   double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
   for (int q = off[c] + t; q < off[c + 1]; q += FMM_TPB) {
-    const int i = list[q];
+    const int64_t i = list[q];
     for (int a = 0; a < 3; ++a) {
       lo[a] = fmin(lo[a], X[3 * i + a]);
       hi[a] = fmax(hi[a], X[3 * i + a]);
@@ -472,7 +472,7 @@ __global__ void k_tgt_box(const double* __restrict__ Y, const double* __restrict
   double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
   double dmax = 0.0;
   for (int q = off[c] + t; q < off[c + 1]; q += FMM_TPB) {
-    const int i = list[q];
+    const int64_t i = list[q];
     for (int a = 0; a < 3; ++a) {
       lo[a] = fmin(lo[a], Y[3 * i + a]);
       hi[a] = fmax(hi[a], Y[3 * i + a]);
@@ -543,7 +543,7 @@ __global__ void k_fmm_upward(const double* __restrict__ X, const double* __restr
                  pz = cz + R_CHECK * a * unit[3 * j + 2];
     double u0 = 0.0, u1 = 0.0, u2 = 0.0;
     for (int q = off[c]; q < off[c + 1]; ++q) {
-      const int i = list[q];
+      const int64_t i = list[q];
       const double dx = px - X[3 * i], dy = py - X[3 * i + 1], dz = pz - X[3 * i + 2];
       const double r2 = dx * dx + dy * dy + dz * dz;
       const double ir = rsqrt(r2), ir3 = ir * ir * ir;
@@ -579,7 +579,7 @@ __global__ void k_fmm_eval(const double* __restrict__ Y, const double* __restric
                            const double* __restrict__ f, double scale, double* __restrict__ u) {
   const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (q >= M) return;
-  const int t = tlist[q];
+  const int64_t t = tlist[q];
   const int bi = tlab[t];
   const double x = Y[3 * t], y = Y[3 * t + 1], z = Y[3 * t + 2];
   const double d = delta[n_delta == 1 ? 0 : t], invd = 1.0 / d;
@@ -605,7 +605,7 @@ __global__ void k_fmm_eval(const double* __restrict__ Y, const double* __restric
       }
     } else {
       for (int qq = off[c]; qq < off[c + 1]; ++qq) {
-        const int i = list[qq];
+        const int64_t i = list[qq];
         const double dx = x - X[3 * i], dy = y - X[3 * i + 1], dz = z - X[3 * i + 2];
         const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
         if (r2 >= rf2) {  // s1 = s2 = 1 to double precision
@@ -663,7 +663,7 @@ __global__ void __launch_bounds__(FMM_TPB) k_fmm_check32(
     for (int b0 = p0; b0 < p1; b0 += FMM_TPB) {
       __syncthreads();
       if (b0 + t < p1) {
-        const int i = list[b0 + t];
+        const int64_t i = list[b0 + t];
         sp[t] = make_float4((float)(X[3 * i] - cx), (float)(X[3 * i + 1] - cy),
                             (float)(X[3 * i + 2] - cz), 0.f);
         sg[t] = make_float4((float)(w[i] * f[3 * i]), (float)(w[i] * f[3 * i + 1]),
@@ -735,7 +735,7 @@ __global__ void k_fmm_pack_near(const double* __restrict__ X, const double* __re
   const int j = tile_cluster[s / TILE];
   const int64_t q = s - src_first[j];
   const bool real = q < count[j];
-  const int i = real ? list[off[j] + q] : -1;
+  const int64_t i = real ? list[off[j] + q] : -1;
   float x = PAD_POS, y = PAD_POS, z = PAD_POS;
   if (real) {
     x = (float)X[3 * i];
@@ -754,7 +754,7 @@ __global__ void k_fmm_pack_near(const double* __restrict__ X, const double* __re
     g2 = (float)(ws * f[3 * i + 2]);
   }
   write_sl_record(srcF + s * V_SL, x, y, z, g0, g1, g2);
-  src_orig[s] = i;
+  src_orig[s] = (int)i;
 }
 
 // Equivalent sources, eqp slots per cluster (Np real ones, the rest padding),
@@ -804,7 +804,7 @@ __global__ void k_fmm_pack_tgt(const double* __restrict__ Y, const double* __res
   const int i = block_box[t / tb];
   const int64_t q = t - box_first[i];
   const bool real = q < tcount[i];
-  const int j = tlist[toff[i] + (real ? q : 0)];
+  const int64_t j = tlist[toff[i] + (real ? q : 0)];
   const double x = Y[3 * j], y = Y[3 * j + 1], z = Y[3 * j + 2];
   const double d = delta[n_delta == 1 ? 0 : j];
   const double rc = rho_c * d, rt = rho_T * d;
@@ -812,7 +812,7 @@ __global__ void k_fmm_pack_tgt(const double* __restrict__ Y, const double* __res
   tgtF[2 * t + 1] = real ? make_float4((float)(rc * rc), (float)(rt * rt), 0.f, 0.f)
                          : make_float4(-1.f, -1.f, 0.f, 0.f);
   tgt64[t] = make_double4_32a(x, y, z, d);
-  perm[t] = real ? j : -1;
+  perm[t] = real ? (int)j : -1;
 }
 
 // One work item per CTA: (target block, first tile descriptor, tiles,
@@ -840,7 +840,7 @@ __global__ void __launch_bounds__(G)
   extern __shared__ unsigned fsm[];
   int cnt = p32::near_group<p32::SLayer, G>(
       oa, fa, blockIdx.x, fsm, threadIdx.x, [&](int64_t t, double n0, double n1, double n2) {
-        const int j = fa.perm[t];
+        const int64_t j = fa.perm[t];
         if (j < 0) return;
         const int64_t b = t / tb, l = t - b * tb;
         double u0 = 0.0, u1 = 0.0, u2 = 0.0;

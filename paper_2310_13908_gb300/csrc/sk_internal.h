@@ -35,6 +35,8 @@ constexpr int NEAR_GROUP_MIN = 64;      // targets per near-list group: 64 * (f3
 constexpr int NEAR_SRC_BITS = 25;       // near-list entry: source index bits (the rest: target)
 // SK_FP32C lists near pairs by the source's original index in NEAR_SRC_BITS bits
 constexpr int64_t FP32C_MAX_SOURCES = int64_t(1) << NEAR_SRC_BITS;
+// any precision: sources and targets of one evaluation (sorted indices are int)
+constexpr int64_t MAX_POINTS = int64_t(1) << 30;
 constexpr int RHO_C64 = 7;              // FP64 path: s_i == 1 to double precision beyond 7
 
 // layer kinds

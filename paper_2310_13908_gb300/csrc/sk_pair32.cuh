@@ -922,7 +922,7 @@ struct Near64;
 template <>
 struct Near64<SLayer> {
   __device__ __forceinline__ static void eval(double4_32a x, const double* xyz, const double* w,
-                                              const double* f, const double* /*nrm*/, int j,
+                                              const double* f, const double* /*nrm*/, int64_t j,
                                               double scale, double invd, double& u0, double& u1,
                                               double& u2) {
     sl_pair64(x.x - xyz[3 * j], x.y - xyz[3 * j + 1], x.z - xyz[3 * j + 2], f[3 * j], f[3 * j + 1],
@@ -933,7 +933,7 @@ struct Near64<SLayer> {
 template <>
 struct Near64<DLayer> {
   __device__ __forceinline__ static void eval(double4_32a x, const double* xyz, const double* w,
-                                              const double* q, const double* nrm, int j,
+                                              const double* q, const double* nrm, int64_t j,
                                               double scale, double invd, double& u0, double& u1,
                                               double& u2) {
     dl_pair64(x.x - xyz[3 * j], x.y - xyz[3 * j + 1], x.z - xyz[3 * j + 2], q[3 * j], q[3 * j + 1],
@@ -1199,7 +1199,7 @@ __device__ __forceinline__ void finish_merge(const FinishArgs& a, int64_t t, dou
     u1 += p[1];
     u2 += p[2];
   }
-  const int j = a.perm[t];
+  const int64_t j = a.perm[t];
   a.u[3 * j] = u0 + n0;
   a.u[3 * j + 1] = u1 + n1;
   a.u[3 * j + 2] = u2 + n2;

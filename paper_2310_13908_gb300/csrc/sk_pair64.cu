@@ -249,7 +249,7 @@ __global__ void k_finish64(const int* __restrict__ perm, int64_t M, int64_t M_pa
     u1 += p[1];
     u2 += p[2];
   }
-  const int j = perm[t];
+  const int64_t j = perm[t];
   u_out[3 * j] = u0;
   u_out[3 * j + 1] = u1;
   u_out[3 * j + 2] = u2;

@@ -369,7 +369,7 @@ __global__ void k_pack_src32(const double* __restrict__ xyz, const double* __res
   if (s == 0) meta[META_NS_PAD] = Ns_pad;
   if (s >= Ns_pad || s >= N_pad) return;  // whole warps leave together (multiples of 32)
   const bool real = s < Ns;
-  const int j = real ? sorted[s] : -1;
+  const int64_t j = real ? sorted[s] : -1;
   float x = PAD_POS, y = PAD_POS, z = PAD_POS;
   if (real) {
     x = (float)xyz[3 * j];
@@ -406,7 +406,7 @@ __global__ void k_pack_src32(const double* __restrict__ xyz, const double* __res
     o[4] = make_float4(n2, n2, 0.f, 0.f);
     srcLo[s] = res;
   }
-  src_orig[s] = j;
+  src_orig[s] = (int)j;
 }
 
 // FP64 packed layout: src64[2s] = (x, y, z, 0), src64[2s+1] = (g or q scaled, 0);
@@ -426,7 +426,7 @@ __global__ void k_pack_src64(const double* __restrict__ xyz, const double* __res
   double x = PAD_POS, y = PAD_POS, z = PAD_POS, d0 = 0, d1 = 0, d2 = 0;
   double4_32a nn = make_double4_32a(0, 0, 0, 0);
   if (real) {
-    const int j = sorted[s];
+    const int64_t j = sorted[s];
     x = xyz[3 * j];
     y = xyz[3 * j + 1];
     z = xyz[3 * j + 2];
@@ -449,7 +449,7 @@ __global__ void k_pack_tgt32(const double* __restrict__ xyz, const double* __res
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= M_pad) return;
   const bool real = t < M;
-  const int j = sorted[real ? t : M - 1];
+  const int64_t j = sorted[real ? t : M - 1];
   const double x = xyz[3 * j], y = xyz[3 * j + 1], z = xyz[3 * j + 2];
   const double d = delta[n_delta == 1 ? 0 : j];
   const double rc = rho_c * d, rt = rho_T * d;
@@ -457,7 +457,7 @@ __global__ void k_pack_tgt32(const double* __restrict__ xyz, const double* __res
   tgtF[2 * t + 1] = real ? make_float4((float)(rc * rc), (float)(rt * rt), 0.f, 0.f)
                          : make_float4(-1.f, -1.f, 0.f, 0.f);
   tgt64[t] = make_double4_32a(x, y, z, d);
-  perm[t] = real ? j : -1;
+  perm[t] = real ? (int)j : -1;
 }
 
 __global__ void k_pack_tgt64(const double* __restrict__ xyz, const double* __restrict__ delta,
@@ -466,11 +466,11 @@ __global__ void k_pack_tgt64(const double* __restrict__ xyz, const double* __res
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= M_pad) return;
   const bool real = t < M;
-  const int j = sorted[real ? t : M - 1];
+  const int64_t j = sorted[real ? t : M - 1];
   const double d = delta[n_delta == 1 ? 0 : j];
   // padding targets get a negative delta: the pair kernel skips them
   tgt64[t] = make_double4_32a(xyz[3 * j], xyz[3 * j + 1], xyz[3 * j + 2], real ? d : -1.0);
-  perm[t] = real ? j : -1;
+  perm[t] = real ? (int)j : -1;
 }
 
 inline unsigned blocks_for(int64_t n, int tpb) { return (unsigned)((n + tpb - 1) / tpb); }
