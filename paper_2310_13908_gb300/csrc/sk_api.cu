@@ -101,6 +101,26 @@ void carve_eval_buffers(Bump& bp, const EvalShape& s, EvalBufs& b) {
     b.near_ovf = bp.take<double>((size_t)b.M_pad * 3);
   }
   b.flags = bp.take<unsigned long long>(N_FLAGS);
+  // the target sort's own scratch last, so that the buffers above keep the
+  // offsets they have without it
+  if (s.split_sorts && s.N > 0) {
+    const int64_t mt = s.M > 0 ? s.M : 1;
+    b.tkeys_a = bp.take<uint32_t>(mt);
+    b.tkeys_b = bp.take<uint32_t>(mt);
+    b.tvals_a = bp.take<int>(mt);
+    b.tvals_b = bp.take<int>(mt);
+    b.thist = bp.take<uint32_t>(256 * (size_t)sort_grid_blocks(mt) + 256);
+    b.tbbox_part = bp.take<float>(128 * 6);
+    b.tbbox = bp.take<float>(8);
+  } else {
+    b.tkeys_a = b.keys_a;
+    b.tkeys_b = b.keys_b;
+    b.tvals_a = b.vals_a;
+    b.tvals_b = b.vals_b;
+    b.thist = b.hist;
+    b.tbbox_part = b.bbox_part;
+    b.tbbox = b.bbox;
+  }
 }
 
 double layer_scale(const EvalShape& s) {
@@ -114,9 +134,12 @@ __global__ void k_check_delta(const double* __restrict__ d, int64_t n,
 }
 
 // Preparation of one evaluation on `st`: clear the counters, check delta,
-// sort and pack sources and targets. Returns the number of kernels launched.
+// sort and pack sources and targets. With split sorts and a fork, the target
+// sort and pack run on pf->aux beside the source sort and pack (the two touch
+// disjoint buffers; the result does not change), and `st` waits for them.
+// Returns the number of kernels launched.
 int enqueue_prep(const EvalShape& s, const EvalBufs& b, double rho_T, double rho_c,
-                 cudaStream_t st) {
+                 cudaStream_t st, const PrepFork* pf) {
   const bool fp32 = s.precision == SK_FP32C;
   const double scale = layer_scale(s);
   // bbox (2) + keys + 4 radix passes x 3 (hist, row scan, scatter), or the single-block sort
@@ -130,6 +153,20 @@ int enqueue_prep(const EvalShape& s, const EvalBufs& b, double rho_T, double rho
   }
   k_check_delta<<<(unsigned)((s.n_delta + 255) / 256), 256, 0, st>>>(b.delta, s.n_delta, b.flags);
   launches += 1;
+  const bool fork = pf && pf->aux && s.split_sorts && s.N > 0;
+  cudaStream_t tst = st;
+  if (fork) {
+    cudaEventRecord(pf->fork, st);
+    cudaStreamWaitEvent(pf->aux, pf->fork, 0);
+    tst = pf->aux;
+  }
+  launch_sort_points(b.tgt_xyz, nullptr, s.M, b.tkeys_a, b.tkeys_b, b.tvals_a, b.tvals_b, b.thist,
+                     b.tbbox_part, b.tbbox, b.meta + META_SCRATCH, s.small_sort_points, tst);
+  launches += sort_launches(s.M);
+  if (fp32)
+    launch_pack_targets32(b, s.n_delta, rho_T, rho_c, tst);
+  else
+    launch_pack_targets64(b, s.n_delta, tst);
   if (s.N > 0) {
     launch_sort_points(b.src_xyz, b.src_w, s.N, b.keys_a, b.keys_b, b.vals_a, b.vals_b, b.hist,
                        b.bbox_part, b.bbox, b.meta + META_NS, s.small_sort_points, st);
@@ -139,23 +176,20 @@ int enqueue_prep(const EvalShape& s, const EvalBufs& b, double rho_T, double rho
       launch_pack_sources64(s.layer, b, scale, st);
     launches += sort_launches(s.N) + 1;
   }
-  launch_sort_points(b.tgt_xyz, nullptr, s.M, b.keys_a, b.keys_b, b.vals_a, b.vals_b, b.hist,
-                     b.bbox_part, b.bbox, b.meta + META_SCRATCH, s.small_sort_points, st);
-  launches += sort_launches(s.M);
-  if (fp32)
-    launch_pack_targets32(b, s.n_delta, rho_T, rho_c, st);
-  else
-    launch_pack_targets64(b, s.n_delta, st);
+  if (fork) {
+    cudaEventRecord(pf->join, pf->aux);
+    cudaStreamWaitEvent(st, pf->join, 0);
+  }
   return launches + 1;
 }
 
 // Enqueue one evaluation on `st`; inputs and output are device pointers in b.
 int enqueue_eval(const EvalShape& s, const EvalBufs& b, double rho_T, double rho_c,
-                 cudaStream_t st, cudaEvent_t* ev) {
+                 cudaStream_t st, cudaEvent_t* ev, const PrepFork* pf) {
   const bool fp32 = s.precision == SK_FP32C;
   const double scale = layer_scale(s);
   if (ev) cudaEventRecord(ev[0], st);
-  int launches = enqueue_prep(s, b, rho_T, rho_c, st);
+  int launches = enqueue_prep(s, b, rho_T, rho_c, st, pf);
   if (ev) cudaEventRecord(ev[1], st);
   if (fp32) {
     launch_pair32(s.layer, b, rho_T, scale, st, ev ? ev[2] : nullptr);  // with the finish
@@ -200,6 +234,9 @@ int sk_create(sk_ctx** out, int device, size_t workspace_bytes) {
   if ((e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device)) !=
           cudaSuccess ||
       (e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaStreamCreateWithFlags(&ctx->aux_stream, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&ctx->join_ev, cudaEventDisableTiming)) != cudaSuccess ||
       (e = cudaMallocHost(&ctx->h_flags, 256)) != cudaSuccess) {
     code = e == cudaErrorMemoryAllocation ? SK_ENOMEM : SK_ECUDA;
   } else if (workspace_bytes > 0) {
@@ -239,6 +276,9 @@ void sk_destroy(sk_ctx* ctx) {
   if (ctx->h_flags) cudaFreeHost(ctx->h_flags);
   for (int i = 0; i < 4; ++i)
     if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
+  if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
+  if (ctx->join_ev) cudaEventDestroy(ctx->join_ev);
+  if (ctx->aux_stream) cudaStreamDestroy(ctx->aux_stream);
   if (ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
 }
@@ -357,6 +397,7 @@ int eval_entry(sk_ctx* ctx, int layer, int precision, int mem, int64_t N, const 
   s.mu = mu;
   s.copy_inputs = mem == SK_HOST;
   s.small_sort_points = ctx->small_sort_points;
+  s.split_sorts = true;
   choose_decomposition(s, ctx->sm_count);
   const size_t need = eval_workspace_bytes(s);
   int rc = ensure_workspace(ctx, need);
@@ -385,7 +426,9 @@ int eval_entry(sk_ctx* ctx, int layer, int precision, int mem, int64_t N, const 
     b.delta = delta;
     b.u = u_out;
   }
-  const int launches = enqueue_eval(s, b, ctx->rho_T, ctx->rho_c, st, ctx->profile ? ctx->ev : nullptr);
+  const PrepFork pf{ctx->aux_stream, ctx->fork_ev, ctx->join_ev};
+  const int launches =
+      enqueue_eval(s, b, ctx->rho_T, ctx->rho_c, st, ctx->profile ? ctx->ev : nullptr, &pf);
   if (mem == SK_HOST)
     cudaMemcpyAsync(u_out, b.u, 3 * M * sizeof(double), cudaMemcpyDeviceToHost, st);
   cudaMemcpyAsync(ctx->h_flags, b.flags, N_FLAGS * sizeof(unsigned long long),

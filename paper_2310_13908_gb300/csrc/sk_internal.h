@@ -146,6 +146,16 @@ struct EvalBufs {
   uint32_t* hist = nullptr;       // [256][sort_blocks] digit counts, then 256 row totals
   float* bbox_part = nullptr;
   float* bbox = nullptr;
+  // scratch of the target sort: the sort scratch above, unless the shape
+  // splits the sorts (then a set of its own, so that the two sorts can run at
+  // the same time)
+  uint32_t* tkeys_a = nullptr;
+  uint32_t* tkeys_b = nullptr;
+  int* tvals_a = nullptr;
+  int* tvals_b = nullptr;
+  uint32_t* thist = nullptr;
+  float* tbbox_part = nullptr;
+  float* tbbox = nullptr;
   // prepared sources / targets
   int* meta = nullptr;
   int* src_orig = nullptr;        // packed source -> original index (-1: padding)
@@ -203,6 +213,10 @@ struct sk_ctx {
   int device = 0;
   sk_server* server = nullptr;  // at most one server per context
   cudaStream_t stream = nullptr;
+  // second stream and fork/join events of the preparation (sk::PrepFork)
+  cudaStream_t aux_stream = nullptr;
+  cudaEvent_t fork_ev = nullptr;
+  cudaEvent_t join_ev = nullptr;
   char* ws = nullptr;
   size_t ws_bytes = 0;
   bool ws_fixed = false;
@@ -246,6 +260,19 @@ struct EvalShape {
   // point sets of at most this many points are ordered by one single-block
   // kernel instead of fifteen launches (0: never)
   int64_t small_sort_points = SMALL_SORT_POINTS;
+  // the target sort takes scratch of its own and runs beside the source sort
+  // on a second stream (calls through a context; the allocation-free call
+  // keeps one set)
+  bool split_sorts = false;
+};
+
+// A second stream and two events that let the preparation run the target
+// sort beside the source sort: fork is recorded on the evaluation's stream
+// and waited for on aux; join the other way round.
+struct PrepFork {
+  cudaStream_t aux = nullptr;
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t join = nullptr;
 };
 
 // sk_api.cu
@@ -256,12 +283,13 @@ size_t eval_workspace_bytes(const EvalShape& s);
 void carve_eval_buffers(Bump& bp, const EvalShape& s, EvalBufs& b);
 // choose_chunks and choose_decomposition (the split into work items): sk_decomp.h
 double layer_scale(const EvalShape& s);  // 1/(8 pi mu) or -6/(8 pi)
+// pf (optional) forks the target sort onto pf->aux when s.split_sorts.
 int enqueue_prep(const EvalShape& s, const EvalBufs& b, double rho_T, double rho_c,
-                 cudaStream_t st);
+                 cudaStream_t st, const PrepFork* pf = nullptr);
 // Returns the number of kernels launched. ev (optional, 4 events) brackets
 // the whole evaluation (ev[0], ev[3]) and the pair kernel (ev[1], ev[2]).
 int enqueue_eval(const EvalShape& s, const EvalBufs& b, double rho_T, double rho_c,
-                 cudaStream_t st, cudaEvent_t* ev = nullptr);
+                 cudaStream_t st, cudaEvent_t* ev = nullptr, const PrepFork* pf = nullptr);
 
 // launchers (sk_prep.cu)
 void launch_sort_points(const double* xyz, const double* w, int64_t n, uint32_t* keys_a,

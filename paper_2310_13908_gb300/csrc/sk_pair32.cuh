@@ -64,6 +64,19 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b) {
 __device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
 __device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
 
+// Fresh loads of an evaluation's prepared data inside a pair item (kFresh).
+// The server's persistent kernel outlives the evaluations it serves: the
+// memory of a finished one is rewritten for the next while the kernel runs,
+// and an SM may still hold lines of the old contents in L1 or in the
+// read-only path. ld.global.cg goes to L2, which every write reaches. A
+// kernel launched per evaluation starts with clean L1 and keeps its ordinary
+// loads.
+__device__ __forceinline__ double4_32a ldcg4d(const double4_32a* p) {
+  const double2* q = reinterpret_cast<const double2*>(p);
+  const double2 a = __ldcg(q), b = __ldcg(q + 1);
+  return make_double4_32a(a.x, a.y, b.x, b.y);
+}
+
 // ---- bulk async copy + mbarrier helpers (bounded waits) --------------------
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -156,13 +169,13 @@ __device__ __forceinline__ float box_margin(float coord_max, float rc) {
 // for the lane's target 64p + 32h + lane. A list longer than NEAR_K * 64 * NP
 // entries keeps counting but stores no more; the group's targets then take
 // the rescan of overflow_target.
-template <int NP>
+template <int NP, bool kFresh>
 __device__ __noinline__ void near_append_list(unsigned near_bits, int lane, int64_t g,
                                               const int* jo_at, int* __restrict__ cnt,
                                               unsigned* __restrict__ idx,
                                               unsigned long long* __restrict__ flags) {
   constexpr int CAP = NEAR_K * 64 * NP;
-  const unsigned jo = (unsigned)*jo_at;
+  const unsigned jo = (unsigned)(kFresh ? __ldcg(jo_at) : *jo_at);
   const unsigned lt = (1u << lane) - 1u;
   int total = 0;
 #pragma unroll
@@ -188,12 +201,13 @@ __device__ __noinline__ void near_append_list(unsigned near_bits, int lane, int6
 
 // Out of line beyond the vote: few general-path sources have a near pair,
 // and the append's registers then do not weigh on the pair loop.
-template <int NP>
+template <int NP, bool kFresh>
 __device__ __forceinline__ void near_append_warp(unsigned near_bits, int lane, int64_t g,
                                                  const int* jo_at, int* __restrict__ cnt,
                                                  unsigned* __restrict__ idx,
                                                  unsigned long long* __restrict__ flags) {
-  if (__any_sync(FULL, near_bits)) near_append_list<NP>(near_bits, lane, g, jo_at, cnt, idx, flags);
+  if (__any_sync(FULL, near_bits))
+    near_append_list<NP, kFresh>(near_bits, lane, g, jo_at, cnt, idx, flags);
 }
 
 // ---- layer policies ---------------------------------------------------------
@@ -406,7 +420,7 @@ struct LaneTgt {
 // result) and the warp's near-pair append. Out of line:
 // its registers do not weigh on the far loop, and such segments are few (the
 // ones within rho_c delta of the warp's box).
-template <class L, int NP>
+template <class L, int NP, bool kFresh>
 __device__ __noinline__ LaneAcc<NP> general_segment(LaneAcc<NP> acc, LaneTgt<NP> tg,
                                                     const float4* SS, const int* orig,
                                                     int64_t group, int* near_cnt,
@@ -437,7 +451,7 @@ __device__ __noinline__ LaneAcc<NP> general_segment(LaneAcc<NP> acc, LaneTgt<NP>
         else
           L::far(src, dx[p], dy[p], dz[p], r2[p], acc.u[p]);
       }
-      near_append_warp<NP>(near_bits, lane, group, orig + j, near_cnt, near_idx, flags);
+      near_append_warp<NP, kFresh>(near_bits, lane, group, orig + j, near_cnt, near_idx, flags);
     } else {
 #pragma unroll
       for (int p = 0; p < NP; ++p) L::far(src, dx[p], dy[p], dz[p], r2[p], acc.u[p]);
@@ -454,7 +468,7 @@ __device__ __noinline__ LaneAcc<NP> general_segment(LaneAcc<NP> acc, LaneTgt<NP>
 // general loop computes, in the same order, so the accumulators come out bit
 // for bit as there. Out of line: its registers do not weigh on the pair loop,
 // and wide segments are rare on dense surfaces.
-template <class L, int NP>
+template <class L, int NP, bool kFresh>
 __device__ __noinline__ LaneAcc<NP> exact_segment(
     LaneAcc<NP> acc, LaneTgt<NP> tg, const float4* SS, const float4* __restrict__ ylo,
     const int* orig, const float4* ts, float sx, float sy, float sz, float hs, int64_t group,
@@ -472,7 +486,7 @@ __device__ __noinline__ LaneAcc<NP> exact_segment(
       any |= (r2[p].x < tg.t[p].rc2.x) | (r2[p].y < tg.t[p].rc2.y);
     }
     if (__any_sync(FULL, any)) {
-      const float4 yl = ylo[j];
+      const float4 yl = kFresh ? __ldcg(ylo + j) : ylo[j];
       unsigned near_bits = 0;
 #pragma unroll
       for (int p = 0; p < NP; ++p) {
@@ -490,7 +504,7 @@ __device__ __noinline__ LaneAcc<NP> exact_segment(
                                        make_float2(yl.z, yl.z))))
                      << (2 * p);
       }
-      near_append_warp<NP>(near_bits, lane, group, orig + j, near_cnt, near_idx, flags);
+      near_append_warp<NP, kFresh>(near_bits, lane, group, orig + j, near_cnt, near_idx, flags);
     } else {
 #pragma unroll
       for (int p = 0; p < NP; ++p) L::far(src, dx[p], dy[p], dz[p], r2[p], acc.u[p]);
@@ -592,8 +606,9 @@ struct TileRange {
 
 // Tiles of source chunk ch of a direct evaluation: an even split of the
 // padded sources into a.n_chunks contiguous ranges.
+template <bool kFresh = false>
 __device__ __forceinline__ TileRange chunk_tiles(const PairArgs& a, int ch) {
-  const int n_tiles = a.meta[META_NS_PAD] / TILE;
+  const int n_tiles = (kFresh ? __ldcg(a.meta + META_NS_PAD) : a.meta[META_NS_PAD]) / TILE;
   const int k0 = (int)((long long)ch * n_tiles / a.n_chunks);
   const int k1 = (int)((long long)(ch + 1) * n_tiles / a.n_chunks);
   return TileRange{k0, k1 - k0, ch};
@@ -603,7 +618,9 @@ __device__ __forceinline__ TileRange chunk_tiles(const PairArgs& a, int ch) {
 // the source tiles tl. Writes the block's partials (target t at
 // tl.out(a, t)); returns false if a bounded wait expired (the flag is set,
 // nothing is written).
-template <class L, int NP, class TL>
+// kFresh: the evaluation's data is read with fresh loads (ld.global.cg), for
+// the server's persistent kernel.
+template <class L, int NP, bool kFresh = false, class TL>
 __device__ __forceinline__ bool pair_item(const PairArgs& a, int tb, const TL& tl, float4* sm,
                                           PipeSmem<pair_stages<L, NP>()>& ps) {
   constexpr int V = L::V;
@@ -641,8 +658,8 @@ __device__ __forceinline__ bool pair_item(const PairArgs& a, int tb, const TL& t
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int64_t t = wbase + 64 * p + 32 * h;
-      a[h] = tgtF[2 * t];
-      b[h] = tgtF[2 * t + 1];
+      a[h] = kFresh ? __ldcg(tgtF + 2 * t) : tgtF[2 * t];
+      b[h] = kFresh ? __ldcg(tgtF + 2 * t + 1) : tgtF[2 * t + 1];
       if (b[h].x >= 0.f) {
         blo[0] = fminf(blo[0], a[h].x); bhi[0] = fmaxf(bhi[0], a[h].x);
         blo[1] = fminf(blo[1], a[h].y); bhi[1] = fmaxf(bhi[1], a[h].y);
@@ -666,7 +683,9 @@ __device__ __forceinline__ bool pair_item(const PairArgs& a, int tb, const TL& t
   // FP32 (hi, lo) split of the targets' FP64 coordinates
 #pragma unroll
   for (int p = 0; p < NP; ++p) {
-    const double4_32a x0 = tgt64[wbase + 64 * p], x1 = tgt64[wbase + 64 * p + 32];
+    const double4_32a x0 = kFresh ? ldcg4d(tgt64 + wbase + 64 * p) : tgt64[wbase + 64 * p],
+                      x1 = kFresh ? ldcg4d(tgt64 + wbase + 64 * p + 32)
+                                  : tgt64[wbase + 64 * p + 32];
     const double a0[3] = {x0.x, x0.y, x0.z}, a1[3] = {x1.x, x1.y, x1.z};
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -753,8 +772,9 @@ __device__ __forceinline__ bool pair_item(const PairArgs& a, int tb, const TL& t
       float chs = 0.f;                        // ... and the half extent of its box
       if (lane < nseg) {
         const size_t sg = tl.first_segment(it, src0);
-        const float4 lo = segbox[2 * (sg + lane)];
-        const float4 hi = segbox[2 * (sg + lane) + 1];
+        const float4 lo = kFresh ? __ldcg(segbox + 2 * (sg + lane)) : segbox[2 * (sg + lane)];
+        const float4 hi =
+            kFresh ? __ldcg(segbox + 2 * (sg + lane) + 1) : segbox[2 * (sg + lane) + 1];
         const float dx = fmaxf(0.f, fmaxf(lo.x - bhi[0], blo[0] - hi.x));
         const float dy = fmaxf(0.f, fmaxf(lo.y - bhi[1], blo[1] - hi.y));
         const float dz = fmaxf(0.f, fmaxf(lo.z - bhi[2], blo[2] - hi.z));
@@ -821,7 +841,7 @@ __device__ __forceinline__ bool pair_item(const PairArgs& a, int tb, const TL& t
 #pragma unroll
               for (int c = 0; c < 3; ++c) acc.u[p][c] = U[p][c];
             }
-            acc = general_segment<L, NP>(acc, tg, SS, orig, group, near_cnt, near_idx, flags,
+            acc = general_segment<L, NP, kFresh>(acc, tg, SS, orig, group, near_cnt, near_idx, flags,
                                          rho_lo, rho_hi);
 #pragma unroll
             for (int p = 0; p < NP; ++p)
@@ -836,7 +856,7 @@ __device__ __forceinline__ bool pair_item(const PairArgs& a, int tb, const TL& t
 #pragma unroll
               for (int c = 0; c < 3; ++c) acc.u[p][c] = U[p][c];
             }
-            acc = exact_segment<L, NP>(acc, tg, SS, a.srcLo + (size_t)src0 + s * SEG,
+            acc = exact_segment<L, NP, kFresh>(acc, tg, SS, a.srcLo + (size_t)src0 + s * SEG,
                                        orig, ts, sx, sy, sz, hs, group, near_cnt, near_idx,
                                        flags, rho_lo, rho_hi);
 #pragma unroll

@@ -564,13 +564,13 @@ void launch_pack_sources64(int layer, const EvalBufs& b, double scale, cudaStrea
 
 void launch_pack_targets32(const EvalBufs& b, int64_t n_delta, double rho_T, double rho_c,
                            cudaStream_t st) {
-  k_pack_tgt32<<<blocks_for(b.M_pad, 256), 256, 0, st>>>(b.tgt_xyz, b.delta, n_delta, b.vals_a,
+  k_pack_tgt32<<<blocks_for(b.M_pad, 256), 256, 0, st>>>(b.tgt_xyz, b.delta, n_delta, b.tvals_a,
                                                          b.M, b.M_pad, rho_T, rho_c, b.tgtF,
                                                          b.tgt64, b.tgt_perm);
 }
 
 void launch_pack_targets64(const EvalBufs& b, int64_t n_delta, cudaStream_t st) {
-  k_pack_tgt64<<<blocks_for(b.M_pad, 256), 256, 0, st>>>(b.tgt_xyz, b.delta, n_delta, b.vals_a,
+  k_pack_tgt64<<<blocks_for(b.M_pad, 256), 256, 0, st>>>(b.tgt_xyz, b.delta, n_delta, b.tvals_a,
                                                          b.M, b.M_pad, b.tgt64, b.tgt_perm);
 }
 

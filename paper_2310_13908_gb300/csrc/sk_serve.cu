@@ -170,7 +170,10 @@ __global__ void __launch_bounds__(TPB32, SERVE_MINB)
     __syncthreads();
     const int item = s_item;
     const int tb = item / d.n_chunks, ch = item % d.n_chunks;
-    pair_item<SLayer, SERVE_NP>(d.pa, tb, chunk_tiles(d.pa, ch), sm, ps);  // a timeout sets the request's flag
+    // fresh loads: the arena block of an earlier request may have held other
+    // data at these addresses while this kernel ran (a timeout sets the
+    // request's flag)
+    pair_item<SLayer, SERVE_NP, true>(d.pa, tb, chunk_tiles<true>(d.pa, ch), sm, ps);
     __syncthreads();
     if (tid == 0) {
       __threadfence();
