@@ -218,6 +218,7 @@ EvalShape capsule_shape(const sk_capsule* c) {
     s.n_delta = c->n_delta;
   }
   s.small_sort_points = c->ctx->small_sort_points;
+  s.split_sorts = true;  // the step graphs fork the target sort onto a second stream
   choose_decomposition(s, c->ctx->sm_count);
   return s;
 }
@@ -257,7 +258,8 @@ void enqueue_velocity(sk_capsule* c, const double* P, int mode, const EvalShape&
   }
   b.tgt_xyz = P;
   b.u = c->u;
-  enqueue_eval(s, b, ctx->rho_T, ctx->rho_c, st);
+  const PrepFork pf{ctx->aux_stream, ctx->fork_ev, ctx->join_ev};
+  enqueue_eval(s, b, ctx->rho_T, ctx->rho_c, st, nullptr, &pf);
   k_sticky<<<1, 32, 0, st>>>(b.flags, c->sticky);
 }
 
