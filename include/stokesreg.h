@@ -64,14 +64,17 @@ typedef struct sk_ctx sk_ctx;
 /* Create a context on CUDA device `device`. workspace_bytes = 0 lets the
  * context grow its device workspace on demand; > 0 preallocates exactly
  * that much and never grows it (calls needing more return SK_ENOMEM).
- * The context owns one CUDA stream and its workspace. *out is set to NULL
+ * The context owns two CUDA streams and its workspace: an evaluation runs
+ * part of its preparation (the target sort) on the second stream, forked
+ * from and joined back into the evaluation's stream by events, so the
+ * caller's stream still orders all of the call's work. *out is set to NULL
  * on failure. The environment variable SK_SMALL_SORT_POINTS (an integer
  * 0..2^24, read here) sets the largest point set that is ordered by the
  * single-block sort (default 3072; 0: always the multi-block sort); results
  * do not depend on it. */
 int sk_create(sk_ctx** out, int device, size_t workspace_bytes);
 
-/* Release the context, its stream and workspace. NULL is ignored. */
+/* Release the context, its streams and workspace. NULL is ignored. */
 void sk_destroy(sk_ctx* ctx);
 
 /* Message of the most recent failure on ctx ("" if none). Valid until the
