@@ -235,6 +235,8 @@ struct Slot {
   int* tb_counters = nullptr;  // [n_tb + 1]
   unsigned seq = 0;
   cudaEvent_t prep_done = nullptr, copy_done = nullptr, update_done = nullptr;
+  // fork and join of the target sort onto the preparation stream's partner
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   // pinned per-slot block (PIN_WORDS words): [0, 8) device flags, [8, 12)
   // meta ints, [12] claim word, [16, ...) descriptor being published
   unsigned long long* h_flags = nullptr;
@@ -257,6 +259,9 @@ struct sk_server {
   // uses stream i mod SERVE_PREP_STREAMS), so a burst of admissions does not
   // queue behind one stream
   cudaStream_t s_prep[sk::SERVE_PREP_STREAMS] = {};
+  // each preparation stream's partner: a request's target sort and pack run
+  // there beside its source sort and pack
+  cudaStream_t s_prep_aux[sk::SERVE_PREP_STREAMS] = {};
   sk::SlotDesc* d_desc = nullptr;
   sk::SlotClaim* d_claim = nullptr;
   int* d_ctl = nullptr;  // CTL_WORDS device control words
@@ -340,7 +345,8 @@ void enqueue_capsule_step(sk_server* srv, Slot& sl, int slot, cudaStream_t st) {
   capsule_enqueue_step_inputs(r->cap, sl.b, st, capsule_set(slot));
   const int n_tb = (int)(sl.b.M_pad / SERVE_TGT_CTA);
   cudaMemsetAsync(sl.tb_counters, 0, (n_tb + 1) * sizeof(int), st);
-  enqueue_prep(r->shape, sl.b, srv->ctx->rho_T, srv->ctx->rho_c, st);
+  const PrepFork pf{srv->s_prep_aux[slot % SERVE_PREP_STREAMS], sl.fork_ev, sl.join_ev};
+  enqueue_prep(r->shape, sl.b, srv->ctx->rho_T, srv->ctx->rho_c, st, &pf);
   cudaEventRecord(sl.prep_done, st);
 }
 
@@ -377,7 +383,8 @@ bool admit_one(sk_server* srv, Req* r, Slot& sl, int slot) {
   cudaMemcpyAsync((void*)b.tgt_xyz, r->h_txyz, 3 * s.M * sizeof(double), cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync((void*)b.delta, r->h_delta, s.n_delta * sizeof(double), cudaMemcpyHostToDevice, st);
   cudaMemsetAsync(sl.tb_counters, 0, (n_tb + 1) * sizeof(int), st);
-  enqueue_prep(s, b, srv->ctx->rho_T, srv->ctx->rho_c, st);
+  const PrepFork pf{srv->s_prep_aux[slot % SERVE_PREP_STREAMS], sl.fork_ev, sl.join_ev};
+  enqueue_prep(s, b, srv->ctx->rho_T, srv->ctx->rho_c, st, &pf);
   cudaEventRecord(sl.prep_done, st);
   r->st.admit_us = now_us(srv);
   return true;
@@ -554,11 +561,15 @@ void free_server(sk_server* srv) {
     if (sl.prep_done) cudaEventDestroy(sl.prep_done);
     if (sl.copy_done) cudaEventDestroy(sl.copy_done);
     if (sl.update_done) cudaEventDestroy(sl.update_done);
+    if (sl.fork_ev) cudaEventDestroy(sl.fork_ev);
+    if (sl.join_ev) cudaEventDestroy(sl.join_ev);
   }
   if (srv->kernel_done) cudaEventDestroy(srv->kernel_done);
   for (cudaStream_t s : {srv->s_kernel, srv->s_ctl, srv->s_copy})
     if (s) cudaStreamDestroy(s);
   for (cudaStream_t s : srv->s_prep)
+    if (s) cudaStreamDestroy(s);
+  for (cudaStream_t s : srv->s_prep_aux)
     if (s) cudaStreamDestroy(s);
   for (auto& kv : srv->reqs) {
     if (kv.second->cap) capsule_release(kv.second->cap);
@@ -612,6 +623,7 @@ int serve_create(sk_ctx* ctx, const sk_serve_cfg* cfg_in, sk_server** out) {
   };
   ok(cudaStreamCreateWithFlags(&srv->s_kernel, cudaStreamNonBlocking));
   for (cudaStream_t& s : srv->s_prep) ok(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  for (cudaStream_t& s : srv->s_prep_aux) ok(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
   ok(cudaStreamCreateWithFlags(&srv->s_ctl, cudaStreamNonBlocking));
   ok(cudaStreamCreateWithFlags(&srv->s_copy, cudaStreamNonBlocking));
   ok(cudaMalloc(&srv->d_desc, MAX_SLOTS * sizeof(SlotDesc)));
@@ -628,6 +640,8 @@ int serve_create(sk_ctx* ctx, const sk_serve_cfg* cfg_in, sk_server** out) {
     ok(cudaEventCreateWithFlags(&sl.prep_done, cudaEventDisableTiming));
     ok(cudaEventCreateWithFlags(&sl.copy_done, cudaEventDisableTiming));
     ok(cudaEventCreateWithFlags(&sl.update_done, cudaEventDisableTiming));
+    ok(cudaEventCreateWithFlags(&sl.fork_ev, cudaEventDisableTiming));
+    ok(cudaEventCreateWithFlags(&sl.join_ev, cudaEventDisableTiming));
   }
   if (e == cudaSuccess) {
     ok(cudaHostGetDevicePointer((void**)&srv->d_done, srv->h_done, 0));
@@ -733,6 +747,7 @@ int serve_submit(sk_server* srv, const sk_request* q, uint64_t* ticket) {
   s.mu = q->mu;
   s.copy_inputs = true;
   s.small_sort_points = srv->ctx->small_sort_points;
+  s.split_sorts = true;  // the target sort runs on the preparation stream's partner
   s.n_chunks = choose_chunks(SK_FP32C, N, M, srv->ctx->sm_count);
   const int n_tb = (int)(align_up((size_t)M, TGT_CTA32) / SERVE_TGT_CTA);
   r->footprint = request_footprint(s, n_tb);
