@@ -261,8 +261,8 @@ struct EvalShape {
   // kernel instead of fifteen launches (0: never)
   int64_t small_sort_points = SMALL_SORT_POINTS;
   // the target sort takes scratch of its own and runs beside the source sort
-  // on a second stream (calls through a context; the allocation-free call
-  // keeps one set)
+  // on a second stream (context evaluations, capsule steps, served requests;
+  // the allocation-free call keeps one set)
   bool split_sorts = false;
 };
 
