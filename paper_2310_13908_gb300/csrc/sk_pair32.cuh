@@ -36,6 +36,7 @@
 #include <cfloat>
 
 #include "sk_internal.h"
+#include "sk_erfc_scaled.h"
 #include "sk_series.cuh"
 
 // unroll factor of the far loop over the 32 sources of a segment
@@ -246,13 +247,17 @@ struct SLayer {
     U[1] = fma2(fma2(dy, a, mul2(S.gy, s1)), ri, U[1]);
     U[2] = fma2(fma2(dz, a, mul2(S.gz, s1)), ri, U[2]);
   }
-  // FP32 closed forms at rho (Sec. 3.4); the caller clamps rho into range.
+  // FP32 closed forms at rho (Sec. 3.4), with erf(rho) = 1 - exp(-rho^2) E(rho):
+  // s = 1 - exp(-rho^2) (E(rho) + (2 / (3 sqrt(pi))) rho q(rho)), q the
+  // factor's polynomial; one exponential and the fitted E (sk_erfc_scaled.h)
+  // instead of erff and an exponential. The caller clamps rho into range.
   __device__ __forceinline__ static void smooth(float rho, float& s1, float& s2) {
     const float p2 = rho * rho;
-    const float e = __expf(-p2) * (float)INV_SQRT_PI;
-    const float er = erff(rho);
-    s1 = er - (2.f / 3.f) * rho * (2.f * p2 - 5.f) * e;
-    s2 = er - (2.f / 3.f) * rho * ((4.f * p2 - 14.f) * p2 + 3.f) * e;
+    const float e = __expf(-p2);
+    const float E = erfc_scaled(rho);
+    const float cr = (float)(2.0 / 3.0 * INV_SQRT_PI) * rho;
+    s1 = 1.f - e * fmaf(cr, 2.f * p2 - 5.f, E);
+    s2 = 1.f - e * fmaf(cr, fmaf(4.f * p2 - 14.f, p2, 3.f), E);
   }
 };
 
@@ -295,10 +300,13 @@ struct DLayer {
     U[1] = fma2(c, dy, U[1]);
     U[2] = fma2(c, dz, U[2]);
   }
+  // as SLayer::smooth: s3 = 1 - exp(-rho^2) (E(rho) + (2 / (9 sqrt(pi))) rho q3(rho))
   __device__ __forceinline__ static void smooth(float rho, float& s3, float& unused) {
     const float p2 = rho * rho;
-    const float e = __expf(-p2) * (float)INV_SQRT_PI;
-    s3 = erff(rho) - (2.f / 9.f) * rho * (((8.f * p2 - 36.f) * p2 + 6.f) * p2 + 9.f) * e;
+    const float e = __expf(-p2);
+    const float E = erfc_scaled(rho);
+    const float cr = (float)(2.0 / 9.0 * INV_SQRT_PI) * rho;
+    s3 = 1.f - e * fmaf(cr, fmaf(fmaf(8.f * p2 - 36.f, p2, 6.f), p2, 9.f), E);
     unused = 1.f;
   }
 };
